@@ -1,0 +1,226 @@
+"""FP64 CPU oracle for image-domain gridding -- TEST INFRASTRUCTURE ONLY.
+
+This package wraps ``idg_oracle.c`` (plain double-precision C, OpenMP over
+subgrids) with ctypes.  It is the independent reference that the GPU library
+is checked against.  Only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import it; the library never does, and it
+imports nothing from the library.
+
+Every function follows a passage of the paper (arXiv 2502.17789):
+  plan()    Section 3.1 partitioning + Section 3.3 A-term constraint
+  grid()    Section 2.5 imaging steps 2a-2c, Eq. 10 and Eq. 6
+  degrid()  Section 2.5 prediction steps 3a-3c, Eq. 13 (adjoint reading)
+  taper()   Section 4.2 Kaiser-Bessel taper
+  dft2()    the subgrid Fourier transform of Eq. 8 (centred, unnormalised)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "idg_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+FLAG_DROP = 1
+FLAG_SPLIT_INTERVALS = 2
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "unsorted frequencies", 3: "uv out of grid",
+          4: "w too large", 9: "capacity"}
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"oracle {what}: status {code} ({STATUS.get(code, '?')})")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (no FMA contraction: the planner must
+    round exactly like the library's planner)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-std=c11", "-o", _LIB + ".tmp", _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        i32, f64 = ctypes.c_int, ctypes.c_double
+        lib.oracle_plan.argtypes = [i32, i32, i32, f64, i32, i32, i32, i32, P, P, P, i32,
+                                    P, i32, P, P, i32, P]
+        lib.oracle_plan.restype = i32
+        common = [i32, i32, i32, f64, i32, f64, P, i32, i32, i32, i32, i32, P, P, P, i32, P, i32, P, i32]
+        lib.oracle_grid.argtypes = common + [P, P, P, P, P]
+        lib.oracle_grid.restype = i32
+        lib.oracle_degrid.argtypes = common + [P, P, P]
+        lib.oracle_degrid.restype = i32
+        lib.oracle_taper.argtypes = [i32, i32, f64, P, P]
+        lib.oracle_taper.restype = i32
+        lib.oracle_bessel_i0.argtypes = [f64]
+        lib.oracle_bessel_i0.restype = f64
+        lib.oracle_dft2.argtypes = [i32, i32, i32, P, P]
+        lib.oracle_dft2.restype = i32
+        lib.oracle_aterm_interp.argtypes = [i32, i32, P, P]
+        lib.oracle_aterm_interp.restype = i32
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+@dataclass
+class Geometry:
+    """Imaging geometry: N (grid), L (subgrid), P (kernel padding), FOV."""
+    grid_size: int
+    subgrid_size: int
+    kernel_padding: int
+    image_size: float
+    taper_kind: int = 0          # 0 Kaiser-Bessel, 1 user table
+    taper_beta: float | None = None   # default pi * P / 2
+    taper_user: np.ndarray | None = None
+    aterm_nodes: int = 9
+    flags: int = 0
+
+    @property
+    def beta(self) -> float:
+        return float(np.pi * self.kernel_padding / 2.0) if self.taper_beta is None else float(self.taper_beta)
+
+
+@dataclass
+class Plan:
+    subgrids: np.ndarray   # int32 [n_sg, 8]: b, t0, t1, c0, c1, x0, y0, dropped
+    segments: np.ndarray   # int32 [n_seg, 4]: subgrid, interval, t_begin, t_end
+
+
+def plan(geom: Geometry, uvw: np.ndarray, freqs: np.ndarray, aterm_offsets: np.ndarray) -> Plan:
+    """Partition the visibilities into subgrids (Section 3.1)."""
+    lib = _load()
+    uvw = np.ascontiguousarray(uvw, dtype=np.float64)
+    freqs = np.ascontiguousarray(freqs, dtype=np.float64)
+    offs = np.ascontiguousarray(aterm_offsets, dtype=np.int32)
+    n_bl, n_t, _ = uvw.shape
+    n_ch = freqs.shape[0]
+    n_int = offs.shape[0] - 1
+    cap = max(64, n_bl * max(n_t, 1) * max(n_ch, 1) + 1)
+    cap = min(cap, 1 << 24)
+    while True:
+        sg = np.zeros((cap, 8), np.int32)
+        seg = np.zeros((cap, 4), np.int32)
+        nsg = ctypes.c_int(0)
+        nseg = ctypes.c_int(0)
+        st = lib.oracle_plan(geom.grid_size, geom.subgrid_size, geom.kernel_padding, geom.image_size,
+                             geom.flags, n_bl, n_t, n_ch, _ptr(uvw), _ptr(freqs), _ptr(offs), n_int,
+                             _ptr(sg), cap, ctypes.byref(nsg), _ptr(seg), cap, ctypes.byref(nseg))
+        if st == 9:
+            cap *= 2
+            continue
+        if st != 0:
+            raise OracleError(st, "plan")
+        return Plan(sg[: nsg.value].copy(), seg[: nseg.value].copy())
+
+
+def _common(geom, baselines, uvw, freqs, aterm_offsets, pl, n_st):
+    uvw = np.ascontiguousarray(uvw, dtype=np.float64)
+    freqs = np.ascontiguousarray(freqs, dtype=np.float64)
+    bl = np.ascontiguousarray(baselines, dtype=np.int32)
+    tu = None if geom.taper_user is None else np.ascontiguousarray(geom.taper_user, dtype=np.float64)
+    sg = np.ascontiguousarray(pl.subgrids, dtype=np.int32)
+    seg = np.ascontiguousarray(pl.segments, dtype=np.int32)
+    n_bl, n_t, _ = uvw.shape
+    args = [geom.grid_size, geom.subgrid_size, geom.kernel_padding, geom.image_size, geom.taper_kind,
+            geom.beta, _ptr(tu), geom.aterm_nodes, n_st, n_bl, n_t, freqs.shape[0], _ptr(bl), _ptr(uvw),
+            _ptr(freqs), len(aterm_offsets) - 1, _ptr(sg), sg.shape[0], _ptr(seg), seg.shape[0]]
+    keep = (uvw, freqs, bl, tu, sg, seg)
+    return args, keep
+
+
+def grid(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Plan, vis, aterms,
+         grid_in=None, want_subgrids: bool = False):
+    """Grid visibilities (complex [n_bl][n_t][n_ch][4]) with A-terms
+    (complex [n_int][n_st][nodes][nodes][4]) onto a complex128 [4][N][N] grid.
+    Returns grid (and the subgrid images before / after the FFT if asked)."""
+    lib = _load()
+    args, keep = _common(geom, baselines, uvw, freqs, aterm_offsets, pl, n_st)
+    v = np.ascontiguousarray(vis, dtype=np.complex128)
+    a = np.ascontiguousarray(aterms, dtype=np.complex128)
+    N, L = geom.grid_size, geom.subgrid_size
+    g = np.zeros((4, N, N), np.complex128) if grid_in is None else np.array(grid_in, dtype=np.complex128, copy=True)
+    img = uv = None
+    if want_subgrids:
+        img = np.zeros((pl.subgrids.shape[0], 4, L, L), np.complex128)
+        uv = np.zeros_like(img)
+    st = lib.oracle_grid(*args, _ptr(v), _ptr(a), _ptr(g), _ptr(img), _ptr(uv))
+    if st != 0:
+        raise OracleError(st, "grid")
+    del keep
+    return (g, img, uv) if want_subgrids else g
+
+
+def degrid(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Plan, grid_arr, aterms):
+    """Predict visibilities complex128 [n_bl][n_t][n_ch][4] from a [4][N][N] grid."""
+    lib = _load()
+    args, keep = _common(geom, baselines, uvw, freqs, aterm_offsets, pl, n_st)
+    gr = np.ascontiguousarray(grid_arr, dtype=np.complex128)
+    a = np.ascontiguousarray(aterms, dtype=np.complex128)
+    n_bl, n_t = np.shape(uvw)[:2]
+    out = np.zeros((n_bl, n_t, len(freqs), 4), np.complex128)
+    st = lib.oracle_degrid(*args, _ptr(gr), _ptr(a), _ptr(out))
+    if st != 0:
+        raise OracleError(st, "degrid")
+    del keep
+    return out
+
+
+def taper(L: int, beta: float, kind: int = 0, user=None) -> np.ndarray:
+    lib = _load()
+    out = np.zeros(L, np.float64)
+    u = None if user is None else np.ascontiguousarray(user, dtype=np.float64)
+    st = lib.oracle_taper(L, kind, beta, _ptr(u), _ptr(out))
+    if st != 0:
+        raise OracleError(st, "taper")
+    return out
+
+
+def bessel_i0(x: float) -> float:
+    return float(_load().oracle_bessel_i0(float(x)))
+
+
+def dft2(planes: np.ndarray, sign: int) -> np.ndarray:
+    """Centred unnormalised 2-D DFT of [..., L, L] planes (sign -1 forward)."""
+    lib = _load()
+    a = np.ascontiguousarray(planes, dtype=np.complex128)
+    L = a.shape[-1]
+    flat = a.reshape(-1, L, L)
+    out = np.zeros_like(flat)
+    st = lib.oracle_dft2(L, sign, flat.shape[0], _ptr(flat), _ptr(out))
+    if st != 0:
+        raise OracleError(st, "dft2")
+    return out.reshape(a.shape)
+
+
+def aterm_interp(A: np.ndarray, L: int) -> np.ndarray:
+    """Interpolate one station's [nodes][nodes][4] Jones samples to [L][L][4]."""
+    lib = _load()
+    a = np.ascontiguousarray(A, dtype=np.complex128)
+    out = np.zeros((L, L, 4), np.complex128)
+    st = lib.oracle_aterm_interp(a.shape[0], L, _ptr(a), _ptr(out))
+    if st != 0:
+        raise OracleError(st, "aterm_interp")
+    return out

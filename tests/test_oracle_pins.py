@@ -1,0 +1,327 @@
+"""Pins for the FP64 oracle: each test checks it against something other than
+itself -- a library routine, a closed form, an exact identity of the method,
+a hand-worked example or a textbook brute force (tests/_brute.py)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.special
+
+from paper_2502_17789_gb300 import synth
+from tests import _brute
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _geom(oracle_mod, obs, flags=0, beta=None):
+    return oracle_mod.Geometry(obs.grid_size, obs.subgrid_size, obs.kernel_padding, obs.image_size,
+                               taper_beta=beta, aterm_nodes=obs.aterm_nodes, flags=flags)
+
+
+def _tiny(seed=0, height=15.0, **kw):
+    obs = _brute.tiny_observation(seed=seed, **kw)
+    rng = np.random.default_rng(seed + 100)
+    obs.enu[:, 2] = rng.normal(0.0, height, obs.enu.shape[0])
+    hours = obs.times * synth.EARTH_ROTATION
+    obs.uvw = synth.uvw_tracks(obs.enu, obs.baselines, hours)
+    return obs
+
+
+def _relerr(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+# ---------------------------------------------------------------- taper / DFT / interpolation
+
+def test_bessel_i0_matches_scipy(oracle_mod):
+    for x in [0.0, 0.3, 1.0, 5.0, 9.42, 18.8, 28.27, 40.0]:
+        assert oracle_mod.bessel_i0(x) == pytest.approx(float(scipy.special.i0(x)), rel=1e-14)
+
+
+@pytest.mark.parametrize("L,P", [(16, 6), (32, 12), (96, 18)])
+def test_taper_matches_scipy_kaiser_bessel(oracle_mod, L, P):
+    beta = np.pi * P / 2
+    T = oracle_mod.taper(L, beta)
+    np.testing.assert_allclose(T, _brute.kb_taper(L, beta), rtol=1e-13, atol=1e-300)
+    assert T[L // 2] == 1.0  # T(0) = 1
+
+
+@pytest.mark.parametrize("L", [6, 16, 32])
+def test_dft2_matches_numpy_fft(oracle_mod, L):
+    rng = np.random.default_rng(L)
+    X = rng.standard_normal((3, L, L)) + 1j * rng.standard_normal((3, L, L))
+    s = (-1.0) ** (np.arange(L)[:, None] + np.arange(L)[None, :])
+    # centred kernel e^{-2 pi i (x-L/2)(i-L/2)/L} = (-1)^{x+i+L/2} e^{-2 pi i x i / L}; the
+    # (-1)^{L/2} factors of the two axes cancel.
+    fwd = s * np.fft.fft2(s * X)
+    inv = s * np.fft.ifft2(s * X) * L * L
+    np.testing.assert_allclose(oracle_mod.dft2(X, -1), fwd, rtol=0, atol=1e-11 * np.abs(fwd).max())
+    np.testing.assert_allclose(oracle_mod.dft2(X, +1), inv, rtol=0, atol=1e-11 * np.abs(inv).max())
+
+
+def test_aterm_interp_nodes_and_linear_fields(oracle_mod):
+    nodes, L, fov = 9, 32, 0.4
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((nodes, nodes, 4)) + 1j * rng.standard_normal((nodes, nodes, 4))
+    out = oracle_mod.aterm_interp(A, L)
+    # pixel i sits on node a when (nodes-1) i / L = a, i.e. i = 4a for L=32
+    for a in range(8):
+        for b in range(8):
+            np.testing.assert_allclose(out[4 * b, 4 * a], A[b, a], rtol=1e-14)
+    # a field linear in (l, m) is reproduced exactly between nodes
+    c = -0.5 * fov + fov * np.arange(nodes) / (nodes - 1)
+    lin = (0.3 + 1.7j) * c[None, :, None] + (2.1 - 0.4j) * c[:, None, None] + np.array([1, 2j, 3, 4j])
+    out = oracle_mod.aterm_interp(lin, L)
+    pix = (np.arange(L) - L // 2) * fov / L
+    expect = (0.3 + 1.7j) * pix[None, :, None] + (2.1 - 0.4j) * pix[:, None, None] + np.array([1, 2j, 3, 4j])
+    np.testing.assert_allclose(out, expect, rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------- planner
+
+def _golden():
+    with open(os.path.join(HERE, "golden", "planner_handworked.json")) as f:
+        return json.load(f)
+
+
+def _golden_obs(gd, n_t=5, steps_per_interval=3):
+    c = synth.SPEED_OF_LIGHT
+    g = gd["geometry"]
+    ch = gd["channels"]
+    freqs = ch["f0"] + ch["df"] * np.arange(ch["n"])
+    uvw = np.zeros((2, n_t, 3))
+    uvw[0, :, 0] = 2.9 * c / 1e6
+    uvw[1, :, 1] = -3.9 * c / 1e6
+    offs = np.array([0, steps_per_interval, n_t], np.int32)
+    return g, uvw, freqs, offs
+
+
+def test_plan_handworked_golden(oracle_mod):
+    gd = _golden()
+    g, uvw, freqs, offs = _golden_obs(gd)
+    geom = oracle_mod.Geometry(g["N"], g["L"], g["P"], g["fov"])
+    pl = oracle_mod.plan(geom, uvw, freqs, offs)
+    np.testing.assert_array_equal(pl.subgrids, np.array(gd["expected_merged"], np.int32))
+    # two segments per subgrid: intervals [0,3) and [3,5)
+    assert pl.segments.shape[0] == 2 * pl.subgrids.shape[0]
+    for s in range(pl.subgrids.shape[0]):
+        segs = pl.segments[pl.segments[:, 0] == s]
+        np.testing.assert_array_equal(segs[:, 1:], [[0, 0, 3], [1, 3, 5]])
+    geom.flags = oracle_mod.FLAG_SPLIT_INTERVALS
+    pl = oracle_mod.plan(geom, uvw, freqs, offs)
+    assert int((pl.subgrids[:, 0] == 0).sum()) == gd["expected_split_counts"]["baseline0"]
+    assert int((pl.subgrids[:, 0] == 1).sum()) == gd["expected_split_counts"]["baseline1"]
+    assert pl.segments.shape[0] == pl.subgrids.shape[0]
+    # time case
+    tc = gd["time_case"]
+    n_t = tc["n_t"]
+    uvw = np.zeros((1, n_t, 3))
+    uvw[0, :, 0] = (tc["xi0"] - g["N"] / 2 + tc["step"] * np.arange(n_t)) * synth.SPEED_OF_LIGHT / tc["f0"]
+    geom = oracle_mod.Geometry(g["N"], g["L"], g["P"], g["fov"])
+    pl = oracle_mod.plan(geom, uvw, np.array([tc["f0"]]), np.array([0, n_t], np.int32))
+    np.testing.assert_array_equal(pl.subgrids, np.array(tc["expected"], np.int32))
+
+
+def _check_plan_invariants(obs, pl, split):
+    N, L, P, fov = obs.grid_size, obs.subgrid_size, obs.kernel_padding, obs.image_size
+    u, v, _ = _brute.uvw_lambda(obs)
+    xi = u * fov + N // 2
+    eta = v * fov + N // 2
+    count = np.zeros((obs.n_baselines, obs.n_timesteps, obs.n_channels), int)
+    offs = obs.aterm_offsets
+    for s, (b, t0, t1, c0, c1, x0, y0, dropped) in enumerate(pl.subgrids):
+        assert t1 > t0 and c1 > c0
+        count[b, t0:t1, c0:c1] += 1
+        if not dropped:
+            xs, ys = xi[b, t0:t1, c0:c1], eta[b, t0:t1, c0:c1]
+            assert (xs - x0).min() >= P / 2 and (xs - x0).max() <= L - 1 - P / 2
+            assert (ys - y0).min() >= P / 2 and (ys - y0).max() <= L - 1 - P / 2
+            assert 0 <= x0 <= N - L and 0 <= y0 <= N - L
+        segs = pl.segments[pl.segments[:, 0] == s]
+        assert segs.shape[0] >= 1
+        assert segs[0, 2] == t0 and segs[-1, 3] == t1
+        for (_, a, tb, te) in segs:
+            assert offs[a] <= tb < te <= offs[a + 1]
+        assert np.all(segs[1:, 2] == segs[:-1, 3])
+        if split:
+            assert segs.shape[0] == 1
+    assert np.all(count == 1), "every visibility belongs to exactly one subgrid"
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_plan_invariants_cfg1(oracle_mod, split):
+    obs = synth.config(1)
+    obs.aterm_offsets = np.array([0, 5, 11, 16], np.int32)
+    geom = _geom(oracle_mod, obs, flags=oracle_mod.FLAG_SPLIT_INTERVALS if split else 0)
+    pl = oracle_mod.plan(geom, obs.uvw, obs.freqs, obs.aterm_offsets)
+    _check_plan_invariants(obs, pl, split)
+
+
+def test_plan_invariants_cfg2_reduced(oracle_mod):
+    obs = synth.config(2, n_stations=24, n_timesteps=12)
+    pl = oracle_mod.plan(_geom(oracle_mod, obs), obs.uvw, obs.freqs, obs.aterm_offsets)
+    _check_plan_invariants(obs, pl, False)
+    assert pl.subgrids.shape[0] > obs.n_baselines  # long baselines split along channels
+
+
+def test_plan_error_codes(oracle_mod):
+    obs = _tiny()
+    geom = _geom(oracle_mod, obs)
+    with pytest.raises(oracle_mod.OracleError) as e:
+        oracle_mod.plan(geom, obs.uvw, obs.freqs[::-1].copy(), obs.aterm_offsets)
+    assert e.value.code == 2
+    u, v, _ = _brute.uvw_lambda(obs)
+    reach = np.abs(np.stack([u, v])).max(axis=(0, 2, 3)) * obs.image_size  # pixels from centre, per baseline
+    limit = obs.grid_size / 2 - obs.subgrid_size / 2
+    big = obs.uvw * (1.2 * limit / np.median(reach))  # pushes the longer baselines off the 64-pixel grid
+    big[..., 2] = 0.0
+    with pytest.raises(oracle_mod.OracleError) as e:
+        oracle_mod.plan(geom, big, obs.freqs, obs.aterm_offsets)
+    assert e.value.code == 3
+    geom.flags = oracle_mod.FLAG_DROP
+    pl = oracle_mod.plan(geom, big, obs.freqs, obs.aterm_offsets)
+    assert pl.subgrids[:, 7].sum() > 0 and pl.subgrids[:, 7].sum() < pl.subgrids.shape[0]
+    geom.flags = 0
+    wbig = obs.uvw.copy()
+    wbig[..., 2] = 500.0
+    with pytest.raises(oracle_mod.OracleError) as e:
+        oracle_mod.plan(geom, wbig, obs.freqs, obs.aterm_offsets)
+    assert e.value.code == 4
+
+
+# ---------------------------------------------------------------- gridding / degridding
+
+def _problem(oracle_mod, seed=0, n_int=2, n_t=4, split=False, **kw):
+    obs = _tiny(seed=seed, n_t=n_t, steps_per_interval=max(1, n_t // n_int), **kw)
+    rng = np.random.default_rng(seed + 7)
+    A = synth.aterms_random(rng, obs.n_intervals, obs.n_stations, obs.aterm_nodes).astype(np.complex128)
+    vis = synth.random_visibilities(rng, obs).astype(np.complex128)
+    geom = _geom(oracle_mod, obs, flags=oracle_mod.FLAG_SPLIT_INTERVALS if split else 0)
+    pl = oracle_mod.plan(geom, obs.uvw, obs.freqs, obs.aterm_offsets)
+    return obs, geom, pl, A, vis
+
+
+def _grid(oracle_mod, obs, geom, pl, vis, A, **kw):
+    return oracle_mod.grid(geom, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets, pl,
+                           vis, A, **kw)
+
+
+def _degrid(oracle_mod, obs, geom, pl, G, A):
+    return oracle_mod.degrid(geom, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets, pl,
+                             G, A)
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_grid_image_equals_direct_dft_at_coarse_points(oracle_mod, split):
+    """At l_i = (i - L/2) FOV/L the dirty image of the master grid is exactly
+    L^2 T_i T_j times the adjoint of the discrete measurement equation (Eq. 1)
+    with A-terms: the L-point subgrid transform reproduces every sample point
+    of the subgrid image, so no aliasing term enters."""
+    obs, geom, pl, A, vis = _problem(oracle_mod, split=split)
+    G = _grid(oracle_mod, obs, geom, pl, vis, A)
+    L, fov = obs.subgrid_size, obs.image_size
+    T = _brute.kb_taper(L, geom.beta)
+    worst = 0.0
+    for (i, j) in [(8, 8), (3, 11), (12, 2), (0, 5), (15, 15), (6, 9)]:
+        l, m = (i - L // 2) * fov / L, (j - L // 2) * fov / L
+        got = _brute.image_from_grid(G, fov, l, m)
+        want = L * L * T[i] * T[j] * _brute.dft_image(obs, vis, A, l, m)
+        worst = max(worst, np.abs(got - want).max() / np.abs(want).max())
+    assert worst < 1e-9
+
+
+def test_degrid_point_source_equals_measurement_equation(oracle_mod):
+    """Degridding the Fourier transform of a point source sitting on a coarse
+    image point gives Eq. 1 exactly, times L^2 T_i T_j."""
+    obs, geom, pl, A, _ = _problem(oracle_mod, seed=3)
+    L, fov, N = obs.subgrid_size, obs.image_size, obs.grid_size
+    T = _brute.kb_taper(L, geom.beta)
+    B = np.array([[1.3, 0.2 - 0.1j], [0.2 + 0.1j, 0.7]])
+    for (i0, j0) in [(8, 8), (5, 10), (11, 4)]:
+        l, m = (i0 - L // 2) * fov / L, (j0 - L // 2) * fov / L
+        G = _brute.point_source_grid(N, fov, l, m, B)
+        V = _degrid(oracle_mod, obs, geom, pl, G, A)
+        want = L * L * T[i0] * T[j0] * _brute.measurement_equation(obs, A, l, m, B)
+        assert _relerr(V, want) < 1e-10
+
+
+def test_dc_invariant_with_aterms(oracle_mod):
+    """sum_{x,y} G = L^2 T(0)^2 sum_segments A_p(0,0)^H (sum_k V_k) A_q(0,0):
+    only the centre pixel survives the sum, where the phase is zero."""
+    obs, geom, pl, A, vis = _problem(oracle_mod, seed=5, n_int=3, n_t=6)
+    G = _grid(oracle_mod, obs, geom, pl, vis, A)
+    L = obs.subgrid_size
+    c = obs.aterm_nodes // 2
+    want = np.zeros((2, 2), complex)
+    for (s, a, tb, te) in pl.segments:
+        b, _, _, c0, c1 = pl.subgrids[s, :5]
+        p, q = obs.baselines[b]
+        S = vis[b, tb:te, c0:c1].sum(axis=(0, 1)).reshape(2, 2)
+        want += A[a, p, c, c].reshape(2, 2).conj().T @ S @ A[a, q, c, c].reshape(2, 2)
+    got = G.sum(axis=(1, 2)).reshape(2, 2)
+    assert _relerr(got, L * L * want) < 1e-12
+
+
+def test_point_source_at_phase_centre(oracle_mod):
+    obs = _tiny(seed=2)
+    A = synth.aterms_identity(obs.n_intervals, obs.n_stations).astype(np.complex128)
+    geom = _geom(oracle_mod, obs)
+    pl = oracle_mod.plan(geom, obs.uvw, obs.freqs, obs.aterm_offsets)
+    L = obs.subgrid_size
+    S = 2.5
+    vis = np.zeros((obs.n_baselines, obs.n_timesteps, obs.n_channels, 4), complex)
+    vis[..., 0] = S
+    vis[..., 3] = S
+    G = _grid(oracle_mod, obs, geom, pl, vis, A)
+    tot = G.sum(axis=(1, 2))
+    np.testing.assert_allclose(tot, [L * L * S * obs.n_vis, 0, 0, L * L * S * obs.n_vis], rtol=1e-13, atol=1e-9)
+    Gc = np.zeros((4, obs.grid_size, obs.grid_size), complex)
+    Gc[0] = S
+    Gc[3] = S
+    V = _degrid(oracle_mod, obs, geom, pl, Gc, A)
+    want = np.zeros_like(V)
+    want[..., 0] = L * L * S
+    want[..., 3] = L * L * S
+    np.testing.assert_allclose(V, want, rtol=1e-13, atol=1e-9)
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_adjoint_identity(oracle_mod, split):
+    obs, geom, pl, A, vis = _problem(oracle_mod, seed=11, split=split)
+    rng = np.random.default_rng(4)
+    N = obs.grid_size
+    G = rng.standard_normal((4, N, N)) + 1j * rng.standard_normal((4, N, N))
+    lhs = np.vdot(_degrid(oracle_mod, obs, geom, pl, G, A), vis)
+    rhs = np.vdot(G, _grid(oracle_mod, obs, geom, pl, vis, A))
+    assert abs(lhs - rhs) / abs(lhs) < 1e-12
+
+
+def test_convolutional_gridding_closed_form(oracle_mod):
+    obs, geom, pl, A, vis = _problem(oracle_mod, seed=13, n_st=3, n_t=2, n_ch=2)
+    G = _grid(oracle_mod, obs, geom, pl, vis, A)
+    T = _brute.kb_taper(obs.subgrid_size, geom.beta)
+    Gc = _brute.convolutional_grid(obs, pl, vis.astype(np.complex128), A, T)
+    assert _relerr(G, Gc) < 1e-12
+
+
+def test_linearity(oracle_mod):
+    obs, geom, pl, A, v1 = _problem(oracle_mod, seed=17)
+    v2 = synth.random_visibilities(np.random.default_rng(99), obs).astype(np.complex128)
+    a, b = 0.7 - 1.1j, -2.0 + 0.3j
+    lhs = _grid(oracle_mod, obs, geom, pl, a * v1 + b * v2, A)
+    rhs = a * _grid(oracle_mod, obs, geom, pl, v1, A) + b * _grid(oracle_mod, obs, geom, pl, v2, A)
+    assert _relerr(lhs, rhs) < 1e-13
+
+
+def test_subgrid_images_match_grid(oracle_mod):
+    """The exported pre-FFT subgrid images transform and add up to the grid."""
+    obs, geom, pl, A, vis = _problem(oracle_mod, seed=19)
+    G, img, uv = _grid(oracle_mod, obs, geom, pl, vis, A, want_subgrids=True)
+    np.testing.assert_allclose(uv, oracle_mod.dft2(img, -1), rtol=0, atol=1e-10 * np.abs(uv).max())
+    L = obs.subgrid_size
+    G2 = np.zeros_like(G)
+    for s, row in enumerate(pl.subgrids):
+        x0, y0 = row[5], row[6]
+        G2[:, y0:y0 + L, x0:x0 + L] += uv[s]
+    assert _relerr(G, G2) < 1e-14
