@@ -1,0 +1,187 @@
+/*
+ * idg.h -- C ABI of libidg, a GB300 (sm_103a) implementation of the
+ * image-domain gridding (IDG) hot path of arXiv 2502.17789 ("That pesky
+ * A-term", the Pigi imager).
+ *
+ * The library partitions visibilities into subgrids (Section 3.1), grids
+ * them (Section 2.5 imaging steps 2a-2c: direct phasor sum per subgrid with
+ * the A-term and taper applied afterwards, subgrid FFT, add into the master
+ * uv grid) and degrids them (Section 2.5 prediction steps 3a-3c: split,
+ * inverse subgrid FFT, A-term and taper, direct phasor sum per visibility).
+ *
+ * Conventions (all sizes in elements unless stated):
+ *   visibility    complex64 [n_baselines][n_timesteps][n_channels][4]; the 4
+ *                 entries are the 2x2 Jones matrix [XX XY; YX YY] row-major.
+ *   uvw           float64 [n_baselines][n_timesteps][3], metres; u,v,w in
+ *                 wavelengths are uvw * f / c.
+ *   A-terms       complex64 [n_intervals][n_stations][nodes][nodes][4]: each
+ *                 station's 2x2 Jones matrix sampled on a nodes x nodes grid
+ *                 of directions l,m = -FOV/2 + a FOV/(nodes-1), indexed
+ *                 [a_m][a_l], bilinearly interpolated to subgrid pixels.
+ *   master grid   complex128 [4][N][N] = [pol][y][x]; cell x holds
+ *                 u = (x - N/2) / FOV wavelengths.
+ * Gridding applies A_p^H X A_q per pixel and degridding A_p Y A_q^H (the
+ * adjoint pair of the paper's A^{-1} / A, Eq. 10 and Eq. 13); both multiply
+ * by the taper T(l) T(m), so idg_degrid is the exact adjoint of idg_grid.
+ *
+ * Ownership: the caller owns every buffer it passes and the CUDA stream.
+ * A plan owns copies of the baseline table, uvw, frequencies and interval
+ * offsets, the subgrid and work tables, and its device scratch.
+ *
+ * Errors: every function returns an idg_status and never aborts or traps.
+ * idg_last_error() gives a message for the last failure on a plan (or, for
+ * a NULL plan, for the calling thread).
+ *
+ * Threading: calls on one plan are asynchronous on the plan's stream; a plan
+ * must not be used from two host threads at once.
+ */
+#ifndef IDG_H
+#define IDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IDG_ABI_VERSION 1
+
+typedef struct idg_plan idg_plan; /* opaque, owned by the library */
+
+typedef enum {
+  IDG_OK = 0,
+  IDG_ERR_INVALID_ARG = 1,   /* bad geometry, sizes, NULL pointer, mismatched plan */
+  IDG_ERR_UNSORTED_FREQ = 2, /* channel frequencies not strictly ascending */
+  IDG_ERR_UV_OUT_OF_GRID = 3,/* a subgrid would leave the master grid (without IDG_DROP_OUT_OF_GRID) */
+  IDG_ERR_W_TOO_LARGE = 4,   /* |w| fringe across a subgrid exceeds P/2 - 1 pixels (Section 2.4) */
+  IDG_ERR_OOM = 5,           /* device or host allocation failed */
+  IDG_ERR_CUDA = 6,          /* a CUDA runtime call failed; see idg_last_error */
+  IDG_ERR_TIMEOUT = 7,       /* a bounded device wait gave up */
+  IDG_ERR_UNSUPPORTED = 8    /* valid request this build does not implement (e.g. subgrid size) */
+} idg_status;
+
+enum { IDG_TAPER_KB = 0, IDG_TAPER_USER = 1 };
+
+enum {
+  IDG_DROP_OUT_OF_GRID = 1,         /* drop subgrids that leave the grid instead of failing */
+  IDG_SPLIT_AT_ATERM_INTERVALS = 2, /* never let a subgrid span two A-term intervals (Section 3.3 as written) */
+  IDG_HOST_ONLY = 4                 /* plan on the host only: no device memory, grid/degrid refused */
+};
+
+typedef struct {
+  int32_t grid_size;      /* N: even, > 0 */
+  int32_t subgrid_size;   /* L: one of 32, 64, 96, 128 for device plans (even, <= N for host plans) */
+  int32_t kernel_padding; /* P: even, L - P - 4 >= 1 */
+  double image_size;      /* FOV in direction cosines; du = 1/FOV; FOV^2/2 < 1 */
+  int32_t taper_kind;     /* IDG_TAPER_KB (beta = taper_beta, or pi*P/2 when <= 0) or IDG_TAPER_USER */
+  double taper_beta;
+  const double* taper_user; /* host [L] taper samples at l_i = (i - L/2) FOV/L (IDG_TAPER_USER), copied */
+  int32_t aterm_nodes;    /* nodes per axis of the A-term samples, >= 2 */
+  int32_t flags;          /* IDG_DROP_OUT_OF_GRID | IDG_SPLIT_AT_ATERM_INTERVALS | IDG_HOST_ONLY */
+} idg_geometry;
+
+typedef struct {
+  int64_t n_subgrids;         /* all subgrids of the partition, dropped ones included */
+  int64_t n_segments;         /* (subgrid, A-term interval) pieces */
+  int64_t n_vis;              /* n_baselines * n_timesteps * n_channels */
+  int64_t n_vis_dropped;      /* visibilities of dropped subgrids */
+  int64_t n_subgrids_dropped;
+  int64_t n_grid_items;       /* gridder work items (subgrid, pixel tile) */
+  int64_t n_degrid_items;     /* degridder work items (segment, <= 256 visibilities) */
+  int64_t n_batches;          /* device batches the subgrids are processed in */
+  int64_t occupancy_hist[16]; /* subgrids with visibility count in [2^k, 2^(k+1)), last bin open */
+  int64_t device_bytes;       /* device memory held by the plan */
+  int64_t vis_pixels;         /* sum over non-dropped subgrids of n_vis * L^2 */
+  int32_t subgrid_size;
+  int32_t batch_capacity;     /* subgrids per batch */
+} idg_plan_stats_t;
+
+/*
+ * idg_plan_create -- partition and prepare one observation (Section 3.1, 3.3).
+ *   out            receives the plan (NULL on failure)
+ *   g              geometry, copied
+ *   n_stations     stations referenced by `baselines`
+ *   baselines      host int32 [n_baselines][2] station pairs (p, q), copied
+ *   uvw_m          host float64 [n_baselines][n_timesteps][3] metres, copied
+ *   freqs_hz       host float64 [n_channels], strictly ascending, copied
+ *   aterm_offsets  host int32 [n_intervals + 1] timestep boundaries of the
+ *                  A-term intervals: [0] = 0, last = n_timesteps, ascending
+ *   cuda_stream    cudaStream_t every later call runs on (NULL = legacy default)
+ * Every visibility lands in exactly one subgrid; subgrids share one baseline
+ * and carry one segment per A-term interval they cover.  Fails with
+ * IDG_ERR_UNSORTED_FREQ, IDG_ERR_UV_OUT_OF_GRID, IDG_ERR_W_TOO_LARGE,
+ * IDG_ERR_INVALID_ARG, IDG_ERR_UNSUPPORTED, IDG_ERR_OOM or IDG_ERR_CUDA.
+ * Synchronises the stream (uploads the plan tables).
+ */
+idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stations, int32_t n_baselines,
+                           int32_t n_timesteps, int32_t n_channels, const int32_t* baselines,
+                           const double* uvw_m, const double* freqs_hz, const int32_t* aterm_offsets,
+                           int32_t n_intervals, void* cuda_stream);
+
+/*
+ * idg_grid -- imaging direction (Section 2.5 steps 2a-2c, Eq. 10, Eq. 6).
+ *   vis_c64     device complex64 [n_baselines][n_timesteps][n_channels][4]
+ *   aterms_c64  device complex64 [n_intervals][n_stations][nodes][nodes][4]
+ *   grid_c128   device complex128 [4][N][N], ACCUMULATED INTO (+=)
+ * Dropped subgrids contribute nothing.  Asynchronous on the plan's stream.
+ * Buffers must be 16-byte aligned.
+ */
+idg_status idg_grid(idg_plan* plan, const void* vis_c64, const void* aterms_c64, void* grid_c128);
+
+/*
+ * idg_degrid -- prediction direction (Section 2.5 steps 3a-3c, Eq. 13 read
+ * as the adjoint of idg_grid).
+ *   grid_c128   device complex128 [4][N][N], read only
+ *   aterms_c64  device complex64 [n_intervals][n_stations][nodes][nodes][4]
+ *   vis_c64     device complex64 [n_baselines][n_timesteps][n_channels][4],
+ *               OVERWRITTEN; visibilities of dropped subgrids are set to 0
+ * Asynchronous on the plan's stream.  Buffers must be 16-byte aligned.
+ */
+idg_status idg_degrid(idg_plan* plan, const void* grid_c128, const void* aterms_c64, void* vis_c64);
+
+/* Set the stream later calls run on (cudaStream_t; NULL = legacy default). */
+idg_status idg_set_stream(idg_plan* plan, void* cuda_stream);
+
+/* Plan statistics (host only, no device work). */
+idg_status idg_plan_stats(const idg_plan* plan, idg_plan_stats_t* out);
+
+/*
+ * idg_plan_subgrids -- copy the partition, in plan order, to host memory.
+ *   out   host int32 [cap][8] rows {baseline, t0, t1, c0, c1, x0, y0, dropped}
+ *         (member timesteps [t0,t1), channels [c0,c1), corner (x0,y0))
+ *   n     receives the number of subgrids; rows beyond cap are not written
+ */
+idg_status idg_plan_subgrids(const idg_plan* plan, int32_t* out, int64_t cap, int64_t* n);
+
+/*
+ * idg_plan_segments -- copy the segments to host memory.
+ *   out   host int32 [cap][4] rows {subgrid, interval, t_begin, t_end}
+ */
+idg_status idg_plan_segments(const idg_plan* plan, int32_t* out, int64_t cap, int64_t* n);
+
+/*
+ * idg_subgrid_images -- stage output of the gridder for inspection
+ * (Section 2.5 step 2a, or 2a+2b with stage = 1).
+ *   stage 0: subgrid images X(i,j) after the phasor sum, A-term and taper
+ *   stage 1: the same after the centred subgrid FFT, Vhat(x,y)
+ *   out_c64: device complex64 [n_subgrids][4][L][L] in plan order, written;
+ *            rows of dropped subgrids are zero
+ * Does not touch any grid.  Asynchronous on the plan's stream.
+ */
+idg_status idg_subgrid_images(idg_plan* plan, const void* vis_c64, const void* aterms_c64, int32_t stage,
+                              void* out_c64);
+
+/* Message for the last failure (never NULL; "" when none). */
+const char* idg_last_error(const idg_plan* plan);
+
+/* Release the plan and its device memory (synchronises its stream). NULL is a no-op. */
+idg_status idg_plan_destroy(idg_plan* plan);
+
+/* Library version (IDG_ABI_VERSION). */
+int32_t idg_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IDG_H */

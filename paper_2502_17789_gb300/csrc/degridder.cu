@@ -1,0 +1,211 @@
+// Degridder kernel: Section 2.5 prediction step 3c (Eq. 13), read as the
+// exact adjoint of the gridder:
+//   Z(i,j) = (-1)^(i+j) T_i T_j A_p(i,j) Y(i,j) A_q(i,j)^H
+//   V_k    = sum_{ij} Z(i,j) e^{-2 pi i phi_k(i,j)}
+// where Y is the uncentred inverse subgrid FFT of the split-out grid
+// footprint (the splitter applied (-1)^(x+y)).
+//
+// Work item = up to 256 visibilities of one segment (one A-term).  Each
+// thread owns one visibility; the block walks the subgrid in chunks of
+// 32 pixel blocks (8 consecutive pixels of a row each).  Per chunk all
+// threads first compute Z for 256 pixels into shared memory (the A-term
+// prologue), then every warp sums its visibilities over its share of the
+// chunk.  When a segment has fewer than 256 visibilities the 8 warps split
+// the pixel blocks between them (8 / vis-warps ways) and the partial sums
+// are combined through shared memory at the end.  Phases use the same FP64
+// offset / exact anchor reduction / FP32 increment scheme as the gridder.
+#include "kernels_common.cuh"
+
+namespace idg {
+
+constexpr int kDegridThreads = 256;
+constexpr int kChunkBlocks = 32;  // pixel blocks (of 8) per chunk = 256 pixels
+
+template <int L>
+__global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const DegridArgs a) {
+  constexpr int TPR = L / 8;
+  constexpr int NBLK = L * L / 8;
+  static_assert(NBLK % kChunkBlocks == 0, "chunking");
+  extern __shared__ float4 smem[];
+  float4* s_Z = smem;                                                  // [CB][4 pairs][4 pols] {Zr_a, Zr_b, Zi_a, Zi_b}
+  float2* s_N = reinterpret_cast<float2*>(s_Z + kChunkBlocks * 16);    // [CB][4][4] {-Zr_a, -Zr_b}
+  float4* s_G = reinterpret_cast<float4*>(s_N + kChunkBlocks * 16);    // [CB][3] block geometry
+  float* s_red = reinterpret_cast<float*>(s_G + kChunkBlocks * 3);     // [8][256]
+  float2* s_A = reinterpret_cast<float2*>(s_red + 8 * kDegridThreads); // [2][nodes*nodes*4]
+
+  const DegridItem item = a.items[blockIdx.x];
+  const SubgridDesc sd = a.sg[item.sg];
+  const SegmentDesc seg = a.seg[item.segment];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nv = item.k_end - item.k_begin;
+  const int wv = (nv + 31) >> 5;            // warps of visibilities, 1..8
+  const int nsplit = 8 / wv;                // pixel splits, >= 1
+  const int vgroup = warp % wv, split = warp / wv;
+  const bool active = split < nsplit;
+  const int kloc = vgroup * 32 + lane;
+  const bool valid = active && kloc < nv;
+  const int nodes = a.g.nodes;
+  const int nA = nodes * nodes * 4;
+
+  // A-terms of this segment
+  {
+    const float2* Ap = a.aterms + (size_t(seg.interval) * a.g.n_st + sd.p) * nA;
+    const float2* Aq = a.aterms + (size_t(seg.interval) * a.g.n_st + sd.q) * nA;
+    for (int e = tid; e < nA; e += kDegridThreads) {
+      s_A[e] = Ap[e];
+      s_A[nA + e] = Aq[e];
+    }
+  }
+
+  // this thread's visibility: FP64 offsets -> FP32 phase coefficients
+  const int nc = sd.c1 - sd.c0;
+  float ah = 0.f, bh = 0.f, al = 0.f, bl = 0.f, cw = 0.f, ar = 0.f, cr = 0.f;
+  size_t vidx = 0;
+  if (valid) {
+    const int k = item.k_begin + kloc;
+    const int t = sd.t0 + k / nc, ch = sd.c0 + k % nc;
+    vidx = (size_t(sd.b) * a.g.n_t + t) * a.g.n_ch + ch;
+    const double* r = a.uvw + (size_t(sd.b) * a.g.n_t + t) * 3;
+    const double fs = a.fscale[ch];
+    const double inv_l = 1.0 / double(L);
+    const double dx = (r[0] * fs) * a.g.fov - double(sd.x0 + L / 2 - a.g.N / 2);
+    const double dy = (r[1] * fs) * a.g.fov - double(sd.y0 + L / 2 - a.g.N / 2);
+    const double w = r[2] * fs;
+    const double aa = dx * inv_l, bb = dy * inv_l;
+    const double dah = rint(aa * 65536.0) * (1.0 / 65536.0);
+    const double dbh = rint(bb * 65536.0) * (1.0 / 65536.0);
+    ah = float(dah);
+    bh = float(dbh);
+    al = float(aa - dah);
+    bl = float(bb - dbh);
+    cw = float(w);
+    ar = float(kTwoPi * aa);
+    cr = float(kTwoPi * w);
+  }
+  const float2 ARR = make_float2(ar, ar), CRR = make_float2(cr, cr);
+  const float2 DI[4] = {{-4.f, -3.f}, {-2.f, -1.f}, {0.f, 1.f}, {2.f, 3.f}};
+
+  float2 RE[4], IM[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    RE[p] = make_float2(0.f, 0.f);
+    IM[p] = make_float2(0.f, 0.f);
+  }
+  const float2* Y = a.scratch + size_t(item.sg) * 4 * L * L;
+
+  for (int chunk = 0; chunk < NBLK / kChunkBlocks; ++chunk) {
+    __syncthreads();  // previous chunk consumed (and s_A loaded on the first pass)
+    // ---- prologue: Z for 256 pixels
+    {
+      const int bl_loc = tid >> 3, pos = tid & 7;
+      const int bidx = chunk * kChunkBlocks + bl_loc;
+      const int j = bidx / TPR, i = (bidx % TPR) * 8 + pos;
+      Jones Yp;
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const float2 y = Y[(size_t(p) * L + j) * L + i];
+        Yp.m[p] = {y.x, y.y};
+      }
+      const NodeWeight wx = node_weight(i, nodes, L), wy = node_weight(j, nodes, L);
+      const Jones Apj = interp_jones(s_A, nodes, wx, wy);
+      const Jones Aqj = interp_jones(s_A + nA, nodes, wx, wy);
+      const Jones Z = jmul_bh(jmul(Apj, Yp), Aqj);
+      const float wgt = a.taper[i] * a.taper[j] * (((i + j) & 1) ? -1.f : 1.f);
+      const int q = pos >> 1, half = pos & 1;
+      float* zf = reinterpret_cast<float*>(s_Z + (bl_loc * 4 + q) * 4);
+      float* nf = reinterpret_cast<float*>(s_N + (bl_loc * 4 + q) * 4);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const float zr = wgt * Z.m[p].re, zi = wgt * Z.m[p].im;
+        zf[p * 4 + half] = zr;
+        zf[p * 4 + 2 + half] = zi;
+        nf[p * 2 + half] = -zr;
+      }
+      if (tid < kChunkBlocks * 3) {
+        const int b = tid / 3, c = tid % 3;
+        s_G[tid] = a.blk[size_t(chunk * kChunkBlocks + b) * 3 + c];
+      }
+    }
+    __syncthreads();
+    // ---- sum over this warp's pixel blocks
+    if (active) {
+#pragma unroll 1
+      for (int b = split; b < kChunkBlocks; b += nsplit) {
+        const float4 g0 = s_G[b * 3], g1 = s_G[b * 3 + 1], g2 = s_G[b * 3 + 2];
+        const float n0 = g0.x, di0 = g2.y, dj0 = g2.z;
+        const float2 DN[4] = {{g0.y, g0.z}, {g0.w, g1.x}, {g1.y, g1.z}, {g1.w, g2.x}};
+        const float sh = fmaf(ah, di0, bh * dj0);
+        const float d1 = __fsub_rn(sh, round_nearest(sh));
+        const float lo = fmaf(cw, n0, fmaf(al, di0, bl * dj0));
+        float rr = __fadd_rn(d1, lo);
+        rr = __fmul_rn(__fsub_rn(rr, round_nearest(rr)), kTwoPiF);
+        const float2 R0 = make_float2(rr, rr);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 ph = ffma2(CRR, DN[q], ffma2(ARR, DI[q], R0));
+          float2 Cs, Sn;
+          __sincosf(ph.x, &Sn.x, &Cs.x);
+          __sincosf(ph.y, &Sn.y, &Cs.y);
+          const float4* zq = s_Z + (b * 4 + q) * 4;
+          const float2* nq = s_N + (b * 4 + q) * 4;
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const float4 z = zq[p];
+            const float2 ZR = make_float2(z.x, z.y), ZI = make_float2(z.z, z.w), NZR = nq[p];
+            RE[p] = ffma2(ZR, Cs, RE[p]);
+            RE[p] = ffma2(ZI, Sn, RE[p]);
+            IM[p] = ffma2(ZI, Cs, IM[p]);
+            IM[p] = ffma2(NZR, Sn, IM[p]);
+          }
+        }
+      }
+    }
+  }
+
+  // ---- combine pixel splits and write the visibility
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    s_red[(2 * p) * kDegridThreads + tid] = RE[p].x + RE[p].y;
+    s_red[(2 * p + 1) * kDegridThreads + tid] = IM[p].x + IM[p].y;
+  }
+  __syncthreads();
+  if (valid && split == 0) {
+    float v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      float s = 0.f;
+      for (int sp = 0; sp < nsplit; ++sp) s += s_red[c * kDegridThreads + (sp * wv + vgroup) * 32 + lane];
+      v[c] = s;
+    }
+    a.vis[2 * vidx] = make_float4(v[0], v[1], v[2], v[3]);
+    a.vis[2 * vidx + 1] = make_float4(v[4], v[5], v[6], v[7]);
+  }
+}
+
+template <int L>
+static size_t degridder_smem(int nodes) {
+  return sizeof(float4) * kChunkBlocks * 16 + sizeof(float2) * kChunkBlocks * 16 + sizeof(float4) * kChunkBlocks * 3 +
+         sizeof(float) * 8 * kDegridThreads + sizeof(float2) * 2 * nodes * nodes * 4;
+}
+
+template <int L>
+static int launch_degridder_t(const DegridArgs& a, int n_items, void* stream) {
+  const size_t smem = degridder_smem<L>(a.g.nodes);
+  cudaError_t e = cudaFuncSetAttribute(degridder_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return int(e);
+  if (n_items <= 0) return 0;
+  degridder_kernel<L><<<n_items, kDegridThreads, smem, cudaStream_t(stream)>>>(a);
+  return int(cudaGetLastError());
+}
+
+int launch_degridder(int L, const DegridArgs& a, int n_items, void* stream) {
+  switch (L) {
+    case 32: return launch_degridder_t<32>(a, n_items, stream);
+    case 64: return launch_degridder_t<64>(a, n_items, stream);
+    case 96: return launch_degridder_t<96>(a, n_items, stream);
+    case 128: return launch_degridder_t<128>(a, n_items, stream);
+    default: return int(cudaErrorInvalidValue);
+  }
+}
+
+}  // namespace idg

@@ -1,0 +1,480 @@
+// C ABI of libidg (include/idg.h): plan creation, gridding, degridding.
+//
+// A plan holds the partition (Section 3.1) and everything the kernels need
+// on the device.  Subgrids run in batches whose subgrid images fit the
+// plan's scratch buffer (Section 3.4 batches by memory; here the batch is a
+// set of subgrids, ordered so that neighbouring subgrids of the uv plane run
+// together and their adds into the master grid stay in L2).  Within a batch
+// the work items are ordered longest-first so the tail of the launch is
+// short.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "idg_internal.h"
+
+using namespace idg;
+
+namespace {
+
+thread_local std::string g_thread_error;
+constexpr double kPi = 3.14159265358979323846;
+
+struct Batch {
+  int32_t sg_offset, sg_count;
+  int32_t gi_offset, gi_count;
+  int32_t di_offset, di_count;
+};
+
+template <typename T>
+struct DevBuf {
+  T* ptr = nullptr;
+  size_t n = 0;
+};
+
+}  // namespace
+
+struct idg_plan {
+  idg_geometry geom{};
+  int32_t n_st = 0, n_bl = 0, n_t = 0, n_ch = 0, n_int = 0;
+  int32_t L = 0, N = 0;
+  cudaStream_t stream = nullptr;
+  bool host_only = false;
+  Partition part;
+  std::vector<SubgridDesc> exec;  // non-dropped subgrids in execution order
+  std::vector<Batch> batches;
+  int32_t batch_cap = 0;
+  int64_t n_grid_items = 0, n_degrid_items = 0;
+  int64_t n_vis_dropped = 0, n_sg_dropped = 0;
+  int64_t vis_pixels = 0;
+  int64_t device_bytes = 0;
+  std::string last_error;
+  // device
+  double* d_uvw = nullptr;
+  double* d_fscale = nullptr;
+  float* d_taper = nullptr;
+  float4* d_blk = nullptr;
+  float2* d_twiddle = nullptr;
+  SubgridDesc* d_sg = nullptr;
+  SegmentDesc* d_seg = nullptr;
+  GridItem* d_gitems = nullptr;
+  DegridItem* d_ditems = nullptr;
+  float2* d_scratch = nullptr;
+};
+
+namespace {
+
+idg_status set_err(idg_plan* p, idg_status st, const std::string& msg) {
+  if (p)
+    p->last_error = msg;
+  else
+    g_thread_error = msg;
+  return st;
+}
+
+idg_status cuda_err(idg_plan* p, int code, const char* where) {
+  if (code == 0) return IDG_OK;
+  const cudaError_t e = cudaError_t(code);
+  std::string msg = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return set_err(p, e == cudaErrorMemoryAllocation ? IDG_ERR_OOM : IDG_ERR_CUDA, msg);
+}
+
+template <typename T>
+int upload(idg_plan* p, T** dst, const T* src, size_t n) {
+  if (n == 0) {
+    *dst = nullptr;
+    return 0;
+  }
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), n * sizeof(T));
+  if (e != cudaSuccess) return int(e);
+  p->device_bytes += int64_t(n * sizeof(T));
+  return int(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, p->stream));
+}
+
+void free_device(idg_plan* p) {
+  void* ptrs[] = {p->d_uvw, p->d_fscale, p->d_taper, p->d_blk, p->d_twiddle, p->d_sg,
+                  p->d_seg, p->d_gitems, p->d_ditems, p->d_scratch};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  p->d_uvw = nullptr;
+  p->d_fscale = nullptr;
+  p->d_taper = nullptr;
+  p->d_blk = nullptr;
+  p->d_twiddle = nullptr;
+  p->d_sg = nullptr;
+  p->d_seg = nullptr;
+  p->d_gitems = nullptr;
+  p->d_ditems = nullptr;
+  p->d_scratch = nullptr;
+}
+
+// Block geometry table, FP64 -> FP32: for each row j and block ib of 8
+// pixels, n'(anchor) and n'(pixel) - n'(anchor) (anchor = pixel 4 of the
+// block), plus the anchor offsets (i_a - L/2, j - L/2).
+std::vector<float4> block_geometry(int L, double fov) {
+  const int tpr = L / 8;
+  std::vector<float4> t(size_t(L) * tpr * 3);
+  auto nprime = [&](int i, int j) {
+    const double l = double(i - L / 2) * fov / double(L), m = double(j - L / 2) * fov / double(L);
+    return std::sqrt(1.0 - l * l - m * m) - 1.0;
+  };
+  for (int j = 0; j < L; ++j)
+    for (int ib = 0; ib < tpr; ++ib) {
+      const int ia = ib * 8 + 4;
+      const double n0 = nprime(ia, j);
+      float dn[8];
+      for (int k = 0; k < 8; ++k) dn[k] = float(nprime(ib * 8 + k, j) - n0);
+      float4* g = &t[(size_t(j) * tpr + ib) * 3];
+      g[0] = make_float4(float(n0), dn[0], dn[1], dn[2]);
+      g[1] = make_float4(dn[3], dn[4], dn[5], dn[6]);
+      g[2] = make_float4(dn[7], float(ia - L / 2), float(j - L / 2), 0.f);
+    }
+  return t;
+}
+
+size_t scratch_budget_bytes() {
+  const char* s = std::getenv("IDG_SCRATCH_BYTES");
+  if (s && *s) {
+    const double v = std::atof(s);
+    if (v >= 1.0) return size_t(v);
+  }
+  return size_t(1) << 30;  // 1 GiB of subgrid images per batch
+}
+
+idg_status check_buffer(idg_plan* p, const void* ptr, const char* name) {
+  if (!ptr) return set_err(p, IDG_ERR_INVALID_ARG, std::string(name) + " is NULL");
+  if (reinterpret_cast<uintptr_t>(ptr) % 16) return set_err(p, IDG_ERR_INVALID_ARG, std::string(name) + " is not 16-byte aligned");
+  return IDG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t idg_abi_version(void) { return IDG_ABI_VERSION; }
+
+const char* idg_last_error(const idg_plan* plan) {
+  return plan ? plan->last_error.c_str() : g_thread_error.c_str();
+}
+
+idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stations, int32_t n_baselines,
+                           int32_t n_timesteps, int32_t n_channels, const int32_t* baselines, const double* uvw_m,
+                           const double* freqs_hz, const int32_t* aterm_offsets, int32_t n_intervals,
+                           void* cuda_stream) {
+  if (!out) return set_err(nullptr, IDG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!g) return set_err(nullptr, IDG_ERR_INVALID_ARG, "geometry is NULL");
+  if (n_baselines < 0 || n_timesteps < 0 || n_channels < 0 || n_stations < 0 || n_intervals < 1)
+    return set_err(nullptr, IDG_ERR_INVALID_ARG, "negative size or n_intervals < 1");
+  if (!aterm_offsets) return set_err(nullptr, IDG_ERR_INVALID_ARG, "aterm_offsets is NULL");
+  if ((n_baselines > 0 && !baselines) || (n_baselines > 0 && n_timesteps > 0 && !uvw_m) || (n_channels > 0 && !freqs_hz))
+    return set_err(nullptr, IDG_ERR_INVALID_ARG, "NULL input table");
+  if (g->aterm_nodes < 2) return set_err(nullptr, IDG_ERR_INVALID_ARG, "aterm_nodes must be >= 2");
+  const bool host_only = (g->flags & IDG_HOST_ONLY) != 0;
+  if (!host_only && !supported_subgrid_size(g->subgrid_size))
+    return set_err(nullptr, IDG_ERR_UNSUPPORTED, "device plans support subgrid_size 32, 64, 96 or 128");
+  if (g->taper_kind != IDG_TAPER_KB && g->taper_kind != IDG_TAPER_USER)
+    return set_err(nullptr, IDG_ERR_INVALID_ARG, "unknown taper_kind");
+  if (g->taper_kind == IDG_TAPER_USER && !g->taper_user)
+    return set_err(nullptr, IDG_ERR_INVALID_ARG, "taper_user is NULL");
+
+  idg_plan* p = new (std::nothrow) idg_plan();
+  if (!p) return set_err(nullptr, IDG_ERR_OOM, "host allocation failed");
+  p->geom = *g;
+  p->geom.taper_user = nullptr;
+  p->n_st = n_stations;
+  p->n_bl = n_baselines;
+  p->n_t = n_timesteps;
+  p->n_ch = n_channels;
+  p->n_int = n_intervals;
+  p->L = g->subgrid_size;
+  p->N = g->grid_size;
+  p->stream = cudaStream_t(cuda_stream);
+  p->host_only = host_only;
+
+  PlanInput in{g->grid_size, g->subgrid_size, g->kernel_padding, g->image_size, g->flags, n_stations,
+               n_baselines, n_timesteps, n_channels, n_intervals, baselines, uvw_m, freqs_hz, aterm_offsets};
+  std::string err;
+  idg_status st = partition(in, &p->part, &err);
+  if (st != IDG_OK) {
+    set_err(nullptr, st, err);
+    delete p;
+    return st;
+  }
+  const int L = p->L;
+  for (const SubgridDesc& d : p->part.subgrids) {
+    if (d.dropped) {
+      ++p->n_sg_dropped;
+      p->n_vis_dropped += d.n_vis;
+    } else {
+      p->exec.push_back(d);
+      p->vis_pixels += int64_t(d.n_vis) * L * L;
+    }
+  }
+  if (host_only) {
+    *out = p;
+    return IDG_OK;
+  }
+
+  // execution order: row-major position on the uv plane (adder locality)
+  std::stable_sort(p->exec.begin(), p->exec.end(), [](const SubgridDesc& x, const SubgridDesc& y) {
+    if (x.y0 != y.y0) return x.y0 < y.y0;
+    return x.x0 < y.x0;
+  });
+  const size_t per_sg = size_t(4) * L * L * sizeof(float2);
+  const size_t cap = std::max<size_t>(1, scratch_budget_bytes() / per_sg);
+  p->batch_cap = int32_t(std::min<size_t>(cap, std::max<size_t>(1, p->exec.size())));
+  const int rows = gridder_rows(L);
+  const int tiles = L / rows;
+  std::vector<GridItem> gitems;
+  std::vector<DegridItem> ditems;
+  for (size_t s0 = 0; s0 < p->exec.size(); s0 += p->batch_cap) {
+    const int32_t cnt = int32_t(std::min<size_t>(p->batch_cap, p->exec.size() - s0));
+    Batch b{int32_t(s0), cnt, int32_t(gitems.size()), 0, int32_t(ditems.size()), 0};
+    // longest first: order batch subgrids by visibility count
+    std::vector<int32_t> order(cnt);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+      return p->exec[s0 + x].n_vis > p->exec[s0 + y].n_vis;
+    });
+    for (int32_t o : order)
+      for (int t = 0; t < tiles; ++t) gitems.push_back(GridItem{o, t});
+    std::vector<DegridItem> dloc;
+    for (int32_t o = 0; o < cnt; ++o) {
+      const SubgridDesc& d = p->exec[s0 + o];
+      for (int gidx = d.seg_begin; gidx < d.seg_begin + d.seg_count; ++gidx) {
+        const SegmentDesc& sgd = p->part.segments[gidx];
+        for (int k = sgd.k_begin; k < sgd.k_end; k += kDegridMaxVis)
+          dloc.push_back(DegridItem{o, gidx, k, std::min(k + kDegridMaxVis, sgd.k_end)});
+      }
+    }
+    std::stable_sort(dloc.begin(), dloc.end(), [](const DegridItem& x, const DegridItem& y) {
+      return (x.k_end - x.k_begin) > (y.k_end - y.k_begin);
+    });
+    ditems.insert(ditems.end(), dloc.begin(), dloc.end());
+    b.gi_count = int32_t(gitems.size()) - b.gi_offset;
+    b.di_count = int32_t(ditems.size()) - b.di_offset;
+    p->batches.push_back(b);
+  }
+  p->n_grid_items = int64_t(gitems.size());
+  p->n_degrid_items = int64_t(ditems.size());
+
+  // device tables
+  std::vector<double> fscale(n_channels);
+  for (int c = 0; c < n_channels; ++c) fscale[c] = freqs_hz[c] / kSpeedOfLight;
+  std::vector<double> taper_d;
+  if (g->taper_kind == IDG_TAPER_USER)
+    taper_d.assign(g->taper_user, g->taper_user + L);
+  else
+    taper_d = kaiser_bessel_taper(L, g->taper_beta > 0.0 ? g->taper_beta : kPi * g->kernel_padding / 2.0);
+  std::vector<float> taper_f(taper_d.begin(), taper_d.end());
+  std::vector<float4> blk = block_geometry(L, g->image_size);
+  std::vector<float2> tw(L);
+  for (int m = 0; m < L; ++m) {
+    const double ang = -2.0 * kPi * double(m) / double(L);
+    tw[m] = make_float2(float(std::cos(ang)), float(std::sin(ang)));
+  }
+  int e = configure_kernels(L);
+  if (!e) e = upload(p, &p->d_uvw, uvw_m, size_t(n_baselines) * n_timesteps * 3);
+  if (!e) e = upload(p, &p->d_fscale, fscale.data(), fscale.size());
+  if (!e) e = upload(p, &p->d_taper, taper_f.data(), taper_f.size());
+  if (!e) e = upload(p, &p->d_blk, blk.data(), blk.size());
+  if (!e) e = upload(p, &p->d_twiddle, tw.data(), tw.size());
+  if (!e) e = upload(p, &p->d_sg, p->exec.data(), p->exec.size());
+  if (!e) e = upload(p, &p->d_seg, p->part.segments.data(), p->part.segments.size());
+  if (!e) e = upload(p, &p->d_gitems, gitems.data(), gitems.size());
+  if (!e) e = upload(p, &p->d_ditems, ditems.data(), ditems.size());
+  if (!e && !p->exec.empty()) {
+    e = int(cudaMalloc(reinterpret_cast<void**>(&p->d_scratch), per_sg * p->batch_cap));
+    if (!e) p->device_bytes += int64_t(per_sg * p->batch_cap);
+  }
+  if (!e) e = int(cudaStreamSynchronize(p->stream));
+  if (e) {
+    st = cuda_err(nullptr, e, "idg_plan_create");
+    free_device(p);
+    delete p;
+    return st;
+  }
+  *out = p;
+  return IDG_OK;
+}
+
+idg_status idg_plan_destroy(idg_plan* plan) {
+  if (!plan) return IDG_OK;
+  if (!plan->host_only) cudaStreamSynchronize(plan->stream);
+  free_device(plan);
+  delete plan;
+  return IDG_OK;
+}
+
+idg_status idg_set_stream(idg_plan* plan, void* cuda_stream) {
+  if (!plan) return set_err(nullptr, IDG_ERR_INVALID_ARG, "plan is NULL");
+  plan->stream = cudaStream_t(cuda_stream);
+  return IDG_OK;
+}
+
+static KernelGeom kgeom(const idg_plan* p) {
+  return KernelGeom{p->N, p->L, p->n_t, p->n_ch, p->n_st, p->geom.aterm_nodes, p->geom.image_size};
+}
+
+idg_status idg_grid(idg_plan* plan, const void* vis_c64, const void* aterms_c64, void* grid_c128) {
+  if (!plan) return set_err(nullptr, IDG_ERR_INVALID_ARG, "plan is NULL");
+  if (plan->host_only) return set_err(plan, IDG_ERR_INVALID_ARG, "plan was created with IDG_HOST_ONLY");
+  idg_status st;
+  if ((st = check_buffer(plan, vis_c64, "vis")) || (st = check_buffer(plan, aterms_c64, "aterms")) ||
+      (st = check_buffer(plan, grid_c128, "grid")))
+    return st;
+  const int L = plan->L;
+  for (const Batch& b : plan->batches) {
+    GridArgs ga{};
+    ga.vis = static_cast<const float4*>(vis_c64);
+    ga.uvw = plan->d_uvw;
+    ga.fscale = plan->d_fscale;
+    ga.aterms = static_cast<const float2*>(aterms_c64);
+    ga.sg = plan->d_sg + b.sg_offset;
+    ga.seg = plan->d_seg;
+    ga.items = plan->d_gitems + b.gi_offset;
+    ga.taper = plan->d_taper;
+    ga.blk = plan->d_blk;
+    ga.scratch = plan->d_scratch;
+    ga.g = kgeom(plan);
+    int e = launch_gridder(L, ga, b.gi_count, plan->stream);
+    if (e) return cuda_err(plan, e, "gridder launch");
+    FftArgs fa{plan->d_sg + b.sg_offset, plan->d_scratch, static_cast<double2*>(grid_c128), plan->d_twiddle, plan->N};
+    e = launch_fft_adder(L, fa, b.sg_count, 0, plan->stream);
+    if (e) return cuda_err(plan, e, "fft/adder launch");
+  }
+  return IDG_OK;
+}
+
+idg_status idg_degrid(idg_plan* plan, const void* grid_c128, const void* aterms_c64, void* vis_c64) {
+  if (!plan) return set_err(nullptr, IDG_ERR_INVALID_ARG, "plan is NULL");
+  if (plan->host_only) return set_err(plan, IDG_ERR_INVALID_ARG, "plan was created with IDG_HOST_ONLY");
+  idg_status st;
+  if ((st = check_buffer(plan, vis_c64, "vis")) || (st = check_buffer(plan, aterms_c64, "aterms")) ||
+      (st = check_buffer(plan, grid_c128, "grid")))
+    return st;
+  const int L = plan->L;
+  if (plan->n_vis_dropped > 0) {
+    const size_t bytes = size_t(plan->n_bl) * plan->n_t * plan->n_ch * 4 * sizeof(float2);
+    const int e = int(cudaMemsetAsync(vis_c64, 0, bytes, plan->stream));
+    if (e) return cuda_err(plan, e, "zeroing dropped visibilities");
+  }
+  for (const Batch& b : plan->batches) {
+    FftArgs fa{plan->d_sg + b.sg_offset, plan->d_scratch, const_cast<double2*>(static_cast<const double2*>(grid_c128)),
+               plan->d_twiddle, plan->N};
+    int e = launch_splitter_ifft(L, fa, b.sg_count, plan->stream);
+    if (e) return cuda_err(plan, e, "splitter/ifft launch");
+    DegridArgs da{};
+    da.vis = static_cast<float4*>(vis_c64);
+    da.uvw = plan->d_uvw;
+    da.fscale = plan->d_fscale;
+    da.aterms = static_cast<const float2*>(aterms_c64);
+    da.sg = plan->d_sg + b.sg_offset;
+    da.seg = plan->d_seg;
+    da.items = plan->d_ditems + b.di_offset;
+    da.taper = plan->d_taper;
+    da.blk = plan->d_blk;
+    da.scratch = plan->d_scratch;
+    da.g = kgeom(plan);
+    e = launch_degridder(L, da, b.di_count, plan->stream);
+    if (e) return cuda_err(plan, e, "degridder launch");
+  }
+  return IDG_OK;
+}
+
+idg_status idg_subgrid_images(idg_plan* plan, const void* vis_c64, const void* aterms_c64, int32_t stage,
+                              void* out_c64) {
+  if (!plan) return set_err(nullptr, IDG_ERR_INVALID_ARG, "plan is NULL");
+  if (plan->host_only) return set_err(plan, IDG_ERR_INVALID_ARG, "plan was created with IDG_HOST_ONLY");
+  if (stage != 0 && stage != 1) return set_err(plan, IDG_ERR_INVALID_ARG, "stage must be 0 or 1");
+  idg_status st;
+  if ((st = check_buffer(plan, vis_c64, "vis")) || (st = check_buffer(plan, aterms_c64, "aterms")) ||
+      (st = check_buffer(plan, out_c64, "out")))
+    return st;
+  const int L = plan->L;
+  const size_t total = plan->part.subgrids.size() * size_t(4) * L * L * sizeof(float2);
+  int e = int(cudaMemsetAsync(out_c64, 0, total, plan->stream));
+  if (e) return cuda_err(plan, e, "zeroing output");
+  for (const Batch& b : plan->batches) {
+    GridArgs ga{};
+    ga.vis = static_cast<const float4*>(vis_c64);
+    ga.uvw = plan->d_uvw;
+    ga.fscale = plan->d_fscale;
+    ga.aterms = static_cast<const float2*>(aterms_c64);
+    ga.sg = plan->d_sg + b.sg_offset;
+    ga.seg = plan->d_seg;
+    ga.items = plan->d_gitems + b.gi_offset;
+    ga.taper = plan->d_taper;
+    ga.blk = plan->d_blk;
+    ga.scratch = plan->d_scratch;
+    ga.g = kgeom(plan);
+    e = launch_gridder(L, ga, b.gi_count, plan->stream);
+    if (e) return cuda_err(plan, e, "gridder launch");
+    if (stage == 1) {
+      FftArgs fa{plan->d_sg + b.sg_offset, plan->d_scratch, nullptr, plan->d_twiddle, plan->N};
+      e = launch_fft_adder(L, fa, b.sg_count, 1, plan->stream);
+      if (e) return cuda_err(plan, e, "fft launch");
+    }
+    e = launch_export_subgrids(L, plan->d_sg + b.sg_offset, plan->d_scratch, static_cast<float2*>(out_c64),
+                               b.sg_count, plan->stream);
+    if (e) return cuda_err(plan, e, "export launch");
+  }
+  return IDG_OK;
+}
+
+idg_status idg_plan_stats(const idg_plan* plan, idg_plan_stats_t* out) {
+  if (!plan || !out) return set_err(nullptr, IDG_ERR_INVALID_ARG, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  out->n_subgrids = int64_t(plan->part.subgrids.size());
+  out->n_segments = int64_t(plan->part.segments.size());
+  out->n_vis = int64_t(plan->n_bl) * plan->n_t * plan->n_ch;
+  out->n_vis_dropped = plan->n_vis_dropped;
+  out->n_subgrids_dropped = plan->n_sg_dropped;
+  out->n_grid_items = plan->n_grid_items;
+  out->n_degrid_items = plan->n_degrid_items;
+  out->n_batches = int64_t(plan->batches.size());
+  for (const SubgridDesc& d : plan->part.subgrids) {
+    int k = 0;
+    while (k < 15 && (int64_t(1) << (k + 1)) <= d.n_vis) ++k;
+    out->occupancy_hist[k] += 1;
+  }
+  out->device_bytes = plan->device_bytes;
+  out->vis_pixels = plan->vis_pixels;
+  out->subgrid_size = plan->L;
+  out->batch_capacity = plan->batch_cap;
+  return IDG_OK;
+}
+
+idg_status idg_plan_subgrids(const idg_plan* plan, int32_t* out, int64_t cap, int64_t* n) {
+  if (!plan || !n || (cap > 0 && !out)) return set_err(nullptr, IDG_ERR_INVALID_ARG, "NULL argument");
+  *n = int64_t(plan->part.subgrids.size());
+  for (int64_t s = 0; s < std::min<int64_t>(cap, *n); ++s) {
+    const SubgridDesc& d = plan->part.subgrids[s];
+    const int32_t row[8] = {d.b, d.t0, d.t1, d.c0, d.c1, d.x0, d.y0, d.dropped};
+    std::memcpy(out + s * 8, row, sizeof row);
+  }
+  return IDG_OK;
+}
+
+idg_status idg_plan_segments(const idg_plan* plan, int32_t* out, int64_t cap, int64_t* n) {
+  if (!plan || !n || (cap > 0 && !out)) return set_err(nullptr, IDG_ERR_INVALID_ARG, "NULL argument");
+  *n = int64_t(plan->part.segments.size());
+  for (int64_t s = 0; s < std::min<int64_t>(cap, *n); ++s) {
+    const SegmentDesc& g = plan->part.segments[s];
+    const SubgridDesc& d = plan->part.subgrids[g.subgrid];
+    const int width = d.c1 - d.c0;
+    const int32_t row[4] = {g.subgrid, g.interval, d.t0 + g.k_begin / width, d.t0 + g.k_end / width};
+    std::memcpy(out + s * 4, row, sizeof row);
+  }
+  return IDG_OK;
+}
+
+}  // extern "C"

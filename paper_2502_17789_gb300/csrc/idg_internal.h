@@ -1,0 +1,134 @@
+// Internal types of libidg shared by the host planner, the API layer and the
+// CUDA kernels.  Not part of the ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <vector_types.h>
+
+#include "../../include/idg.h"
+
+namespace idg {
+
+constexpr double kSpeedOfLight = 299792458.0;
+
+// One subgrid (Section 2.2): the subtable [t0,t1) x [c0,c1) of baseline b,
+// placed with corner (x0, y0) on the master grid.  64 bytes.
+struct SubgridDesc {
+  int32_t b, p, q;
+  int32_t t0, t1, c0, c1;
+  int32_t x0, y0;
+  int32_t seg_begin, seg_count;  // into the segment table
+  int32_t n_vis;
+  int32_t dropped;
+  int32_t plan_index;            // position in plan order
+  int32_t pad0, pad1;
+};
+static_assert(sizeof(SubgridDesc) == 64, "SubgridDesc layout");
+
+// The part of a subgrid that shares one A-term interval (Section 3.3).
+// Members are enumerated t-major: k = (t - t0) * (c1 - c0) + (c - c0).
+struct SegmentDesc {
+  int32_t subgrid;   // plan index
+  int32_t interval;
+  int32_t k_begin, k_end;
+};
+
+// Gridder work item: one pixel tile of one subgrid of the current batch.
+struct GridItem {
+  int32_t sg;    // index into the batch's device subgrid table
+  int32_t tile;  // row tile
+};
+
+// Degridder work item: up to kDegridMaxVis visibilities of one segment.
+struct DegridItem {
+  int32_t sg;       // index into the batch's device subgrid table
+  int32_t segment;  // global segment index
+  int32_t k_begin, k_end;
+};
+
+constexpr int kDegridMaxVis = 256;
+
+// ---------------------------------------------------------------- planner
+
+struct PlanInput {
+  int32_t N, L, P;
+  double fov;
+  int32_t flags;
+  int32_t n_st, n_bl, n_t, n_ch, n_int;
+  const int32_t* baselines;
+  const double* uvw;
+  const double* freqs;
+  const int32_t* aterm_offsets;
+};
+
+struct Partition {
+  std::vector<SubgridDesc> subgrids;  // plan order
+  std::vector<SegmentDesc> segments;
+};
+
+// Returns IDG_OK or an error status with a message in `err`.
+idg_status partition(const PlanInput& in, Partition* out, std::string* err);
+
+// Kaiser-Bessel taper samples T_i, i in [0,L), at x = (2i - L)/L.
+std::vector<double> kaiser_bessel_taper(int L, double beta);
+
+// ---------------------------------------------------------------- kernels
+
+struct KernelGeom {
+  int32_t N, L, n_t, n_ch, n_st, nodes;
+  double fov;
+};
+
+struct GridArgs {
+  const float4* vis;          // [bl][t][ch][4] complex64, 2 float4 per visibility
+  const double* uvw;          // [bl][t][3] metres
+  const double* fscale;       // [ch] f / c
+  const float2* aterms;       // [n_int][n_st][nodes][nodes][4]
+  const SubgridDesc* sg;      // batch subgrid table
+  const SegmentDesc* seg;     // global segment table
+  const GridItem* items;
+  const float* taper;         // [L]
+  const float4* blk;          // [L][L/8][3] block geometry (n0, dn[8], anchor offsets)
+  float2* scratch;            // [batch][4][L][L]
+  KernelGeom g;
+};
+
+struct DegridArgs {
+  float4* vis;
+  const double* uvw;
+  const double* fscale;
+  const float2* aterms;
+  const SubgridDesc* sg;
+  const SegmentDesc* seg;
+  const DegridItem* items;
+  const float* taper;
+  const float4* blk;
+  const float2* scratch;      // [batch][4][L][L] subgrid images Y
+  KernelGeom g;
+};
+
+struct FftArgs {
+  const SubgridDesc* sg;   // batch subgrid table
+  float2* scratch;         // [batch][4][L][L]
+  double2* grid;           // [4][N][N] (adder: +=, splitter: read)
+  const float2* twiddle;   // [L] e^{-2 pi i m / L}
+  int32_t N;
+};
+
+// Launchers (return cudaError_t as int).  `n` is the item or subgrid count.
+int launch_gridder(int L, const GridArgs& a, int n_items, void* stream);
+int launch_degridder(int L, const DegridArgs& a, int n_items, void* stream);
+// mode 0: FFT + add into grid; mode 1: FFT in place in scratch (inspection)
+int launch_fft_adder(int L, const FftArgs& a, int n_subgrids, int mode, void* stream);
+int launch_splitter_ifft(int L, const FftArgs& a, int n_subgrids, void* stream);
+// copy a batch of subgrid images to plan order with the (-1)^(x+y) centring undone
+int launch_export_subgrids(int L, const SubgridDesc* sg, const float2* scratch, float2* out, int n_subgrids,
+                           void* stream);
+int configure_kernels(int L);  // one-time attributes (dynamic shared memory opt-in)
+bool supported_subgrid_size(int L);
+int gridder_rows(int L);  // rows per gridder pixel tile (0 if unsupported)
+
+}  // namespace idg

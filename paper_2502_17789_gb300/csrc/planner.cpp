@@ -1,0 +1,235 @@
+// Host partitioner of libidg: splits each baseline's (timestep x channel)
+// table into subtables that each fit one L x L subgrid (Section 3.1), with
+// the A-term constraint of Section 3.3 applied per segment (or per subgrid
+// under IDG_SPLIT_AT_ATERM_INTERVALS).
+//
+// Must be compiled without floating-point contraction (-ffp-contract=off):
+// the decisions depend on pixel coordinates that have to round identically
+// on every machine.
+//
+// Rules (reading of Section 3.1; the paper names the idea, not constants):
+//   span S = L - P - 4, growth margin G = max(2, S/4), channel span Sc = S - G
+//   1. pending subtables (t_start, c_lo, c_hi) start as (block start, 0, n_ch)
+//   2. at t_start, cut [c_lo, c_hi) into maximal runs whose end channels lie
+//      within Sc pixels in u and in v ("comfortably")
+//   3. extend each run in time while its four corner visibilities stay within
+//      S pixels, then shrink while any member falls outside S
+//   4. emit it; its later timesteps become a new pending subtable
+//   subgrids are ordered by (baseline, block, t_start, c_lo)
+//   corner x0 = floor((xi_min + xi_max) / 2) - L/2, likewise y0
+//   w check: |w| * max|grad n'| * FOV <= P/2 - 1 (footnote of Section 2.4)
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <numeric>
+
+#include "idg_internal.h"
+
+namespace idg {
+namespace {
+
+struct Pending {
+  int32_t ts, c_lo, c_hi;
+};
+struct Run {
+  int32_t blk, ts, te, c_lo, c_hi;
+};
+
+// Pixel coordinates of every visibility of one baseline, [t][ch].
+class BaselinePixels {
+ public:
+  BaselinePixels(const PlanInput& in, int b) : n_ch_(in.n_ch), xi_(size_t(in.n_t) * in.n_ch), eta_(xi_.size()) {
+    const double half = double(in.N / 2);
+    for (int t = 0; t < in.n_t; ++t) {
+      const double* r = in.uvw + (size_t(b) * in.n_t + t) * 3;
+      for (int c = 0; c < in.n_ch; ++c) {
+        const double f = in.freqs[c];
+        const double u = (r[0] * f) / kSpeedOfLight;
+        const double v = (r[1] * f) / kSpeedOfLight;
+        xi_[size_t(t) * n_ch_ + c] = u * in.fov + half;
+        eta_[size_t(t) * n_ch_ + c] = v * in.fov + half;
+      }
+    }
+  }
+  double xi(int t, int c) const { return xi_[size_t(t) * n_ch_ + c]; }
+  double eta(int t, int c) const { return eta_[size_t(t) * n_ch_ + c]; }
+
+  // Extent of a set of (t, c) points along u and v.
+  template <size_t K>
+  bool within(const int (&ts)[K], const int (&cs)[K], double span) const {
+    double xmin = xi(ts[0], cs[0]), xmax = xmin, ymin = eta(ts[0], cs[0]), ymax = ymin;
+    for (size_t n = 1; n < K; ++n) {
+      const double x = xi(ts[n], cs[n]), y = eta(ts[n], cs[n]);
+      xmin = std::min(xmin, x);
+      xmax = std::max(xmax, x);
+      ymin = std::min(ymin, y);
+      ymax = std::max(ymax, y);
+    }
+    return (xmax - xmin) <= span && (ymax - ymin) <= span;
+  }
+
+  struct Box {
+    double xmin, xmax, ymin, ymax;
+  };
+  Box box(int ts, int te, int c_lo, int c_hi) const {
+    Box bx{xi(ts, c_lo), xi(ts, c_lo), eta(ts, c_lo), eta(ts, c_lo)};
+    for (int t = ts; t < te; ++t)
+      for (int c = c_lo; c < c_hi; ++c) {
+        bx.xmin = std::min(bx.xmin, xi(t, c));
+        bx.xmax = std::max(bx.xmax, xi(t, c));
+        bx.ymin = std::min(bx.ymin, eta(t, c));
+        bx.ymax = std::max(bx.ymax, eta(t, c));
+      }
+    return bx;
+  }
+
+ private:
+  int n_ch_;
+  std::vector<double> xi_, eta_;
+};
+
+}  // namespace
+
+idg_status partition(const PlanInput& in, Partition* out, std::string* err) {
+  char msg[256];
+  auto fail = [&](idg_status st, const char* what) {
+    *err = what;
+    return st;
+  };
+  if (in.N <= 0 || in.N % 2 || in.L <= 0 || in.L % 2 || in.L > in.N || in.P < 0 || in.P % 2)
+    return fail(IDG_ERR_INVALID_ARG, "grid_size and subgrid_size must be even with 0 < L <= N; padding even, >= 0");
+  if (!(in.fov > 0.0) || !(0.5 * in.fov * in.fov < 1.0))
+    return fail(IDG_ERR_INVALID_ARG, "image_size must satisfy 0 < FOV and FOV^2/2 < 1");
+  if (in.n_st < 0 || in.n_bl < 0 || in.n_t < 0 || in.n_ch < 0 || in.n_int < 1)
+    return fail(IDG_ERR_INVALID_ARG, "negative sizes or no A-term interval");
+  if (in.aterm_offsets[0] != 0 || in.aterm_offsets[in.n_int] != in.n_t)
+    return fail(IDG_ERR_INVALID_ARG, "aterm_offsets must start at 0 and end at n_timesteps");
+  for (int a = 0; a < in.n_int; ++a)
+    if (in.aterm_offsets[a + 1] < in.aterm_offsets[a]) return fail(IDG_ERR_INVALID_ARG, "aterm_offsets must ascend");
+  for (int c = 1; c < in.n_ch; ++c)
+    if (!(in.freqs[c] > in.freqs[c - 1]))
+      return fail(IDG_ERR_UNSORTED_FREQ, "channel frequencies must be strictly ascending");
+  for (int b = 0; b < in.n_bl; ++b) {
+    const int p = in.baselines[2 * b], q = in.baselines[2 * b + 1];
+    if (p < 0 || q < 0 || p >= in.n_st || q >= in.n_st) return fail(IDG_ERR_INVALID_ARG, "baseline station out of range");
+  }
+  const int S = in.L - in.P - 4;
+  if (S < 1) return fail(IDG_ERR_INVALID_ARG, "subgrid_size - kernel_padding - 4 must be >= 1");
+  const int G = std::max(2, S / 4);
+  const int Sc = std::max(0, S - G);
+
+  // w limit: steepest n' gradient is at the subgrid corner l = m = -FOV/2
+  const double r2 = 0.5 * in.fov * in.fov;
+  const double grad = std::sqrt(r2) / std::sqrt(1.0 - r2);
+  const double w_limit = 0.5 * in.P - 1.0;
+  for (int b = 0; b < in.n_bl; ++b)
+    for (int t = 0; t < in.n_t; ++t) {
+      const double wm = in.uvw[(size_t(b) * in.n_t + t) * 3 + 2];
+      for (int c = 0; c < in.n_ch; ++c) {
+        const double w = (wm * in.freqs[c]) / kSpeedOfLight;
+        if (std::fabs(w) * grad * in.fov > w_limit) {
+          std::snprintf(msg, sizeof msg, "|w| = %.3f wavelengths (baseline %d, t %d, ch %d) exceeds the %.2f-pixel "
+                        "w fringe limit", std::fabs(w), b, t, c, w_limit);
+          return fail(IDG_ERR_W_TOO_LARGE, msg);
+        }
+      }
+    }
+
+  out->subgrids.clear();
+  out->segments.clear();
+  const bool split = (in.flags & IDG_SPLIT_AT_ATERM_INTERVALS) != 0;
+  std::vector<Run> runs;
+  std::vector<Pending> todo;
+  for (int b = 0; b < in.n_bl; ++b) {
+    if (in.n_t == 0 || in.n_ch == 0) break;
+    const BaselinePixels px(in, b);
+    runs.clear();
+    const int n_blocks = split ? in.n_int : 1;
+    for (int blk = 0; blk < n_blocks; ++blk) {
+      const int ta = split ? in.aterm_offsets[blk] : 0;
+      const int tb = split ? in.aterm_offsets[blk + 1] : in.n_t;
+      if (ta >= tb) continue;
+      todo.assign(1, Pending{ta, 0, in.n_ch});
+      while (!todo.empty()) {
+        const Pending cur = todo.back();
+        todo.pop_back();
+        for (int lo = cur.c_lo; lo < cur.c_hi;) {
+          int hi = lo + 1;
+          while (hi < cur.c_hi) {
+            const int ts2[2] = {cur.ts, cur.ts}, cs2[2] = {lo, hi};
+            if (!px.within(ts2, cs2, double(Sc))) break;
+            ++hi;
+          }
+          int te = cur.ts + 1;
+          while (te < tb) {
+            const int ts4[4] = {cur.ts, cur.ts, te, te}, cs4[4] = {lo, hi - 1, lo, hi - 1};
+            if (!px.within(ts4, cs4, double(S))) break;
+            ++te;
+          }
+          while (te > cur.ts + 1) {
+            const auto bx = px.box(cur.ts, te, lo, hi);
+            if ((bx.xmax - bx.xmin) <= double(S) && (bx.ymax - bx.ymin) <= double(S)) break;
+            --te;
+          }
+          runs.push_back(Run{blk, cur.ts, te, lo, hi});
+          if (te < tb) todo.push_back(Pending{te, lo, hi});
+          lo = hi;
+        }
+      }
+    }
+    std::sort(runs.begin(), runs.end(), [](const Run& x, const Run& y) {
+      if (x.blk != y.blk) return x.blk < y.blk;
+      if (x.ts != y.ts) return x.ts < y.ts;
+      return x.c_lo < y.c_lo;
+    });
+    for (const Run& r : runs) {
+      const auto bx = px.box(r.ts, r.te, r.c_lo, r.c_hi);
+      SubgridDesc d{};
+      d.b = b;
+      d.p = in.baselines[2 * b];
+      d.q = in.baselines[2 * b + 1];
+      d.t0 = r.ts;
+      d.t1 = r.te;
+      d.c0 = r.c_lo;
+      d.c1 = r.c_hi;
+      d.x0 = int32_t(std::floor((bx.xmin + bx.xmax) / 2.0)) - in.L / 2;
+      d.y0 = int32_t(std::floor((bx.ymin + bx.ymax) / 2.0)) - in.L / 2;
+      d.n_vis = (r.te - r.ts) * (r.c_hi - r.c_lo);
+      d.plan_index = int32_t(out->subgrids.size());
+      const bool outside = d.x0 < 0 || d.y0 < 0 || d.x0 > in.N - in.L || d.y0 > in.N - in.L;
+      if (outside) {
+        if (!(in.flags & IDG_DROP_OUT_OF_GRID)) {
+          std::snprintf(msg, sizeof msg, "baseline %d timesteps [%d,%d) channels [%d,%d) need a subgrid at (%d,%d), "
+                        "outside the %d-pixel grid", b, r.ts, r.te, r.c_lo, r.c_hi, d.x0, d.y0, in.N);
+          return fail(IDG_ERR_UV_OUT_OF_GRID, msg);
+        }
+        d.dropped = 1;
+      }
+      d.seg_begin = int32_t(out->segments.size());
+      for (int a = 0; a < in.n_int; ++a) {
+        const int lo = std::max(in.aterm_offsets[a], r.ts), hi = std::min(in.aterm_offsets[a + 1], r.te);
+        if (lo >= hi) continue;
+        const int width = r.c_hi - r.c_lo;
+        out->segments.push_back(SegmentDesc{d.plan_index, a, (lo - r.ts) * width, (hi - r.ts) * width});
+      }
+      d.seg_count = int32_t(out->segments.size()) - d.seg_begin;
+      out->subgrids.push_back(d);
+    }
+  }
+  return IDG_OK;
+}
+
+std::vector<double> kaiser_bessel_taper(int L, double beta) {
+  // T(l) = I0(beta sqrt(1 - x^2)) / I0(beta), x = 2 l / FOV (Section 4.2);
+  // the standard library provides I0, as the paper notes.
+  std::vector<double> t(L);
+  const double norm = std::cyl_bessel_i(0.0, beta);
+  for (int i = 0; i < L; ++i) {
+    const double x = double(2 * i - L) / double(L);
+    const double r = 1.0 - x * x;
+    t[i] = (r > 0.0 ? std::cyl_bessel_i(0.0, beta * std::sqrt(r)) : 1.0) / norm;
+  }
+  return t;
+}
+
+}  // namespace idg

@@ -1,0 +1,122 @@
+"""CPU tests of libidg: the C ABI exports and the host planner (no device
+work; plans are created with IDG_HOST_ONLY)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2502_17789_gb300 import synth
+from tests import _brute
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "idg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(idg_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for must in ["idg_plan_create", "idg_grid", "idg_degrid", "idg_plan_destroy"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(idg_mod):
+    lib = idg_mod.load()
+    names = _declared_functions()
+    assert sorted(idg_mod.EXPORTS) == names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert idg_mod.idg_abi_version() == 1
+
+
+def _host_plan(idg_mod, obs, flags=0, L=None):
+    g, keep = idg_mod.make_geometry(obs.grid_size, L or obs.subgrid_size, obs.kernel_padding, obs.image_size,
+                                    aterm_nodes=obs.aterm_nodes, flags=flags | idg_mod.IDG_HOST_ONLY)
+    h = idg_mod.idg_plan_create(g, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets)
+    try:
+        return idg_mod.idg_plan_subgrids(h), idg_mod.idg_plan_segments(h), idg_mod.idg_plan_stats(h)
+    finally:
+        idg_mod.idg_plan_destroy(h)
+
+
+def _oracle_plan(oracle_mod, obs, flags=0, L=None):
+    geom = oracle_mod.Geometry(obs.grid_size, L or obs.subgrid_size, obs.kernel_padding, obs.image_size,
+                               aterm_nodes=obs.aterm_nodes, flags=flags)
+    return oracle_mod.plan(geom, obs.uvw, obs.freqs, obs.aterm_offsets)
+
+
+CASES = [
+    ("cfg1", lambda: synth.config(1), None),
+    ("cfg1-L64", lambda: synth.config(1), 64),
+    ("cfg2-reduced", lambda: synth.config(2, n_stations=40, n_timesteps=20), None),
+    ("cfg2-reduced-L128", lambda: synth.config(2, n_stations=30, n_timesteps=16), 128),
+    ("cfg4-reduced", lambda: synth.config(4, n_stations=48, n_timesteps=40), 64),
+]
+
+
+@pytest.mark.parametrize("name,make,L", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("split", [False, True])
+def test_planner_bit_exact_against_oracle(idg_mod, oracle_mod, name, make, L, split):
+    obs = make()
+    f_lib = idg_mod.IDG_SPLIT_AT_ATERM_INTERVALS if split else 0
+    f_or = oracle_mod.FLAG_SPLIT_INTERVALS if split else 0
+    sg, seg, st = _host_plan(idg_mod, obs, f_lib, L)
+    ref = _oracle_plan(oracle_mod, obs, f_or, L)
+    np.testing.assert_array_equal(sg, ref.subgrids)
+    np.testing.assert_array_equal(seg, ref.segments)
+    assert st.n_vis == obs.n_vis and st.n_subgrids == len(sg)
+    assert sum(st.occupancy_hist) == len(sg)
+
+
+def test_planner_drop_flag_bit_exact(idg_mod, oracle_mod):
+    obs = _brute.tiny_observation(seed=4, n_st=8)
+    u, v, _ = _brute.uvw_lambda(obs)
+    reach = np.abs(np.stack([u, v])).max(axis=(0, 2, 3)) * obs.image_size
+    obs.uvw = obs.uvw * (1.2 * (obs.grid_size / 2 - obs.subgrid_size / 2) / np.median(reach))
+    obs.uvw[..., 2] = 0.0
+    with pytest.raises(idg_mod.IdgError) as e:
+        _host_plan(idg_mod, obs)
+    assert e.value.status == 3
+    sg, seg, st = _host_plan(idg_mod, obs, idg_mod.IDG_DROP_OUT_OF_GRID)
+    ref = _oracle_plan(oracle_mod, obs, oracle_mod.FLAG_DROP)
+    np.testing.assert_array_equal(sg, ref.subgrids)
+    np.testing.assert_array_equal(seg, ref.segments)
+    assert st.n_subgrids_dropped == int(ref.subgrids[:, 7].sum()) > 0
+
+
+def test_planner_error_codes(idg_mod):
+    obs = _brute.tiny_observation(seed=1)
+    bad = obs.freqs[::-1].copy()
+    g, _ = idg_mod.make_geometry(obs.grid_size, obs.subgrid_size, obs.kernel_padding, obs.image_size,
+                                 flags=idg_mod.IDG_HOST_ONLY)
+    with pytest.raises(idg_mod.IdgError) as e:
+        idg_mod.idg_plan_create(g, obs.n_stations, obs.baselines, obs.uvw, bad, obs.aterm_offsets)
+    assert e.value.status == 2 and "ascending" in str(e.value)
+    w = obs.uvw.copy()
+    w[..., 2] = 500.0
+    with pytest.raises(idg_mod.IdgError) as e:
+        idg_mod.idg_plan_create(g, obs.n_stations, obs.baselines, w, obs.freqs, obs.aterm_offsets)
+    assert e.value.status == 4
+    with pytest.raises(idg_mod.IdgError) as e:
+        idg_mod.idg_plan_create(g, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, np.array([0, 1], np.int32))
+    assert e.value.status == 1
+    # device plans accept only the compiled subgrid sizes
+    g2, _ = idg_mod.make_geometry(obs.grid_size, 16, obs.kernel_padding, obs.image_size)
+    with pytest.raises(idg_mod.IdgError) as e:
+        idg_mod.idg_plan_create(g2, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets)
+    assert e.value.status == 8
+    bl = obs.baselines.copy()
+    bl[0, 1] = 99
+    with pytest.raises(idg_mod.IdgError) as e:
+        idg_mod.idg_plan_create(g, obs.n_stations, bl, obs.uvw, obs.freqs, obs.aterm_offsets)
+    assert e.value.status == 1
+
+
+def test_empty_observation_plans_to_nothing(idg_mod):
+    obs = _brute.tiny_observation(seed=1, n_t=0)
+    sg, seg, st = _host_plan(idg_mod, obs)
+    assert len(sg) == 0 and len(seg) == 0 and st.n_vis == 0
