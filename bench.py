@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Benchmark of the IDG hot path: gridded + degridded visibilities per second.
+
+Workload (default): the MWA-like observation -- 128 stations (8128 baselines)
+uniform in a 3 km disk, 56 timesteps x 2 s, 24 channels 140-170 MHz, 4-pol
+complex64 visibilities from 200 point sources plus 1 Jy Gaussian noise,
+4096^2 FP64 master grid, 96^2 subgrids, kernel padding 18, FOV 0.5 rad,
+per-station A-terms every 8 s on 9 x 9 nodes (Gaussian beam x Kolmogorov
+phase screen), synthetic and seeded.
+
+One step = idg_grid of all visibilities into a zeroed master grid plus
+idg_degrid of all visibilities from a model grid.  value = 2 * n_vis * steps
+/ device time.  The inputs (350 MB visibilities, 1 GiB grids) are larger than
+L2, so no flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+build) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gridded+degridded visibilities/sec at 1 GB300 (FP32-batched vs plain) and % FP32/SFU roofline"
+UNIT = "vis/s"
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM per clock
+FLOP_PER_VISPX = 34.0            # 16 FMA (4-pol complex MAC) + 1 FMA (phase) = 17 FMA per visibility-pixel
+SM_MAX_MHZ_FALLBACK = 2070.0
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", type=int, default=2, help="workload index (1 small, 2 MWA-like)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (small profiling runs)")
+    ap.add_argument("--stations", type=int, default=None, help="reduce the workload's stations (profiling)")
+    ap.add_argument("--timesteps", type=int, default=None, help="reduce the workload's timesteps (profiling)")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- workload
+
+def make_workload(idx: int, device, stations=None, timesteps=None):
+    import torch
+    from paper_2502_17789_gb300 import synth
+
+    obs = synth.config(idx, seed=0, n_stations=stations, n_timesteps=timesteps)
+    rng = np.random.default_rng(0)
+    model = synth.beam_screen_model(rng, rms_rad=2.0)
+    aterms = synth.aterms_beam_screen(obs, model) if idx != 1 else \
+        synth.aterms_identity(obs.n_intervals, obs.n_stations, obs.aterm_nodes)
+    n_src, half = (20, 0.0873) if idx == 1 else (200, 0.16)
+    sky = synth.point_sources(rng, n_src, half)
+    vis = synth.simulate_visibilities(obs, sky, model if idx != 1 else None, noise_sigma=1.0, rng=rng,
+                                      device=str(device))
+    desc = {1: "32 stations in a 1 km disk (496 baselines), 16 x 8 s, 8 ch 150-157 MHz, 512^2 grid, L=32, P=12, "
+               "FOV 0.35, identity A-terms, 20 sources + noise",
+            2: "128 stations in a 3 km disk (8128 baselines), 56 x 2 s, 24 ch 140-170 MHz, 4096^2 FP64 grid, "
+               "L=96, P=18, FOV 0.5, A-terms per 8 s on 9x9 nodes (Gaussian beam x Kolmogorov screen, 2 rad rms), "
+               "200 sources + 1 Jy noise"}.get(idx, obs.name)
+    if stations or timesteps:
+        desc = f"REDUCED ({obs.n_stations} stations, {obs.n_timesteps} timesteps) " + desc
+    return obs, torch.as_tensor(aterms, device=device), vis, desc
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) == len(self.FIELDS):
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in rows if num(r[1]) is not None]
+        pw = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"], r[4:]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- CPU baseline (oracle)
+
+def _oracle_sample(obs, aterms_np, vis_np, grid_np, budget_s: float, seed: int = 0):
+    """Time the FP64 oracle on a seeded random sample of subgrids whose size
+    is calibrated to `budget_s` seconds of grid + degrid work."""
+    import oracle
+
+    geom = oracle.Geometry(obs.grid_size, obs.subgrid_size, obs.kernel_padding, obs.image_size,
+                           aterm_nodes=obs.aterm_nodes)
+    full = oracle.plan(geom, obs.uvw, obs.freqs, obs.aterm_offsets)
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(full.subgrids.shape[0])
+    A = aterms_np.astype(np.complex128)
+
+    def subplan(idx):
+        idx = np.sort(idx)
+        sg = full.subgrids[idx]
+        remap = {int(o): n for n, o in enumerate(idx)}
+        segs = np.array([[remap[int(s[0])], s[1], s[2], s[3]] for s in full.segments if int(s[0]) in remap], np.int32)
+        return oracle.Plan(sg, segs), int(sum((r[2] - r[1]) * (r[4] - r[3]) for r in sg))
+
+    args = lambda pl: (geom, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets, pl)
+    vis128 = vis_np.astype(np.complex128)
+
+    def run(pl):
+        t0 = time.perf_counter()
+        oracle.grid(*args(pl), vis128, A)
+        oracle.degrid(*args(pl), grid_np, A)
+        return time.perf_counter() - t0
+
+    n = min(os.cpu_count() or 4, len(order))
+    pl, nv = subplan(order[:n])
+    t = run(pl)
+    per_vis = t / max(nv, 1)
+    target_vis = budget_s / max(per_vis, 1e-12)
+    cum = np.cumsum([(full.subgrids[o][2] - full.subgrids[o][1]) * (full.subgrids[o][4] - full.subgrids[o][3])
+                     for o in order])
+    n = int(min(len(order), max(1, np.searchsorted(cum, target_vis) + 1)))
+    pl, nv = subplan(order[:n])
+    return pl, nv, n, run
+
+
+def cpu_baseline(obs, aterms_np, vis_np, grid_np, budget_s):
+    pl, nv, n, run = _oracle_sample(obs, aterms_np, vis_np, grid_np, budget_s)
+    t = run(pl)
+    cores = os.cpu_count()
+    return {"value": 2.0 * nv / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} seeded-random subgrids ({nv} visibilities) of the workload, grid + degrid, "
+                      f"FP64 C oracle with OpenMP over subgrids, {t:.1f} s",
+            "seconds": t}
+
+
+# --------------------------------------------------------------------------- native arm
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2502_17789_gb300 import build as libbuild
+    from paper_2502_17789_gb300 import idg
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    libbuild.build()
+    obs, A_d, vis_d, desc = make_workload(args.workload, dev, args.stations, args.timesteps)
+    stream = torch.cuda.current_stream(dev)
+    plan = idg.Plan(obs, stream=stream.cuda_stream)
+    st = plan.stats()
+    N = obs.grid_size
+    G_model = torch.zeros((4, N, N), dtype=torch.complex128, device=dev)
+    plan.grid(vis_d, A_d, G_model)                     # the model grid the degrid leg predicts from
+    G_out = torch.empty_like(G_model)
+    vis_pred = torch.empty_like(vis_d)
+
+    def step():
+        G_out.zero_()
+        plan.grid(vis_d, A_d, G_out)
+        plan.degrid(G_model, A_d, vis_pred)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    plan.profile(True)
+    plan.profile_read()
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    prof = plan.profile_read()
+    plan.profile(False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_vis = 2.0 * obs.n_vis * args.steps * world
+    value = total_vis / (ms * 1e-3)
+
+    # roofline of the dominant kernel (gridder or degridder), live from the timed region
+    kern = max(("gridder", "degridder"), key=lambda k: prof[k][0])
+    k_ms, k_launches = prof[kern]
+    vispx = float(st.vis_pixels) * args.steps
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", SM_MAX_MHZ_FALLBACK))
+    peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved_vispx = vispx / (k_ms * 1e-3)
+    achieved = achieved_vispx * FLOP_PER_VISPX / 1e12
+    traffic = None
+    roofline = {"bound": "alu", "kernel": kern, "achieved": round(achieved, 3), "peak": round(peak_tflops, 3),
+                "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": traffic,
+                "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
+                "achieved_vispx_per_s": achieved_vispx, "flop_per_vispx": FLOP_PER_VISPX,
+                "launches": k_launches, "avg_launch_ms": k_ms / max(k_launches, 1)}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = round(achieved / (peak_tflops * clocks["sm_mhz"] / sm_max), 4)
+    kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
+    gpu_launches = int(sum(v[1] for v in prof.values()))
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if args.no_e2e:
+        args.e2e_steps = 0
+    need_host = args.e2e_steps > 0 or (rank == 0 and not args.no_cpu_baseline)
+    vis_h = vis_d.cpu().pin_memory() if need_host else None
+    gmodel_h = G_model.cpu().pin_memory() if need_host else None
+    if args.e2e_steps > 0:
+        gout_h = torch.empty(G_model.shape, dtype=G_model.dtype, pin_memory=True)
+        vpred_h = torch.empty(vis_d.shape, dtype=vis_d.dtype, pin_memory=True)
+        vis_in = torch.empty_like(vis_d)
+        gmodel_in = torch.empty_like(G_model)
+
+    def e2e_step():
+        vis_in.copy_(vis_h, non_blocking=True)
+        gmodel_in.copy_(gmodel_h, non_blocking=True)
+        G_out.zero_()
+        plan.grid(vis_in, A_d, G_out)
+        plan.degrid(gmodel_in, A_d, vis_pred)
+        gout_h.copy_(G_out, non_blocking=True)
+        vpred_h.copy_(vis_pred, non_blocking=True)
+
+    if args.e2e_steps > 0:
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": 2.0 * obs.n_vis * args.e2e_steps * world / (e2e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(vis_h.numel() * 8 + gmodel_h.numel() * 16),
+               "d2h_bytes_per_step": int(gout_h.numel() * 16 + vpred_h.numel() * 8),
+               "ms_per_step": e2e_ms / args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(obs, A_d.cpu().numpy(), vis_h.numpy(), gmodel_h.numpy(), args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded point-source sky through beam x phase-screen A-terms, noise)",
+        "config": {"workload": desc, "n_vis": obs.n_vis, "form": "plain (one observation per call)",
+                   "l2": "inputs larger than L2 (350 MB visibilities, 1 GiB grids); no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "subgrids": st.n_subgrids, "segments": st.n_segments, "batches": st.n_batches,
+                   "vis_pixels_per_direction": st.vis_pixels},
+        "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches,
+        "kernels": kernels,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return
+    from paper_2502_17789_gb300 import synth
+    import oracle
+
+    oracle.build()
+    obs = synth.config(args.workload, seed=0)
+    rng = np.random.default_rng(0)
+    model = synth.beam_screen_model(rng, rms_rad=2.0)
+    aterms = synth.aterms_beam_screen(obs, model) if args.workload != 1 else \
+        synth.aterms_identity(obs.n_intervals, obs.n_stations, obs.aterm_nodes)
+    vis = synth.random_visibilities(rng, obs)
+    N = obs.grid_size
+    grid = np.zeros((4, N, N), np.complex128)
+    grid[:, N // 2 - 64:N // 2 + 64, N // 2 - 64:N // 2 + 64] = 1.0
+    budget = max(2.0, 150.0 / max(args.steps + args.warmup, 1))
+    pl, nv, n, run = _oracle_sample(obs, aterms, vis, grid, budget)
+    for _ in range(args.warmup):
+        run(pl)
+    t = [run(pl) for _ in range(args.steps)]
+    total = sum(t)
+    value = 2.0 * nv * args.steps / total
+    sample = f"{n} seeded-random subgrids ({nv} visibilities) of the workload per step, grid + degrid"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": obs.name, "n_vis": obs.n_vis},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

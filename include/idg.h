@@ -171,6 +171,20 @@ idg_status idg_plan_segments(const idg_plan* plan, int32_t* out, int64_t cap, in
 idg_status idg_subgrid_images(idg_plan* plan, const void* vis_c64, const void* aterms_c64, int32_t stage,
                               void* out_c64);
 
+/*
+ * idg_profile_enable -- time every later kernel launch of the plan with CUDA
+ * events recorded on the plan's stream around it (on != 0), or stop (0).
+ */
+idg_status idg_profile_enable(idg_plan* plan, int32_t on);
+
+/*
+ * idg_profile_read -- accumulated device time and launch counts per kernel
+ * since the last read, then reset.  Synchronises the plan's stream.
+ *   ms        host double [4]: gridder, fft+adder, splitter+ifft, degridder
+ *   launches  host int64 [4], same order
+ */
+idg_status idg_profile_read(idg_plan* plan, double* ms, int64_t* launches);
+
 /* Message for the last failure (never NULL; "" when none). */
 const char* idg_last_error(const idg_plan* plan);
 

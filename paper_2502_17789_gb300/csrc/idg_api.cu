@@ -67,6 +67,10 @@ struct idg_plan {
   GridItem* d_gitems = nullptr;
   DegridItem* d_ditems = nullptr;
   float2* d_scratch = nullptr;
+  // profiling: event pairs recorded around launches, per kernel class
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
 };
 
 namespace {
@@ -96,6 +100,41 @@ int upload(idg_plan* p, T** dst, const T* src, size_t n) {
   if (e != cudaSuccess) return int(e);
   p->device_bytes += int64_t(n * sizeof(T));
   return int(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, p->stream));
+}
+
+enum KernelClass { kGridder = 0, kFftAdder = 1, kSplitter = 2, kDegridder = 3 };
+
+cudaEvent_t take_event(idg_plan* p) {
+  if (!p->ev_pool.empty()) {
+    cudaEvent_t e = p->ev_pool.back();
+    p->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Launch `fn` (returning a cudaError_t as int), bracketed by events when profiling.
+template <typename F>
+int timed(idg_plan* p, int cls, F&& fn) {
+  if (!p->profiling) return fn();
+  cudaEvent_t a = take_event(p), b = take_event(p);
+  if (a) cudaEventRecord(a, p->stream);
+  const int e = fn();
+  if (b) cudaEventRecord(b, p->stream);
+  if (a && b) p->ev_pending.push_back({cls, {a, b}});
+  return e;
+}
+
+void release_events(idg_plan* p) {
+  for (auto& pe : p->ev_pending) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  p->ev_pending.clear();
+  p->ev_pool.clear();
 }
 
 void free_device(idg_plan* p) {
@@ -309,6 +348,7 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
 idg_status idg_plan_destroy(idg_plan* plan) {
   if (!plan) return IDG_OK;
   if (!plan->host_only) cudaStreamSynchronize(plan->stream);
+  release_events(plan);
   free_device(plan);
   delete plan;
   return IDG_OK;
@@ -345,10 +385,10 @@ idg_status idg_grid(idg_plan* plan, const void* vis_c64, const void* aterms_c64,
     ga.blk = plan->d_blk;
     ga.scratch = plan->d_scratch;
     ga.g = kgeom(plan);
-    int e = launch_gridder(L, ga, b.gi_count, plan->stream);
+    int e = timed(plan, kGridder, [&] { return launch_gridder(L, ga, b.gi_count, plan->stream); });
     if (e) return cuda_err(plan, e, "gridder launch");
     FftArgs fa{plan->d_sg + b.sg_offset, plan->d_scratch, static_cast<double2*>(grid_c128), plan->d_twiddle, plan->N};
-    e = launch_fft_adder(L, fa, b.sg_count, 0, plan->stream);
+    e = timed(plan, kFftAdder, [&] { return launch_fft_adder(L, fa, b.sg_count, 0, plan->stream); });
     if (e) return cuda_err(plan, e, "fft/adder launch");
   }
   return IDG_OK;
@@ -370,7 +410,7 @@ idg_status idg_degrid(idg_plan* plan, const void* grid_c128, const void* aterms_
   for (const Batch& b : plan->batches) {
     FftArgs fa{plan->d_sg + b.sg_offset, plan->d_scratch, const_cast<double2*>(static_cast<const double2*>(grid_c128)),
                plan->d_twiddle, plan->N};
-    int e = launch_splitter_ifft(L, fa, b.sg_count, plan->stream);
+    int e = timed(plan, kSplitter, [&] { return launch_splitter_ifft(L, fa, b.sg_count, plan->stream); });
     if (e) return cuda_err(plan, e, "splitter/ifft launch");
     DegridArgs da{};
     da.vis = static_cast<float4*>(vis_c64);
@@ -384,7 +424,7 @@ idg_status idg_degrid(idg_plan* plan, const void* grid_c128, const void* aterms_
     da.blk = plan->d_blk;
     da.scratch = plan->d_scratch;
     da.g = kgeom(plan);
-    e = launch_degridder(L, da, b.di_count, plan->stream);
+    e = timed(plan, kDegridder, [&] { return launch_degridder(L, da, b.di_count, plan->stream); });
     if (e) return cuda_err(plan, e, "degridder launch");
   }
   return IDG_OK;
@@ -427,6 +467,32 @@ idg_status idg_subgrid_images(idg_plan* plan, const void* vis_c64, const void* a
                                b.sg_count, plan->stream);
     if (e) return cuda_err(plan, e, "export launch");
   }
+  return IDG_OK;
+}
+
+idg_status idg_profile_enable(idg_plan* plan, int32_t on) {
+  if (!plan) return set_err(nullptr, IDG_ERR_INVALID_ARG, "plan is NULL");
+  plan->profiling = on != 0;
+  return IDG_OK;
+}
+
+idg_status idg_profile_read(idg_plan* plan, double* ms, int64_t* launches) {
+  if (!plan || !ms || !launches) return set_err(plan, IDG_ERR_INVALID_ARG, "NULL argument");
+  for (int c = 0; c < 4; ++c) {
+    ms[c] = 0.0;
+    launches[c] = 0;
+  }
+  if (plan->host_only) return IDG_OK;
+  const int e = int(cudaStreamSynchronize(plan->stream));
+  if (e) return cuda_err(plan, e, "idg_profile_read");
+  for (auto& pe : plan->ev_pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pe.second.first, pe.second.second) == cudaSuccess) ms[pe.first] += double(t);
+    launches[pe.first] += 1;
+    plan->ev_pool.push_back(pe.second.first);
+    plan->ev_pool.push_back(pe.second.second);
+  }
+  plan->ev_pending.clear();
   return IDG_OK;
 }
 
