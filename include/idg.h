@@ -172,6 +172,14 @@ idg_status idg_subgrid_images(idg_plan* plan, const void* vis_c64, const void* a
                               void* out_c64);
 
 /*
+ * idg_synchronize -- wait for the plan's stream and report device-side
+ * failures of earlier calls: IDG_ERR_TIMEOUT if a kernel gave up a bounded
+ * wait (the call's results are then incomplete), IDG_ERR_CUDA on an
+ * asynchronous CUDA error.  Clears the recorded status.
+ */
+idg_status idg_synchronize(idg_plan* plan);
+
+/*
  * idg_profile_enable -- time every later kernel launch of the plan with CUDA
  * events recorded on the plan's stream around it (on != 0), or stop (0).
  */
@@ -180,8 +188,9 @@ idg_status idg_profile_enable(idg_plan* plan, int32_t on);
 /*
  * idg_profile_read -- accumulated device time and launch counts per kernel
  * since the last read, then reset.  Synchronises the plan's stream.
- *   ms        host double [4]: gridder, fft+adder, splitter+ifft, degridder
- *   launches  host int64 [4], same order
+ *   ms        host double [5]: gridder, fft+adder, splitter+ifft, degridder,
+ *             visibility staging
+ *   launches  host int64 [5], same order
  */
 idg_status idg_profile_read(idg_plan* plan, double* ms, int64_t* launches);
 

@@ -6,40 +6,48 @@
 // footprint (the splitter applied (-1)^(x+y)).
 //
 // Work item = up to 256 visibilities of one segment (one A-term).  Each
-// thread owns one visibility; the block walks the subgrid in chunks of
-// 32 pixel blocks (8 consecutive pixels of a row each).  Per chunk all
-// threads first compute Z for 256 pixels into shared memory (the A-term
-// prologue), then every warp sums its visibilities over its share of the
-// chunk.  When a segment has fewer than 256 visibilities the 8 warps split
-// the pixel blocks between them (8 / vis-warps ways) and the partial sums
-// are combined through shared memory at the end.  Phases use the same FP64
-// offset / exact anchor reduction / FP32 increment scheme as the gridder.
+// thread owns one visibility; the block walks the subgrid in chunks of 64
+// pixel blocks (8 consecutive pixels of a row each, 512 pixels).  Z of the
+// next chunk is built while the current chunk is summed: its Y values are
+// loaded into registers before the phasor sum and turned into Z (A-term
+// prologue) after it, into the other half of a double buffer, so one
+// barrier per chunk separates producer and consumer.  When a segment has
+// fewer than 256 visibilities the warps split the pixel blocks between
+// them and combine partial sums through shared memory at the end.  Phases
+// use the same FP64 offset / exact anchor reduction / FP32 increment
+// scheme as the gridder.
 #include "kernels_common.cuh"
 
 namespace idg {
 
 constexpr int kDegridThreads = 256;
-constexpr int kChunkBlocks = 32;  // pixel blocks (of 8) per chunk = 256 pixels
+constexpr int kChunkBlocks = 64;  // pixel blocks (of 8) per chunk = 512 pixels
+
+template <int L>
+struct DegridSmem {
+  float4 z[2][kChunkBlocks][4][4];  // [buf][block][pixel pair][pol] {Zr_a, Zr_b, Zi_a, Zi_b}
+  float2 n[2][kChunkBlocks][4][4];  // {-Zr_a, -Zr_b}
+  float4 g[2][kChunkBlocks][3];     // block geometry
+  float red[8][kDegridThreads];     // split partial sums
+};
 
 template <int L>
 __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const DegridArgs a) {
   constexpr int TPR = L / 8;
   constexpr int NBLK = L * L / 8;
+  constexpr int NCH = NBLK / kChunkBlocks;
   static_assert(NBLK % kChunkBlocks == 0, "chunking");
-  extern __shared__ float4 smem[];
-  float4* s_Z = smem;                                                  // [CB][4 pairs][4 pols] {Zr_a, Zr_b, Zi_a, Zi_b}
-  float2* s_N = reinterpret_cast<float2*>(s_Z + kChunkBlocks * 16);    // [CB][4][4] {-Zr_a, -Zr_b}
-  float4* s_G = reinterpret_cast<float4*>(s_N + kChunkBlocks * 16);    // [CB][3] block geometry
-  float* s_red = reinterpret_cast<float*>(s_G + kChunkBlocks * 3);     // [8][256]
-  float2* s_A = reinterpret_cast<float2*>(s_red + 8 * kDegridThreads); // [2][nodes*nodes*4]
+  extern __shared__ float4 smem_raw[];
+  DegridSmem<L>& S = *reinterpret_cast<DegridSmem<L>*>(smem_raw);
+  float2* s_A = reinterpret_cast<float2*>(&S + 1);  // [2][nodes*nodes*4]
 
   const DegridItem item = a.items[blockIdx.x];
   const SubgridDesc sd = a.sg[item.sg];
   const SegmentDesc seg = a.seg[item.segment];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nv = item.k_end - item.k_begin;
-  const int wv = (nv + 31) >> 5;            // warps of visibilities, 1..8
-  const int nsplit = 8 / wv;                // pixel splits, >= 1
+  const int wv = (nv + 31) >> 5;  // warps of visibilities, 1..8
+  const int nsplit = 8 / wv;      // pixel splits, >= 1
   const int vgroup = warp % wv, split = warp / wv;
   const bool active = split < nsplit;
   const int kloc = vgroup * 32 + lane;
@@ -47,7 +55,6 @@ __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const Degr
   const int nodes = a.g.nodes;
   const int nA = nodes * nodes * 4;
 
-  // A-terms of this segment
   {
     const float2* Ap = a.aterms + (size_t(seg.interval) * a.g.n_st + sd.p) * nA;
     const float2* Aq = a.aterms + (size_t(seg.interval) * a.g.n_st + sd.q) * nA;
@@ -93,45 +100,80 @@ __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const Degr
   }
   const float2* Y = a.scratch + size_t(item.sg) * 4 * L * L;
 
-  for (int chunk = 0; chunk < NBLK / kChunkBlocks; ++chunk) {
-    __syncthreads();  // previous chunk consumed (and s_A loaded on the first pass)
-    // ---- prologue: Z for 256 pixels
-    {
-      const int bl_loc = tid >> 3, pos = tid & 7;
-      const int bidx = chunk * kChunkBlocks + bl_loc;
-      const int j = bidx / TPR, i = (bidx % TPR) * 8 + pos;
+  // prologue geometry: each thread builds one pixel pair (2 consecutive pixels) per chunk
+  const int pb = tid >> 2;          // block within the chunk, 0..63
+  const int pq = tid & 3;           // pixel pair within the block
+  float2 ya[4], yb[4];              // Y of the pair, prefetched
+
+  auto load_y = [&](int chunk) {
+    const int bidx = chunk * kChunkBlocks + pb;
+    const int j = bidx / TPR, i = (bidx % TPR) * 8 + 2 * pq;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const float4 v = *reinterpret_cast<const float4*>(Y + (size_t(p) * L + j) * L + i);
+      ya[p] = make_float2(v.x, v.y);
+      yb[p] = make_float2(v.z, v.w);
+    }
+  };
+  auto build_z = [&](int chunk, int buf) {
+    const int bidx = chunk * kChunkBlocks + pb;
+    const int j = bidx / TPR, i = (bidx % TPR) * 8 + 2 * pq;
+    const NodeWeight wy = node_weight(j, nodes, L);
+    const float tj = a.taper[j];
+    float4 zo[4];
+    float2 no[4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int ii = i + h;
       Jones Yp;
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
-        const float2 y = Y[(size_t(p) * L + j) * L + i];
+        const float2 y = h ? yb[p] : ya[p];
         Yp.m[p] = {y.x, y.y};
       }
-      const NodeWeight wx = node_weight(i, nodes, L), wy = node_weight(j, nodes, L);
+      const NodeWeight wx = node_weight(ii, nodes, L);
       const Jones Apj = interp_jones(s_A, nodes, wx, wy);
       const Jones Aqj = interp_jones(s_A + nA, nodes, wx, wy);
       const Jones Z = jmul_bh(jmul(Apj, Yp), Aqj);
-      const float wgt = a.taper[i] * a.taper[j] * (((i + j) & 1) ? -1.f : 1.f);
-      const int q = pos >> 1, half = pos & 1;
-      float* zf = reinterpret_cast<float*>(s_Z + (bl_loc * 4 + q) * 4);
-      float* nf = reinterpret_cast<float*>(s_N + (bl_loc * 4 + q) * 4);
+      const float wgt = a.taper[ii] * tj * (((ii + j) & 1) ? -1.f : 1.f);
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
         const float zr = wgt * Z.m[p].re, zi = wgt * Z.m[p].im;
-        zf[p * 4 + half] = zr;
-        zf[p * 4 + 2 + half] = zi;
-        nf[p * 2 + half] = -zr;
-      }
-      if (tid < kChunkBlocks * 3) {
-        const int b = tid / 3, c = tid % 3;
-        s_G[tid] = a.blk[size_t(chunk * kChunkBlocks + b) * 3 + c];
+        if (h == 0) {
+          zo[p].x = zr;
+          zo[p].z = zi;
+          no[p].x = -zr;
+        } else {
+          zo[p].y = zr;
+          zo[p].w = zi;
+          no[p].y = -zr;
+        }
       }
     }
-    __syncthreads();
-    // ---- sum over this warp's pixel blocks
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      S.z[buf][pb][pq][p] = zo[p];
+      S.n[buf][pb][pq][p] = no[p];
+    }
+    if (tid < kChunkBlocks * 3) {
+      const int b = tid / 3, c = tid % 3;
+      S.g[buf][b][c] = a.blk[size_t(chunk * kChunkBlocks + b) * 3 + c];
+    }
+  };
+
+  load_y(0);
+  __syncthreads();  // s_A visible
+  build_z(0, 0);
+  __syncthreads();
+
+  for (int chunk = 0; chunk < NCH; ++chunk) {
+    const int buf = chunk & 1;
+    const bool more = chunk + 1 < NCH;
+    if (more) load_y(chunk + 1);
     if (active) {
 #pragma unroll 1
       for (int b = split; b < kChunkBlocks; b += nsplit) {
-        const float4 g0 = s_G[b * 3], g1 = s_G[b * 3 + 1], g2 = s_G[b * 3 + 2];
+        const float4 g0 = S.g[buf][b][0], g1 = S.g[buf][b][1], g2 = S.g[buf][b][2];
         const float n0 = g0.x, di0 = g2.y, dj0 = g2.z;
         const float2 DN[4] = {{g0.y, g0.z}, {g0.w, g1.x}, {g1.y, g1.z}, {g1.w, g2.x}};
         const float sh = fmaf(ah, di0, bh * dj0);
@@ -146,12 +188,10 @@ __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const Degr
           float2 Cs, Sn;
           __sincosf(ph.x, &Sn.x, &Cs.x);
           __sincosf(ph.y, &Sn.y, &Cs.y);
-          const float4* zq = s_Z + (b * 4 + q) * 4;
-          const float2* nq = s_N + (b * 4 + q) * 4;
 #pragma unroll
           for (int p = 0; p < 4; ++p) {
-            const float4 z = zq[p];
-            const float2 ZR = make_float2(z.x, z.y), ZI = make_float2(z.z, z.w), NZR = nq[p];
+            const float4 z = S.z[buf][b][q][p];
+            const float2 ZR = make_float2(z.x, z.y), ZI = make_float2(z.z, z.w), NZR = S.n[buf][b][q][p];
             RE[p] = ffma2(ZR, Cs, RE[p]);
             RE[p] = ffma2(ZI, Sn, RE[p]);
             IM[p] = ffma2(ZI, Cs, IM[p]);
@@ -160,13 +200,15 @@ __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const Degr
         }
       }
     }
+    if (more) build_z(chunk + 1, buf ^ 1);
+    __syncthreads();
   }
 
   // ---- combine pixel splits and write the visibility
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
-    s_red[(2 * p) * kDegridThreads + tid] = RE[p].x + RE[p].y;
-    s_red[(2 * p + 1) * kDegridThreads + tid] = IM[p].x + IM[p].y;
+    S.red[2 * p][tid] = RE[p].x + RE[p].y;
+    S.red[2 * p + 1][tid] = IM[p].x + IM[p].y;
   }
   __syncthreads();
   if (valid && split == 0) {
@@ -174,7 +216,7 @@ __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const Degr
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       float s = 0.f;
-      for (int sp = 0; sp < nsplit; ++sp) s += s_red[c * kDegridThreads + (sp * wv + vgroup) * 32 + lane];
+      for (int sp = 0; sp < nsplit; ++sp) s += S.red[c][(sp * wv + vgroup) * 32 + lane];
       v[c] = s;
     }
     a.vis[2 * vidx] = make_float4(v[0], v[1], v[2], v[3]);
@@ -184,8 +226,7 @@ __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const Degr
 
 template <int L>
 static size_t degridder_smem(int nodes) {
-  return sizeof(float4) * kChunkBlocks * 16 + sizeof(float2) * kChunkBlocks * 16 + sizeof(float4) * kChunkBlocks * 3 +
-         sizeof(float) * 8 * kDegridThreads + sizeof(float2) * 2 * nodes * nodes * 4;
+  return sizeof(DegridSmem<L>) + sizeof(float2) * 2 * nodes * nodes * 4;
 }
 
 template <int L>

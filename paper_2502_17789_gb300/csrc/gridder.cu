@@ -1,5 +1,5 @@
-// Gridder kernel: Section 2.5 imaging step 2a (Eq. 10) plus the deferred
-// A-term of Section 3.3.
+// Gridder: Section 2.5 imaging step 2a (Eq. 10) plus the deferred A-term of
+// Section 3.3.
 //
 // For subgrid s with corner (x0, y0) and pixel (i, j):
 //   X(i,j) = (-1)^(i+j) T_i T_j sum_g A_p,g(i,j)^H [ sum_{k in g} V_k e^{2 pi i phi_k(i,j)} ] A_q,g(i,j)
@@ -7,36 +7,104 @@
 //   a_k    = (xi_k - x0 - L/2) / L = (u_k - u0) FOV / L,  b_k likewise
 // The (-1)^(i+j) factor lets the subgrid FFT run uncentred.
 //
-// Work item = (subgrid, tile of ROWS rows).  Each thread owns 8 consecutive
-// pixels of one row.  Visibilities are staged in shared memory in chunks;
-// staging computes a_k, b_k, w_k in FP64 (the per-visibility subgrid offset)
-// and splits a_k, b_k into a 16-fractional-bit head and a small tail, so
-// that the anchor phase a_k di0 + b_k dj0 of a thread is range-reduced
-// exactly in FP32.  The 8 pixel phases are anchor + FP32 increments, the
-// phasors come from __sincosf, and the 4-polarisation complex
-// multiply-accumulate runs as packed f32x2 FMAs over pixel pairs.
+// Two kernels per batch of subgrids:
+//  * stage_records_kernel writes every member visibility of the batch, in
+//    subgrid member order, as a 128-byte record: the 4 complex values as the
+//    operand pairs of the packed multiply-accumulate, and the phase slopes
+//    computed in FP64 from uvw and the subgrid offset.  a_k and b_k are split
+//    into a head with 16 fractional bits and a tail, so a thread's anchor
+//    phase a_k di0 + b_k dj0 is range-reduced exactly in FP32.
+//  * gridder_kernel: work item = (subgrid, tile of ROWS rows), each thread
+//    owns 8 consecutive pixels of one row.  Records stream into a double
+//    buffer in shared memory by 1-D bulk copies (cp.async.bulk, completion on
+//    an mbarrier), one chunk ahead of the phasor sum.  The 8 pixel phases are
+//    the reduced anchor plus FP32 increments, the phasors come from
+//    __sincosf, and the 4-polarisation complex multiply-accumulate runs as
+//    packed f32x2 FMAs over pixel pairs.  After each A-term segment the
+//    thread applies A_p^H X A_q, the taper and the centring sign and adds
+//    the result into its private columns of a shared-memory image sum.
 #include "kernels_common.cuh"
 
 namespace idg {
 
+// ------------------------------------------------------------------ staging
+
+__global__ void __launch_bounds__(256) stage_records_kernel(const StageArgs a, int L) {
+  const SubgridDesc sd = a.sg[blockIdx.x];
+  const int nc = sd.c1 - sd.c0;
+  const double inv_l = 1.0 / double(L);
+  const double off_x = double(sd.x0 + L / 2 - a.g.N / 2);
+  const double off_y = double(sd.y0 + L / 2 - a.g.N / 2);
+  for (int k = threadIdx.x; k < sd.n_vis; k += blockDim.x) {
+    const int t = sd.t0 + k / nc, ch = sd.c0 + k % nc;
+    const size_t vidx = (size_t(sd.b) * a.g.n_t + t) * a.g.n_ch + ch;
+    const float4 v0 = a.vis[2 * vidx], v1 = a.vis[2 * vidx + 1];
+    const double* r = a.uvw + (size_t(sd.b) * a.g.n_t + t) * 3;
+    const double fs = a.fscale[ch];
+    const double dx = (r[0] * fs) * a.g.fov - off_x;
+    const double dy = (r[1] * fs) * a.g.fov - off_y;
+    const double w = r[2] * fs;
+    const double aa = dx * inv_l, bb = dy * inv_l;
+    const double ah = rint(aa * 65536.0) * (1.0 / 65536.0);
+    const double bh = rint(bb * 65536.0) * (1.0 / 65536.0);
+    float4* rec = a.records + (size_t(sd.rec_offset) + k) * kRecordFloat4;
+    rec[0] = make_float4(v0.x, v0.x, v0.y, v0.y);
+    rec[1] = make_float4(-v0.y, -v0.y, v0.z, v0.z);
+    rec[2] = make_float4(v0.w, v0.w, -v0.w, -v0.w);
+    rec[3] = make_float4(v1.x, v1.x, v1.y, v1.y);
+    rec[4] = make_float4(-v1.y, -v1.y, v1.z, v1.z);
+    rec[5] = make_float4(v1.w, v1.w, -v1.w, -v1.w);
+    rec[6] = make_float4(float(ah), float(bh), float(aa - ah), float(bb - bh));
+    rec[7] = make_float4(float(w), float(kTwoPi * aa), float(kTwoPi * w), 0.f);
+  }
+}
+
+int launch_stage_records(int L, const StageArgs& a, int n_subgrids, void* stream) {
+  if (n_subgrids <= 0) return 0;
+  stage_records_kernel<<<n_subgrids, 256, 0, cudaStream_t(stream)>>>(a, L);
+  return int(cudaGetLastError());
+}
+
+// ------------------------------------------------------------------ gridder
+
 template <int L, int ROWS>
 struct GridCfg {
-  static constexpr int TPR = L / 8;         // threads per row
-  static constexpr int NT = ROWS * TPR;     // threads per block
-  static constexpr int VC = 64;             // visibilities per staged chunk
-  static constexpr int REC = 9;             // float4 per staged visibility
+  static constexpr int TPR = L / 8;      // threads per row
+  static constexpr int NT = ROWS * TPR;  // threads per block
+  static constexpr int VC = 64;          // records per chunk
   static constexpr int MINB = NT <= 128 ? 3 : (NT <= 192 ? 2 : 1);
-  static_assert(L % 8 == 0 && L % ROWS == 0 && NT >= VC, "gridder shape");
+  static_assert(L % 8 == 0 && L % ROWS == 0, "gridder shape");
 };
+
+// Position of chunk `c` of a subgrid: chunks never straddle segments.
+struct ChunkCursor {
+  int seg;    // segment index within the subgrid
+  int k;      // first member of the chunk
+  int end;    // end of the segment
+};
+
+template <int VC>
+__device__ __forceinline__ void cursor_advance(ChunkCursor& cur, const SegmentDesc* seg, int seg_begin, int seg_count) {
+  cur.k += VC;
+  if (cur.k >= cur.end) {
+    ++cur.seg;
+    if (cur.seg < seg_count) {
+      const SegmentDesc s = seg[seg_begin + cur.seg];
+      cur.k = s.k_begin;
+      cur.end = s.k_end;
+    }
+  }
+}
 
 template <int L, int ROWS>
 __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
     gridder_kernel(const GridArgs a) {
   using C = GridCfg<L, ROWS>;
+  constexpr uint32_t kChunkBytes = C::VC * kRecordFloat4 * 16;
   extern __shared__ float4 smem[];
-  float4* s_vis = smem;                                      // [VC][REC]
-  float* s_acc = reinterpret_cast<float*>(s_vis + C::VC * C::REC);  // [64][NT]
-  float2* s_A = reinterpret_cast<float2*>(s_acc + 64 * C::NT);      // [2][nodes*nodes*4]
+  float4* s_rec = smem;                                              // [2][VC][8]
+  float* s_acc = reinterpret_cast<float*>(s_rec + 2 * C::VC * kRecordFloat4);  // [64][NT]
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_acc + 64 * C::NT);          // [2]
 
   const GridItem item = a.items[blockIdx.x];
   const SubgridDesc sd = a.sg[item.sg];
@@ -47,6 +115,36 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
   const int nodes = a.g.nodes;
   const int nA = nodes * nodes * 4;
 
+  // number of chunks
+  int n_chunks = 0;
+  for (int g = 0; g < sd.seg_count; ++g) {
+    const SegmentDesc s = a.seg[sd.seg_begin + g];
+    n_chunks += (s.k_end - s.k_begin + C::VC - 1) / C::VC;
+  }
+  const float4* rec_base = a.records + size_t(sd.rec_offset) * kRecordFloat4;
+
+  // producer (thread 0): issue the copy of the chunk at `pc` into buffer `buf`
+  ChunkCursor pc{0, 0, 0};
+  if (tid == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_mbar_init();
+    const SegmentDesc s0 = a.seg[sd.seg_begin];
+    pc = {0, s0.k_begin, s0.k_end};
+  }
+  __syncthreads();
+  auto issue = [&](int buf) {
+    const int nv = imin(C::VC, pc.end - pc.k);
+    const uint32_t bytes = uint32_t(nv) * kRecordFloat4 * 16;
+    mbar_arrive_expect_tx(&s_bar[buf], bytes);
+    bulk_copy_g2s(s_rec + buf * C::VC * kRecordFloat4, rec_base + size_t(pc.k) * kRecordFloat4, bytes, &s_bar[buf]);
+    cursor_advance<C::VC>(pc, a.seg, sd.seg_begin, sd.seg_count);
+  };
+  if (tid == 0) {
+    issue(0);
+    if (n_chunks > 1) issue(1);
+  }
+
   // pixel geometry of this thread's block: anchor at i0 + 4
   const float4* bg = a.blk + (size_t(j) * C::TPR + ib) * 3;
   const float4 g0 = bg[0], g1 = bg[1], g2 = bg[2];
@@ -54,68 +152,42 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
   const float2 DN[4] = {{g0.y, g0.z}, {g0.w, g1.x}, {g1.y, g1.z}, {g1.w, g2.x}};
   const float di0 = g2.y, dj0 = g2.z;
   const float2 DI[4] = {{-4.f, -3.f}, {-2.f, -1.f}, {0.f, 1.f}, {2.f, 3.f}};
+  (void)kChunkBytes;
 
-  const int nc = sd.c1 - sd.c0;
-  const double inv_l = 1.0 / double(L);
-  const double off_x = double(sd.x0 + L / 2 - a.g.N / 2);
-  const double off_y = double(sd.y0 + L / 2 - a.g.N / 2);
-
-  for (int gi = 0; gi < sd.seg_count; ++gi) {
-    const SegmentDesc seg = a.seg[sd.seg_begin + gi];
-    float2 RE[4][4], IM[4][4];
+  float2 RE[4][4], IM[4][4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+  for (int p = 0; p < 4; ++p)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        RE[p][q] = make_float2(0.f, 0.f);
-        IM[p][q] = make_float2(0.f, 0.f);
-      }
+    for (int q = 0; q < 4; ++q) {
+      RE[p][q] = make_float2(0.f, 0.f);
+      IM[p][q] = make_float2(0.f, 0.f);
+    }
 
-    for (int kc = seg.k_begin; kc < seg.k_end; kc += C::VC) {
-      const int nv = imin(C::VC, seg.k_end - kc);
-      if (tid < nv) {
-        // ---- stage one visibility (FP64 offset, FP32 record)
-        const int k = kc + tid;
-        const int t = sd.t0 + k / nc, ch = sd.c0 + k % nc;
-        const size_t vidx = (size_t(sd.b) * a.g.n_t + t) * a.g.n_ch + ch;
-        const float4 v0 = a.vis[2 * vidx], v1 = a.vis[2 * vidx + 1];
-        const double* r = a.uvw + (size_t(sd.b) * a.g.n_t + t) * 3;
-        const double fs = a.fscale[ch];
-        const double dx = (r[0] * fs) * a.g.fov - off_x;
-        const double dy = (r[1] * fs) * a.g.fov - off_y;
-        const double w = r[2] * fs;
-        const double aa = dx * inv_l, bb = dy * inv_l;
-        const double ah = rint(aa * 65536.0) * (1.0 / 65536.0);
-        const double bh = rint(bb * 65536.0) * (1.0 / 65536.0);
-        float4* rec = s_vis + tid * C::REC;
-        rec[0] = make_float4(v0.x, v0.x, v0.y, v0.y);
-        rec[1] = make_float4(-v0.y, -v0.y, v0.z, v0.z);
-        rec[2] = make_float4(v0.w, v0.w, -v0.w, -v0.w);
-        rec[3] = make_float4(v1.x, v1.x, v1.y, v1.y);
-        rec[4] = make_float4(-v1.y, -v1.y, v1.z, v1.z);
-        rec[5] = make_float4(v1.w, v1.w, -v1.w, -v1.w);
-        rec[6] = make_float4(float(ah), float(bh), float(aa - ah), float(bb - bh));
-        rec[7] = make_float4(float(w), 0.f, 0.f, 0.f);
-        const float ar = float(kTwoPi * aa), cr = float(kTwoPi * w);
-        rec[8] = make_float4(ar, ar, cr, cr);
-      }
-      __syncthreads();
-
-      // ---- phasor sum over the chunk
+  ChunkCursor cc;
+  {
+    const SegmentDesc s0 = a.seg[sd.seg_begin];
+    cc = {0, s0.k_begin, s0.k_end};
+  }
+  bool first_seg = true;
+  for (int c = 0; c < n_chunks; ++c) {
+    const int buf = c & 1;
+    const bool ok = mbar_wait_bounded(&s_bar[buf], uint32_t((c >> 1) & 1));
+    const int nv = imin(C::VC, cc.end - cc.k);
+    if (ok) {
+      const float4* rb = s_rec + buf * C::VC * kRecordFloat4;
 #pragma unroll 1
       for (int v = 0; v < nv; ++v) {
-        const float4* rec = s_vis + v * C::REC;
+        const float4* rec = rb + v * kRecordFloat4;
         const float4 cf = rec[6];
-        const float cw = rec[7].x;
-        const float4 cr = rec[8];
+        const float4 cw = rec[7];
         // anchor phase in turns: head part exact, then two range reductions
         const float sh = fmaf(cf.x, di0, cf.y * dj0);
         const float d1 = __fsub_rn(sh, round_nearest(sh));
-        const float lo = fmaf(cw, n0, fmaf(cf.z, di0, cf.w * dj0));
+        const float lo = fmaf(cw.x, n0, fmaf(cf.z, di0, cf.w * dj0));
         float rr = __fadd_rn(d1, lo);
         rr = __fmul_rn(__fsub_rn(rr, round_nearest(rr)), kTwoPiF);
         const float2 R0 = make_float2(rr, rr);
-        const float2 ARR = make_float2(cr.x, cr.y), CRR = make_float2(cr.z, cr.w);
+        const float2 ARR = make_float2(cw.y, cw.y), CRR = make_float2(cw.z, cw.z);
         float2 Cs[4], Sn[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -137,53 +209,68 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
             IM[p][q] = ffma2(VII[p], Cs[q], IM[p][q]);
           }
       }
-      __syncthreads();
     }
-
-    // ---- epilogue: A_p^H X A_q, taper, centring sign (Section 3.3)
-    {
+    // every thread is done with this buffer: refill it with chunk c + 2
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(a.status, kStatusTimeout);
+        mbar_wait_bounded(&s_bar[buf ^ 1], uint32_t(((c + 1) >> 1) & 1));  // let a copy in flight land
+      }
+      return;
+    }
+    if (tid == 0 && c + 2 < n_chunks) {
+      fence_proxy_async();
+      issue(buf);
+    }
+    const bool seg_done = cc.k + C::VC >= cc.end;
+    if (seg_done) {
+      // ---- epilogue of segment cc.seg: A_p^H X A_q, taper, centring sign (Section 3.3)
+      const SegmentDesc seg = a.seg[sd.seg_begin + cc.seg];
       const float2* Ap = a.aterms + (size_t(seg.interval) * a.g.n_st + sd.p) * nA;
       const float2* Aq = a.aterms + (size_t(seg.interval) * a.g.n_st + sd.q) * nA;
-      for (int e = tid; e < nA; e += C::NT) {
-        s_A[e] = Ap[e];
-        s_A[nA + e] = Aq[e];
-      }
-    }
-    __syncthreads();
-    const NodeWeight wy = node_weight(j, nodes, L);
-    const float tj = a.taper[j];
+      const NodeWeight wy = node_weight(j, nodes, L);
+      const float tj = a.taper[j];
 #pragma unroll
-    for (int px = 0; px < 8; ++px) {
-      const int i = i0 + px;
-      const int q = px >> 1;
-      Jones X;
+      for (int px = 0; px < 8; ++px) {
+        const int i = i0 + px;
+        const int q = px >> 1;
+        const NodeWeight wx = node_weight(i, nodes, L);
+        const Jones Apj = interp_jones_ldg(Ap, nodes, wx, wy);
+        const Jones Aqj = interp_jones_ldg(Aq, nodes, wx, wy);
+        Jones X;
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        X.m[p].re = (px & 1) ? RE[p][q].y : RE[p][q].x;
-        X.m[p].im = (px & 1) ? IM[p][q].y : IM[p][q].x;
-      }
-      const NodeWeight wx = node_weight(i, nodes, L);
-      const Jones Apj = interp_jones(s_A, nodes, wx, wy);
-      const Jones Aqj = interp_jones(s_A + nA, nodes, wx, wy);
-      const Jones E = jmul_ah(Apj, jmul(X, Aqj));
-      const float wgt = a.taper[i] * tj * (((i + j) & 1) ? -1.f : 1.f);
+        for (int p = 0; p < 4; ++p) {
+          X.m[p].re = (px & 1) ? RE[p][q].y : RE[p][q].x;
+          X.m[p].im = (px & 1) ? IM[p][q].y : IM[p][q].x;
+        }
+        const Jones E = jmul_ah(Apj, jmul(X, Aqj));
+        const float wgt = a.taper[i] * tj * (((i + j) & 1) ? -1.f : 1.f);
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        float* acc = s_acc + (px * 8 + 2 * p) * C::NT + tid;
-        if (gi == 0) {
-          acc[0] = wgt * E.m[p].re;
-          acc[C::NT] = wgt * E.m[p].im;
-        } else {
-          acc[0] += wgt * E.m[p].re;
-          acc[C::NT] += wgt * E.m[p].im;
+        for (int p = 0; p < 4; ++p) {
+          float* acc = s_acc + (px * 8 + 2 * p) * C::NT + tid;
+          if (first_seg) {
+            acc[0] = wgt * E.m[p].re;
+            acc[C::NT] = wgt * E.m[p].im;
+          } else {
+            acc[0] += wgt * E.m[p].re;
+            acc[C::NT] += wgt * E.m[p].im;
+          }
         }
       }
+      first_seg = false;
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          RE[p][q] = make_float2(0.f, 0.f);
+          IM[p][q] = make_float2(0.f, 0.f);
+        }
     }
-    __syncthreads();
+    cursor_advance<C::VC>(cc, a.seg, sd.seg_begin, sd.seg_count);
   }
 
   // ---- write the subgrid image rows: [sg][pol][j][i]
-  if (sd.seg_count > 0) {
+  if (n_chunks > 0) {
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
       float4* dst = reinterpret_cast<float4*>(a.scratch + ((size_t(item.sg) * 4 + p) * L + j) * L + i0);
@@ -199,15 +286,15 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
 }
 
 template <int L, int ROWS>
-static size_t gridder_smem(int nodes) {
+static size_t gridder_smem() {
   using C = GridCfg<L, ROWS>;
-  return sizeof(float4) * C::VC * C::REC + sizeof(float) * 64 * C::NT + sizeof(float2) * 2 * nodes * nodes * 4;
+  return sizeof(float4) * 2 * C::VC * kRecordFloat4 + sizeof(float) * 64 * C::NT + 2 * sizeof(uint64_t);
 }
 
 template <int L, int ROWS>
 static int launch_gridder_t(const GridArgs& a, int n_items, void* stream) {
   using C = GridCfg<L, ROWS>;
-  const size_t smem = gridder_smem<L, ROWS>(a.g.nodes);
+  const size_t smem = gridder_smem<L, ROWS>();
   cudaError_t e = cudaFuncSetAttribute(gridder_kernel<L, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return int(e);
   if (n_items <= 0) return 0;

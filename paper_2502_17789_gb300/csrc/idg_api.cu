@@ -67,6 +67,9 @@ struct idg_plan {
   GridItem* d_gitems = nullptr;
   DegridItem* d_ditems = nullptr;
   float2* d_scratch = nullptr;
+  float4* d_records = nullptr;  // staged visibility records of one batch
+  int* d_status = nullptr;      // kernel status word (timeouts)
+  int64_t max_batch_vis = 0;
   // profiling: event pairs recorded around launches, per kernel class
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -102,7 +105,7 @@ int upload(idg_plan* p, T** dst, const T* src, size_t n) {
   return int(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, p->stream));
 }
 
-enum KernelClass { kGridder = 0, kFftAdder = 1, kSplitter = 2, kDegridder = 3 };
+enum KernelClass { kGridder = 0, kFftAdder = 1, kSplitter = 2, kDegridder = 3, kStage = 4 };
 
 cudaEvent_t take_event(idg_plan* p) {
   if (!p->ev_pool.empty()) {
@@ -138,8 +141,8 @@ void release_events(idg_plan* p) {
 }
 
 void free_device(idg_plan* p) {
-  void* ptrs[] = {p->d_uvw, p->d_fscale, p->d_taper, p->d_blk, p->d_twiddle, p->d_sg,
-                  p->d_seg, p->d_gitems, p->d_ditems, p->d_scratch};
+  void* ptrs[] = {p->d_uvw,    p->d_fscale, p->d_taper,   p->d_blk,     p->d_twiddle, p->d_sg,
+                  p->d_seg,    p->d_gitems, p->d_ditems,  p->d_scratch, p->d_records, p->d_status};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   p->d_uvw = nullptr;
@@ -152,6 +155,8 @@ void free_device(idg_plan* p) {
   p->d_gitems = nullptr;
   p->d_ditems = nullptr;
   p->d_scratch = nullptr;
+  p->d_records = nullptr;
+  p->d_status = nullptr;
 }
 
 // Block geometry table, FP64 -> FP32: for each row j and block ib of 8
@@ -277,7 +282,15 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
   for (size_t s0 = 0; s0 < p->exec.size(); s0 += p->batch_cap) {
     const int32_t cnt = int32_t(std::min<size_t>(p->batch_cap, p->exec.size() - s0));
     Batch b{int32_t(s0), cnt, int32_t(gitems.size()), 0, int32_t(ditems.size()), 0};
-    // longest first: order batch subgrids by visibility count
+    // staged records of the batch, in batch order
+    int64_t recs = 0;
+    for (int32_t o = 0; o < cnt; ++o) {
+      p->exec[s0 + o].rec_offset = int32_t(recs);
+      recs += p->exec[s0 + o].n_vis;
+    }
+    p->max_batch_vis = std::max(p->max_batch_vis, recs);
+    // longest first: order batch subgrids by visibility count; the items of
+    // one subgrid stay adjacent so its data is reused from L2
     std::vector<int32_t> order(cnt);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
@@ -285,19 +298,14 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     });
     for (int32_t o : order)
       for (int t = 0; t < tiles; ++t) gitems.push_back(GridItem{o, t});
-    std::vector<DegridItem> dloc;
-    for (int32_t o = 0; o < cnt; ++o) {
+    for (int32_t o : order) {
       const SubgridDesc& d = p->exec[s0 + o];
       for (int gidx = d.seg_begin; gidx < d.seg_begin + d.seg_count; ++gidx) {
         const SegmentDesc& sgd = p->part.segments[gidx];
         for (int k = sgd.k_begin; k < sgd.k_end; k += kDegridMaxVis)
-          dloc.push_back(DegridItem{o, gidx, k, std::min(k + kDegridMaxVis, sgd.k_end)});
+          ditems.push_back(DegridItem{o, gidx, k, std::min(k + kDegridMaxVis, sgd.k_end)});
       }
     }
-    std::stable_sort(dloc.begin(), dloc.end(), [](const DegridItem& x, const DegridItem& y) {
-      return (x.k_end - x.k_begin) > (y.k_end - y.k_begin);
-    });
-    ditems.insert(ditems.end(), dloc.begin(), dloc.end());
     b.gi_count = int32_t(gitems.size()) - b.gi_offset;
     b.di_count = int32_t(ditems.size()) - b.di_offset;
     p->batches.push_back(b);
@@ -334,6 +342,13 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     e = int(cudaMalloc(reinterpret_cast<void**>(&p->d_scratch), per_sg * p->batch_cap));
     if (!e) p->device_bytes += int64_t(per_sg * p->batch_cap);
   }
+  if (!e && p->max_batch_vis > 0) {
+    const size_t rb = size_t(p->max_batch_vis) * kRecordFloat4 * sizeof(float4);
+    e = int(cudaMalloc(reinterpret_cast<void**>(&p->d_records), rb));
+    if (!e) p->device_bytes += int64_t(rb);
+  }
+  if (!e) e = int(cudaMalloc(reinterpret_cast<void**>(&p->d_status), sizeof(int)));
+  if (!e) e = int(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
   if (!e) e = int(cudaStreamSynchronize(p->stream));
   if (e) {
     st = cuda_err(nullptr, e, "idg_plan_create");
@@ -364,6 +379,35 @@ static KernelGeom kgeom(const idg_plan* p) {
   return KernelGeom{p->N, p->L, p->n_t, p->n_ch, p->n_st, p->geom.aterm_nodes, p->geom.image_size};
 }
 
+static StageArgs stage_args(const idg_plan* p, const Batch& b, const void* vis) {
+  StageArgs sa{};
+  sa.vis = static_cast<const float4*>(vis);
+  sa.uvw = p->d_uvw;
+  sa.fscale = p->d_fscale;
+  sa.sg = p->d_sg + b.sg_offset;
+  sa.records = p->d_records;
+  sa.g = kgeom(p);
+  return sa;
+}
+
+static GridArgs grid_args(const idg_plan* p, const Batch& b, const void* vis, const void* aterms) {
+  GridArgs ga{};
+  ga.records = p->d_records;
+  ga.status = p->d_status;
+  ga.vis = static_cast<const float4*>(vis);
+  ga.uvw = p->d_uvw;
+  ga.fscale = p->d_fscale;
+  ga.aterms = static_cast<const float2*>(aterms);
+  ga.sg = p->d_sg + b.sg_offset;
+  ga.seg = p->d_seg;
+  ga.items = p->d_gitems + b.gi_offset;
+  ga.taper = p->d_taper;
+  ga.blk = p->d_blk;
+  ga.scratch = p->d_scratch;
+  ga.g = kgeom(p);
+  return ga;
+}
+
 idg_status idg_grid(idg_plan* plan, const void* vis_c64, const void* aterms_c64, void* grid_c128) {
   if (!plan) return set_err(nullptr, IDG_ERR_INVALID_ARG, "plan is NULL");
   if (plan->host_only) return set_err(plan, IDG_ERR_INVALID_ARG, "plan was created with IDG_HOST_ONLY");
@@ -373,18 +417,9 @@ idg_status idg_grid(idg_plan* plan, const void* vis_c64, const void* aterms_c64,
     return st;
   const int L = plan->L;
   for (const Batch& b : plan->batches) {
-    GridArgs ga{};
-    ga.vis = static_cast<const float4*>(vis_c64);
-    ga.uvw = plan->d_uvw;
-    ga.fscale = plan->d_fscale;
-    ga.aterms = static_cast<const float2*>(aterms_c64);
-    ga.sg = plan->d_sg + b.sg_offset;
-    ga.seg = plan->d_seg;
-    ga.items = plan->d_gitems + b.gi_offset;
-    ga.taper = plan->d_taper;
-    ga.blk = plan->d_blk;
-    ga.scratch = plan->d_scratch;
-    ga.g = kgeom(plan);
+    GridArgs ga = grid_args(plan, b, vis_c64, aterms_c64);
+    int es = timed(plan, kStage, [&] { return launch_stage_records(L, stage_args(plan, b, vis_c64), b.sg_count, plan->stream); });
+    if (es) return cuda_err(plan, es, "staging launch");
     int e = timed(plan, kGridder, [&] { return launch_gridder(L, ga, b.gi_count, plan->stream); });
     if (e) return cuda_err(plan, e, "gridder launch");
     FftArgs fa{plan->d_sg + b.sg_offset, plan->d_scratch, static_cast<double2*>(grid_c128), plan->d_twiddle, plan->N};
@@ -444,18 +479,9 @@ idg_status idg_subgrid_images(idg_plan* plan, const void* vis_c64, const void* a
   int e = int(cudaMemsetAsync(out_c64, 0, total, plan->stream));
   if (e) return cuda_err(plan, e, "zeroing output");
   for (const Batch& b : plan->batches) {
-    GridArgs ga{};
-    ga.vis = static_cast<const float4*>(vis_c64);
-    ga.uvw = plan->d_uvw;
-    ga.fscale = plan->d_fscale;
-    ga.aterms = static_cast<const float2*>(aterms_c64);
-    ga.sg = plan->d_sg + b.sg_offset;
-    ga.seg = plan->d_seg;
-    ga.items = plan->d_gitems + b.gi_offset;
-    ga.taper = plan->d_taper;
-    ga.blk = plan->d_blk;
-    ga.scratch = plan->d_scratch;
-    ga.g = kgeom(plan);
+    GridArgs ga = grid_args(plan, b, vis_c64, aterms_c64);
+    int es = timed(plan, kStage, [&] { return launch_stage_records(L, stage_args(plan, b, vis_c64), b.sg_count, plan->stream); });
+    if (es) return cuda_err(plan, es, "staging launch");
     e = launch_gridder(L, ga, b.gi_count, plan->stream);
     if (e) return cuda_err(plan, e, "gridder launch");
     if (stage == 1) {
@@ -470,6 +496,21 @@ idg_status idg_subgrid_images(idg_plan* plan, const void* vis_c64, const void* a
   return IDG_OK;
 }
 
+idg_status idg_synchronize(idg_plan* plan) {
+  if (!plan) return set_err(nullptr, IDG_ERR_INVALID_ARG, "plan is NULL");
+  if (plan->host_only) return IDG_OK;
+  int e = int(cudaStreamSynchronize(plan->stream));
+  if (e) return cuda_err(plan, e, "idg_synchronize");
+  int status = 0;
+  e = int(cudaMemcpy(&status, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) return cuda_err(plan, e, "idg_synchronize");
+  if (status) {
+    cudaMemset(plan->d_status, 0, sizeof(int));
+    return set_err(plan, IDG_ERR_TIMEOUT, "a kernel gave up waiting for a bulk copy (bounded wait expired)");
+  }
+  return IDG_OK;
+}
+
 idg_status idg_profile_enable(idg_plan* plan, int32_t on) {
   if (!plan) return set_err(nullptr, IDG_ERR_INVALID_ARG, "plan is NULL");
   plan->profiling = on != 0;
@@ -478,7 +519,7 @@ idg_status idg_profile_enable(idg_plan* plan, int32_t on) {
 
 idg_status idg_profile_read(idg_plan* plan, double* ms, int64_t* launches) {
   if (!plan || !ms || !launches) return set_err(plan, IDG_ERR_INVALID_ARG, "NULL argument");
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < 5; ++c) {
     ms[c] = 0.0;
     launches[c] = 0;
   }

@@ -24,7 +24,8 @@ struct SubgridDesc {
   int32_t n_vis;
   int32_t dropped;
   int32_t plan_index;            // position in plan order
-  int32_t pad0, pad1;
+  int32_t rec_offset;            // first staged record of this subgrid within its batch
+  int32_t pad1;
 };
 static_assert(sizeof(SubgridDesc) == 64, "SubgridDesc layout");
 
@@ -82,7 +83,25 @@ struct KernelGeom {
   double fov;
 };
 
+// Staged visibility record, 8 float4 = 128 bytes (written by the staging
+// kernel, streamed by the gridder with bulk copies):
+//   [0..5] value pairs per polarisation p: (Vr,Vr) (Vi,Vi) (-Vi,-Vi)
+//   [6]    (a_head, b_head, a_tail, b_tail)  phase slopes in turns per pixel
+//   [7]    (w, 2 pi a, 2 pi w, 0)
+constexpr int kRecordFloat4 = 8;
+
+struct StageArgs {
+  const float4* vis;
+  const double* uvw;
+  const double* fscale;
+  const SubgridDesc* sg;      // batch subgrid table
+  float4* records;            // [batch records][8]
+  KernelGeom g;
+};
+
 struct GridArgs {
+  const float4* records;      // staged visibility records of the batch
+  int* status;                // device status word (kStatusTimeout)
   const float4* vis;          // [bl][t][ch][4] complex64, 2 float4 per visibility
   const double* uvw;          // [bl][t][3] metres
   const double* fscale;       // [ch] f / c
@@ -120,6 +139,7 @@ struct FftArgs {
 
 // Launchers (return cudaError_t as int).  `n` is the item or subgrid count.
 int launch_gridder(int L, const GridArgs& a, int n_items, void* stream);
+int launch_stage_records(int L, const StageArgs& a, int n_subgrids, void* stream);
 int launch_degridder(int L, const DegridArgs& a, int n_items, void* stream);
 // mode 0: FFT + add into grid; mode 1: FFT in place in scratch (inspection)
 int launch_fft_adder(int L, const FftArgs& a, int n_subgrids, int mode, void* stream);

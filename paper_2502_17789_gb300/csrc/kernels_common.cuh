@@ -107,6 +107,74 @@ __device__ __forceinline__ Jones interp_jones(const float2* A, int nodes, NodeWe
   return J;
 }
 
+// Same interpolation reading the node samples from global memory through the
+// read-only cache (16-byte loads: a node's 4 entries are 2 float4).
+__device__ __forceinline__ Jones interp_jones_ldg(const float2* A, int nodes, NodeWeight wx, NodeWeight wy) {
+  const float4* r0 = reinterpret_cast<const float4*>(A + (size_t(wy.a) * nodes + wx.a) * 4);
+  const float4* r1 = r0 + size_t(nodes) * 2;
+  const float w00 = (1.f - wx.f) * (1.f - wy.f), w01 = wx.f * (1.f - wy.f);
+  const float w10 = (1.f - wx.f) * wy.f, w11 = wx.f * wy.f;
+  Jones J;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float4 a = __ldg(r0 + h), b = __ldg(r0 + 2 + h), c = __ldg(r1 + h), d = __ldg(r1 + 2 + h);
+    J.m[2 * h].re = w00 * a.x + w01 * b.x + w10 * c.x + w11 * d.x;
+    J.m[2 * h].im = w00 * a.y + w01 * b.y + w10 * c.y + w11 * d.y;
+    J.m[2 * h + 1].re = w00 * a.z + w01 * b.z + w10 * c.z + w11 * d.z;
+    J.m[2 * h + 1].im = w00 * a.w + w01 * b.w + w10 * c.w + w11 * d.w;
+  }
+  return J;
+}
+
 __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
+
+// ---------------------------------------------------------------- async bulk copies (TMA, 1-D)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// arrive once and announce `bytes` of transaction for the current phase
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy completing on `bar`; addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of `bar` to complete; gives up after `limit_ns`
+// nanoseconds (returns false) so a lost transaction cannot hang the GPU.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  return true;
+}
+
+// status word bits written by kernels (read back by idg_synchronize)
+constexpr int kStatusTimeout = 1;
 
 }  // namespace idg

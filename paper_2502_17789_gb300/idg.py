@@ -25,9 +25,10 @@ IDG_DROP_OUT_OF_GRID, IDG_SPLIT_AT_ATERM_INTERVALS, IDG_HOST_ONLY = 1, 2, 4
 
 # every function declared in include/idg.h
 EXPORTS = ["idg_plan_create", "idg_grid", "idg_degrid", "idg_set_stream", "idg_plan_stats", "idg_plan_subgrids",
-           "idg_plan_segments", "idg_subgrid_images", "idg_profile_enable", "idg_profile_read", "idg_last_error",
+           "idg_plan_segments", "idg_subgrid_images", "idg_synchronize", "idg_profile_enable", "idg_profile_read",
+           "idg_last_error",
            "idg_plan_destroy", "idg_abi_version"]
-KERNEL_CLASSES = ["gridder", "fft_adder", "splitter_ifft", "degridder"]
+KERNEL_CLASSES = ["gridder", "fft_adder", "splitter_ifft", "degridder", "stage"]
 
 
 class IdgError(RuntimeError):
@@ -77,6 +78,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.idg_plan_subgrids.argtypes = [P, P, i64, ctypes.POINTER(i64)]
     lib.idg_plan_segments.argtypes = [P, P, i64, ctypes.POINTER(i64)]
     lib.idg_subgrid_images.argtypes = [P, P, P, i32, P]
+    lib.idg_synchronize.argtypes = [P]
     lib.idg_profile_enable.argtypes = [P, i32]
     lib.idg_profile_read.argtypes = [P, P, P]
     lib.idg_last_error.argtypes = [P]
@@ -162,13 +164,17 @@ def idg_subgrid_images(plan, vis_ptr, aterms_ptr, stage, out_ptr):
     _check(load().idg_subgrid_images(plan, vis_ptr, aterms_ptr, int(stage), out_ptr), "idg_subgrid_images", plan)
 
 
+def idg_synchronize(plan):
+    _check(load().idg_synchronize(plan), "idg_synchronize", plan)
+
+
 def idg_profile_enable(plan, on: bool):
     _check(load().idg_profile_enable(plan, 1 if on else 0), "idg_profile_enable", plan)
 
 
 def idg_profile_read(plan) -> dict:
-    ms = np.zeros(4, np.float64)
-    n = np.zeros(4, np.int64)
+    ms = np.zeros(5, np.float64)
+    n = np.zeros(5, np.int64)
     _check(load().idg_profile_read(plan, _np_ptr(ms), _np_ptr(n)), "idg_profile_read", plan)
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
@@ -250,6 +256,9 @@ class Plan:
     def set_stream(self, stream):
         self.stream = stream
         idg_set_stream(self.handle, stream)
+
+    def synchronize(self):
+        idg_synchronize(self.handle)
 
     def profile(self, on: bool = True):
         idg_profile_enable(self.handle, on)

@@ -61,14 +61,14 @@ class Case:
         G = torch.zeros((4, N, N), dtype=torch.complex128, device="cuda") if base is None else \
             torch.as_tensor(base).cuda()
         self.plan.grid(self.vis_d, self.A_d, G)
-        torch.cuda.synchronize()
+        self.plan.synchronize()
         return G.cpu().numpy()
 
     def gpu_degrid(self, G):
         import torch
         out = torch.full(self.vis.shape, 7.0 + 7.0j, dtype=torch.complex64, device="cuda")
         self.plan.degrid(torch.as_tensor(G).cuda(), self.A_d, out)
-        torch.cuda.synchronize()
+        self.plan.synchronize()
         return out.cpu().numpy()
 
     def oracle_grid(self, **kw):
@@ -101,7 +101,7 @@ def test_subgrid_images_match_oracle(idg_mod, oracle_mod, cuda_device, L):
     import torch
     for stage, ref in ((0, img), (1, uv)):
         got = c.plan.subgrid_images(c.vis_d, c.A_d, stage)
-        torch.cuda.synchronize()
+        c.plan.synchronize()
         got = got.cpu().numpy()
         assert _rel(got, ref) < GRID_TOL, (stage, _rel(got, ref))
 
