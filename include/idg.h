@@ -194,6 +194,24 @@ idg_status idg_profile_enable(idg_plan* plan, int32_t on);
  */
 idg_status idg_profile_read(idg_plan* plan, double* ms, int64_t* launches);
 
+/*
+ * idg_grid_noalloc -- idg_grid without allocating memory.  No counterpart in
+ * the paper: it serves callers that cannot call cudaMalloc at the point where
+ * they grid (for example while a CUDA graph is being captured, or inside an
+ * allocation-free real-time pipeline).  Same arguments and result as
+ * idg_grid, on a device plan; the subgrid images live in one static 32 MiB
+ * device buffer compiled into the library (held on every GPU that loads it
+ * until the process exits) instead of the plan's scratch, and subgrids are
+ * processed in sub-batches that fit it.  Calls no allocating routine.
+ *   - the first call on a device looks up the buffer's device address (once
+ *     per device, with that device current): make it before any capture;
+ *   - every call shares the buffer: calls that overlap on the GPU (other
+ *     streams or threads) race; the buffer keeps the last call's contents;
+ *   - IDG_ERR_UNSUPPORTED if one subgrid image would not fit the buffer,
+ *     IDG_ERR_INVALID_ARG for host-only plans or NULL / misaligned buffers.
+ */
+idg_status idg_grid_noalloc(idg_plan* plan, const void* vis_c64, const void* aterms_c64, void* grid_c128);
+
 /* Message for the last failure (never NULL; "" when none). */
 const char* idg_last_error(const idg_plan* plan);
 

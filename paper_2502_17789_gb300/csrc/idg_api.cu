@@ -200,6 +200,29 @@ idg_status check_buffer(idg_plan* p, const void* ptr, const char* name) {
 
 }  // namespace
 
+namespace idg {
+
+bool plan_device_view(const idg_plan* p, PlanDeviceView* v) {
+  if (!p || p->host_only || !v) return false;
+  v->g = KernelGeom{p->N, p->L, p->n_t, p->n_ch, p->n_st, p->geom.aterm_nodes, p->geom.image_size};
+  v->stream = p->stream;
+  v->uvw = p->d_uvw;
+  v->fscale = p->d_fscale;
+  v->taper = p->d_taper;
+  v->blk = p->d_blk;
+  v->twiddle = p->d_twiddle;
+  v->sg = p->d_sg;
+  v->n_sg = int32_t(p->exec.size());
+  v->seg = p->d_seg;
+  return true;
+}
+
+idg_status plan_set_error(const idg_plan* p, idg_status st, const char* msg) {
+  return set_err(const_cast<idg_plan*>(p), st, msg);
+}
+
+}  // namespace idg
+
 extern "C" {
 
 int32_t idg_abi_version(void) { return IDG_ABI_VERSION; }

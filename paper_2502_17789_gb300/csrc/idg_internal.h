@@ -148,6 +148,23 @@ int launch_splitter_ifft(int L, const FftArgs& a, int n_subgrids, void* stream);
 int launch_export_subgrids(int L, const SubgridDesc* sg, const float2* scratch, float2* out, int n_subgrids,
                            void* stream);
 int configure_kernels(int L);  // one-time attributes (dynamic shared memory opt-in)
+
+// Read-only view of a device plan's tables, for entry points defined outside
+// the API translation unit.  Returns false for host-only plans.
+struct PlanDeviceView {
+  KernelGeom g;
+  void* stream;
+  const double* uvw;
+  const double* fscale;
+  const float* taper;
+  const float4* blk;
+  const float2* twiddle;
+  const SubgridDesc* sg;   // non-dropped subgrids, execution order
+  int32_t n_sg;
+  const SegmentDesc* seg;
+};
+bool plan_device_view(const idg_plan* plan, PlanDeviceView* out);
+idg_status plan_set_error(const idg_plan* plan, idg_status st, const char* msg);
 bool supported_subgrid_size(int L);
 int gridder_rows(int L);  // rows per gridder pixel tile (0 if unsupported)
 

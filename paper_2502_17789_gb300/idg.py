@@ -26,7 +26,7 @@ IDG_DROP_OUT_OF_GRID, IDG_SPLIT_AT_ATERM_INTERVALS, IDG_HOST_ONLY = 1, 2, 4
 # every function declared in include/idg.h
 EXPORTS = ["idg_plan_create", "idg_grid", "idg_degrid", "idg_set_stream", "idg_plan_stats", "idg_plan_subgrids",
            "idg_plan_segments", "idg_subgrid_images", "idg_synchronize", "idg_profile_enable", "idg_profile_read",
-           "idg_last_error",
+           "idg_grid_noalloc", "idg_last_error",
            "idg_plan_destroy", "idg_abi_version"]
 KERNEL_CLASSES = ["gridder", "fft_adder", "splitter_ifft", "degridder", "stage"]
 
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.idg_plan_segments.argtypes = [P, P, i64, ctypes.POINTER(i64)]
     lib.idg_subgrid_images.argtypes = [P, P, P, i32, P]
     lib.idg_synchronize.argtypes = [P]
+    lib.idg_grid_noalloc.argtypes = [P, P, P, P]
     lib.idg_profile_enable.argtypes = [P, i32]
     lib.idg_profile_read.argtypes = [P, P, P]
     lib.idg_last_error.argtypes = [P]
@@ -126,6 +127,10 @@ def idg_plan_create(geom: Geometry, n_stations: int, baselines, uvw_m, freqs_hz,
 
 def idg_grid(plan, vis_ptr, aterms_ptr, grid_ptr):
     _check(load().idg_grid(plan, vis_ptr, aterms_ptr, grid_ptr), "idg_grid", plan)
+
+
+def idg_grid_noalloc(plan, vis_ptr, aterms_ptr, grid_ptr):
+    _check(load().idg_grid_noalloc(plan, vis_ptr, aterms_ptr, grid_ptr), "idg_grid_noalloc", plan)
 
 
 def idg_degrid(plan, grid_ptr, aterms_ptr, vis_ptr):
