@@ -5,16 +5,16 @@
 // where Y is the uncentred inverse subgrid FFT of the split-out grid
 // footprint (the splitter applied (-1)^(x+y)).
 //
-// Work item = up to 256 visibilities of one segment (one A-term).  Each
-// thread owns one visibility; the block walks the subgrid in chunks of 64
-// pixel blocks (8 consecutive pixels of a row each, 512 pixels).  Z of the
-// next chunk is built while the current chunk is summed: its Y values are
-// loaded into registers before the phasor sum and turned into Z (A-term
-// prologue) after it, into the other half of a double buffer, so one
-// barrier per chunk separates producer and consumer.  When a segment has
-// fewer than 256 visibilities the warps split the pixel blocks between
-// them and combine partial sums through shared memory at the end.  Phases
-// use the same FP64 offset / exact anchor reduction / FP32 increment
+// Work item = up to 256 visibilities of one segment (one A-term), in groups
+// of 32 (one per lane).  The block walks the subgrid in chunks of 64 pixel
+// blocks (8 consecutive pixels of a row each, 512 pixels).  Within a chunk,
+// warp w sums pixel blocks [8w, 8w+8) for every visibility group in turn and
+// adds its partial sums into a shared-memory accumulator with shared-memory
+// atomics, so all warps stay busy whatever the segment size.  Z of the next
+// chunk is built while the current chunk is summed: its Y values are loaded
+// into registers before the phasor sum and turned into Z (A-term prologue)
+// after it, into the other half of a double buffer, one barrier per chunk.
+// Phases use the same FP64 offset / exact anchor reduction / FP32 increment
 // scheme as the gridder.
 #include "kernels_common.cuh"
 
@@ -22,13 +22,14 @@ namespace idg {
 
 constexpr int kDegridThreads = 256;
 constexpr int kChunkBlocks = 64;  // pixel blocks (of 8) per chunk = 512 pixels
+constexpr int kRangeBlocks = 8;   // pixel blocks per work unit (one per warp per visibility group)
 
 template <int L>
 struct DegridSmem {
   float4 z[2][kChunkBlocks][4][4];  // [buf][block][pixel pair][pol] {Zr_a, Zr_b, Zi_a, Zi_b}
-  float2 n[2][kChunkBlocks][4][4];  // {-Zr_a, -Zr_b}
   float4 g[2][kChunkBlocks][3];     // block geometry
-  float red[8][kDegridThreads];     // split partial sums
+  float4 coef[8][2][32];            // [vis group][half][lane]: (ah, bh, al, bl), (w, 2 pi a, 2 pi w, 0)
+  float out[8][kDegridThreads];     // [component][visibility slot], accumulated with shared atomics
 };
 
 template <int L>
@@ -36,7 +37,7 @@ __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const Degr
   constexpr int TPR = L / 8;
   constexpr int NBLK = L * L / 8;
   constexpr int NCH = NBLK / kChunkBlocks;
-  static_assert(NBLK % kChunkBlocks == 0, "chunking");
+  static_assert(NBLK % kChunkBlocks == 0 && kChunkBlocks == 8 * kRangeBlocks, "chunking");
   extern __shared__ float4 smem_raw[];
   DegridSmem<L>& S = *reinterpret_cast<DegridSmem<L>*>(smem_raw);
   float2* s_A = reinterpret_cast<float2*>(&S + 1);  // [2][nodes*nodes*4]
@@ -46,12 +47,7 @@ __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const Degr
   const SegmentDesc seg = a.seg[item.segment];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nv = item.k_end - item.k_begin;
-  const int wv = (nv + 31) >> 5;  // warps of visibilities, 1..8
-  const int nsplit = 8 / wv;      // pixel splits, >= 1
-  const int vgroup = warp % wv, split = warp / wv;
-  const bool active = split < nsplit;
-  const int kloc = vgroup * 32 + lane;
-  const bool valid = active && kloc < nv;
+  const int n_vg = (nv + 31) >> 5;  // groups of 32 visibilities, 1..8
   const int nodes = a.g.nodes;
   const int nA = nodes * nodes * 4;
 
@@ -63,41 +59,31 @@ __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const Degr
       s_A[nA + e] = Aq[e];
     }
   }
-
-  // this thread's visibility: FP64 offsets -> FP32 phase coefficients
-  const int nc = sd.c1 - sd.c0;
-  float ah = 0.f, bh = 0.f, al = 0.f, bl = 0.f, cw = 0.f, ar = 0.f, cr = 0.f;
-  size_t vidx = 0;
-  if (valid) {
-    const int k = item.k_begin + kloc;
-    const int t = sd.t0 + k / nc, ch = sd.c0 + k % nc;
-    vidx = (size_t(sd.b) * a.g.n_t + t) * a.g.n_ch + ch;
-    const double* r = a.uvw + (size_t(sd.b) * a.g.n_t + t) * 3;
-    const double fs = a.fscale[ch];
-    const double inv_l = 1.0 / double(L);
-    const double dx = (r[0] * fs) * a.g.fov - double(sd.x0 + L / 2 - a.g.N / 2);
-    const double dy = (r[1] * fs) * a.g.fov - double(sd.y0 + L / 2 - a.g.N / 2);
-    const double w = r[2] * fs;
-    const double aa = dx * inv_l, bb = dy * inv_l;
-    const double dah = rint(aa * 65536.0) * (1.0 / 65536.0);
-    const double dbh = rint(bb * 65536.0) * (1.0 / 65536.0);
-    ah = float(dah);
-    bh = float(dbh);
-    al = float(aa - dah);
-    bl = float(bb - dbh);
-    cw = float(w);
-    ar = float(kTwoPi * aa);
-    cr = float(kTwoPi * w);
-  }
-  const float2 ARR = make_float2(ar, ar), CRR = make_float2(cr, cr);
-  const float2 DI[4] = {{-4.f, -3.f}, {-2.f, -1.f}, {0.f, 1.f}, {2.f, 3.f}};
-
-  float2 RE[4], IM[4];
+  // visibility slot tid: FP64 offsets -> FP32 phase coefficients (zeros for empty slots)
+  {
+    const int nc = sd.c1 - sd.c0;
+    float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
+    if (tid < nv) {
+      const int k = item.k_begin + tid;
+      const int t = sd.t0 + k / nc, ch = sd.c0 + k % nc;
+      const double* r = a.uvw + (size_t(sd.b) * a.g.n_t + t) * 3;
+      const double fs = a.fscale[ch];
+      const double inv_l = 1.0 / double(L);
+      const double dx = (r[0] * fs) * a.g.fov - double(sd.x0 + L / 2 - a.g.N / 2);
+      const double dy = (r[1] * fs) * a.g.fov - double(sd.y0 + L / 2 - a.g.N / 2);
+      const double w = r[2] * fs;
+      const double aa = dx * inv_l, bb = dy * inv_l;
+      const double dah = rint(aa * 65536.0) * (1.0 / 65536.0);
+      const double dbh = rint(bb * 65536.0) * (1.0 / 65536.0);
+      c0 = make_float4(float(dah), float(dbh), float(aa - dah), float(bb - dbh));
+      c1 = make_float4(float(w), float(kTwoPi * aa), float(kTwoPi * w), 0.f);
+    }
+    S.coef[tid >> 5][0][tid & 31] = c0;
+    S.coef[tid >> 5][1][tid & 31] = c1;
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    RE[p] = make_float2(0.f, 0.f);
-    IM[p] = make_float2(0.f, 0.f);
+    for (int c = 0; c < 8; ++c) S.out[c][tid] = 0.f;
   }
+  const float2 DI[4] = {{-4.f, -3.f}, {-2.f, -1.f}, {0.f, 1.f}, {2.f, 3.f}};
   const float2* Y = a.scratch + size_t(item.sg) * 4 * L * L;
 
   // prologue geometry: each thread builds one pixel pair (2 consecutive pixels) per chunk
@@ -121,7 +107,6 @@ __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const Degr
     const NodeWeight wy = node_weight(j, nodes, L);
     const float tj = a.taper[j];
     float4 zo[4];
-    float2 no[4];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int ii = i + h;
@@ -138,23 +123,17 @@ __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const Degr
       const float wgt = a.taper[ii] * tj * (((ii + j) & 1) ? -1.f : 1.f);
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
-        const float zr = wgt * Z.m[p].re, zi = wgt * Z.m[p].im;
         if (h == 0) {
-          zo[p].x = zr;
-          zo[p].z = zi;
-          no[p].x = -zr;
+          zo[p].x = wgt * Z.m[p].re;
+          zo[p].z = wgt * Z.m[p].im;
         } else {
-          zo[p].y = zr;
-          zo[p].w = zi;
-          no[p].y = -zr;
+          zo[p].y = wgt * Z.m[p].re;
+          zo[p].w = wgt * Z.m[p].im;
         }
       }
     }
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      S.z[buf][pb][pq][p] = zo[p];
-      S.n[buf][pb][pq][p] = no[p];
-    }
+    for (int p = 0; p < 4; ++p) S.z[buf][pb][pq][p] = zo[p];
     if (tid < kChunkBlocks * 3) {
       const int b = tid / 3, c = tid % 3;
       S.g[buf][b][c] = a.blk[size_t(chunk * kChunkBlocks + b) * 3 + c];
@@ -162,7 +141,7 @@ __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const Degr
   };
 
   load_y(0);
-  __syncthreads();  // s_A visible
+  __syncthreads();  // s_A and the coefficient table visible
   build_z(0, 0);
   __syncthreads();
 
@@ -170,15 +149,24 @@ __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const Degr
     const int buf = chunk & 1;
     const bool more = chunk + 1 < NCH;
     if (more) load_y(chunk + 1);
-    if (active) {
+    // warp `warp` sums pixel blocks [warp*8, warp*8+8) of the chunk for every visibility group
+    for (int g = 0; g < n_vg; ++g) {
+      const float4 c0 = S.coef[g][0][lane], c1 = S.coef[g][1][lane];
+      const float2 ARR = make_float2(c1.y, c1.y), CRR = make_float2(c1.z, c1.z);
+      float2 RE[4], IM[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        RE[p] = make_float2(0.f, 0.f);
+        IM[p] = make_float2(0.f, 0.f);
+      }
 #pragma unroll 1
-      for (int b = split; b < kChunkBlocks; b += nsplit) {
+      for (int b = warp * kRangeBlocks; b < (warp + 1) * kRangeBlocks; ++b) {
         const float4 g0 = S.g[buf][b][0], g1 = S.g[buf][b][1], g2 = S.g[buf][b][2];
         const float n0 = g0.x, di0 = g2.y, dj0 = g2.z;
         const float2 DN[4] = {{g0.y, g0.z}, {g0.w, g1.x}, {g1.y, g1.z}, {g1.w, g2.x}};
-        const float sh = fmaf(ah, di0, bh * dj0);
+        const float sh = fmaf(c0.x, di0, c0.y * dj0);
         const float d1 = __fsub_rn(sh, round_nearest(sh));
-        const float lo = fmaf(cw, n0, fmaf(al, di0, bl * dj0));
+        const float lo = fmaf(c1.x, n0, fmaf(c0.z, di0, c0.w * dj0));
         float rr = __fadd_rn(d1, lo);
         rr = __fmul_rn(__fsub_rn(rr, round_nearest(rr)), kTwoPiF);
         const float2 R0 = make_float2(rr, rr);
@@ -188,39 +176,38 @@ __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const Degr
           float2 Cs, Sn;
           __sincosf(ph.x, &Sn.x, &Cs.x);
           __sincosf(ph.y, &Sn.y, &Cs.y);
+          const float2 NS = make_float2(-Sn.x, -Sn.y);
 #pragma unroll
           for (int p = 0; p < 4; ++p) {
             const float4 z = S.z[buf][b][q][p];
-            const float2 ZR = make_float2(z.x, z.y), ZI = make_float2(z.z, z.w), NZR = S.n[buf][b][q][p];
+            const float2 ZR = make_float2(z.x, z.y), ZI = make_float2(z.z, z.w);
+            // V += Z conj(e): re += Zr c + Zi s, im += Zi c - Zr s
             RE[p] = ffma2(ZR, Cs, RE[p]);
             RE[p] = ffma2(ZI, Sn, RE[p]);
             IM[p] = ffma2(ZI, Cs, IM[p]);
-            IM[p] = ffma2(NZR, Sn, IM[p]);
+            IM[p] = ffma2(ZR, NS, IM[p]);
           }
         }
+      }
+      const int slot = g * 32 + lane;
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        atomicAdd(&S.out[2 * p][slot], RE[p].x + RE[p].y);
+        atomicAdd(&S.out[2 * p + 1][slot], IM[p].x + IM[p].y);
       }
     }
     if (more) build_z(chunk + 1, buf ^ 1);
     __syncthreads();
   }
 
-  // ---- combine pixel splits and write the visibility
-#pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    S.red[2 * p][tid] = RE[p].x + RE[p].y;
-    S.red[2 * p + 1][tid] = IM[p].x + IM[p].y;
-  }
-  __syncthreads();
-  if (valid && split == 0) {
-    float v[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      float s = 0.f;
-      for (int sp = 0; sp < nsplit; ++sp) s += S.red[c][(sp * wv + vgroup) * 32 + lane];
-      v[c] = s;
-    }
-    a.vis[2 * vidx] = make_float4(v[0], v[1], v[2], v[3]);
-    a.vis[2 * vidx + 1] = make_float4(v[4], v[5], v[6], v[7]);
+  // ---- write the visibilities of this item
+  if (tid < nv) {
+    const int nc = sd.c1 - sd.c0;
+    const int k = item.k_begin + tid;
+    const int t = sd.t0 + k / nc, ch = sd.c0 + k % nc;
+    const size_t vidx = (size_t(sd.b) * a.g.n_t + t) * a.g.n_ch + ch;
+    a.vis[2 * vidx] = make_float4(S.out[0][tid], S.out[1][tid], S.out[2][tid], S.out[3][tid]);
+    a.vis[2 * vidx + 1] = make_float4(S.out[4][tid], S.out[5][tid], S.out[6][tid], S.out[7][tid]);
   }
 }
 
