@@ -65,7 +65,8 @@ enum { IDG_TAPER_KB = 0, IDG_TAPER_USER = 1 };
 enum {
   IDG_DROP_OUT_OF_GRID = 1,         /* drop subgrids that leave the grid instead of failing */
   IDG_SPLIT_AT_ATERM_INTERVALS = 2, /* never let a subgrid span two A-term intervals (Section 3.3 as written) */
-  IDG_HOST_ONLY = 4                 /* plan on the host only: no device memory, grid/degrid refused */
+  IDG_HOST_ONLY = 4,                /* plan on the host only: no device memory, grid/degrid refused */
+  IDG_PERSISTENT = 8                /* persistent launches: #SMs x occupancy blocks drain a work queue */
 };
 
 typedef struct {
@@ -73,11 +74,11 @@ typedef struct {
   int32_t subgrid_size;   /* L: one of 32, 64, 96, 128 for device plans (even, <= N for host plans) */
   int32_t kernel_padding; /* P: even, L - P - 4 >= 1 */
   double image_size;      /* FOV in direction cosines; du = 1/FOV; FOV^2/2 < 1 */
-  int32_t taper_kind;     /* IDG_TAPER_KB (beta = taper_beta, or pi*P/2 when <= 0) or IDG_TAPER_USER */
+  int32_t taper_kind;     /* IDG_TAPER_KB (beta = taper_beta, or 0.35*pi*P when <= 0) or IDG_TAPER_USER */
   double taper_beta;
   const double* taper_user; /* host [L] taper samples at l_i = (i - L/2) FOV/L (IDG_TAPER_USER), copied */
   int32_t aterm_nodes;    /* nodes per axis of the A-term samples, >= 2 */
-  int32_t flags;          /* IDG_DROP_OUT_OF_GRID | IDG_SPLIT_AT_ATERM_INTERVALS | IDG_HOST_ONLY */
+  int32_t flags;          /* IDG_DROP_OUT_OF_GRID | IDG_SPLIT_AT_ATERM_INTERVALS | IDG_HOST_ONLY | IDG_PERSISTENT */
 } idg_geometry;
 
 typedef struct {
@@ -138,6 +139,18 @@ idg_status idg_grid(idg_plan* plan, const void* vis_c64, const void* aterms_c64,
  * Asynchronous on the plan's stream.  Buffers must be 16-byte aligned.
  */
 idg_status idg_degrid(idg_plan* plan, const void* grid_c128, const void* aterms_c64, void* vis_c64);
+
+/*
+ * idg_grid_graph / idg_degrid_graph -- the same operations replayed from a
+ * CUDA graph (Section 3.4 batches, all captured as one graph): the first call
+ * with a given set of buffers captures the whole call on the plan's stream
+ * and instantiates it; later calls with the same buffers launch the graph.
+ * Different buffers trigger a new capture.  The plan's stream must not be the
+ * legacy default stream (IDG_ERR_INVALID_ARG).  Profiling does not see
+ * graph replays.
+ */
+idg_status idg_grid_graph(idg_plan* plan, const void* vis_c64, const void* aterms_c64, void* grid_c128);
+idg_status idg_degrid_graph(idg_plan* plan, const void* grid_c128, const void* aterms_c64, void* vis_c64);
 
 /* Set the stream later calls run on (cudaStream_t; NULL = legacy default). */
 idg_status idg_set_stream(idg_plan* plan, void* cuda_stream);

@@ -93,14 +93,16 @@ class Geometry:
     kernel_padding: int
     image_size: float
     taper_kind: int = 0          # 0 Kaiser-Bessel, 1 user table
-    taper_beta: float | None = None   # default pi * P / 2
+    taper_beta: float | None = None   # default 0.35 pi P
     taper_user: np.ndarray | None = None
     aterm_nodes: int = 9
     flags: int = 0
 
     @property
     def beta(self) -> float:
-        return float(np.pi * self.kernel_padding / 2.0) if self.taper_beta is None else float(self.taper_beta)
+        # Section 4.2 fixes no beta; 0.35 pi P balances the taper kernel's aliasing
+        # against the dynamic range 1/T^2 of taper-corrected models
+        return float(0.35 * np.pi * self.kernel_padding) if self.taper_beta is None else float(self.taper_beta)
 
 
 @dataclass

@@ -1,0 +1,141 @@
+"""Autotuner for the batched launch.
+
+Chooses, for one observation, the subgrid size L, the launch mode (one block
+per work item, or a persistent grid draining the work queue) and the
+per-batch scratch budget (how many subgrid images a batch holds) by timing a
+grid + degrid pass on the observation's own plans with CUDA events, and
+caches the winner in a JSON file keyed by the GPU and the observation's
+shape.  Changing L changes the partition and hence the numbers (legitimately:
+each L has its own oracle result); the launch mode and budget do not.
+
+The timing function is injectable so the selection and cache logic can be
+tested without a GPU.
+"""
+from __future__ import annotations
+
+import json
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+CANDIDATE_L = (64, 96, 128)
+MODES = ("blocks", "persistent")
+BUDGETS = (1 << 30,)
+
+
+@dataclass
+class Choice:
+    subgrid_size: int
+    mode: str
+    scratch_bytes: int
+    ms: float
+    timings: dict = field(default_factory=dict)
+
+    def as_dict(self):
+        return {"subgrid_size": self.subgrid_size, "mode": self.mode, "scratch_bytes": self.scratch_bytes,
+                "ms": self.ms, "timings": self.timings}
+
+
+def shape_key(obs, device_name: str) -> str:
+    """Cache key: GPU name, geometry and table shape.  The longest baseline
+    (in grid pixels at the top frequency) stands in for the occupancy
+    distribution, which depends on L."""
+    u = np.abs(obs.uvw[..., :2]).max() * obs.freqs.max() / 299792458.0 * obs.image_size if obs.n_vis else 0.0
+    return (f"{device_name}|N{obs.grid_size}|fov{obs.image_size:.6g}|P{obs.kernel_padding}|bl{obs.n_baselines}"
+            f"|t{obs.n_timesteps}|ch{obs.n_channels}|int{obs.n_intervals}|reach{int(u)}")
+
+
+def _load_cache(path):
+    if path and os.path.exists(path):
+        try:
+            with open(path) as f:
+                return json.load(f)
+        except (OSError, ValueError):
+            return {}
+    return {}
+
+
+def _save_cache(path, cache):
+    if not path:
+        return
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def gpu_measure(obs, subgrid_size, mode, scratch_bytes, trials=2, aterms=None):
+    """Time one grid + degrid pass (ms, best of `trials`) on a plan with the
+    given settings; None if the plan cannot be made (e.g. w too large)."""
+    import torch
+
+    from . import idg
+
+    os.environ["IDG_SCRATCH_BYTES"] = str(int(scratch_bytes))
+    try:
+        flags = idg.IDG_PERSISTENT if mode == "persistent" else 0
+        try:
+            plan = idg.Plan(obs, subgrid_size=subgrid_size, flags=flags)
+        except idg.IdgError:
+            return None
+    finally:
+        del os.environ["IDG_SCRATCH_BYTES"]
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    vis = torch.randn((obs.n_baselines, obs.n_timesteps, obs.n_channels, 4), dtype=torch.complex64, device=dev,
+                      generator=g)
+    if aterms is None:
+        from . import synth
+        aterms = synth.aterms_identity(obs.n_intervals, obs.n_stations, obs.aterm_nodes)
+    A = torch.as_tensor(aterms, device=dev)
+    N = obs.grid_size
+    G = torch.zeros((4, N, N), dtype=torch.complex128, device=dev)
+    out = torch.empty_like(vis)
+    s = torch.cuda.current_stream(dev)
+    best = None
+    for t in range(trials + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        plan.grid(vis, A, G)
+        plan.degrid(G, A, out)
+        e1.record(s)
+        plan.synchronize()
+        if t > 0:
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+    plan.close()
+    del vis, G, out
+    torch.cuda.empty_cache()
+    return best
+
+
+def autotune(obs, *, candidates=CANDIDATE_L, modes=MODES, budgets=BUDGETS, cache_path=None, device_name=None,
+             measure=None, refresh=False) -> Choice:
+    """Return the fastest (L, mode, budget) for `obs`, from the cache when
+    the key is present, else by measuring every candidate."""
+    if device_name is None:
+        import torch
+        device_name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    measure = measure or gpu_measure
+    key = shape_key(obs, device_name)
+    cache = _load_cache(cache_path)
+    if not refresh and key in cache:
+        c = cache[key]
+        return Choice(c["subgrid_size"], c["mode"], c["scratch_bytes"], c["ms"], c.get("timings", {}))
+    timings = {}
+    best = None
+    for L in candidates:
+        for mode in modes:
+            for budget in budgets:
+                ms = measure(obs, L, mode, budget)
+                timings[f"L{L}/{mode}/{budget}"] = ms
+                if ms is not None and (best is None or ms < best.ms):
+                    best = Choice(L, mode, budget, ms)
+    if best is None:
+        raise RuntimeError("autotune: no candidate configuration could be planned for this observation")
+    best.timings = timings
+    cache[key] = best.as_dict()
+    _save_cache(cache_path, cache)
+    return best

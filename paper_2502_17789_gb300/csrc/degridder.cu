@@ -33,16 +33,12 @@ struct DegridSmem {
 };
 
 template <int L>
-__global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const DegridArgs a) {
+__device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx, DegridSmem<L>& S, float2* s_A) {
   constexpr int TPR = L / 8;
   constexpr int NBLK = L * L / 8;
   constexpr int NCH = NBLK / kChunkBlocks;
   static_assert(NBLK % kChunkBlocks == 0 && kChunkBlocks == 8 * kRangeBlocks, "chunking");
-  extern __shared__ float4 smem_raw[];
-  DegridSmem<L>& S = *reinterpret_cast<DegridSmem<L>*>(smem_raw);
-  float2* s_A = reinterpret_cast<float2*>(&S + 1);  // [2][nodes*nodes*4]
-
-  const DegridItem item = a.items[blockIdx.x];
+  const DegridItem item = a.items[item_idx];
   const SubgridDesc sd = a.sg[item.sg];
   const SegmentDesc seg = a.seg[item.segment];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -211,27 +207,75 @@ __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const Degr
   }
 }
 
+// PERSIST = false: one item per block; true: blocks drain the a.queue counter.
+template <int L, bool PERSIST>
+__global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const DegridArgs a) {
+  extern __shared__ float4 smem_raw[];
+  DegridSmem<L>& S = *reinterpret_cast<DegridSmem<L>*>(smem_raw);
+  float2* s_A = reinterpret_cast<float2*>(&S + 1);  // [2][nodes*nodes*4]
+  __shared__ int s_item;
+  if constexpr (!PERSIST) {
+    degridder_item<L>(a, blockIdx.x, S, s_A);
+  } else {
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= a.n_items) return;
+    degridder_item<L>(a, it, S, s_A);
+    __syncthreads();  // shared memory and s_item free for the next item
+  }
+  }
+}
+
 template <int L>
 static size_t degridder_smem(int nodes) {
   return sizeof(DegridSmem<L>) + sizeof(float2) * 2 * nodes * nodes * 4;
 }
 
 template <int L>
-static int launch_degridder_t(const DegridArgs& a, int n_items, void* stream) {
+static int configure_degridder_t(int nodes, int* persistent_blocks) {
+  const int smem = int(degridder_smem<L>(nodes));
+  cudaError_t e = cudaFuncSetAttribute(degridder_kernel<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(degridder_kernel<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int per_sm = 0, dev = 0, sms = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, degridder_kernel<L, true>, kDegridThreads, smem);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  *persistent_blocks = per_sm * sms;
+  return int(e);
+}
+
+template <int L>
+static int launch_degridder_t(const DegridArgs& a, int n_items, int persistent_blocks, void* stream) {
   const size_t smem = degridder_smem<L>(a.g.nodes);
-  cudaError_t e = cudaFuncSetAttribute(degridder_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return int(e);
   if (n_items <= 0) return 0;
-  degridder_kernel<L><<<n_items, kDegridThreads, smem, cudaStream_t(stream)>>>(a);
+  if (persistent_blocks > 0)
+    degridder_kernel<L, true><<<persistent_blocks < n_items ? persistent_blocks : n_items, kDegridThreads, smem,
+                                cudaStream_t(stream)>>>(a);
+  else
+    degridder_kernel<L, false><<<n_items, kDegridThreads, smem, cudaStream_t(stream)>>>(a);
   return int(cudaGetLastError());
 }
 
-int launch_degridder(int L, const DegridArgs& a, int n_items, void* stream) {
+int launch_degridder(int L, const DegridArgs& a, int n_items, int persistent_blocks, void* stream) {
   switch (L) {
-    case 32: return launch_degridder_t<32>(a, n_items, stream);
-    case 64: return launch_degridder_t<64>(a, n_items, stream);
-    case 96: return launch_degridder_t<96>(a, n_items, stream);
-    case 128: return launch_degridder_t<128>(a, n_items, stream);
+    case 32: return launch_degridder_t<32>(a, n_items, persistent_blocks, stream);
+    case 64: return launch_degridder_t<64>(a, n_items, persistent_blocks, stream);
+    case 96: return launch_degridder_t<96>(a, n_items, persistent_blocks, stream);
+    case 128: return launch_degridder_t<128>(a, n_items, persistent_blocks, stream);
+    default: return int(cudaErrorInvalidValue);
+  }
+}
+
+int configure_degridder(int L, int nodes, int* persistent_blocks) {
+  switch (L) {
+    case 32: return configure_degridder_t<32>(nodes, persistent_blocks);
+    case 64: return configure_degridder_t<64>(nodes, persistent_blocks);
+    case 96: return configure_degridder_t<96>(nodes, persistent_blocks);
+    case 128: return configure_degridder_t<128>(nodes, persistent_blocks);
     default: return int(cudaErrorInvalidValue);
   }
 }

@@ -96,17 +96,14 @@ __device__ __forceinline__ void cursor_advance(ChunkCursor& cur, const SegmentDe
   }
 }
 
+// One work item.  `cg` counts the chunks this block has consumed so far (it
+// selects the buffer and the mbarrier phase, and carries over between the
+// items of a persistent block).  Returns false if a bounded wait expired.
 template <int L, int ROWS>
-__global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
-    gridder_kernel(const GridArgs a) {
+__device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, uint32_t& cg, float4* s_rec,
+                                             float* s_acc, uint64_t* s_bar) {
   using C = GridCfg<L, ROWS>;
-  constexpr uint32_t kChunkBytes = C::VC * kRecordFloat4 * 16;
-  extern __shared__ float4 smem[];
-  float4* s_rec = smem;                                              // [2][VC][8]
-  float* s_acc = reinterpret_cast<float*>(s_rec + 2 * C::VC * kRecordFloat4);  // [64][NT]
-  uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_acc + 64 * C::NT);          // [2]
-
-  const GridItem item = a.items[blockIdx.x];
+  const GridItem item = a.items[item_idx];
   const SubgridDesc sd = a.sg[item.sg];
   const int tid = threadIdx.x;
   const int j = item.tile * ROWS + tid / C::TPR;
@@ -126,13 +123,9 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
   // producer (thread 0): issue the copy of the chunk at `pc` into buffer `buf`
   ChunkCursor pc{0, 0, 0};
   if (tid == 0) {
-    mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
-    fence_mbar_init();
     const SegmentDesc s0 = a.seg[sd.seg_begin];
     pc = {0, s0.k_begin, s0.k_end};
   }
-  __syncthreads();
   auto issue = [&](int buf) {
     const int nv = imin(C::VC, pc.end - pc.k);
     const uint32_t bytes = uint32_t(nv) * kRecordFloat4 * 16;
@@ -141,8 +134,8 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
     cursor_advance<C::VC>(pc, a.seg, sd.seg_begin, sd.seg_count);
   };
   if (tid == 0) {
-    issue(0);
-    if (n_chunks > 1) issue(1);
+    issue(int(cg & 1));
+    if (n_chunks > 1) issue(int((cg + 1) & 1));
   }
 
   // pixel geometry of this thread's block: anchor at i0 + 4
@@ -152,7 +145,6 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
   const float2 DN[4] = {{g0.y, g0.z}, {g0.w, g1.x}, {g1.y, g1.z}, {g1.w, g2.x}};
   const float di0 = g2.y, dj0 = g2.z;
   const float2 DI[4] = {{-4.f, -3.f}, {-2.f, -1.f}, {0.f, 1.f}, {2.f, 3.f}};
-  (void)kChunkBytes;
 
   float2 RE[4][4], IM[4][4];
 #pragma unroll
@@ -170,8 +162,9 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
   }
   bool first_seg = true;
   for (int c = 0; c < n_chunks; ++c) {
-    const int buf = c & 1;
-    const bool ok = mbar_wait_bounded(&s_bar[buf], uint32_t((c >> 1) & 1));
+    const uint32_t cc_g = cg + uint32_t(c);
+    const int buf = int(cc_g & 1);
+    const bool ok = mbar_wait_bounded(&s_bar[buf], (cc_g >> 1) & 1);
     const int nv = imin(C::VC, cc.end - cc.k);
     if (ok) {
       const float4* rb = s_rec + buf * C::VC * kRecordFloat4;
@@ -214,9 +207,11 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(a.status, kStatusTimeout);
-        mbar_wait_bounded(&s_bar[buf ^ 1], uint32_t(((c + 1) >> 1) & 1));  // let a copy in flight land
+        // let copies in flight land before the block's shared memory is released
+        mbar_wait_bounded(&s_bar[buf], (cc_g >> 1) & 1);
+        mbar_wait_bounded(&s_bar[buf ^ 1], ((cc_g + 1) >> 1) & 1);
       }
-      return;
+      return false;
     }
     if (tid == 0 && c + 2 < n_chunks) {
       fence_proxy_async();
@@ -283,22 +278,75 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
       }
     }
   }
+  cg += uint32_t(n_chunks);
+  return true;
+}
+
+// PERSIST = false: one item per block (block index, LPT order).
+// PERSIST = true: #SMs x occupancy blocks pull items from the work-queue
+// counter a.queue until the n_items are drained.
+template <int L, int ROWS, bool PERSIST>
+__global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
+    gridder_kernel(const GridArgs a) {
+  using C = GridCfg<L, ROWS>;
+  extern __shared__ float4 smem[];
+  float4* s_rec = smem;                                                        // [2][VC][8]
+  float* s_acc = reinterpret_cast<float*>(s_rec + 2 * C::VC * kRecordFloat4);  // [64][NT]
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_acc + 64 * C::NT);          // [2]
+  int* s_item = reinterpret_cast<int*>(s_bar + 2);
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t cg = 0;
+  if constexpr (!PERSIST) {
+    gridder_item<L, ROWS>(a, blockIdx.x, cg, s_rec, s_acc, s_bar);
+  } else {
+  for (;;) {
+    if (threadIdx.x == 0) *s_item = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int it = *s_item;
+    if (it >= a.n_items) return;
+    if (!gridder_item<L, ROWS>(a, it, cg, s_rec, s_acc, s_bar)) return;
+    __syncthreads();  // shared buffers and s_item free for the next item
+  }
+  }
 }
 
 template <int L, int ROWS>
 static size_t gridder_smem() {
   using C = GridCfg<L, ROWS>;
-  return sizeof(float4) * 2 * C::VC * kRecordFloat4 + sizeof(float) * 64 * C::NT + 2 * sizeof(uint64_t);
+  return sizeof(float4) * 2 * C::VC * kRecordFloat4 + sizeof(float) * 64 * C::NT + 2 * sizeof(uint64_t) + 16;
 }
 
 template <int L, int ROWS>
-static int launch_gridder_t(const GridArgs& a, int n_items, void* stream) {
+static int configure_gridder_t(int* persistent_blocks) {
+  using C = GridCfg<L, ROWS>;
+  const int smem = int(gridder_smem<L, ROWS>());
+  cudaError_t e = cudaFuncSetAttribute(gridder_kernel<L, ROWS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gridder_kernel<L, ROWS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int per_sm = 0, dev = 0, sms = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gridder_kernel<L, ROWS, true>, C::NT, smem);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  *persistent_blocks = per_sm * sms;
+  return int(e);
+}
+
+template <int L, int ROWS>
+static int launch_gridder_t(const GridArgs& a, int n_items, int persistent_blocks, void* stream) {
   using C = GridCfg<L, ROWS>;
   const size_t smem = gridder_smem<L, ROWS>();
-  cudaError_t e = cudaFuncSetAttribute(gridder_kernel<L, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return int(e);
   if (n_items <= 0) return 0;
-  gridder_kernel<L, ROWS><<<n_items, C::NT, smem, cudaStream_t(stream)>>>(a);
+  if (persistent_blocks > 0)
+    gridder_kernel<L, ROWS, true>
+        <<<persistent_blocks < n_items ? persistent_blocks : n_items, C::NT, smem, cudaStream_t(stream)>>>(a);
+  else
+    gridder_kernel<L, ROWS, false><<<n_items, C::NT, smem, cudaStream_t(stream)>>>(a);
   return int(cudaGetLastError());
 }
 
@@ -313,12 +361,22 @@ int gridder_rows(int L) {
   }
 }
 
-int launch_gridder(int L, const GridArgs& a, int n_items, void* stream) {
+int launch_gridder(int L, const GridArgs& a, int n_items, int persistent_blocks, void* stream) {
   switch (L) {
-    case 32: return launch_gridder_t<32, 32>(a, n_items, stream);
-    case 64: return launch_gridder_t<64, 16>(a, n_items, stream);
-    case 96: return launch_gridder_t<96, 16>(a, n_items, stream);
-    case 128: return launch_gridder_t<128, 8>(a, n_items, stream);
+    case 32: return launch_gridder_t<32, 32>(a, n_items, persistent_blocks, stream);
+    case 64: return launch_gridder_t<64, 16>(a, n_items, persistent_blocks, stream);
+    case 96: return launch_gridder_t<96, 16>(a, n_items, persistent_blocks, stream);
+    case 128: return launch_gridder_t<128, 8>(a, n_items, persistent_blocks, stream);
+    default: return int(cudaErrorInvalidValue);
+  }
+}
+
+int configure_gridder(int L, int* persistent_blocks) {
+  switch (L) {
+    case 32: return configure_gridder_t<32, 32>(persistent_blocks);
+    case 64: return configure_gridder_t<64, 16>(persistent_blocks);
+    case 96: return configure_gridder_t<96, 16>(persistent_blocks);
+    case 128: return configure_gridder_t<128, 8>(persistent_blocks);
     default: return int(cudaErrorInvalidValue);
   }
 }

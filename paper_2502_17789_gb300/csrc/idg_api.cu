@@ -69,7 +69,15 @@ struct idg_plan {
   float2* d_scratch = nullptr;
   float4* d_records = nullptr;  // staged visibility records of one batch
   int* d_status = nullptr;      // kernel status word (timeouts)
+  int* d_queue = nullptr;       // work-queue counters, 2 per batch (gridder, degridder)
   int64_t max_batch_vis = 0;
+  int persistent_grid_blocks = 0, persistent_degrid_blocks = 0;  // > 0: persistent launches
+  struct GraphCache {
+    const void* x = nullptr;
+    const void* y = nullptr;
+    const void* z = nullptr;
+    cudaGraphExec_t exec = nullptr;
+  } graph_grid, graph_degrid;
   // profiling: event pairs recorded around launches, per kernel class
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -141,8 +149,12 @@ void release_events(idg_plan* p) {
 }
 
 void free_device(idg_plan* p) {
-  void* ptrs[] = {p->d_uvw,    p->d_fscale, p->d_taper,   p->d_blk,     p->d_twiddle, p->d_sg,
-                  p->d_seg,    p->d_gitems, p->d_ditems,  p->d_scratch, p->d_records, p->d_status};
+  if (p->graph_grid.exec) cudaGraphExecDestroy(p->graph_grid.exec);
+  if (p->graph_degrid.exec) cudaGraphExecDestroy(p->graph_degrid.exec);
+  p->graph_grid = {};
+  p->graph_degrid = {};
+  void* ptrs[] = {p->d_uvw,    p->d_fscale, p->d_taper,   p->d_blk,     p->d_twiddle, p->d_sg,     p->d_seg,
+                  p->d_gitems, p->d_ditems, p->d_scratch, p->d_records, p->d_status,  p->d_queue};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   p->d_uvw = nullptr;
@@ -157,6 +169,7 @@ void free_device(idg_plan* p) {
   p->d_scratch = nullptr;
   p->d_records = nullptr;
   p->d_status = nullptr;
+  p->d_queue = nullptr;
 }
 
 // Block geometry table, FP64 -> FP32: for each row j and block ib of 8
@@ -343,7 +356,7 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
   if (g->taper_kind == IDG_TAPER_USER)
     taper_d.assign(g->taper_user, g->taper_user + L);
   else
-    taper_d = kaiser_bessel_taper(L, g->taper_beta > 0.0 ? g->taper_beta : kPi * g->kernel_padding / 2.0);
+    taper_d = kaiser_bessel_taper(L, g->taper_beta > 0.0 ? g->taper_beta : 0.35 * kPi * g->kernel_padding);
   std::vector<float> taper_f(taper_d.begin(), taper_d.end());
   std::vector<float4> blk = block_geometry(L, g->image_size);
   std::vector<float2> tw(L);
@@ -351,7 +364,14 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     const double ang = -2.0 * kPi * double(m) / double(L);
     tw[m] = make_float2(float(std::cos(ang)), float(std::sin(ang)));
   }
+  int pg = 0, pd = 0;
   int e = configure_kernels(L);
+  if (!e) e = configure_gridder(L, &pg);
+  if (!e) e = configure_degridder(L, g->aterm_nodes, &pd);
+  if (g->flags & IDG_PERSISTENT) {
+    p->persistent_grid_blocks = pg;
+    p->persistent_degrid_blocks = pd;
+  }
   if (!e) e = upload(p, &p->d_uvw, uvw_m, size_t(n_baselines) * n_timesteps * 3);
   if (!e) e = upload(p, &p->d_fscale, fscale.data(), fscale.size());
   if (!e) e = upload(p, &p->d_taper, taper_f.data(), taper_f.size());
@@ -371,6 +391,10 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     if (!e) p->device_bytes += int64_t(rb);
   }
   if (!e) e = int(cudaMalloc(reinterpret_cast<void**>(&p->d_status), sizeof(int)));
+  if (!e && !p->batches.empty()) {
+    e = int(cudaMalloc(reinterpret_cast<void**>(&p->d_queue), sizeof(int) * 2 * p->batches.size()));
+    if (!e) p->device_bytes += int64_t(sizeof(int) * 2 * p->batches.size());
+  }
   if (!e) e = int(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
   if (!e) e = int(cudaStreamSynchronize(p->stream));
   if (e) {
@@ -439,11 +463,20 @@ idg_status idg_grid(idg_plan* plan, const void* vis_c64, const void* aterms_c64,
       (st = check_buffer(plan, grid_c128, "grid")))
     return st;
   const int L = plan->L;
-  for (const Batch& b : plan->batches) {
+  if (plan->persistent_grid_blocks > 0 && plan->d_queue) {
+    const int e = int(cudaMemsetAsync(plan->d_queue, 0, sizeof(int) * 2 * plan->batches.size(), plan->stream));
+    if (e) return cuda_err(plan, e, "work-queue reset");
+  }
+  for (size_t bi = 0; bi < plan->batches.size(); ++bi) {
+    const Batch& b = plan->batches[bi];
     GridArgs ga = grid_args(plan, b, vis_c64, aterms_c64);
+    ga.queue = plan->d_queue + 2 * bi;
+    ga.n_items = b.gi_count;
     int es = timed(plan, kStage, [&] { return launch_stage_records(L, stage_args(plan, b, vis_c64), b.sg_count, plan->stream); });
     if (es) return cuda_err(plan, es, "staging launch");
-    int e = timed(plan, kGridder, [&] { return launch_gridder(L, ga, b.gi_count, plan->stream); });
+    int e = timed(plan, kGridder, [&] {
+      return launch_gridder(L, ga, b.gi_count, plan->persistent_grid_blocks, plan->stream);
+    });
     if (e) return cuda_err(plan, e, "gridder launch");
     FftArgs fa{plan->d_sg + b.sg_offset, plan->d_scratch, static_cast<double2*>(grid_c128), plan->d_twiddle, plan->N};
     e = timed(plan, kFftAdder, [&] { return launch_fft_adder(L, fa, b.sg_count, 0, plan->stream); });
@@ -465,12 +498,19 @@ idg_status idg_degrid(idg_plan* plan, const void* grid_c128, const void* aterms_
     const int e = int(cudaMemsetAsync(vis_c64, 0, bytes, plan->stream));
     if (e) return cuda_err(plan, e, "zeroing dropped visibilities");
   }
-  for (const Batch& b : plan->batches) {
+  if (plan->persistent_degrid_blocks > 0 && plan->d_queue) {
+    const int e = int(cudaMemsetAsync(plan->d_queue, 0, sizeof(int) * 2 * plan->batches.size(), plan->stream));
+    if (e) return cuda_err(plan, e, "work-queue reset");
+  }
+  for (size_t bi = 0; bi < plan->batches.size(); ++bi) {
+    const Batch& b = plan->batches[bi];
     FftArgs fa{plan->d_sg + b.sg_offset, plan->d_scratch, const_cast<double2*>(static_cast<const double2*>(grid_c128)),
                plan->d_twiddle, plan->N};
     int e = timed(plan, kSplitter, [&] { return launch_splitter_ifft(L, fa, b.sg_count, plan->stream); });
     if (e) return cuda_err(plan, e, "splitter/ifft launch");
     DegridArgs da{};
+    da.queue = plan->d_queue + 2 * bi + 1;
+    da.n_items = b.di_count;
     da.vis = static_cast<float4*>(vis_c64);
     da.uvw = plan->d_uvw;
     da.fscale = plan->d_fscale;
@@ -482,7 +522,9 @@ idg_status idg_degrid(idg_plan* plan, const void* grid_c128, const void* aterms_
     da.blk = plan->d_blk;
     da.scratch = plan->d_scratch;
     da.g = kgeom(plan);
-    e = timed(plan, kDegridder, [&] { return launch_degridder(L, da, b.di_count, plan->stream); });
+    e = timed(plan, kDegridder, [&] {
+      return launch_degridder(L, da, b.di_count, plan->persistent_degrid_blocks, plan->stream);
+    });
     if (e) return cuda_err(plan, e, "degridder launch");
   }
   return IDG_OK;
@@ -505,7 +547,7 @@ idg_status idg_subgrid_images(idg_plan* plan, const void* vis_c64, const void* a
     GridArgs ga = grid_args(plan, b, vis_c64, aterms_c64);
     int es = timed(plan, kStage, [&] { return launch_stage_records(L, stage_args(plan, b, vis_c64), b.sg_count, plan->stream); });
     if (es) return cuda_err(plan, es, "staging launch");
-    e = launch_gridder(L, ga, b.gi_count, plan->stream);
+    e = launch_gridder(L, ga, b.gi_count, 0, plan->stream);
     if (e) return cuda_err(plan, e, "gridder launch");
     if (stage == 1) {
       FftArgs fa{plan->d_sg + b.sg_offset, plan->d_scratch, nullptr, plan->d_twiddle, plan->N};
@@ -517,6 +559,55 @@ idg_status idg_subgrid_images(idg_plan* plan, const void* vis_c64, const void* a
     if (e) return cuda_err(plan, e, "export launch");
   }
   return IDG_OK;
+}
+
+// Capture one whole grid or degrid call into a CUDA graph (once per buffer
+// set) and replay it.
+static idg_status run_graph(idg_plan* p, bool degrid, const void* x, const void* y, void* z) {
+  if (!p) return set_err(nullptr, IDG_ERR_INVALID_ARG, "plan is NULL");
+  if (p->host_only) return set_err(p, IDG_ERR_INVALID_ARG, "plan was created with IDG_HOST_ONLY");
+  if (!p->stream) return set_err(p, IDG_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+  idg_plan::GraphCache& gc = degrid ? p->graph_degrid : p->graph_grid;
+  if (!(gc.exec && gc.x == x && gc.y == y && gc.z == z)) {
+    if (gc.exec) cudaGraphExecDestroy(gc.exec);
+    gc = {};
+    const bool prof = p->profiling;
+    p->profiling = false;
+    int e = int(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    if (e) {
+      p->profiling = prof;
+      return cuda_err(p, e, "cudaStreamBeginCapture");
+    }
+    const idg_status st = degrid ? idg_degrid(p, x, y, z) : idg_grid(p, x, y, z);
+    cudaGraph_t graph = nullptr;
+    e = int(cudaStreamEndCapture(p->stream, &graph));
+    p->profiling = prof;
+    if (st != IDG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e) return cuda_err(p, e, "cudaStreamEndCapture");
+    e = int(cudaGraphInstantiate(&gc.exec, graph, 0));
+    cudaGraphDestroy(graph);
+    if (e) {
+      gc.exec = nullptr;
+      return cuda_err(p, e, "cudaGraphInstantiate");
+    }
+    gc.x = x;
+    gc.y = y;
+    gc.z = z;
+  }
+  const int e = int(cudaGraphLaunch(gc.exec, p->stream));
+  if (e) return cuda_err(p, e, "cudaGraphLaunch");
+  return IDG_OK;
+}
+
+idg_status idg_grid_graph(idg_plan* plan, const void* vis_c64, const void* aterms_c64, void* grid_c128) {
+  return run_graph(plan, false, vis_c64, aterms_c64, grid_c128);
+}
+
+idg_status idg_degrid_graph(idg_plan* plan, const void* grid_c128, const void* aterms_c64, void* vis_c64) {
+  return run_graph(plan, true, grid_c128, aterms_c64, vis_c64);
 }
 
 idg_status idg_synchronize(idg_plan* plan) {

@@ -102,6 +102,8 @@ struct StageArgs {
 struct GridArgs {
   const float4* records;      // staged visibility records of the batch
   int* status;                // device status word (kStatusTimeout)
+  int* queue;                 // work-queue counter (persistent launches), zero before the launch
+  int n_items;
   const float4* vis;          // [bl][t][ch][4] complex64, 2 float4 per visibility
   const double* uvw;          // [bl][t][3] metres
   const double* fscale;       // [ch] f / c
@@ -116,6 +118,8 @@ struct GridArgs {
 };
 
 struct DegridArgs {
+  int* queue;                 // work-queue counter (persistent launches), zero before the launch
+  int n_items;
   float4* vis;
   const double* uvw;
   const double* fscale;
@@ -138,9 +142,12 @@ struct FftArgs {
 };
 
 // Launchers (return cudaError_t as int).  `n` is the item or subgrid count.
-int launch_gridder(int L, const GridArgs& a, int n_items, void* stream);
+// persistent_blocks > 0: persistent launch of that many blocks draining a.queue
+int launch_gridder(int L, const GridArgs& a, int n_items, int persistent_blocks, void* stream);
+int configure_gridder(int L, int* persistent_blocks);   // attributes + persistent grid size
+int configure_degridder(int L, int nodes, int* persistent_blocks);
 int launch_stage_records(int L, const StageArgs& a, int n_subgrids, void* stream);
-int launch_degridder(int L, const DegridArgs& a, int n_items, void* stream);
+int launch_degridder(int L, const DegridArgs& a, int n_items, int persistent_blocks, void* stream);
 // mode 0: FFT + add into grid; mode 1: FFT in place in scratch (inspection)
 int launch_fft_adder(int L, const FftArgs& a, int n_subgrids, int mode, void* stream);
 int launch_splitter_ifft(int L, const FftArgs& a, int n_subgrids, void* stream);

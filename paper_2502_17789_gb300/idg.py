@@ -21,10 +21,10 @@ STATUS_NAMES = {0: "IDG_OK", 1: "IDG_ERR_INVALID_ARG", 2: "IDG_ERR_UNSORTED_FREQ
                 4: "IDG_ERR_W_TOO_LARGE", 5: "IDG_ERR_OOM", 6: "IDG_ERR_CUDA", 7: "IDG_ERR_TIMEOUT",
                 8: "IDG_ERR_UNSUPPORTED"}
 IDG_TAPER_KB, IDG_TAPER_USER = 0, 1
-IDG_DROP_OUT_OF_GRID, IDG_SPLIT_AT_ATERM_INTERVALS, IDG_HOST_ONLY = 1, 2, 4
+IDG_DROP_OUT_OF_GRID, IDG_SPLIT_AT_ATERM_INTERVALS, IDG_HOST_ONLY, IDG_PERSISTENT = 1, 2, 4, 8
 
 # every function declared in include/idg.h
-EXPORTS = ["idg_plan_create", "idg_grid", "idg_degrid", "idg_set_stream", "idg_plan_stats", "idg_plan_subgrids",
+EXPORTS = ["idg_plan_create", "idg_grid", "idg_degrid", "idg_grid_graph", "idg_degrid_graph", "idg_set_stream", "idg_plan_stats", "idg_plan_subgrids",
            "idg_plan_segments", "idg_subgrid_images", "idg_synchronize", "idg_profile_enable", "idg_profile_read",
            "idg_grid_noalloc", "idg_last_error",
            "idg_plan_destroy", "idg_abi_version"]
@@ -73,6 +73,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.idg_plan_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Geometry), i32, i32, i32, i32, P, P, P, P, i32, P]
     lib.idg_grid.argtypes = [P, P, P, P]
     lib.idg_degrid.argtypes = [P, P, P, P]
+    lib.idg_grid_graph.argtypes = [P, P, P, P]
+    lib.idg_degrid_graph.argtypes = [P, P, P, P]
     lib.idg_set_stream.argtypes = [P, P]
     lib.idg_plan_stats.argtypes = [P, ctypes.POINTER(PlanStats)]
     lib.idg_plan_subgrids.argtypes = [P, P, i64, ctypes.POINTER(i64)]
@@ -135,6 +137,14 @@ def idg_grid_noalloc(plan, vis_ptr, aterms_ptr, grid_ptr):
 
 def idg_degrid(plan, grid_ptr, aterms_ptr, vis_ptr):
     _check(load().idg_degrid(plan, grid_ptr, aterms_ptr, vis_ptr), "idg_degrid", plan)
+
+
+def idg_grid_graph(plan, vis_ptr, aterms_ptr, grid_ptr):
+    _check(load().idg_grid_graph(plan, vis_ptr, aterms_ptr, grid_ptr), "idg_grid_graph", plan)
+
+
+def idg_degrid_graph(plan, grid_ptr, aterms_ptr, vis_ptr):
+    _check(load().idg_degrid_graph(plan, grid_ptr, aterms_ptr, vis_ptr), "idg_degrid_graph", plan)
 
 
 def idg_set_stream(plan, stream):
@@ -238,7 +248,7 @@ class Plan:
                                                   aterm_nodes, flags)
         if stream is None and not (flags & IDG_HOST_ONLY):
             import torch
-            stream = torch.cuda.current_stream().cuda_stream
+            stream = torch.cuda.current_stream().cuda_stream  # 0 when that is the legacy default stream
         self.stream = stream
         self.handle = idg_plan_create(self.geometry, n_stations, baselines, uvw, freqs, aterm_offsets, stream)
         self.shape = (int(np.shape(uvw)[0]), int(np.shape(uvw)[1]), int(len(freqs)))
@@ -249,6 +259,14 @@ class Plan:
 
     def degrid(self, grid, aterms, vis):
         idg_degrid(self.handle, _dev_ptr(grid), _dev_ptr(aterms), _dev_ptr(vis))
+        return vis
+
+    def grid_graph(self, vis, aterms, grid):
+        idg_grid_graph(self.handle, _dev_ptr(vis), _dev_ptr(aterms), _dev_ptr(grid))
+        return grid
+
+    def degrid_graph(self, grid, aterms, vis):
+        idg_degrid_graph(self.handle, _dev_ptr(grid), _dev_ptr(aterms), _dev_ptr(vis))
         return vis
 
     def subgrid_images(self, vis, aterms, stage: int):

@@ -1,0 +1,160 @@
+"""Full-size parity on the MWA-like workload, in the launch configuration
+bench.py times (default plan: batches of 1 GiB of subgrid images), and the
+mixed-precision report with a 1000-source degrid -> grid round trip.
+
+At full size the oracle checks sampled outputs it can compute one subgrid at
+a time (degridded visibilities of a seeded, occupancy-stratified sample of
+subgrids); the full grid is checked through identities that hold at any
+size: the DC invariant and the adjoint identity."""
+import numpy as np
+import pytest
+
+from paper_2502_17789_gb300 import synth
+from tests import _brute
+
+pytestmark = pytest.mark.gpu
+
+GRID_TOL = 1e-5
+DEGRID_TOL = 1e-5
+
+
+def _subplan(oracle_mod, full, idx):
+    idx = np.sort(np.asarray(idx))
+    remap = {int(o): n for n, o in enumerate(idx)}
+    keep = np.isin(full.segments[:, 0], idx)
+    segs = full.segments[keep].copy()
+    segs[:, 0] = [remap[int(s)] for s in segs[:, 0]]
+    return oracle_mod.Plan(full.subgrids[idx].copy(), segs)
+
+
+def _stratified(rng, counts, n):
+    """n subgrid indices spread over the occupancy distribution."""
+    order = np.argsort(counts, kind="stable")
+    picks = [order[int(q)] for q in np.linspace(0, len(order) - 1, n)]
+    extra = rng.choice(len(order), size=n // 2, replace=False)
+    return np.unique(np.concatenate([picks, extra]))
+
+
+@pytest.fixture(scope="module")
+def mwa_full(idg_mod, oracle_mod, cuda_device):
+    import torch
+    obs = synth.config(2, seed=0)
+    rng = np.random.default_rng(0)
+    model = synth.beam_screen_model(rng, rms_rad=2.0)
+    A = synth.aterms_beam_screen(obs, model)
+    vis = synth.random_visibilities(rng, obs)
+    plan = idg_mod.Plan(obs)
+    geom = oracle_mod.Geometry(obs.grid_size, obs.subgrid_size, obs.kernel_padding, obs.image_size)
+    ref_plan = oracle_mod.plan(geom, obs.uvw, obs.freqs, obs.aterm_offsets)
+    yield dict(obs=obs, A=A, vis=vis, plan=plan, geom=geom, ref_plan=ref_plan,
+               A_d=torch.as_tensor(A).cuda(), vis_d=torch.as_tensor(vis).cuda())
+    plan.close()
+
+
+def test_full_size_plan_is_bit_exact(mwa_full):
+    np.testing.assert_array_equal(mwa_full["plan"].subgrids(), mwa_full["ref_plan"].subgrids)
+    np.testing.assert_array_equal(mwa_full["plan"].segments(), mwa_full["ref_plan"].segments)
+    st = mwa_full["plan"].stats()
+    assert st.n_batches > 1 and st.n_subgrids == mwa_full["ref_plan"].subgrids.shape[0]
+
+
+def test_full_size_degrid_sampled_subgrids(mwa_full, oracle_mod):
+    import torch
+    obs, plan = mwa_full["obs"], mwa_full["plan"]
+    N = obs.grid_size
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    G_d = torch.randn((4, N, N), dtype=torch.complex128, device="cuda", generator=g)
+    V_d = torch.empty_like(mwa_full["vis_d"])
+    plan.degrid(G_d, mwa_full["A_d"], V_d)
+    plan.synchronize()
+    V = V_d.cpu().numpy()
+    G = G_d.cpu().numpy()
+    full = mwa_full["ref_plan"]
+    counts = (full.subgrids[:, 2] - full.subgrids[:, 1]) * (full.subgrids[:, 4] - full.subgrids[:, 3])
+    idx = _stratified(np.random.default_rng(11), counts, 16)
+    sub = _subplan(oracle_mod, full, idx)
+    V_ref = oracle_mod.degrid(mwa_full["geom"], obs.n_stations, obs.baselines, obs.uvw, obs.freqs,
+                              obs.aterm_offsets, sub, G, mwa_full["A"].astype(np.complex128))
+    mask = np.zeros(V.shape[:3], bool)
+    for b, t0, t1, c0, c1, *_ in full.subgrids[idx]:
+        mask[b, t0:t1, c0:c1] = True
+    got, ref = V[mask], V_ref[mask]
+    err = np.sqrt(np.mean(np.abs(got - ref) ** 2)) / np.abs(ref).max()
+    assert err < DEGRID_TOL, err
+
+
+def test_full_size_grid_identities(mwa_full):
+    """DC invariant and adjoint identity on the full MWA-like workload."""
+    import torch
+    obs, plan, A = mwa_full["obs"], mwa_full["plan"], mwa_full["A"]
+    N, L = obs.grid_size, obs.subgrid_size
+    G_d = torch.zeros((4, N, N), dtype=torch.complex128, device="cuda")
+    plan.grid(mwa_full["vis_d"], mwa_full["A_d"], G_d)
+    plan.synchronize()
+    # DC invariant: sum G = L^2 T(0)^2 sum_seg A_p(0)^H (sum V) A_q(0), T(0) = 1
+    vis = mwa_full["vis"].astype(np.complex128)
+    full = mwa_full["ref_plan"]
+    c = obs.aterm_nodes // 2
+    Ac = A[:, :, c, c].astype(np.complex128).reshape(A.shape[0], A.shape[1], 2, 2)
+    # per (baseline, timestep) sums over channel ranges via cumulative sums
+    csum = np.concatenate([np.zeros(vis.shape[:2] + (1, 4), complex), np.cumsum(vis, axis=2)], axis=2)
+    want = np.zeros((2, 2), complex)
+    for (s, a, tb, te) in full.segments:
+        b, _, _, c0, c1 = full.subgrids[s, :5]
+        S = (csum[b, tb:te, c1] - csum[b, tb:te, c0]).sum(axis=0).reshape(2, 2)
+        p, q = obs.baselines[b]
+        want += Ac[a, p].conj().T @ S @ Ac[a, q]
+    got = G_d.sum(dim=(1, 2)).cpu().numpy().reshape(2, 2)
+    assert np.abs(got - L * L * want).max() / np.abs(L * L * want).max() < GRID_TOL
+    # adjoint identity with a random grid
+    g = torch.Generator(device="cuda")
+    g.manual_seed(9)
+    R = torch.randn((4, N, N), dtype=torch.complex128, device="cuda", generator=g)
+    V_d = torch.empty_like(mwa_full["vis_d"])
+    plan.degrid(R, mwa_full["A_d"], V_d)
+    plan.synchronize()
+    lhs = torch.vdot(V_d.reshape(-1).to(torch.complex128), mwa_full["vis_d"].reshape(-1).to(torch.complex128))
+    rhs = torch.vdot(R.reshape(-1), G_d.reshape(-1))
+    assert abs(complex(lhs) - complex(rhs)) / abs(complex(rhs)) < GRID_TOL
+
+
+def test_mixed_precision_round_trip(idg_mod, oracle_mod, cuda_device):
+    """Workload 3: FP32 phasors with FP64 subgrid offsets against the FP64
+    oracle, on a 1000-source model: model grid -> degrid -> grid."""
+    import torch
+    obs = synth.config(3, seed=0, n_stations=16)
+    rng = np.random.default_rng(3)
+    model = synth.beam_screen_model(rng, rms_rad=2.0)
+    A = synth.aterms_beam_screen(obs, model)
+    N, L, fov = obs.grid_size, obs.subgrid_size, obs.image_size
+    sky = synth.point_sources(rng, 1000, 0.16)
+    # model image / T transformed to the grid: sum_s S_s/(T(l)T(m)) e^{-2 pi i (u l + v m)}
+    beta = oracle_mod.Geometry(obs.grid_size, obs.subgrid_size, obs.kernel_padding, obs.image_size).beta
+    import scipy.special
+    T = lambda x: scipy.special.i0(beta * np.sqrt(1 - (2 * x / fov) ** 2)) / scipy.special.i0(beta)
+    u = (np.arange(N) - N // 2) / fov
+    ex = np.exp(-2j * np.pi * np.outer(u, sky.l))
+    ey = np.exp(-2j * np.pi * np.outer(u, sky.m))
+    G_model = np.zeros((4, N, N), complex)
+    w = sky.flux / (T(sky.l) * T(sky.m))
+    G_model[0] = (ey * w) @ ex.T
+    G_model[3] = G_model[0]
+    plan = idg_mod.Plan(obs)
+    geom = oracle_mod.Geometry(obs.grid_size, L, obs.kernel_padding, fov)
+    pl = oracle_mod.plan(geom, obs.uvw, obs.freqs, obs.aterm_offsets)
+    args = (geom, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets, pl)
+    A_d = torch.as_tensor(A).cuda()
+    V_d = torch.empty((obs.n_baselines, obs.n_timesteps, obs.n_channels, 4), dtype=torch.complex64, device="cuda")
+    plan.degrid(torch.as_tensor(G_model).cuda(), A_d, V_d)
+    G_d = torch.zeros((4, N, N), dtype=torch.complex128, device="cuda")
+    plan.grid(V_d, A_d, G_d)
+    plan.synchronize()
+    V_gpu, G_gpu = V_d.cpu().numpy(), G_d.cpu().numpy()
+    V_ref = oracle_mod.degrid(*args, G_model, A.astype(np.complex128))
+    G_ref = oracle_mod.grid(*args, V_gpu.astype(np.complex128), A.astype(np.complex128))
+    deg_err = np.sqrt(np.mean(np.abs(V_gpu - V_ref) ** 2)) / np.abs(V_ref).max()
+    grid_err = np.linalg.norm(G_gpu - G_ref) / np.linalg.norm(G_ref)
+    print(f"mixed precision: degrid rms/peak {deg_err:.2e}, grid rel {grid_err:.2e}")
+    assert deg_err < DEGRID_TOL and grid_err < GRID_TOL
+    plan.close()

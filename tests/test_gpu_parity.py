@@ -214,3 +214,56 @@ def test_invalid_arguments_return_status(idg_mod, cuda_device):
     assert lib.idg_degrid(None, None, None, None) == 1
     assert "NULL" in idg_mod.idg_last_error(None)
     assert lib.idg_subgrid_images(plan.handle, ctypes.c_void_p(16), ctypes.c_void_p(16), 5, ctypes.c_void_p(16)) == 1
+
+
+def test_persistent_queue_and_graph_replay(idg_mod, oracle_mod, cuda_device):
+    """The batched forms (persistent work-queue launches, CUDA-graph replay of
+    a whole call) give the oracle's result, on a plan with several batches."""
+    import os
+    import torch
+    obs = synth.config(2, n_stations=14, n_timesteps=16, n_channels=24)
+    A, vis = _random_problem(31, obs, n_int=4)
+    os.environ["IDG_SCRATCH_BYTES"] = str(64 * 4 * 96 * 96 * 8)  # 64 subgrids per batch
+    try:
+        c = Case(idg_mod, oracle_mod, obs, A, vis)
+        stream = torch.cuda.Stream()
+        pp = idg_mod.Plan(obs, flags=idg_mod.IDG_PERSISTENT, stream=stream.cuda_stream)
+    finally:
+        del os.environ["IDG_SCRATCH_BYTES"]
+    assert pp.stats().n_batches > 1
+    G_ref = c.oracle_grid()
+    N = obs.grid_size
+    rng = np.random.default_rng(3)
+    Gin = rng.standard_normal((4, N, N)) + 1j * rng.standard_normal((4, N, N))
+    V_ref = c.oracle_degrid(Gin)
+    Gin_d = torch.as_tensor(Gin).cuda()
+    with torch.cuda.stream(stream):
+        for use_graph in (False, True, True):
+            G = torch.zeros((4, N, N), dtype=torch.complex128, device="cuda")
+            V = torch.full(vis.shape, 7.0, dtype=torch.complex64, device="cuda")
+            if use_graph:
+                pp.grid_graph(c.vis_d, c.A_d, G)
+                pp.degrid_graph(Gin_d, c.A_d, V)
+            else:
+                pp.grid(c.vis_d, c.A_d, G)
+                pp.degrid(Gin_d, c.A_d, V)
+            pp.synchronize()
+            assert _rel(G.cpu().numpy(), G_ref) < GRID_TOL
+            assert _degrid_err(V.cpu().numpy(), V_ref) < DEGRID_TOL
+        # graph replay with the same buffers accumulates again into G
+        pp.grid_graph(c.vis_d, c.A_d, G)
+        pp.synchronize()
+        assert _rel(G.cpu().numpy(), 2 * G_ref) < GRID_TOL
+    pp.close()
+
+
+def test_graph_needs_a_stream(idg_mod, cuda_device):
+    import torch
+    obs = synth.config(1, n_stations=4)
+    plan = idg_mod.Plan(obs, stream=0)
+    v = torch.zeros((obs.n_baselines, obs.n_timesteps, obs.n_channels, 4), dtype=torch.complex64, device="cuda")
+    A = torch.as_tensor(synth.aterms_identity(1, obs.n_stations)).cuda()
+    G = torch.zeros((4, obs.grid_size, obs.grid_size), dtype=torch.complex128, device="cuda")
+    with pytest.raises(idg_mod.IdgError) as e:
+        plan.grid_graph(v, A, G)
+    assert e.value.status == 1

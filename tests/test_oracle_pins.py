@@ -325,3 +325,24 @@ def test_subgrid_images_match_grid(oracle_mod):
         x0, y0 = row[5], row[6]
         G2[:, y0:y0 + L, x0:x0 + L] += uv[s]
     assert _relerr(G, G2) < 1e-14
+
+
+def test_degrid_off_grid_sources_within_aliasing_bound(oracle_mod):
+    """Point sources anywhere in the central 1/1.5 of the field (not on the
+    coarse grid): the oracle's degridded model, transformed with 1/T, agrees
+    with Eq. 1 to the taper kernel's aliasing level, 1e-7 at P = 18 with the
+    default beta = 0.35 pi P (the table in the design doc)."""
+    obs = _tiny(seed=8, n_st=5, n_t=4, n_ch=3, N=1024, L=96, P=18, fov=0.5, diameter=400.0)
+    geom = _geom(oracle_mod, obs)
+    pl = oracle_mod.plan(geom, obs.uvw, obs.freqs, obs.aterm_offsets)
+    A = synth.aterms_identity(obs.n_intervals, obs.n_stations).astype(np.complex128)
+    N, L, fov = obs.grid_size, obs.subgrid_size, obs.image_size
+    T = lambda x: scipy.special.i0(geom.beta * np.sqrt(1 - (2 * x / fov) ** 2)) / scipy.special.i0(geom.beta)
+    u = (np.arange(N) - N // 2) / fov
+    for (l, m) in [(0.1113, -0.0719), (-0.16, 0.155), (0.0533, 0.1499)]:
+        G = np.zeros((4, N, N), complex)
+        G[0] = np.outer(np.exp(-2j * np.pi * u * m), np.exp(-2j * np.pi * u * l)) / (T(l) * T(m))
+        G[3] = G[0]
+        V = _degrid(oracle_mod, obs, geom, pl, G, A)
+        want = L * L * _brute.measurement_equation(obs, A, l, m, np.eye(2))
+        assert np.abs(V - want).max() / np.abs(want).max() < 1e-6
