@@ -112,7 +112,8 @@ typedef struct {
  * and carry one segment per A-term interval they cover.  Fails with
  * IDG_ERR_UNSORTED_FREQ, IDG_ERR_UV_OUT_OF_GRID, IDG_ERR_W_TOO_LARGE,
  * IDG_ERR_INVALID_ARG, IDG_ERR_UNSUPPORTED, IDG_ERR_OOM or IDG_ERR_CUDA.
- * Synchronises the stream (uploads the plan tables).
+ * Device memory comes from the stream-ordered allocator (cudaMallocAsync on
+ * cuda_stream).  Synchronises the stream (uploads the plan tables).
  */
 idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stations, int32_t n_baselines,
                            int32_t n_timesteps, int32_t n_channels, const int32_t* baselines,
@@ -228,7 +229,8 @@ idg_status idg_grid_noalloc(idg_plan* plan, const void* vis_c64, const void* ate
 /* Message for the last failure (never NULL; "" when none). */
 const char* idg_last_error(const idg_plan* plan);
 
-/* Release the plan and its device memory (synchronises its stream). NULL is a no-op. */
+/* Release the plan and its device memory (stream-ordered frees on the plan's
+ * stream, which is synchronised; other streams are not). NULL is a no-op. */
 idg_status idg_plan_destroy(idg_plan* plan);
 
 /* Library version (IDG_ABI_VERSION). */

@@ -107,7 +107,7 @@ int upload(idg_plan* p, T** dst, const T* src, size_t n) {
     *dst = nullptr;
     return 0;
   }
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), n * sizeof(T));
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(dst), n * sizeof(T), p->stream);
   if (e != cudaSuccess) return int(e);
   p->device_bytes += int64_t(n * sizeof(T));
   return int(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, p->stream));
@@ -155,8 +155,10 @@ void free_device(idg_plan* p) {
   p->graph_degrid = {};
   void* ptrs[] = {p->d_uvw,    p->d_fscale, p->d_taper,   p->d_blk,     p->d_twiddle, p->d_sg,     p->d_seg,
                   p->d_gitems, p->d_ditems, p->d_scratch, p->d_records, p->d_status,  p->d_queue};
+  // stream-ordered frees: no device-wide synchronisation, so plans of other
+  // streams keep running while this one is released
   for (void* q : ptrs)
-    if (q) cudaFree(q);
+    if (q) cudaFreeAsync(q, p->stream);
   p->d_uvw = nullptr;
   p->d_fscale = nullptr;
   p->d_taper = nullptr;
@@ -382,17 +384,17 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
   if (!e) e = upload(p, &p->d_gitems, gitems.data(), gitems.size());
   if (!e) e = upload(p, &p->d_ditems, ditems.data(), ditems.size());
   if (!e && !p->exec.empty()) {
-    e = int(cudaMalloc(reinterpret_cast<void**>(&p->d_scratch), per_sg * p->batch_cap));
+    e = int(cudaMallocAsync(reinterpret_cast<void**>(&p->d_scratch), per_sg * p->batch_cap, p->stream));
     if (!e) p->device_bytes += int64_t(per_sg * p->batch_cap);
   }
   if (!e && p->max_batch_vis > 0) {
     const size_t rb = size_t(p->max_batch_vis) * kRecordFloat4 * sizeof(float4);
-    e = int(cudaMalloc(reinterpret_cast<void**>(&p->d_records), rb));
+    e = int(cudaMallocAsync(reinterpret_cast<void**>(&p->d_records), rb, p->stream));
     if (!e) p->device_bytes += int64_t(rb);
   }
-  if (!e) e = int(cudaMalloc(reinterpret_cast<void**>(&p->d_status), sizeof(int)));
+  if (!e) e = int(cudaMallocAsync(reinterpret_cast<void**>(&p->d_status), sizeof(int), p->stream));
   if (!e && !p->batches.empty()) {
-    e = int(cudaMalloc(reinterpret_cast<void**>(&p->d_queue), sizeof(int) * 2 * p->batches.size()));
+    e = int(cudaMallocAsync(reinterpret_cast<void**>(&p->d_queue), sizeof(int) * 2 * p->batches.size(), p->stream));
     if (!e) p->device_bytes += int64_t(sizeof(int) * 2 * p->batches.size());
   }
   if (!e) e = int(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
@@ -412,6 +414,7 @@ idg_status idg_plan_destroy(idg_plan* plan) {
   if (!plan->host_only) cudaStreamSynchronize(plan->stream);
   release_events(plan);
   free_device(plan);
+  if (!plan->host_only) cudaStreamSynchronize(plan->stream);
   delete plan;
   return IDG_OK;
 }

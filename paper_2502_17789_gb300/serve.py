@@ -1,0 +1,312 @@
+"""Serving loop: continuous batching of imaging requests on one GPU.
+
+A request grids the visibilities of one snapshot observation (or degrids a
+model grid into them).  Requests arrive as a Poisson stream.  The server
+admits a request when its device footprint fits the HBM budget and a slot is
+free; every admitted request runs on its own CUDA stream, so work of requests
+that arrive while others are on the GPU overlaps on the device (continuous
+batching at the granularity of the library's kernels).  Its plan,
+visibilities and grid stay resident until its result has been copied back;
+then the memory and the slot are released and the next waiting request is
+admitted.  Plan creation (host partitioning) runs on a thread pool so it
+overlaps GPU work.  The "plain" mode runs one request at a time on one
+stream: the per-request baseline.
+
+Failures stay on the host: a request whose footprint can never fit is
+rejected, a cancelled request is skipped, and a plan that cannot be made
+(for example IDG_ERR_W_TOO_LARGE) fails that request only.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import idg, synth
+
+GRID_BYTES_PER_CELL = 4 * 16  # complex128, 4 correlations
+
+
+@dataclass
+class Request:
+    """One snapshot request.  Its input (visibilities of a grid request, the
+    model grid of a degrid request) is synthesised on the device when the
+    request is admitted, from `seed` -- a stand-in for data arriving from the
+    correlator or left on the GPU by the previous imaging cycle."""
+    rid: int
+    kind: str                       # "grid" or "degrid"
+    obs: synth.Observation
+    arrival: float                  # seconds after the start of the stream
+    aterms: np.ndarray              # complex64 [n_int][n_st][nodes][nodes][4]
+    seed: int = 0
+    cancelled: bool = False
+
+
+@dataclass
+class Result:
+    rid: int
+    kind: str
+    status: str                     # "ok", "rejected", "cancelled", "failed: ..."
+    n_vis: int = 0
+    arrival: float = 0.0
+    admitted: float = 0.0
+    finished: float = 0.0
+    output: np.ndarray | None = None
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+def footprint_bytes(req: Request) -> int:
+    """Device memory a request holds while resident: its input and output
+    arrays, the plan's subgrid scratch (bounded by the 1 GiB batch budget),
+    staged records and tables."""
+    o = req.obs
+    vis = o.n_vis * 32
+    grid = o.grid_size * o.grid_size * GRID_BYTES_PER_CELL
+    per_sg = 4 * o.subgrid_size ** 2 * 8
+    # subgrids <= visibilities; the plan's scratch holds at most 1 GiB of images
+    scratch = min(1 << 30, max(1, o.n_vis) * per_sg)
+    records = o.n_vis * 128
+    tables = o.uvw.nbytes + (64 << 20)
+    return int(vis + grid + scratch + records + tables + req.aterms.nbytes)
+
+
+def request_shape(n_st, n_ch, n_t):
+    return n_st * (n_st - 1) // 2 * n_ch * n_t
+
+
+@dataclass
+class _Slot:
+    req: Request
+    admitted: float
+    future: cf.Future | None = None
+    plan: idg.Plan | None = None
+    stream: object = None
+    event: object = None
+    bufs: dict = field(default_factory=dict)
+    host_out: object = None
+
+
+class Server:
+    def __init__(self, hbm_budget_bytes: int = 64 << 30, max_slots: int = 8, mode: str = "batched",
+                 device: int = 0, keep_outputs: bool = True, plan_workers: int = 4):
+        import torch
+
+        if mode not in ("batched", "plain"):
+            raise ValueError("mode must be 'batched' or 'plain'")
+        self.torch = torch
+        self.budget = int(hbm_budget_bytes)
+        self.max_slots = 1 if mode == "plain" else int(max_slots)
+        self.mode = mode
+        self.device = torch.device("cuda", device)
+        self.keep_outputs = keep_outputs
+        self.plan_workers = plan_workers
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(self.max_slots)]
+
+    # ---------------------------------------------------------------- request lifecycle
+
+    def _make_plan(self, req: Request, stream_handle: int):
+        return idg.Plan(req.obs, stream=stream_handle)
+
+    def _launch(self, slot: _Slot):
+        torch = self.torch
+        req = slot.req
+        o = req.obs
+        with torch.cuda.stream(slot.stream):
+            A = torch.as_tensor(req.aterms).to(self.device, non_blocking=True)
+            N = o.grid_size
+            gen = torch.Generator(device=self.device)
+            gen.manual_seed(req.seed)
+            if req.kind == "grid":
+                vis = torch.randn((o.n_baselines, o.n_timesteps, o.n_channels, 4), dtype=torch.complex64,
+                                  device=self.device, generator=gen)
+                G = torch.zeros((4, N, N), dtype=torch.complex128, device=self.device)
+                slot.plan.grid(vis, A, G)
+                out = torch.empty(G.shape, dtype=G.dtype, pin_memory=True)
+                out.copy_(G, non_blocking=True)
+                slot.bufs = {"A": A, "vis": vis, "G": G}
+            else:
+                # model: a few point sources in the central third of the field,
+                # sum_s a_s exp(-2 pi i (u l_s + v m_s)) on every grid cell
+                u = (torch.arange(N, device=self.device, dtype=torch.float64) - N // 2) / o.image_size
+                lm = (torch.rand((4, 2), device=self.device, dtype=torch.float64, generator=gen) - 0.5) \
+                    * (o.image_size / 1.5)
+                amp = torch.randn((4,), dtype=torch.complex128, device=self.device, generator=gen)
+                ex = torch.polar(torch.ones_like(u)[None, :].expand(4, N), -2 * np.pi * lm[:, :1] * u[None, :])
+                ey = torch.polar(torch.ones_like(u)[None, :].expand(4, N), -2 * np.pi * lm[:, 1:] * u[None, :])
+                G = torch.zeros((4, N, N), dtype=torch.complex128, device=self.device)
+                G[0] = torch.einsum("s,sy,sx->yx", amp, ey, ex)
+                G[3] = G[0]
+                vis = torch.empty((o.n_baselines, o.n_timesteps, o.n_channels, 4), dtype=torch.complex64,
+                                  device=self.device)
+                slot.plan.degrid(G, A, vis)
+                out = torch.empty(vis.shape, dtype=vis.dtype, pin_memory=True)
+                out.copy_(vis, non_blocking=True)
+                slot.bufs = {"A": A, "vis": vis, "G": G}
+            slot.host_out = out
+            slot.event = torch.cuda.Event()
+            slot.event.record(slot.stream)
+
+    def run(self, requests: list[Request]) -> list[Result]:
+        """Serve `requests` (arrival times relative to now); returns one
+        Result per request in request order."""
+        torch = self.torch
+        pending = sorted(requests, key=lambda r: r.arrival)
+        queue: list[Request] = []
+        running: list[_Slot] = []
+        free_streams = list(self.streams)
+        used = 0
+        results: dict[int, Result] = {}
+        pool = cf.ThreadPoolExecutor(max_workers=self.plan_workers)
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0
+        try:
+            while pending or queue or running:
+                t = now()
+                while pending and pending[0].arrival <= t:
+                    queue.append(pending.pop(0))
+                # admission, first come first served
+                while queue and free_streams:
+                    req = queue[0]
+                    if req.cancelled:
+                        queue.pop(0)
+                        results[req.rid] = Result(req.rid, req.kind, "cancelled", req.obs.n_vis, req.arrival)
+                        continue
+                    need = footprint_bytes(req)
+                    if need > self.budget:
+                        queue.pop(0)
+                        results[req.rid] = Result(req.rid, req.kind, "rejected: footprint exceeds the HBM budget",
+                                                  req.obs.n_vis, req.arrival)
+                        continue
+                    if used + need > self.budget:
+                        break
+                    queue.pop(0)
+                    stream = free_streams.pop()
+                    slot = _Slot(req, now(), stream=stream)
+                    slot.future = pool.submit(self._make_plan, req, stream.cuda_stream)
+                    running.append(slot)
+                    used += need
+                progressed = False
+                for slot in list(running):
+                    if slot.plan is None and slot.future is not None and slot.future.done():
+                        try:
+                            slot.plan = slot.future.result()
+                        except idg.IdgError as e:
+                            running.remove(slot)
+                            used -= footprint_bytes(slot.req)
+                            free_streams.append(slot.stream)
+                            results[slot.req.rid] = Result(slot.req.rid, slot.req.kind, f"failed: {e}",
+                                                           slot.req.obs.n_vis, slot.req.arrival, slot.admitted,
+                                                           now())
+                            progressed = True
+                            continue
+                        self._launch(slot)
+                        progressed = True
+                    elif slot.event is not None and slot.event.query():
+                        slot.plan.synchronize()
+                        r = Result(slot.req.rid, slot.req.kind, "ok", slot.req.obs.n_vis, slot.req.arrival,
+                                   slot.admitted, now(), slot.host_out.numpy() if self.keep_outputs else None)
+                        results[r.rid] = r
+                        slot.plan.close()
+                        slot.bufs.clear()
+                        running.remove(slot)
+                        used -= footprint_bytes(slot.req)
+                        free_streams.append(slot.stream)
+                        progressed = True
+                if not progressed:
+                    time.sleep(0.0002)
+        finally:
+            pool.shutdown(wait=True)
+            torch.cuda.synchronize(self.device)
+        return [results[r.rid] for r in requests]
+
+
+# -------------------------------------------------------------------- workload
+
+def make_stream(n_requests: int = 200, seed: int = 0, rate_hz: float = 2.0, stations=(64, 256),
+                channels=(8, 48), timesteps=(8, 120), kinds=("grid", "degrid")) -> list[Request]:
+    """Poisson stream of snapshot requests mixing the small (512^2, L=32) and
+    MWA-like (4096^2, L=96) geometries, half grid half degrid."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    reqs = []
+    for rid in range(n_requests):
+        t += rng.exponential(1.0 / rate_hz)
+        n_st = int(rng.integers(stations[0], stations[1] + 1))
+        n_ch = int(rng.integers(channels[0], channels[1] + 1))
+        n_t = int(rng.integers(timesteps[0], timesteps[1] + 1))
+        kind = kinds[int(rng.integers(0, len(kinds)))]
+        geo = int(rng.integers(0, 3))  # 0: small geometry, 1 and 2: MWA-like
+        sub = int(rng.integers(0, 1 << 30))
+        if geo == 0:
+            obs = synth.config(1, seed=sub, n_stations=n_st, n_timesteps=n_t, n_channels=n_ch)
+        else:
+            obs = synth.config(2, seed=sub, n_stations=n_st, n_timesteps=n_t, n_channels=n_ch)
+        r2 = np.random.default_rng(sub)
+        A = synth.aterms_random(r2, obs.n_intervals, obs.n_stations, obs.aterm_nodes, leakage=0.05)
+        reqs.append(Request(rid, kind, obs, t, A, seed=sub))
+    return reqs
+
+
+def summarize(results: list[Result], t_wall: float | None = None) -> dict:
+    ok = [r for r in results if r.status == "ok"]
+    lat = np.array([r.latency for r in ok]) if ok else np.array([np.nan])
+    span = (max(r.finished for r in ok) - min(r.arrival for r in ok)) if ok else float("nan")
+    return {"requests": len(results), "ok": len(ok),
+            "rejected": sum(r.status.startswith("rejected") for r in results),
+            "failed": sum(r.status.startswith("failed") for r in results),
+            "cancelled": sum(r.status == "cancelled" for r in results),
+            "vis": int(sum(r.n_vis for r in ok)), "makespan_s": span,
+            "throughput_vis_per_s": (sum(r.n_vis for r in ok) / span) if ok else 0.0,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99))}
+
+
+def main(argv=None):
+    import argparse
+    import json
+
+    import torch
+
+    from . import build
+
+    ap = argparse.ArgumentParser(description="IDG serving benchmark: batched vs plain on one GPU")
+    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--load", type=float, default=0.7, help="arrival rate as a fraction of plain capacity")
+    ap.add_argument("--saturated-load", type=float, default=2.0, help="second, saturating arrival rate")
+    ap.add_argument("--budget-gb", type=float, default=64.0)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--stations", type=int, nargs=2, default=(64, 256))
+    ap.add_argument("--channels", type=int, nargs=2, default=(8, 48))
+    ap.add_argument("--timesteps", type=int, nargs=2, default=(8, 120))
+    args = ap.parse_args(argv)
+    build.build()
+    torch.cuda.init()
+    shape = dict(stations=tuple(args.stations), channels=tuple(args.channels), timesteps=tuple(args.timesteps))
+    # calibration: plain capacity (requests per second) on a few requests arriving at once
+    calib = make_stream(min(8, args.requests), seed=args.seed + 1000, rate_hz=1e9, **shape)
+    plain = Server(int(args.budget_gb * 2**30), mode="plain", keep_outputs=False)
+    Server(int(args.budget_gb * 2**30), mode="plain", keep_outputs=False).run(calib[:1])  # warm-up
+    t = time.perf_counter()
+    plain.run(calib)
+    cap = len(calib) / (time.perf_counter() - t)
+    rate = args.load * cap
+    out = {"calibration_plain_requests_per_s": cap, "shape": shape, "budget_gb": args.budget_gb,
+           "slots": args.slots}
+    for load in (args.load, args.saturated_load):
+        key = f"load_{load:g}"
+        out[key] = {"arrival_rate_hz": load * cap}
+        for mode in ("plain", "batched"):
+            stream = make_stream(args.requests, seed=args.seed, rate_hz=load * cap, **shape)
+            srv = Server(int(args.budget_gb * 2**30), max_slots=args.slots, mode=mode, keep_outputs=False)
+            out[key][mode] = summarize(srv.run(stream))
+            del stream
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
