@@ -203,7 +203,7 @@ def run_native(args):
     import torch.distributed as dist
 
     from paper_2502_17789_gb300 import build as libbuild
-    from paper_2502_17789_gb300 import idg
+    from paper_2502_17789_gb300 import idg, parallel
 
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
@@ -252,9 +252,7 @@ def run_native(args):
     prof = plan.profile_read()
     plan.profile(False)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = parallel.max_over_ranks(ms, device=dev)
     total_vis = 2.0 * obs.n_vis * args.steps * world
     value = total_vis / (ms * 1e-3)
 
@@ -319,9 +317,7 @@ def run_native(args):
         torch.cuda.synchronize(dev)
         e2e_ms = e0.elapsed_time(e1)
         if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+            e2e_ms = parallel.max_over_ranks(e2e_ms, device=dev)
         e2e = {"value": 2.0 * obs.n_vis * args.e2e_steps * world / (e2e_ms * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(vis_h.numel() * 8 + gmodel_h.numel() * 16),
                "d2h_bytes_per_step": int(gout_h.numel() * 16 + vpred_h.numel() * 8),
