@@ -58,12 +58,15 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (small profiling runs)")
     ap.add_argument("--stations", type=int, default=None, help="reduce the workload's stations (profiling)")
     ap.add_argument("--timesteps", type=int, default=None, help="reduce the workload's timesteps (profiling)")
+    ap.add_argument("--aterms", choices=["beam", "full"], default="beam",
+                    help="beam: the scalar beam x screen gain (diagonal Jones); full: the same plus 5%% "
+                         "polarisation leakage, so every Jones matrix is full")
     return ap.parse_args()
 
 
 # --------------------------------------------------------------------------- workload
 
-def make_workload(idx: int, device, stations=None, timesteps=None):
+def make_workload(idx: int, device, stations=None, timesteps=None, aterm_kind="beam"):
     import torch
     from paper_2502_17789_gb300 import synth
 
@@ -81,6 +84,9 @@ def make_workload(idx: int, device, stations=None, timesteps=None):
             2: "128 stations in a 3 km disk (8128 baselines), 56 x 2 s, 24 ch 140-170 MHz, 4096^2 FP64 grid, "
                "L=96, P=18, FOV 0.5, A-terms per 8 s on 9x9 nodes (Gaussian beam x Kolmogorov screen, 2 rad rms), "
                "200 sources + 1 Jy noise"}.get(idx, obs.name)
+    if aterm_kind == "full":
+        aterms = synth.aterms_with_leakage(np.random.default_rng(1), aterms, 0.05)
+        desc += ", full-Jones A-terms (5% leakage)"
     if stations or timesteps:
         desc = f"REDUCED ({obs.n_stations} stations, {obs.n_timesteps} timesteps) " + desc
     return obs, torch.as_tensor(aterms, device=device), vis, desc
@@ -213,7 +219,7 @@ def run_native(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     libbuild.build()
-    obs, A_d, vis_d, desc = make_workload(args.workload, dev, args.stations, args.timesteps)
+    obs, A_d, vis_d, desc = make_workload(args.workload, dev, args.stations, args.timesteps, args.aterms)
     stream = torch.cuda.current_stream(dev)
     plan = idg.Plan(obs, stream=stream.cuda_stream)
     st = plan.stats()

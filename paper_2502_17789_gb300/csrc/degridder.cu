@@ -46,6 +46,8 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
   const int n_vg = (nv + 31) >> 5;  // groups of 32 visibilities, 1..8
   const int nodes = a.g.nodes;
   const int nA = nodes * nodes * 4;
+  // uniform over the block: both stations' A-terms diagonal -> quarter of the Jones work
+  const bool diag = a.adiag[seg.interval * a.g.n_st + sd.p] && a.adiag[seg.interval * a.g.n_st + sd.q];
 
   {
     const float2* Ap = a.aterms + (size_t(seg.interval) * a.g.n_st + sd.p) * nA;
@@ -113,9 +115,14 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
         Yp.m[p] = {y.x, y.y};
       }
       const NodeWeight wx = node_weight(ii, nodes, L);
-      const Jones Apj = interp_jones(s_A, nodes, wx, wy);
-      const Jones Aqj = interp_jones(s_A + nA, nodes, wx, wy);
-      const Jones Z = jmul_bh(jmul(Apj, Yp), Aqj);
+      Jones Z;
+      if (diag) {
+        Z = jdiag_a_y_bh(interp_diag(s_A, nodes, wx, wy), Yp, interp_diag(s_A + nA, nodes, wx, wy));
+      } else {
+        const Jones Apj = interp_jones(s_A, nodes, wx, wy);
+        const Jones Aqj = interp_jones(s_A + nA, nodes, wx, wy);
+        Z = jmul_bh(jmul(Apj, Yp), Aqj);
+      }
       const float wgt = a.taper[ii] * tj * (((ii + j) & 1) ? -1.f : 1.f);
 #pragma unroll
       for (int p = 0; p < 4; ++p) {

@@ -59,6 +59,28 @@ __global__ void __launch_bounds__(256) stage_records_kernel(const StageArgs a, i
   }
 }
 
+// one warp per (interval, station): are all off-diagonal node entries zero?
+__global__ void aterm_flags_kernel(const float2* aterms, uint8_t* flags, int n_pairs, int nodes) {
+  const int pair = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (pair >= n_pairs) return;
+  const float2* A = aterms + size_t(pair) * nodes * nodes * 4;
+  bool diag = true;
+  for (int n = lane; n < nodes * nodes; n += 32) {
+    const float2 b = A[n * 4 + 1], c = A[n * 4 + 2];
+    diag = diag && b.x == 0.f && b.y == 0.f && c.x == 0.f && c.y == 0.f;
+  }
+  diag = __all_sync(0xffffffffu, diag);
+  if (lane == 0) flags[pair] = diag ? 1 : 0;
+}
+
+int launch_aterm_flags(const float2* aterms, uint8_t* flags, int n_int, int n_st, int nodes, void* stream) {
+  const int n = n_int * n_st;
+  if (n <= 0) return 0;
+  aterm_flags_kernel<<<(n + 7) / 8, 256, 0, cudaStream_t(stream)>>>(aterms, flags, n, nodes);
+  return int(cudaGetLastError());
+}
+
 int launch_stage_records(int L, const StageArgs& a, int n_subgrids, void* stream) {
   if (n_subgrids <= 0) return 0;
   stage_records_kernel<<<n_subgrids, 256, 0, cudaStream_t(stream)>>>(a, L);
@@ -225,20 +247,27 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
       const float2* Aq = a.aterms + (size_t(seg.interval) * a.g.n_st + sd.q) * nA;
       const NodeWeight wy = node_weight(j, nodes, L);
       const float tj = a.taper[j];
+      // uniform over the block: both stations' A-terms diagonal -> quarter of the Jones work
+      const bool diag = a.adiag[seg.interval * a.g.n_st + sd.p] && a.adiag[seg.interval * a.g.n_st + sd.q];
 #pragma unroll
       for (int px = 0; px < 8; ++px) {
         const int i = i0 + px;
         const int q = px >> 1;
         const NodeWeight wx = node_weight(i, nodes, L);
-        const Jones Apj = interp_jones_ldg(Ap, nodes, wx, wy);
-        const Jones Aqj = interp_jones_ldg(Aq, nodes, wx, wy);
         Jones X;
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
           X.m[p].re = (px & 1) ? RE[p][q].y : RE[p][q].x;
           X.m[p].im = (px & 1) ? IM[p][q].y : IM[p][q].x;
         }
-        const Jones E = jmul_ah(Apj, jmul(X, Aqj));
+        Jones E;
+        if (diag) {
+          E = jdiag_ah_x_b(interp_diag_ldg(Ap, nodes, wx, wy), X, interp_diag_ldg(Aq, nodes, wx, wy));
+        } else {
+          const Jones Apj = interp_jones_ldg(Ap, nodes, wx, wy);
+          const Jones Aqj = interp_jones_ldg(Aq, nodes, wx, wy);
+          E = jmul_ah(Apj, jmul(X, Aqj));
+        }
         const float wgt = a.taper[i] * tj * (((i + j) & 1) ? -1.f : 1.f);
 #pragma unroll
         for (int p = 0; p < 4; ++p) {

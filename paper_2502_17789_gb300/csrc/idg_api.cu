@@ -70,6 +70,7 @@ struct idg_plan {
   float4* d_records = nullptr;  // staged visibility records of one batch
   int* d_status = nullptr;      // kernel status word (timeouts)
   int* d_queue = nullptr;       // work-queue counters, 2 per batch (gridder, degridder)
+  uint8_t* d_adiag = nullptr;   // [n_int][n_st] diagonal-A-term flags of the current call
   int64_t max_batch_vis = 0;
   int persistent_grid_blocks = 0, persistent_degrid_blocks = 0;  // > 0: persistent launches
   struct GraphCache {
@@ -154,7 +155,8 @@ void free_device(idg_plan* p) {
   p->graph_grid = {};
   p->graph_degrid = {};
   void* ptrs[] = {p->d_uvw,    p->d_fscale, p->d_taper,   p->d_blk,     p->d_twiddle, p->d_sg,     p->d_seg,
-                  p->d_gitems, p->d_ditems, p->d_scratch, p->d_records, p->d_status,  p->d_queue};
+                  p->d_gitems, p->d_ditems, p->d_scratch, p->d_records, p->d_status,  p->d_queue,
+                  p->d_adiag};
   // stream-ordered frees: no device-wide synchronisation, so plans of other
   // streams keep running while this one is released
   for (void* q : ptrs)
@@ -172,6 +174,7 @@ void free_device(idg_plan* p) {
   p->d_records = nullptr;
   p->d_status = nullptr;
   p->d_queue = nullptr;
+  p->d_adiag = nullptr;
 }
 
 // Block geometry table, FP64 -> FP32: for each row j and block ib of 8
@@ -393,6 +396,8 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     if (!e) p->device_bytes += int64_t(rb);
   }
   if (!e) e = int(cudaMallocAsync(reinterpret_cast<void**>(&p->d_status), sizeof(int), p->stream));
+  if (!e) e = int(cudaMallocAsync(reinterpret_cast<void**>(&p->d_adiag), size_t(n_intervals) * std::max(1, n_stations),
+                                  p->stream));
   if (!e && !p->batches.empty()) {
     e = int(cudaMallocAsync(reinterpret_cast<void**>(&p->d_queue), sizeof(int) * 2 * p->batches.size(), p->stream));
     if (!e) p->device_bytes += int64_t(sizeof(int) * 2 * p->batches.size());
@@ -442,6 +447,7 @@ static StageArgs stage_args(const idg_plan* p, const Batch& b, const void* vis) 
 
 static GridArgs grid_args(const idg_plan* p, const Batch& b, const void* vis, const void* aterms) {
   GridArgs ga{};
+  ga.adiag = p->d_adiag;
   ga.records = p->d_records;
   ga.status = p->d_status;
   ga.vis = static_cast<const float4*>(vis);
@@ -466,6 +472,11 @@ idg_status idg_grid(idg_plan* plan, const void* vis_c64, const void* aterms_c64,
       (st = check_buffer(plan, grid_c128, "grid")))
     return st;
   const int L = plan->L;
+  {
+    const int e = launch_aterm_flags(static_cast<const float2*>(aterms_c64), plan->d_adiag, plan->n_int, plan->n_st,
+                                     plan->geom.aterm_nodes, plan->stream);
+    if (e) return cuda_err(plan, e, "A-term flag launch");
+  }
   if (plan->persistent_grid_blocks > 0 && plan->d_queue) {
     const int e = int(cudaMemsetAsync(plan->d_queue, 0, sizeof(int) * 2 * plan->batches.size(), plan->stream));
     if (e) return cuda_err(plan, e, "work-queue reset");
@@ -501,6 +512,11 @@ idg_status idg_degrid(idg_plan* plan, const void* grid_c128, const void* aterms_
     const int e = int(cudaMemsetAsync(vis_c64, 0, bytes, plan->stream));
     if (e) return cuda_err(plan, e, "zeroing dropped visibilities");
   }
+  {
+    const int e = launch_aterm_flags(static_cast<const float2*>(aterms_c64), plan->d_adiag, plan->n_int, plan->n_st,
+                                     plan->geom.aterm_nodes, plan->stream);
+    if (e) return cuda_err(plan, e, "A-term flag launch");
+  }
   if (plan->persistent_degrid_blocks > 0 && plan->d_queue) {
     const int e = int(cudaMemsetAsync(plan->d_queue, 0, sizeof(int) * 2 * plan->batches.size(), plan->stream));
     if (e) return cuda_err(plan, e, "work-queue reset");
@@ -512,6 +528,7 @@ idg_status idg_degrid(idg_plan* plan, const void* grid_c128, const void* aterms_
     int e = timed(plan, kSplitter, [&] { return launch_splitter_ifft(L, fa, b.sg_count, plan->stream); });
     if (e) return cuda_err(plan, e, "splitter/ifft launch");
     DegridArgs da{};
+    da.adiag = plan->d_adiag;
     da.queue = plan->d_queue + 2 * bi + 1;
     da.n_items = b.di_count;
     da.vis = static_cast<float4*>(vis_c64);
@@ -546,6 +563,9 @@ idg_status idg_subgrid_images(idg_plan* plan, const void* vis_c64, const void* a
   const size_t total = plan->part.subgrids.size() * size_t(4) * L * L * sizeof(float2);
   int e = int(cudaMemsetAsync(out_c64, 0, total, plan->stream));
   if (e) return cuda_err(plan, e, "zeroing output");
+  e = launch_aterm_flags(static_cast<const float2*>(aterms_c64), plan->d_adiag, plan->n_int, plan->n_st,
+                         plan->geom.aterm_nodes, plan->stream);
+  if (e) return cuda_err(plan, e, "A-term flag launch");
   for (const Batch& b : plan->batches) {
     GridArgs ga = grid_args(plan, b, vis_c64, aterms_c64);
     int es = timed(plan, kStage, [&] { return launch_stage_records(L, stage_args(plan, b, vis_c64), b.sg_count, plan->stream); });

@@ -100,6 +100,7 @@ struct StageArgs {
 };
 
 struct GridArgs {
+  const uint8_t* adiag;       // [n_int][n_st]: 1 if that station's A-term nodes are diagonal
   const float4* records;      // staged visibility records of the batch
   int* status;                // device status word (kStatusTimeout)
   int* queue;                 // work-queue counter (persistent launches), zero before the launch
@@ -118,6 +119,7 @@ struct GridArgs {
 };
 
 struct DegridArgs {
+  const uint8_t* adiag;       // [n_int][n_st]: 1 if that station's A-term nodes are diagonal
   int* queue;                 // work-queue counter (persistent launches), zero before the launch
   int n_items;
   float4* vis;
@@ -147,6 +149,8 @@ int launch_gridder(int L, const GridArgs& a, int n_items, int persistent_blocks,
 int configure_gridder(int L, int* persistent_blocks);   // attributes + persistent grid size
 int configure_degridder(int L, int nodes, int* persistent_blocks);
 int launch_stage_records(int L, const StageArgs& a, int n_subgrids, void* stream);
+// flags[i][s] = 1 when every node of A-term (interval i, station s) has zero off-diagonal entries
+int launch_aterm_flags(const float2* aterms, uint8_t* flags, int n_int, int n_st, int nodes, void* stream);
 int launch_degridder(int L, const DegridArgs& a, int n_items, int persistent_blocks, void* stream);
 // mode 0: FFT + add into grid; mode 1: FFT in place in scratch (inspection)
 int launch_fft_adder(int L, const FftArgs& a, int n_subgrids, int mode, void* stream);

@@ -126,6 +126,62 @@ __device__ __forceinline__ Jones interp_jones_ldg(const float2* A, int nodes, No
   return J;
 }
 
+// Diagonal entries (XX, YY) of the interpolated Jones matrix, for A-terms
+// flagged diagonal (off-diagonal node samples all zero).
+struct JonesDiag {
+  cf d0, d1;
+};
+__device__ __forceinline__ JonesDiag interp_diag(const float2* A, int nodes, NodeWeight wx, NodeWeight wy) {
+  const float2* r0 = A + (size_t(wy.a) * nodes + wx.a) * 4;
+  const float2* r1 = r0 + size_t(nodes) * 4;
+  const float w00 = (1.f - wx.f) * (1.f - wy.f), w01 = wx.f * (1.f - wy.f);
+  const float w10 = (1.f - wx.f) * wy.f, w11 = wx.f * wy.f;
+  JonesDiag J;
+  {
+    const float2 a = r0[0], b = r0[4], c = r1[0], d = r1[4];
+    J.d0 = {w00 * a.x + w01 * b.x + w10 * c.x + w11 * d.x, w00 * a.y + w01 * b.y + w10 * c.y + w11 * d.y};
+  }
+  {
+    const float2 a = r0[3], b = r0[7], c = r1[3], d = r1[7];
+    J.d1 = {w00 * a.x + w01 * b.x + w10 * c.x + w11 * d.x, w00 * a.y + w01 * b.y + w10 * c.y + w11 * d.y};
+  }
+  return J;
+}
+__device__ __forceinline__ JonesDiag interp_diag_ldg(const float2* A, int nodes, NodeWeight wx, NodeWeight wy) {
+  const float2* r0 = A + (size_t(wy.a) * nodes + wx.a) * 4;
+  const float2* r1 = r0 + size_t(nodes) * 4;
+  const float w00 = (1.f - wx.f) * (1.f - wy.f), w01 = wx.f * (1.f - wy.f);
+  const float w10 = (1.f - wx.f) * wy.f, w11 = wx.f * wy.f;
+  JonesDiag J;
+  {
+    const float2 a = __ldg(r0), b = __ldg(r0 + 4), c = __ldg(r1), d = __ldg(r1 + 4);
+    J.d0 = {w00 * a.x + w01 * b.x + w10 * c.x + w11 * d.x, w00 * a.y + w01 * b.y + w10 * c.y + w11 * d.y};
+  }
+  {
+    const float2 a = __ldg(r0 + 3), b = __ldg(r0 + 7), c = __ldg(r1 + 3), d = __ldg(r1 + 7);
+    J.d1 = {w00 * a.x + w01 * b.x + w10 * c.x + w11 * d.x, w00 * a.y + w01 * b.y + w10 * c.y + w11 * d.y};
+  }
+  return J;
+}
+// E = Ap^H X Aq for diagonal Ap, Aq: E_rc = conj(p_r) X_rc q_c
+__device__ __forceinline__ Jones jdiag_ah_x_b(const JonesDiag& P, const Jones& X, const JonesDiag& Q) {
+  Jones E;
+  E.m[0] = cmul(cmulc(P.d0, X.m[0]), Q.d0);
+  E.m[1] = cmul(cmulc(P.d0, X.m[1]), Q.d1);
+  E.m[2] = cmul(cmulc(P.d1, X.m[2]), Q.d0);
+  E.m[3] = cmul(cmulc(P.d1, X.m[3]), Q.d1);
+  return E;
+}
+// Z = Ap Y Aq^H for diagonal Ap, Aq: Z_rc = p_r Y_rc conj(q_c)
+__device__ __forceinline__ Jones jdiag_a_y_bh(const JonesDiag& P, const Jones& Y, const JonesDiag& Q) {
+  Jones Z;
+  Z.m[0] = cmulc(Q.d0, cmul(P.d0, Y.m[0]));
+  Z.m[1] = cmulc(Q.d1, cmul(P.d0, Y.m[1]));
+  Z.m[2] = cmulc(Q.d0, cmul(P.d1, Y.m[2]));
+  Z.m[3] = cmulc(Q.d1, cmul(P.d1, Y.m[3]));
+  return Z;
+}
+
 __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
 
 // ---------------------------------------------------------------- async bulk copies (TMA, 1-D)

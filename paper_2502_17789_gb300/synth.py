@@ -178,6 +178,18 @@ def aterms_random(rng: np.random.Generator, n_int: int, n_st: int, nodes: int = 
     return a.astype(np.complex64)
 
 
+def aterms_with_leakage(rng: np.random.Generator, aterms: np.ndarray, leakage: float) -> np.ndarray:
+    """Add polarisation leakage to A-terms: off-diagonal entries equal to
+    `leakage` times a unit complex Gaussian times the mean diagonal, so that
+    every Jones matrix is full (complex64)."""
+    a = np.array(aterms, dtype=np.complex128, copy=True)
+    scale = 0.5 * (a[..., 0] + a[..., 3])
+    for e in (1, 2):
+        z = (rng.standard_normal(a.shape[:-1]) + 1j * rng.standard_normal(a.shape[:-1])) / np.sqrt(2.0)
+        a[..., e] += leakage * z * scale
+    return a.astype(np.complex64)
+
+
 def kolmogorov_screen(rng: np.random.Generator, n: int, rms_rad: float) -> np.ndarray:
     """Real random field with a k^(-11/3) power spectrum on an n x n grid,
     scaled to the requested rms phase."""

@@ -267,3 +267,27 @@ def test_graph_needs_a_stream(idg_mod, cuda_device):
     with pytest.raises(idg_mod.IdgError) as e:
         plan.grid_graph(v, A, G)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("L", [64, 96])
+def test_diagonal_and_mixed_aterms(idg_mod, oracle_mod, cuda_device, L):
+    """A-terms whose off-diagonal entries are all zero take the diagonal
+    epilogue (Section 3.3 with diagonal Jones matrices); stations and intervals
+    that mix diagonal and full Jones matrices must give the same result as the
+    full product."""
+    obs = synth.config(2, n_stations=9, n_timesteps=12, n_channels=13)
+    A, vis = _random_problem(300 + L, obs, n_int=3)
+    A[..., 1] = 0
+    A[..., 2] = 0
+    N = obs.grid_size
+    rng = np.random.default_rng(L)
+    Grand = (rng.standard_normal((4, N, N)) + 1j * rng.standard_normal((4, N, N))) * 1e-3
+    mixed = A.copy()
+    full = synth.aterms_random(rng, obs.n_intervals, obs.n_stations, obs.aterm_nodes)
+    mixed[0, ::2] = full[0, ::2]          # interval 0: even stations full Jones
+    mixed[2, 4] = full[2, 4]              # one station of interval 2
+    mixed[1, 3, 4, 4, 1] = 1e-3           # a single off-diagonal node entry
+    for Acase in (A, mixed):
+        c = Case(idg_mod, oracle_mod, obs, Acase, vis, L=L)
+        assert _rel(c.gpu_grid(), c.oracle_grid()) < GRID_TOL
+        assert _degrid_err(c.gpu_degrid(Grand), c.oracle_degrid(Grand)) < DEGRID_TOL
