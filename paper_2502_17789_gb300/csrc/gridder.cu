@@ -18,9 +18,13 @@
 //    owns 8 consecutive pixels of one row.  Records stream into a double
 //    buffer in shared memory by 1-D bulk copies (cp.async.bulk, completion on
 //    an mbarrier), one chunk ahead of the phasor sum.  The 8 pixel phases are
-//    the reduced anchor plus FP32 increments, the phasors come from
-//    __sincosf, and the 4-polarisation complex multiply-accumulate runs as
-//    packed f32x2 FMAs over pixel pairs.  After each A-term segment the
+//    the reduced anchor plus FP32 increments and the phasors come from
+//    __sincosf, for the first channel of each run of kRotateRun channels of a
+//    (baseline, time) row.  phi is linear in frequency, so the other channels
+//    of the run rotate the previous phasors by the phasor of the channel step
+//    (itself evaluated once per row the same way): one complex multiply per
+//    pixel instead of a sine and a cosine.  The 4-polarisation complex
+//    multiply-accumulate runs as packed f32x2 FMAs over pixel pairs.  After each A-term segment the
 //    thread applies A_p^H X A_q, the taper and the centring sign and adds
 //    the result into its private columns of a shared-memory image sum.
 #include "kernels_common.cuh"
@@ -29,24 +33,54 @@ namespace idg {
 
 // ------------------------------------------------------------------ staging
 
-__global__ void __launch_bounds__(256) stage_records_kernel(const StageArgs a, int L) {
-  const SubgridDesc sd = a.sg[blockIdx.x];
-  const int nc = sd.c1 - sd.c0;
+// Phase slopes of a visibility: a = (xi - x0 - L/2) / L, b likewise, w (turns).
+struct Slopes {
+  double a, b, w;
+};
+
+__device__ __forceinline__ Slopes vis_slopes(const StageArgs& a, const SubgridDesc& sd, int t, int ch, int L) {
   const double inv_l = 1.0 / double(L);
   const double off_x = double(sd.x0 + L / 2 - a.g.N / 2);
   const double off_y = double(sd.y0 + L / 2 - a.g.N / 2);
+  const double* r = a.uvw + (size_t(sd.b) * a.g.n_t + t) * 3;
+  const double fs = a.fscale[ch];
+  const double dx = (r[0] * fs) * a.g.fov - off_x;
+  const double dy = (r[1] * fs) * a.g.fov - off_y;
+  return {dx * inv_l, dy * inv_l, r[2] * fs};
+}
+
+// (head, tail) split of the slopes for the exact anchor reduction, plus the
+// FP32 slopes of the per-pixel increments, and the record kind.
+__device__ __forceinline__ void put_slopes(float4* rec, const Slopes& s, float kind) {
+  const double ah = rint(s.a * 65536.0) * (1.0 / 65536.0);
+  const double bh = rint(s.b * 65536.0) * (1.0 / 65536.0);
+  rec[6] = make_float4(float(ah), float(bh), float(s.a - ah), float(s.b - bh));
+  rec[7] = make_float4(float(s.w), float(kTwoPi * s.a), float(kTwoPi * s.w), kind);
+}
+
+__global__ void __launch_bounds__(256) stage_records_kernel(const StageArgs a, int L) {
+  const SubgridDesc sd = a.sg[blockIdx.x];
+  const int nc = sd.c1 - sd.c0;
+  // channels c0 + 1 .. c0 + s_uniform all follow the same step as channel c0 + 1
+  __shared__ int s_uniform;
+  if (threadIdx.x == 0) {
+    int u = nc > 1 ? 1 : 0;
+    if (nc > 1) {
+      const double step1 = a.fscale[sd.c0 + 1] - a.fscale[sd.c0];
+      while (u + 1 < nc) {
+        const double st = a.fscale[sd.c0 + u + 1] - a.fscale[sd.c0 + u];
+        if (fabs(st - step1) > 1e-12 * fabs(step1)) break;
+        ++u;
+      }
+    }
+    s_uniform = u;
+  }
+  __syncthreads();
+  const int uniform = s_uniform;
   for (int k = threadIdx.x; k < sd.n_vis; k += blockDim.x) {
-    const int t = sd.t0 + k / nc, ch = sd.c0 + k % nc;
+    const int t = sd.t0 + k / nc, cc = k % nc, ch = sd.c0 + cc;
     const size_t vidx = (size_t(sd.b) * a.g.n_t + t) * a.g.n_ch + ch;
     const float4 v0 = a.vis[2 * vidx], v1 = a.vis[2 * vidx + 1];
-    const double* r = a.uvw + (size_t(sd.b) * a.g.n_t + t) * 3;
-    const double fs = a.fscale[ch];
-    const double dx = (r[0] * fs) * a.g.fov - off_x;
-    const double dy = (r[1] * fs) * a.g.fov - off_y;
-    const double w = r[2] * fs;
-    const double aa = dx * inv_l, bb = dy * inv_l;
-    const double ah = rint(aa * 65536.0) * (1.0 / 65536.0);
-    const double bh = rint(bb * 65536.0) * (1.0 / 65536.0);
     float4* rec = a.records + (size_t(sd.rec_offset) + k) * kRecordFloat4;
     rec[0] = make_float4(v0.x, v0.x, v0.y, v0.y);
     rec[1] = make_float4(-v0.y, -v0.y, v0.z, v0.z);
@@ -54,8 +88,22 @@ __global__ void __launch_bounds__(256) stage_records_kernel(const StageArgs a, i
     rec[3] = make_float4(v1.x, v1.x, v1.y, v1.y);
     rec[4] = make_float4(-v1.y, -v1.y, v1.z, v1.z);
     rec[5] = make_float4(v1.w, v1.w, -v1.w, -v1.w);
-    rec[6] = make_float4(float(ah), float(bh), float(aa - ah), float(bb - bh));
-    rec[7] = make_float4(float(w), float(kTwoPi * aa), float(kTwoPi * w), 0.f);
+    // Phasors along a row of channels (fixed baseline and time) advance by
+    // a constant factor while the channel step is constant: phi is linear in
+    // frequency.  The first channel of every run of kRotateRun starts from
+    // its own phase (kind 1).  The first step of a row carries the step's
+    // slopes (kind 2), later steps equal to it repeat it (kind 0), and past
+    // the first step that differs every step carries its own slopes.
+    const Slopes cur = vis_slopes(a, sd, t, ch, L);
+    if (cc % kRotateRun == 0) {
+      put_slopes(rec, cur, kKindBase);
+    } else if (cc >= 2 && cc <= uniform) {
+      rec[6] = make_float4(0.f, 0.f, 0.f, 0.f);
+      rec[7] = make_float4(0.f, 0.f, 0.f, kKindRotate);
+    } else {
+      const Slopes prev = vis_slopes(a, sd, t, ch - 1, L);
+      put_slopes(rec, {cur.a - prev.a, cur.b - prev.b, cur.w - prev.w}, kKindStep);
+    }
   }
 }
 
@@ -160,12 +208,8 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
     if (n_chunks > 1) issue(int((cg + 1) & 1));
   }
 
-  // pixel geometry of this thread's block: anchor at i0 + 4
+  // pixel geometry of this thread's block (anchor at i0 + 4), read where phases are evaluated
   const float4* bg = a.blk + (size_t(j) * C::TPR + ib) * 3;
-  const float4 g0 = bg[0], g1 = bg[1], g2 = bg[2];
-  const float n0 = g0.x;
-  const float2 DN[4] = {{g0.y, g0.z}, {g0.w, g1.x}, {g1.y, g1.z}, {g1.w, g2.x}};
-  const float di0 = g2.y, dj0 = g2.z;
   const float2 DI[4] = {{-4.f, -3.f}, {-2.f, -1.f}, {0.f, 1.f}, {2.f, 3.f}};
 
   float2 RE[4][4], IM[4][4];
@@ -176,6 +220,11 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
       RE[p][q] = make_float2(0.f, 0.f);
       IM[p][q] = make_float2(0.f, 0.f);
     }
+  // phasors of the current visibility and of the current channel step; every
+  // row of channels starts with a kind-1 record, so none is read unset
+  float2 Cs[4], Sn[4], Rc[4], Rs[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) Cs[q] = Sn[q] = Rc[q] = Rs[q] = make_float2(0.f, 0.f);
 
   ChunkCursor cc;
   {
@@ -193,22 +242,45 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
 #pragma unroll 1
       for (int v = 0; v < nv; ++v) {
         const float4* rec = rb + v * kRecordFloat4;
-        const float4 cf = rec[6];
         const float4 cw = rec[7];
-        // anchor phase in turns: head part exact, then two range reductions
-        const float sh = fmaf(cf.x, di0, cf.y * dj0);
-        const float d1 = __fsub_rn(sh, round_nearest(sh));
-        const float lo = fmaf(cw.x, n0, fmaf(cf.z, di0, cf.w * dj0));
-        float rr = __fadd_rn(d1, lo);
-        rr = __fmul_rn(__fsub_rn(rr, round_nearest(rr)), kTwoPiF);
-        const float2 R0 = make_float2(rr, rr);
-        const float2 ARR = make_float2(cw.y, cw.y), CRR = make_float2(cw.z, cw.z);
-        float2 Cs[4], Sn[4];
+        const bool base = cw.w == kKindBase;
+        if (cw.w != kKindRotate) {
+          // phases from the record's slopes: anchor phase in turns (head part
+          // exact, then two range reductions) plus FP32 per-pixel increments
+          const float4 cf = rec[6];
+          const float4 g0 = __ldg(bg), g1 = __ldg(bg + 1), g2 = __ldg(bg + 2);
+          const float n0 = g0.x, di0 = g2.y, dj0 = g2.z;
+          const float2 DN[4] = {{g0.y, g0.z}, {g0.w, g1.x}, {g1.y, g1.z}, {g1.w, g2.x}};
+          const float sh = fmaf(cf.x, di0, cf.y * dj0);
+          const float d1 = __fsub_rn(sh, round_nearest(sh));
+          const float lo = fmaf(cw.x, n0, fmaf(cf.z, di0, cf.w * dj0));
+          float rr = __fadd_rn(d1, lo);
+          rr = __fmul_rn(__fsub_rn(rr, round_nearest(rr)), kTwoPiF);
+          const float2 R0 = make_float2(rr, rr);
+          const float2 ARR = make_float2(cw.y, cw.y), CRR = make_float2(cw.z, cw.z);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float2 ph = ffma2(CRR, DN[q], ffma2(ARR, DI[q], R0));
-          __sincosf(ph.x, &Sn[q].x, &Cs[q].x);
-          __sincosf(ph.y, &Sn[q].y, &Cs[q].y);
+          for (int q = 0; q < 4; ++q) {
+            const float2 ph = ffma2(CRR, DN[q], ffma2(ARR, DI[q], R0));
+            float2 c, s;
+            __sincosf(ph.x, &s.x, &c.x);
+            __sincosf(ph.y, &s.y, &c.y);
+            if (base) {
+              Cs[q] = c;
+              Sn[q] = s;
+            } else {
+              Rc[q] = c;
+              Rs[q] = s;
+            }
+          }
+        }
+        if (!base) {
+          // advance by one channel step: e^{i phi} <- e^{i phi} e^{i dphi}
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 c = ffma2(make_float2(-Sn[q].x, -Sn[q].y), Rs[q], fmul2(Cs[q], Rc[q]));
+            Sn[q] = ffma2(Sn[q], Rc[q], fmul2(Cs[q], Rs[q]));
+            Cs[q] = c;
+          }
         }
         const float4 f0 = rec[0], f1 = rec[1], f2 = rec[2], f3 = rec[3], f4 = rec[4], f5 = rec[5];
         const float2 VRR[4] = {{f0.x, f0.y}, {f1.z, f1.w}, {f3.x, f3.y}, {f4.z, f4.w}};

@@ -87,8 +87,16 @@ struct KernelGeom {
 // kernel, streamed by the gridder with bulk copies):
 //   [0..5] value pairs per polarisation p: (Vr,Vr) (Vi,Vi) (-Vi,-Vi)
 //   [6]    (a_head, b_head, a_tail, b_tail)  phase slopes in turns per pixel
-//   [7]    (w, 2 pi a, 2 pi w, 0)
+//   [7]    (w, 2 pi a, 2 pi w, kind)
 constexpr int kRecordFloat4 = 8;
+// Gridder record kinds (record float 31): phasors from the record's own slopes,
+// rotate by the last channel step, or new channel-step slopes then rotate.
+constexpr float kKindRotate = 0.f;
+constexpr float kKindBase = 1.f;
+constexpr float kKindStep = 2.f;
+// channels per run of rotated phasors (one fresh evaluation per run bounds
+// the growth of the rotation's rounding error)
+constexpr int kRotateRun = 8;
 
 struct StageArgs {
   const float4* vis;
