@@ -88,7 +88,7 @@ typedef struct {
   int64_t n_vis_dropped;      /* visibilities of dropped subgrids */
   int64_t n_subgrids_dropped;
   int64_t n_grid_items;       /* gridder work items (subgrid, pixel tile) */
-  int64_t n_degrid_items;     /* degridder work items (segment, <= 256 visibilities) */
+  int64_t n_degrid_items;     /* degridder work items (<= 256 visibilities of one or two segments) */
   int64_t n_batches;          /* device batches the subgrids are processed in */
   int64_t occupancy_hist[16]; /* subgrids with visibility count in [2^k, 2^(k+1)), last bin open */
   int64_t device_bytes;       /* device memory held by the plan */

@@ -5,15 +5,19 @@
 // where Y is the uncentred inverse subgrid FFT of the split-out grid
 // footprint (the splitter applied (-1)^(x+y)).
 //
-// Work item = up to 256 visibilities of one segment (one A-term), in groups
-// of 32 (one per lane).  The block walks the subgrid in chunks of 64 pixel
+// Work item = up to 256 visibilities of one or two consecutive segments of
+// a subgrid (one A-term each), in groups of 32 (one per lane); pairing
+// segments fills the lanes that a lone segment of, say, 40 visibilities
+// would leave idle.  The block walks the subgrid in chunks of 64 pixel
 // blocks (8 consecutive pixels of a row each, 512 pixels).  Within a chunk,
 // warp w sums pixel blocks [8w, 8w+8) for every visibility group in turn and
 // adds its partial sums into a shared-memory accumulator with shared-memory
 // atomics, so all warps stay busy whatever the segment size.  Z of the next
 // chunk is built while the current chunk is summed: its Y values are loaded
 // into registers before the phasor sum and turned into Z (A-term prologue)
-// after it, into the other half of a double buffer, one barrier per chunk.
+// after it, into the other half of a double buffer, one barrier per chunk;
+// with two segments, each pixel pair gets one Z per segment and every lane
+// reads the Z of its own visibility's segment.
 // Phases use the same FP64 offset / exact anchor reduction / FP32 increment
 // scheme as the gridder.
 #include "kernels_common.cuh"
@@ -26,7 +30,7 @@ constexpr int kRangeBlocks = 8;   // pixel blocks per work unit (one per warp pe
 
 template <int L>
 struct DegridSmem {
-  float4 z[2][kChunkBlocks][4][4];  // [buf][block][pixel pair][pol] {Zr_a, Zr_b, Zi_a, Zi_b}
+  float4 z[2][kDegridSegs][kChunkBlocks][4][4];  // [buf][segment][block][pixel pair][pol] {Zr_a, Zr_b, Zi_a, Zi_b}
   float4 g[2][kChunkBlocks][3];     // block geometry
   float4 coef[8][2][32];            // [vis group][half][lane]: (ah, bh, al, bl), (w, 2 pi a, 2 pi w, 0)
   float out[8][kDegridThreads];     // [component][visibility slot], accumulated with shared atomics
@@ -40,21 +44,26 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
   static_assert(NBLK % kChunkBlocks == 0 && kChunkBlocks == 8 * kRangeBlocks, "chunking");
   const DegridItem item = a.items[item_idx];
   const SubgridDesc sd = a.sg[item.sg];
-  const SegmentDesc seg = a.seg[item.segment];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nv = item.k_end - item.k_begin;
+  const int n0 = item.k_mid - item.k_begin;          // visibilities of the first segment
+  const int n_seg = item.k_mid < item.k_end ? 2 : 1;
   const int n_vg = (nv + 31) >> 5;  // groups of 32 visibilities, 1..8
   const int nodes = a.g.nodes;
   const int nA = nodes * nodes * 4;
-  // uniform over the block: both stations' A-terms diagonal -> quarter of the Jones work
-  const bool diag = a.adiag[seg.interval * a.g.n_st + sd.p] && a.adiag[seg.interval * a.g.n_st + sd.q];
-
-  {
-    const float2* Ap = a.aterms + (size_t(seg.interval) * a.g.n_st + sd.p) * nA;
-    const float2* Aq = a.aterms + (size_t(seg.interval) * a.g.n_st + sd.q) * nA;
-    for (int e = tid; e < nA; e += kDegridThreads) {
-      s_A[e] = Ap[e];
-      s_A[nA + e] = Aq[e];
+  // per segment, uniform over the block: both stations' A-terms diagonal -> quarter of the Jones work
+  unsigned diag = 0;  // bit s: segment s
+#pragma unroll
+  for (int s = 0; s < kDegridSegs; ++s) {
+    if (s < n_seg) {
+      const SegmentDesc seg = a.seg[item.segment + s];
+      if (a.adiag[seg.interval * a.g.n_st + sd.p] && a.adiag[seg.interval * a.g.n_st + sd.q]) diag |= 1u << s;
+      const float2* Ap = a.aterms + (size_t(seg.interval) * a.g.n_st + sd.p) * nA;
+      const float2* Aq = a.aterms + (size_t(seg.interval) * a.g.n_st + sd.q) * nA;
+      for (int e = tid; e < nA; e += kDegridThreads) {
+        s_A[2 * s * nA + e] = Ap[e];
+        s_A[(2 * s + 1) * nA + e] = Aq[e];
+      }
     }
   }
   // visibility slot tid: FP64 offsets -> FP32 phase coefficients (zeros for empty slots)
@@ -104,6 +113,10 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
     const int j = bidx / TPR, i = (bidx % TPR) * 8 + 2 * pq;
     const NodeWeight wy = node_weight(j, nodes, L);
     const float tj = a.taper[j];
+#pragma unroll 1
+    for (int s = 0; s < n_seg; ++s) {
+    const float2* sAp = s_A + 2 * s * nA;
+    const float2* sAq = sAp + nA;
     float4 zo[4];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -116,11 +129,11 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
       }
       const NodeWeight wx = node_weight(ii, nodes, L);
       Jones Z;
-      if (diag) {
-        Z = jdiag_a_y_bh(interp_diag(s_A, nodes, wx, wy), Yp, interp_diag(s_A + nA, nodes, wx, wy));
+      if (diag >> s & 1u) {
+        Z = jdiag_a_y_bh(interp_diag(sAp, nodes, wx, wy), Yp, interp_diag(sAq, nodes, wx, wy));
       } else {
-        const Jones Apj = interp_jones(s_A, nodes, wx, wy);
-        const Jones Aqj = interp_jones(s_A + nA, nodes, wx, wy);
+        const Jones Apj = interp_jones(sAp, nodes, wx, wy);
+        const Jones Aqj = interp_jones(sAq, nodes, wx, wy);
         Z = jmul_bh(jmul(Apj, Yp), Aqj);
       }
       const float wgt = a.taper[ii] * tj * (((ii + j) & 1) ? -1.f : 1.f);
@@ -136,7 +149,8 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
       }
     }
 #pragma unroll
-    for (int p = 0; p < 4; ++p) S.z[buf][pb][pq][p] = zo[p];
+    for (int p = 0; p < 4; ++p) S.z[buf][s][pb][pq][p] = zo[p];
+    }
     if (tid < kChunkBlocks * 3) {
       const int b = tid / 3, c = tid % 3;
       S.g[buf][b][c] = a.blk[size_t(chunk * kChunkBlocks + b) * 3 + c];
@@ -155,6 +169,8 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
     // warp `warp` sums pixel blocks [warp*8, warp*8+8) of the chunk for every visibility group
     for (int g = 0; g < n_vg; ++g) {
       const float4 c0 = S.coef[g][0][lane], c1 = S.coef[g][1][lane];
+      // Z of this lane's segment (lanes of one group may straddle the two segments)
+      const float4(*zs)[4][4] = S.z[buf][g * 32 + lane >= n0 ? 1 : 0];
       const float2 ARR = make_float2(c1.y, c1.y), CRR = make_float2(c1.z, c1.z);
       float2 RE[4], IM[4];
 #pragma unroll
@@ -182,7 +198,7 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
           const float2 NS = make_float2(-Sn.x, -Sn.y);
 #pragma unroll
           for (int p = 0; p < 4; ++p) {
-            const float4 z = S.z[buf][b][q][p];
+            const float4 z = zs[b][q][p];
             const float2 ZR = make_float2(z.x, z.y), ZI = make_float2(z.z, z.w);
             // V += Z conj(e): re += Zr c + Zi s, im += Zi c - Zr s
             RE[p] = ffma2(ZR, Cs, RE[p]);
@@ -219,7 +235,7 @@ template <int L, bool PERSIST>
 __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const DegridArgs a) {
   extern __shared__ float4 smem_raw[];
   DegridSmem<L>& S = *reinterpret_cast<DegridSmem<L>*>(smem_raw);
-  float2* s_A = reinterpret_cast<float2*>(&S + 1);  // [2][nodes*nodes*4]
+  float2* s_A = reinterpret_cast<float2*>(&S + 1);  // [segment][station p, q][nodes*nodes*4]
   __shared__ int s_item;
   if constexpr (!PERSIST) {
     degridder_item<L>(a, blockIdx.x, S, s_A);
@@ -237,7 +253,7 @@ __global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const Degr
 
 template <int L>
 static size_t degridder_smem(int nodes) {
-  return sizeof(DegridSmem<L>) + sizeof(float2) * 2 * nodes * nodes * 4;
+  return sizeof(DegridSmem<L>) + sizeof(float2) * 2 * kDegridSegs * nodes * nodes * 4;
 }
 
 template <int L>

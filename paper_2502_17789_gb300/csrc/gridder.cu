@@ -139,11 +139,13 @@ int launch_stage_records(int L, const StageArgs& a, int n_subgrids, void* stream
 
 template <int L, int ROWS>
 struct GridCfg {
-  static constexpr int TPR = L / 8;      // threads per row
+  static constexpr int PX = 8;           // consecutive pixels of a row per thread
+  static constexpr int QN = PX / 2;      // pixel pairs per thread
+  static constexpr int TPR = L / PX;     // threads per row
   static constexpr int NT = ROWS * TPR;  // threads per block
   static constexpr int VC = 64;          // records per chunk
   static constexpr int MINB = NT <= 128 ? 3 : (NT <= 192 ? 2 : 1);
-  static_assert(L % 8 == 0 && L % ROWS == 0, "gridder shape");
+  static_assert(L % 8 == 0 && L % ROWS == 0 && (PX == 4 || PX == 8), "gridder shape");
 };
 
 // Position of chunk `c` of a subgrid: chunks never straddle segments.
@@ -177,8 +179,8 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
   const SubgridDesc sd = a.sg[item.sg];
   const int tid = threadIdx.x;
   const int j = item.tile * ROWS + tid / C::TPR;
-  const int ib = tid % C::TPR;
-  const int i0 = ib * 8;
+  const int i0 = (tid % C::TPR) * C::PX;
+  const int hq = (i0 & 7) >> 1;  // first pixel pair of this thread within its 8-pixel geometry block
   const int nodes = a.g.nodes;
   const int nA = nodes * nodes * 4;
 
@@ -208,23 +210,26 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
     if (n_chunks > 1) issue(int((cg + 1) & 1));
   }
 
-  // pixel geometry of this thread's block (anchor at i0 + 4), read where phases are evaluated
-  const float4* bg = a.blk + (size_t(j) * C::TPR + ib) * 3;
-  const float2 DI[4] = {{-4.f, -3.f}, {-2.f, -1.f}, {0.f, 1.f}, {2.f, 3.f}};
+  // geometry of the 8-pixel block holding this thread's pixels (anchor at
+  // its pixel 4), read where phases are evaluated; DI = pixel offsets from the anchor
+  const float4* bg = a.blk + (size_t(j) * (L / 8) + (i0 >> 3)) * 3;
+  float2 DI[C::QN];
+#pragma unroll
+  for (int q = 0; q < C::QN; ++q) DI[q] = make_float2(float(2 * (hq + q) - 4), float(2 * (hq + q) - 3));
 
-  float2 RE[4][4], IM[4][4];
+  float2 RE[4][C::QN], IM[4][C::QN];
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < C::QN; ++q) {
       RE[p][q] = make_float2(0.f, 0.f);
       IM[p][q] = make_float2(0.f, 0.f);
     }
   // phasors of the current visibility and of the current channel step; every
   // row of channels starts with a kind-1 record, so none is read unset
-  float2 Cs[4], Sn[4], Rc[4], Rs[4];
+  float2 Cs[C::QN], Sn[C::QN], Rc[C::QN], Rs[C::QN];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) Cs[q] = Sn[q] = Rc[q] = Rs[q] = make_float2(0.f, 0.f);
+  for (int q = 0; q < C::QN; ++q) Cs[q] = Sn[q] = Rc[q] = Rs[q] = make_float2(0.f, 0.f);
 
   ChunkCursor cc;
   {
@@ -250,7 +255,10 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
           const float4 cf = rec[6];
           const float4 g0 = __ldg(bg), g1 = __ldg(bg + 1), g2 = __ldg(bg + 2);
           const float n0 = g0.x, di0 = g2.y, dj0 = g2.z;
-          const float2 DN[4] = {{g0.y, g0.z}, {g0.w, g1.x}, {g1.y, g1.z}, {g1.w, g2.x}};
+          const float2 DNB[4] = {{g0.y, g0.z}, {g0.w, g1.x}, {g1.y, g1.z}, {g1.w, g2.x}};
+          float2 DN[C::QN];
+#pragma unroll
+          for (int q = 0; q < C::QN; ++q) DN[q] = C::PX == 8 ? DNB[q] : (hq ? DNB[q + 2] : DNB[q]);
           const float sh = fmaf(cf.x, di0, cf.y * dj0);
           const float d1 = __fsub_rn(sh, round_nearest(sh));
           const float lo = fmaf(cw.x, n0, fmaf(cf.z, di0, cf.w * dj0));
@@ -259,7 +267,7 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
           const float2 R0 = make_float2(rr, rr);
           const float2 ARR = make_float2(cw.y, cw.y), CRR = make_float2(cw.z, cw.z);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < C::QN; ++q) {
             const float2 ph = ffma2(CRR, DN[q], ffma2(ARR, DI[q], R0));
             float2 c, s;
             __sincosf(ph.x, &s.x, &c.x);
@@ -276,7 +284,7 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
         if (!base) {
           // advance by one channel step: e^{i phi} <- e^{i phi} e^{i dphi}
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < C::QN; ++q) {
             const float2 c = ffma2(make_float2(-Sn[q].x, -Sn[q].y), Rs[q], fmul2(Cs[q], Rc[q]));
             Sn[q] = ffma2(Sn[q], Rc[q], fmul2(Cs[q], Rs[q]));
             Cs[q] = c;
@@ -289,7 +297,7 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
 #pragma unroll
         for (int p = 0; p < 4; ++p)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < C::QN; ++q) {
             RE[p][q] = ffma2(VRR[p], Cs[q], RE[p][q]);
             RE[p][q] = ffma2(NVI[p], Sn[q], RE[p][q]);
             IM[p][q] = ffma2(VRR[p], Sn[q], IM[p][q]);
@@ -322,7 +330,7 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
       // uniform over the block: both stations' A-terms diagonal -> quarter of the Jones work
       const bool diag = a.adiag[seg.interval * a.g.n_st + sd.p] && a.adiag[seg.interval * a.g.n_st + sd.q];
 #pragma unroll
-      for (int px = 0; px < 8; ++px) {
+      for (int px = 0; px < C::PX; ++px) {
         const int i = i0 + px;
         const int q = px >> 1;
         const NodeWeight wx = node_weight(i, nodes, L);
@@ -357,7 +365,7 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < C::QN; ++q) {
           RE[p][q] = make_float2(0.f, 0.f);
           IM[p][q] = make_float2(0.f, 0.f);
         }
@@ -371,7 +379,7 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
     for (int p = 0; p < 4; ++p) {
       float4* dst = reinterpret_cast<float4*>(a.scratch + ((size_t(item.sg) * 4 + p) * L + j) * L + i0);
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
+      for (int h = 0; h < C::QN; ++h) {
         const int px = 2 * h;
         dst[h] = make_float4(s_acc[(px * 8 + 2 * p) * C::NT + tid], s_acc[(px * 8 + 2 * p + 1) * C::NT + tid],
                              s_acc[((px + 1) * 8 + 2 * p) * C::NT + tid],
@@ -392,8 +400,8 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
   using C = GridCfg<L, ROWS>;
   extern __shared__ float4 smem[];
   float4* s_rec = smem;                                                        // [2][VC][8]
-  float* s_acc = reinterpret_cast<float*>(s_rec + 2 * C::VC * kRecordFloat4);  // [64][NT]
-  uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_acc + 64 * C::NT);          // [2]
+  float* s_acc = reinterpret_cast<float*>(s_rec + 2 * C::VC * kRecordFloat4);  // [8 PX][NT]
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_acc + 8 * C::PX * C::NT);    // [2]
   int* s_item = reinterpret_cast<int*>(s_bar + 2);
   if (threadIdx.x == 0) {
     mbar_init(&s_bar[0], 1);
@@ -419,7 +427,7 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
 template <int L, int ROWS>
 static size_t gridder_smem() {
   using C = GridCfg<L, ROWS>;
-  return sizeof(float4) * 2 * C::VC * kRecordFloat4 + sizeof(float) * 64 * C::NT + 2 * sizeof(uint64_t) + 16;
+  return sizeof(float4) * 2 * C::VC * kRecordFloat4 + sizeof(float) * 8 * C::PX * C::NT + 2 * sizeof(uint64_t) + 16;
 }
 
 template <int L, int ROWS>

@@ -339,12 +339,24 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     });
     for (int32_t o : order)
       for (int t = 0; t < tiles; ++t) gitems.push_back(GridItem{o, t});
+    // degridder items: pieces of <= kDegridMaxVis visibilities of one
+    // segment; a piece that ends its segment shares its item with the first
+    // piece of the next segment when both fit
     for (int32_t o : order) {
       const SubgridDesc& d = p->exec[s0 + o];
+      bool open = false;  // the last item can take a piece of the next segment
       for (int gidx = d.seg_begin; gidx < d.seg_begin + d.seg_count; ++gidx) {
         const SegmentDesc& sgd = p->part.segments[gidx];
-        for (int k = sgd.k_begin; k < sgd.k_end; k += kDegridMaxVis)
-          ditems.push_back(DegridItem{o, gidx, k, std::min(k + kDegridMaxVis, sgd.k_end)});
+        for (int k = sgd.k_begin; k < sgd.k_end; k += kDegridMaxVis) {
+          const int ke = std::min(k + kDegridMaxVis, sgd.k_end);
+          if (open && k == sgd.k_begin && ditems.back().k_end - ditems.back().k_begin + (ke - k) <= kDegridMaxVis) {
+            ditems.back().k_end = ke;  // second segment of the item
+            open = false;
+          } else {
+            ditems.push_back(DegridItem{o, gidx, k, ke, ke, 0});
+            open = ke == sgd.k_end;
+          }
+        }
       }
     }
     b.gi_count = int32_t(gitems.size()) - b.gi_offset;

@@ -44,13 +44,17 @@ struct GridItem {
 };
 
 // Degridder work item: up to kDegridMaxVis visibilities of one segment.
+// Visibilities [k_begin, k_mid) belong to segment `segment`, [k_mid, k_end)
+// (if any) to segment `segment` + 1 of the same subgrid.
 struct DegridItem {
   int32_t sg;       // index into the batch's device subgrid table
-  int32_t segment;  // global segment index
-  int32_t k_begin, k_end;
+  int32_t segment;  // global index of the first segment
+  int32_t k_begin, k_mid, k_end;
+  int32_t pad;
 };
 
 constexpr int kDegridMaxVis = 256;
+constexpr int kDegridSegs = 2;  // segments per degridder work item
 
 // ---------------------------------------------------------------- planner
 

@@ -291,3 +291,26 @@ def test_diagonal_and_mixed_aterms(idg_mod, oracle_mod, cuda_device, L):
         c = Case(idg_mod, oracle_mod, obs, Acase, vis, L=L)
         assert _rel(c.gpu_grid(), c.oracle_grid()) < GRID_TOL
         assert _degrid_err(c.gpu_degrid(Grand), c.oracle_degrid(Grand)) < DEGRID_TOL
+
+
+@pytest.mark.parametrize("spacing", ["random", "uniform_then_jump", "single"])
+def test_channel_spacing(idg_mod, oracle_mod, cuda_device, spacing):
+    """The gridder rotates phasors along runs of channels with a constant
+    frequency step (phi is linear in frequency, Eq. 7); non-uniform steps,
+    a change of step within a row and single-channel rows must take the
+    direct evaluation and still match the oracle."""
+    rng = np.random.default_rng(11)
+    enu = synth.stations_uniform_disk(rng, 9, 3000.0)
+    if spacing == "random":
+        freqs = 140e6 + np.cumsum(rng.uniform(0.8e6, 1.6e6, 19))
+    elif spacing == "uniform_then_jump":
+        freqs = np.concatenate([140e6 + 1.25e6 * np.arange(11), 160e6 + 0.9e6 * np.arange(9)])
+    else:
+        freqs = np.array([150e6])
+    obs = synth.make_observation(enu, 12, 2.0, freqs, 4, 4096, 96, 18, 0.5, name="spacing")
+    A, vis = _random_problem(5, obs)
+    N = obs.grid_size
+    Grand = (rng.standard_normal((4, N, N)) + 1j * rng.standard_normal((4, N, N))) * 1e-3
+    c = Case(idg_mod, oracle_mod, obs, A, vis)
+    assert _rel(c.gpu_grid(), c.oracle_grid()) < GRID_TOL
+    assert _degrid_err(c.gpu_degrid(Grand), c.oracle_degrid(Grand)) < DEGRID_TOL
