@@ -36,6 +36,14 @@ UNIT = "vis/s"
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM per clock
 FLOP_PER_VISPX = 34.0            # 16 FMA (4-pol complex MAC) + 1 FMA (phase) = 17 FMA per visibility-pixel
 SM_MAX_MHZ_FALLBACK = 2070.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "kernel_traffic.json")
+CSRC = os.path.join(ROOT, "paper_2502_17789_gb300", "csrc")
+# the capture that --record-traffic reads (one pass per launch, full-size workload)
+NCU_LAUNCH_LIST = ('ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum '
+                   '--clock-control none -k regex:"gridder|fft|splitter|stage|aterm" -c 300 --csv '
+                   '--log-file launches.csv python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e')
+KERNEL_SOURCES = {"gridder": ["gridder.cu", "kernels_common.cuh", "idg_internal.h"],
+                  "degridder": ["degridder.cu", "kernels_common.cuh", "idg_internal.h"]}
 
 
 def _env_int(name, default):
@@ -58,6 +66,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (small profiling runs)")
     ap.add_argument("--stations", type=int, default=None, help="reduce the workload's stations (profiling)")
     ap.add_argument("--timesteps", type=int, default=None, help="reduce the workload's timesteps (profiling)")
+    ap.add_argument("--record-traffic", metavar="NCU_CSV", default=None,
+                    help="read an ncu launch list (--csv, with dram__bytes_read.sum and dram__bytes_write.sum) "
+                         "of this command's default workload and store the per-launch DRAM bytes of the gridder "
+                         "and degridder, keyed by the digest of their sources, in profiles/kernel_traffic.json")
     ap.add_argument("--aterms", choices=["beam", "full"], default="beam",
                     help="beam: the scalar beam x screen gain (diagonal Jones); full: the same plus 5%% "
                          "polarisation leakage, so every Jones matrix is full")
@@ -79,17 +91,23 @@ def make_workload(idx: int, device, stations=None, timesteps=None, aterm_kind="b
     sky = synth.point_sources(rng, n_src, half)
     vis = synth.simulate_visibilities(obs, sky, model if idx != 1 else None, noise_sigma=1.0, rng=rng,
                                       device=str(device))
+    if aterm_kind == "full":
+        aterms = synth.aterms_with_leakage(np.random.default_rng(1), aterms, 0.05)
+    desc = workload_description(idx, obs, stations, timesteps, aterm_kind)
+    return obs, torch.as_tensor(aterms, device=device), vis, desc
+
+
+def workload_description(idx, obs, stations=None, timesteps=None, aterm_kind="beam") -> str:
     desc = {1: "32 stations in a 1 km disk (496 baselines), 16 x 8 s, 8 ch 150-157 MHz, 512^2 grid, L=32, P=12, "
                "FOV 0.35, identity A-terms, 20 sources + noise",
             2: "128 stations in a 3 km disk (8128 baselines), 56 x 2 s, 24 ch 140-170 MHz, 4096^2 FP64 grid, "
                "L=96, P=18, FOV 0.5, A-terms per 8 s on 9x9 nodes (Gaussian beam x Kolmogorov screen, 2 rad rms), "
                "200 sources + 1 Jy noise"}.get(idx, obs.name)
     if aterm_kind == "full":
-        aterms = synth.aterms_with_leakage(np.random.default_rng(1), aterms, 0.05)
         desc += ", full-Jones A-terms (5% leakage)"
     if stations or timesteps:
         desc = f"REDUCED ({obs.n_stations} stations, {obs.n_timesteps} timesteps) " + desc
-    return obs, torch.as_tensor(aterms, device=device), vis, desc
+    return desc
 
 
 # --------------------------------------------------------------------------- clocks
@@ -204,6 +222,63 @@ def cpu_baseline(obs, aterms_np, vis_np, grid_np, budget_s):
 
 # --------------------------------------------------------------------------- native arm
 
+# --------------------------------------------------------------------------- DRAM traffic
+
+def source_digest(kern: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kern]:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kern: str, workload: str):
+    """Per-launch DRAM bytes (read + write) of `kern` from the last ncu
+    capture, or None if the kernel's sources changed since or the capture
+    was of another workload."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            entry = json.load(f).get(kern)
+    except (OSError, ValueError):
+        return None
+    if not entry or entry.get("source_sha256") != source_digest(kern) or entry.get("workload") != workload:
+        return None
+    return entry.get("dram_bytes_per_launch")
+
+
+def record_traffic(csv_path: str, workload: str, command: str):
+    import csv
+    import collections
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
+    with open(csv_path) as f:
+        rows = [r for r in csv.reader(f)]
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "Metric Name" in r)
+    h = rows[hi]
+    ki, mi, vi, ui, ii = (h.index(k) for k in ("Kernel Name", "Metric Name", "Metric Value", "Metric Unit", "ID"))
+    per = collections.defaultdict(lambda: [None, 0.0, 0])
+    for r in rows[hi + 1:]:
+        if len(r) <= vi or r[mi] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        name = r[ki]
+        kern = "degridder" if "degridder_kernel" in name else ("gridder" if "gridder_kernel" in name else None)
+        if kern is None or "noalloc" in name:
+            continue
+        e = per[r[ii]]
+        e[0] = kern
+        e[1] += float(r[vi].replace(",", "")) * scale.get(r[ui], 1.0)
+    out = {}
+    for kern in KERNEL_SOURCES:
+        vals = [v[1] for v in per.values() if v[0] == kern]
+        if vals:
+            out[kern] = {"dram_bytes_per_launch": sum(vals) / len(vals), "launches": len(vals),
+                         "source_sha256": source_digest(kern), "workload": workload, "command": command}
+    with open(TRAFFIC_FILE, "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
+        f.write("\n")
+    print(json.dumps(out, indent=1))
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -278,7 +353,7 @@ def run_native(args):
     peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved_vispx = vispx / (k_ms * 1e-3)
     achieved = achieved_vispx * FLOP_PER_VISPX / 1e12
-    traffic = None
+    traffic = recorded_traffic(kern, desc)
     roofline = {"bound": "alu", "kernel": kern, "achieved": round(achieved, 3), "peak": round(peak_tflops, 3),
                 "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": traffic,
                 "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
@@ -391,6 +466,13 @@ def run_reference(args):
 
 def main():
     args = parse_args()
+    if args.record_traffic:
+        import torch  # noqa: F401  (make_workload's description only)
+        from paper_2502_17789_gb300 import synth
+        obs = synth.config(args.workload, seed=0, n_stations=args.stations, n_timesteps=args.timesteps)
+        desc = workload_description(args.workload, obs, args.stations, args.timesteps, args.aterms)
+        record_traffic(args.record_traffic, desc, NCU_LAUNCH_LIST + "; python bench.py --record-traffic launches.csv")
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -202,9 +202,9 @@ idg_status idg_profile_enable(idg_plan* plan, int32_t on);
 /*
  * idg_profile_read -- accumulated device time and launch counts per kernel
  * since the last read, then reset.  Synchronises the plan's stream.
- *   ms        host double [5]: gridder, fft+adder, splitter+ifft, degridder,
- *             visibility staging
- *   launches  host int64 [5], same order
+ *   ms        host double [6]: gridder, fft+adder, splitter+ifft, degridder,
+ *             visibility staging, A-term diagonal flags
+ *   launches  host int64 [6], same order
  */
 idg_status idg_profile_read(idg_plan* plan, double* ms, int64_t* launches);
 

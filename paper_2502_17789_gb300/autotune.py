@@ -65,27 +65,32 @@ def _save_cache(path, cache):
     os.replace(tmp, path)
 
 
-def gpu_measure(obs, subgrid_size, mode, scratch_bytes, trials=2, aterms=None):
+def gpu_measure(obs, subgrid_size, mode, scratch_bytes, trials=2, aterms=None, graph=False, vis=None):
     """Time one grid + degrid pass (ms, best of `trials`) on a plan with the
-    given settings; None if the plan cannot be made (e.g. w too large)."""
+    given settings; None if the plan cannot be made (e.g. w too large).
+    With `graph`, the passes are CUDA-graph replays on a side stream."""
     import torch
 
     from . import idg
 
+    dev = torch.device("cuda")
+    side = torch.cuda.Stream(dev) if graph else None
     os.environ["IDG_SCRATCH_BYTES"] = str(int(scratch_bytes))
     try:
         flags = idg.IDG_PERSISTENT if mode == "persistent" else 0
         try:
-            plan = idg.Plan(obs, subgrid_size=subgrid_size, flags=flags)
+            plan = idg.Plan(obs, subgrid_size=subgrid_size, flags=flags,
+                            stream=side.cuda_stream if graph else None)
         except idg.IdgError:
             return None
     finally:
         del os.environ["IDG_SCRATCH_BYTES"]
-    dev = torch.device("cuda")
-    g = torch.Generator(device=dev)
-    g.manual_seed(0)
-    vis = torch.randn((obs.n_baselines, obs.n_timesteps, obs.n_channels, 4), dtype=torch.complex64, device=dev,
-                      generator=g)
+    own_vis = vis is None
+    if own_vis:
+        g = torch.Generator(device=dev)
+        g.manual_seed(0)
+        vis = torch.randn((obs.n_baselines, obs.n_timesteps, obs.n_channels, 4), dtype=torch.complex64,
+                          device=dev, generator=g)
     if aterms is None:
         from . import synth
         aterms = synth.aterms_identity(obs.n_intervals, obs.n_stations, obs.aterm_nodes)
@@ -93,20 +98,28 @@ def gpu_measure(obs, subgrid_size, mode, scratch_bytes, trials=2, aterms=None):
     N = obs.grid_size
     G = torch.zeros((4, N, N), dtype=torch.complex128, device=dev)
     out = torch.empty_like(vis)
-    s = torch.cuda.current_stream(dev)
+    s = side if graph else torch.cuda.current_stream(dev)
+    if graph:
+        torch.cuda.synchronize(dev)  # inputs made on the current stream are ready for the side stream
     best = None
     for t in range(trials + 1):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
-        plan.grid(vis, A, G)
-        plan.degrid(G, A, out)
+        if graph:
+            plan.grid_graph(vis, A, G)
+            plan.degrid_graph(G, A, out)
+        else:
+            plan.grid(vis, A, G)
+            plan.degrid(G, A, out)
         e1.record(s)
         plan.synchronize()
         if t > 0:
             ms = e0.elapsed_time(e1)
             best = ms if best is None else min(best, ms)
     plan.close()
-    del vis, G, out
+    del G, out
+    if own_vis:
+        del vis
     torch.cuda.empty_cache()
     return best
 

@@ -114,7 +114,7 @@ int upload(idg_plan* p, T** dst, const T* src, size_t n) {
   return int(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, p->stream));
 }
 
-enum KernelClass { kGridder = 0, kFftAdder = 1, kSplitter = 2, kDegridder = 3, kStage = 4 };
+enum KernelClass { kGridder = 0, kFftAdder = 1, kSplitter = 2, kDegridder = 3, kStage = 4, kFlags = 5, kClasses = 6 };
 
 cudaEvent_t take_event(idg_plan* p) {
   if (!p->ev_pool.empty()) {
@@ -485,8 +485,10 @@ idg_status idg_grid(idg_plan* plan, const void* vis_c64, const void* aterms_c64,
     return st;
   const int L = plan->L;
   {
-    const int e = launch_aterm_flags(static_cast<const float2*>(aterms_c64), plan->d_adiag, plan->n_int, plan->n_st,
-                                     plan->geom.aterm_nodes, plan->stream);
+    const int e = timed(plan, kFlags, [&] {
+      return launch_aterm_flags(static_cast<const float2*>(aterms_c64), plan->d_adiag, plan->n_int, plan->n_st,
+                                plan->geom.aterm_nodes, plan->stream);
+    });
     if (e) return cuda_err(plan, e, "A-term flag launch");
   }
   if (plan->persistent_grid_blocks > 0 && plan->d_queue) {
@@ -525,8 +527,10 @@ idg_status idg_degrid(idg_plan* plan, const void* grid_c128, const void* aterms_
     if (e) return cuda_err(plan, e, "zeroing dropped visibilities");
   }
   {
-    const int e = launch_aterm_flags(static_cast<const float2*>(aterms_c64), plan->d_adiag, plan->n_int, plan->n_st,
-                                     plan->geom.aterm_nodes, plan->stream);
+    const int e = timed(plan, kFlags, [&] {
+      return launch_aterm_flags(static_cast<const float2*>(aterms_c64), plan->d_adiag, plan->n_int, plan->n_st,
+                                plan->geom.aterm_nodes, plan->stream);
+    });
     if (e) return cuda_err(plan, e, "A-term flag launch");
   }
   if (plan->persistent_degrid_blocks > 0 && plan->d_queue) {
@@ -575,8 +579,10 @@ idg_status idg_subgrid_images(idg_plan* plan, const void* vis_c64, const void* a
   const size_t total = plan->part.subgrids.size() * size_t(4) * L * L * sizeof(float2);
   int e = int(cudaMemsetAsync(out_c64, 0, total, plan->stream));
   if (e) return cuda_err(plan, e, "zeroing output");
-  e = launch_aterm_flags(static_cast<const float2*>(aterms_c64), plan->d_adiag, plan->n_int, plan->n_st,
-                         plan->geom.aterm_nodes, plan->stream);
+  e = timed(plan, kFlags, [&] {
+    return launch_aterm_flags(static_cast<const float2*>(aterms_c64), plan->d_adiag, plan->n_int, plan->n_st,
+                              plan->geom.aterm_nodes, plan->stream);
+  });
   if (e) return cuda_err(plan, e, "A-term flag launch");
   for (const Batch& b : plan->batches) {
     GridArgs ga = grid_args(plan, b, vis_c64, aterms_c64);
@@ -668,7 +674,7 @@ idg_status idg_profile_enable(idg_plan* plan, int32_t on) {
 
 idg_status idg_profile_read(idg_plan* plan, double* ms, int64_t* launches) {
   if (!plan || !ms || !launches) return set_err(plan, IDG_ERR_INVALID_ARG, "NULL argument");
-  for (int c = 0; c < 5; ++c) {
+  for (int c = 0; c < kClasses; ++c) {
     ms[c] = 0.0;
     launches[c] = 0;
   }

@@ -28,7 +28,7 @@ EXPORTS = ["idg_plan_create", "idg_grid", "idg_degrid", "idg_grid_graph", "idg_d
            "idg_plan_segments", "idg_subgrid_images", "idg_synchronize", "idg_profile_enable", "idg_profile_read",
            "idg_grid_noalloc", "idg_last_error",
            "idg_plan_destroy", "idg_abi_version"]
-KERNEL_CLASSES = ["gridder", "fft_adder", "splitter_ifft", "degridder", "stage"]
+KERNEL_CLASSES = ["gridder", "fft_adder", "splitter_ifft", "degridder", "stage", "aterm_flags"]
 
 
 class IdgError(RuntimeError):
@@ -188,8 +188,8 @@ def idg_profile_enable(plan, on: bool):
 
 
 def idg_profile_read(plan) -> dict:
-    ms = np.zeros(5, np.float64)
-    n = np.zeros(5, np.int64)
+    ms = np.zeros(len(KERNEL_CLASSES), np.float64)
+    n = np.zeros(len(KERNEL_CLASSES), np.int64)
     _check(load().idg_profile_read(plan, _np_ptr(ms), _np_ptr(n)), "idg_profile_read", plan)
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
