@@ -226,6 +226,17 @@ idg_status idg_profile_read(idg_plan* plan, double* ms, int64_t* launches);
  */
 idg_status idg_grid_noalloc(idg_plan* plan, const void* vis_c64, const void* aterms_c64, void* grid_c128);
 
+/*
+ * idg_wait_selftest -- exercise the bounded-wait error path.  No counterpart
+ * in the paper.  Enqueues on the plan's stream one warp that waits on a
+ * shared-memory mbarrier nothing completes; after limit_us microseconds
+ * (1 .. 2e6) it gives up and sets the plan's device status word, exactly as
+ * a kernel whose bulk copy never landed does.  The next idg_synchronize on
+ * the plan returns IDG_ERR_TIMEOUT (and clears the word); the context stays
+ * usable.  IDG_ERR_INVALID_ARG for host-only plans or a limit out of range.
+ */
+idg_status idg_wait_selftest(idg_plan* plan, int32_t limit_us);
+
 /* Message for the last failure (never NULL; "" when none). */
 const char* idg_last_error(const idg_plan* plan);
 

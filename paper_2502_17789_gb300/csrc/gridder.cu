@@ -129,6 +129,26 @@ int launch_aterm_flags(const float2* aterms, uint8_t* flags, int n_int, int n_st
   return int(cudaGetLastError());
 }
 
+// Self-test of the bounded wait: one warp waits on an mbarrier that nothing
+// arrives on; when the limit passes it reports kStatusTimeout, as a kernel
+// whose bulk copy never landed would.  No copy is in flight, so returning is
+// safe.
+__global__ void wait_selftest_kernel(int* status, uint64_t limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+  if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+}
+
+int launch_wait_selftest(int* status, int64_t limit_ns, void* stream) {
+  wait_selftest_kernel<<<1, 32, 0, cudaStream_t(stream)>>>(status, uint64_t(limit_ns));
+  return int(cudaGetLastError());
+}
+
 int launch_stage_records(int L, const StageArgs& a, int n_subgrids, void* stream) {
   if (n_subgrids <= 0) return 0;
   stage_records_kernel<<<n_subgrids, 256, 0, cudaStream_t(stream)>>>(a, L);

@@ -666,6 +666,15 @@ idg_status idg_synchronize(idg_plan* plan) {
   return IDG_OK;
 }
 
+idg_status idg_wait_selftest(idg_plan* plan, int32_t limit_us) {
+  if (!plan) return set_err(nullptr, IDG_ERR_INVALID_ARG, "plan is NULL");
+  if (plan->host_only) return set_err(plan, IDG_ERR_INVALID_ARG, "plan was created with IDG_HOST_ONLY");
+  if (limit_us < 1 || limit_us > 2000000) return set_err(plan, IDG_ERR_INVALID_ARG, "limit_us must be in [1, 2e6]");
+  const int e = launch_wait_selftest(plan->d_status, int64_t(limit_us) * 1000, plan->stream);
+  if (e) return cuda_err(plan, e, "wait self-test launch");
+  return IDG_OK;
+}
+
 idg_status idg_profile_enable(idg_plan* plan, int32_t on) {
   if (!plan) return set_err(nullptr, IDG_ERR_INVALID_ARG, "plan is NULL");
   plan->profiling = on != 0;

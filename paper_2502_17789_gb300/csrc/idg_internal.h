@@ -161,6 +161,8 @@ int launch_gridder(int L, const GridArgs& a, int n_items, int persistent_blocks,
 int configure_gridder(int L, int* persistent_blocks);   // attributes + persistent grid size
 int configure_degridder(int L, int nodes, int* persistent_blocks);
 int launch_stage_records(int L, const StageArgs& a, int n_subgrids, void* stream);
+// one warp waits, bounded by limit_ns, on an mbarrier nothing completes; sets kStatusTimeout bit in *status
+int launch_wait_selftest(int* status, int64_t limit_ns, void* stream);
 // flags[i][s] = 1 when every node of A-term (interval i, station s) has zero off-diagonal entries
 int launch_aterm_flags(const float2* aterms, uint8_t* flags, int n_int, int n_st, int nodes, void* stream);
 int launch_degridder(int L, const DegridArgs& a, int n_items, int persistent_blocks, void* stream);

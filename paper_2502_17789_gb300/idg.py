@@ -26,7 +26,7 @@ IDG_DROP_OUT_OF_GRID, IDG_SPLIT_AT_ATERM_INTERVALS, IDG_HOST_ONLY, IDG_PERSISTEN
 # every function declared in include/idg.h
 EXPORTS = ["idg_plan_create", "idg_grid", "idg_degrid", "idg_grid_graph", "idg_degrid_graph", "idg_set_stream", "idg_plan_stats", "idg_plan_subgrids",
            "idg_plan_segments", "idg_subgrid_images", "idg_synchronize", "idg_profile_enable", "idg_profile_read",
-           "idg_grid_noalloc", "idg_last_error",
+           "idg_grid_noalloc", "idg_wait_selftest", "idg_last_error",
            "idg_plan_destroy", "idg_abi_version"]
 KERNEL_CLASSES = ["gridder", "fft_adder", "splitter_ifft", "degridder", "stage", "aterm_flags"]
 
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.idg_subgrid_images.argtypes = [P, P, P, i32, P]
     lib.idg_synchronize.argtypes = [P]
     lib.idg_grid_noalloc.argtypes = [P, P, P, P]
+    lib.idg_wait_selftest.argtypes = [P, ctypes.c_int32]
     lib.idg_profile_enable.argtypes = [P, i32]
     lib.idg_profile_read.argtypes = [P, P, P]
     lib.idg_last_error.argtypes = [P]
@@ -133,6 +134,10 @@ def idg_grid(plan, vis_ptr, aterms_ptr, grid_ptr):
 
 def idg_grid_noalloc(plan, vis_ptr, aterms_ptr, grid_ptr):
     _check(load().idg_grid_noalloc(plan, vis_ptr, aterms_ptr, grid_ptr), "idg_grid_noalloc", plan)
+
+
+def idg_wait_selftest(plan, limit_us: int):
+    _check(load().idg_wait_selftest(plan, int(limit_us)), "idg_wait_selftest", plan)
 
 
 def idg_degrid(plan, grid_ptr, aterms_ptr, vis_ptr):
@@ -282,6 +287,9 @@ class Plan:
 
     def synchronize(self):
         idg_synchronize(self.handle)
+
+    def wait_selftest(self, limit_us: int = 20000):
+        idg_wait_selftest(self.handle, limit_us)
 
     def profile(self, on: bool = True):
         idg_profile_enable(self.handle, on)

@@ -314,3 +314,21 @@ def test_channel_spacing(idg_mod, oracle_mod, cuda_device, spacing):
     c = Case(idg_mod, oracle_mod, obs, A, vis)
     assert _rel(c.gpu_grid(), c.oracle_grid()) < GRID_TOL
     assert _degrid_err(c.gpu_degrid(Grand), c.oracle_degrid(Grand)) < DEGRID_TOL
+
+
+def test_bounded_wait_reports_timeout(idg_mod, oracle_mod, cuda_device):
+    """A device wait that nothing completes gives up after its limit (20 ms
+    here), the host reads IDG_ERR_TIMEOUT from the plan's status word, the
+    word is cleared, and the plan keeps working."""
+    obs = synth.config(1, n_stations=6, n_timesteps=4)
+    A, vis = _random_problem(3, obs)
+    c = Case(idg_mod, oracle_mod, obs, A, vis)
+    c.plan.wait_selftest(20000)
+    with pytest.raises(idg_mod.IdgError) as e:
+        c.plan.synchronize()
+    assert e.value.status == 7
+    c.plan.synchronize()
+    assert _rel(c.gpu_grid(), c.oracle_grid()) < GRID_TOL
+    with pytest.raises(idg_mod.IdgError) as e:
+        c.plan.wait_selftest(0)
+    assert e.value.status == 1

@@ -120,3 +120,16 @@ def test_empty_observation_plans_to_nothing(idg_mod):
     obs = _brute.tiny_observation(seed=1, n_t=0)
     sg, seg, st = _host_plan(idg_mod, obs)
     assert len(sg) == 0 and len(seg) == 0 and st.n_vis == 0
+
+
+def test_wait_selftest_rejects_host_plans(idg_mod):
+    obs = _brute.tiny_observation(seed=1)
+    g, _ = idg_mod.make_geometry(obs.grid_size, obs.subgrid_size, obs.kernel_padding, obs.image_size,
+                                 flags=idg_mod.IDG_HOST_ONLY)
+    plan = idg_mod.idg_plan_create(g, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets)
+    try:
+        with pytest.raises(idg_mod.IdgError) as e:
+            idg_mod.idg_wait_selftest(plan, 1000)
+        assert e.value.status == 1
+    finally:
+        idg_mod.idg_plan_destroy(plan)
