@@ -70,6 +70,8 @@ def parse_args():
                     help="read an ncu launch list (--csv, with dram__bytes_read.sum and dram__bytes_write.sum) "
                          "of this command's default workload and store the per-launch DRAM bytes of the gridder "
                          "and degridder, keyed by the digest of their sources, in profiles/kernel_traffic.json")
+    ap.add_argument("--serving-requests", type=int, default=24,
+                    help="requests of the serving comparison (batched vs plain at 2x plain capacity); 0 = skip")
     ap.add_argument("--aterms", choices=["beam", "full"], default="beam",
                     help="beam: the scalar beam x screen gain (diagonal Jones); full: the same plus 5%% "
                          "polarisation leakage, so every Jones matrix is full")
@@ -408,6 +410,25 @@ def run_native(args):
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(obs, A_d.cpu().numpy(), vis_h.numpy(), gmodel_h.numpy(), args.cpu_seconds)
 
+    # the serving form (continuous batching) beside the plain one-request-at-a-time form, on a Poisson stream
+    # of snapshot requests at twice the plain capacity (rank 0 of a single-GPU run only)
+    serving = None
+    if rank == 0 and world == 1 and args.serving_requests > 0:
+        from paper_2502_17789_gb300 import serve
+        plan.close()
+        del G_out, vis_pred
+        torch.cuda.empty_cache()
+        cmp = serve.compare(args.serving_requests, seed=0, loads=(2.0,))
+        sat = cmp["load_2"]
+
+        def brief(r):
+            return {"vis_per_s": r["throughput_vis_per_s"], "p50_ms": 1e3 * r["p50_latency_s"],
+                    "p99_ms": 1e3 * r["p99_latency_s"], "requests_ok": r["ok"]}
+        serving = {"requests": args.serving_requests, "arrival": "Poisson at 2x the plain capacity",
+                   "plain_capacity_requests_per_s": cmp["calibration_plain_requests_per_s"],
+                   "batched": brief(sat["batched"]), "plain": brief(sat["plain"])}
+        plan = None
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -418,11 +439,12 @@ def run_native(args):
                    "subgrids": st.n_subgrids, "segments": st.n_segments, "batches": st.n_batches,
                    "vis_pixels_per_direction": st.vis_pixels},
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches,
-        "kernels": kernels,
+        "kernels": kernels, "serving": serving,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
+    if plan is not None:
+        plan.close()
     if world > 1:
         dist.destroy_process_group()
 

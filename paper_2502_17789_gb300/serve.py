@@ -265,11 +265,36 @@ def summarize(results: list[Result], t_wall: float | None = None) -> dict:
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99))}
 
 
+def compare(n_requests: int = 40, seed: int = 0, loads=(0.7, 2.0), budget_gb: float = 64.0, slots: int = 8,
+            stations=(64, 256), channels=(8, 48), timesteps=(8, 120)) -> dict:
+    """Batched vs plain on the same Poisson streams: a calibration pass
+    measures the plain capacity (requests/s, 8 requests arriving at once),
+    then each load (a fraction of that capacity) is run in both modes."""
+    import torch
+
+    torch.cuda.init()
+    shape = dict(stations=tuple(stations), channels=tuple(channels), timesteps=tuple(timesteps))
+    calib = make_stream(min(8, n_requests), seed=seed + 1000, rate_hz=1e9, **shape)
+    plain = Server(int(budget_gb * 2**30), mode="plain", keep_outputs=False)
+    Server(int(budget_gb * 2**30), mode="plain", keep_outputs=False).run(calib[:1])  # warm-up
+    t = time.perf_counter()
+    plain.run(calib)
+    cap = len(calib) / (time.perf_counter() - t)
+    out = {"calibration_plain_requests_per_s": cap, "shape": shape, "budget_gb": budget_gb, "slots": slots}
+    for load in loads:
+        key = f"load_{load:g}"
+        out[key] = {"arrival_rate_hz": load * cap}
+        for mode in ("plain", "batched"):
+            stream = make_stream(n_requests, seed=seed, rate_hz=load * cap, **shape)
+            srv = Server(int(budget_gb * 2**30), max_slots=slots, mode=mode, keep_outputs=False)
+            out[key][mode] = summarize(srv.run(stream))
+            del stream
+    return out
+
+
 def main(argv=None):
     import argparse
     import json
-
-    import torch
 
     from . import build
 
@@ -285,26 +310,8 @@ def main(argv=None):
     ap.add_argument("--timesteps", type=int, nargs=2, default=(8, 120))
     args = ap.parse_args(argv)
     build.build()
-    torch.cuda.init()
-    shape = dict(stations=tuple(args.stations), channels=tuple(args.channels), timesteps=tuple(args.timesteps))
-    # calibration: plain capacity (requests per second) on a few requests arriving at once
-    calib = make_stream(min(8, args.requests), seed=args.seed + 1000, rate_hz=1e9, **shape)
-    plain = Server(int(args.budget_gb * 2**30), mode="plain", keep_outputs=False)
-    Server(int(args.budget_gb * 2**30), mode="plain", keep_outputs=False).run(calib[:1])  # warm-up
-    t = time.perf_counter()
-    plain.run(calib)
-    cap = len(calib) / (time.perf_counter() - t)
-    rate = args.load * cap
-    out = {"calibration_plain_requests_per_s": cap, "shape": shape, "budget_gb": args.budget_gb,
-           "slots": args.slots}
-    for load in (args.load, args.saturated_load):
-        key = f"load_{load:g}"
-        out[key] = {"arrival_rate_hz": load * cap}
-        for mode in ("plain", "batched"):
-            stream = make_stream(args.requests, seed=args.seed, rate_hz=load * cap, **shape)
-            srv = Server(int(args.budget_gb * 2**30), max_slots=args.slots, mode=mode, keep_outputs=False)
-            out[key][mode] = summarize(srv.run(stream))
-            del stream
+    out = compare(args.requests, args.seed, (args.load, args.saturated_load), args.budget_gb, args.slots,
+                  args.stations, args.channels, args.timesteps)
     print(json.dumps(out))
 
 
