@@ -77,7 +77,7 @@ typedef struct {
   int32_t taper_kind;     /* IDG_TAPER_KB (beta = taper_beta, or 0.35*pi*P when <= 0) or IDG_TAPER_USER */
   double taper_beta;
   const double* taper_user; /* host [L] taper samples at l_i = (i - L/2) FOV/L (IDG_TAPER_USER), copied */
-  int32_t aterm_nodes;    /* nodes per axis of the A-term samples, >= 2 */
+  int32_t aterm_nodes;    /* nodes per axis of the A-term samples, 2 .. 25 */
   int32_t flags;          /* IDG_DROP_OUT_OF_GRID | IDG_SPLIT_AT_ATERM_INTERVALS | IDG_HOST_ONLY | IDG_PERSISTENT */
 } idg_geometry;
 

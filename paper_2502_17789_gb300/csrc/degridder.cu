@@ -256,12 +256,17 @@ static size_t degridder_smem(int nodes) {
   return sizeof(DegridSmem<L>) + sizeof(float2) * 2 * kDegridSegs * nodes * nodes * 4;
 }
 
+// The shared-memory limit is set for the largest node count any plan may
+// use, so plans with different node counts can share the kernels; the
+// occupancy (persistent grid size) follows this plan's own footprint.
 template <int L>
 static int configure_degridder_t(int nodes, int* persistent_blocks) {
+  const int smem_max = int(degridder_smem<L>(kMaxAtermNodes));
   const int smem = int(degridder_smem<L>(nodes));
-  cudaError_t e = cudaFuncSetAttribute(degridder_kernel<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(degridder_kernel<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(degridder_kernel<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(degridder_kernel<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   int per_sm = 0, dev = 0, sms = 0;
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, degridder_kernel<L, true>, kDegridThreads, smem);

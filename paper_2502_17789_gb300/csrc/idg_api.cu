@@ -261,7 +261,8 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
   if (!aterm_offsets) return set_err(nullptr, IDG_ERR_INVALID_ARG, "aterm_offsets is NULL");
   if ((n_baselines > 0 && !baselines) || (n_baselines > 0 && n_timesteps > 0 && !uvw_m) || (n_channels > 0 && !freqs_hz))
     return set_err(nullptr, IDG_ERR_INVALID_ARG, "NULL input table");
-  if (g->aterm_nodes < 2) return set_err(nullptr, IDG_ERR_INVALID_ARG, "aterm_nodes must be >= 2");
+  if (g->aterm_nodes < 2 || g->aterm_nodes > kMaxAtermNodes)
+    return set_err(nullptr, IDG_ERR_INVALID_ARG, "aterm_nodes must be in [2, 25]");
   const bool host_only = (g->flags & IDG_HOST_ONLY) != 0;
   if (!host_only && !supported_subgrid_size(g->subgrid_size))
     return set_err(nullptr, IDG_ERR_UNSUPPORTED, "device plans support subgrid_size 32, 64, 96 or 128");

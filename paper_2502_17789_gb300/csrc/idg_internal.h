@@ -54,6 +54,7 @@ struct DegridItem {
 };
 
 constexpr int kDegridMaxVis = 256;
+constexpr int kMaxAtermNodes = 25;  // A-term samples per axis (bounds the degridder's shared memory)
 constexpr int kDegridSegs = 2;  // segments per degridder work item
 
 // ---------------------------------------------------------------- planner

@@ -241,7 +241,7 @@ class Plan:
 
     def __init__(self, obs=None, *, grid_size=None, subgrid_size=None, kernel_padding=None, image_size=None,
                  n_stations=None, baselines=None, uvw=None, freqs=None, aterm_offsets=None, aterm_nodes=9,
-                 flags=0, taper_beta=0.0, stream=None):
+                 flags=0, taper_beta=0.0, taper_user=None, stream=None):
         if obs is not None:
             grid_size = obs.grid_size if grid_size is None else grid_size
             subgrid_size = obs.subgrid_size if subgrid_size is None else subgrid_size
@@ -250,7 +250,7 @@ class Plan:
             n_stations, baselines, uvw = obs.n_stations, obs.baselines, obs.uvw
             freqs, aterm_offsets, aterm_nodes = obs.freqs, obs.aterm_offsets, obs.aterm_nodes
         self.geometry, self._keep = make_geometry(grid_size, subgrid_size, kernel_padding, image_size, taper_beta,
-                                                  aterm_nodes, flags)
+                                                  aterm_nodes, flags, taper_user)
         if stream is None and not (flags & IDG_HOST_ONLY):
             import torch
             stream = torch.cuda.current_stream().cuda_stream  # 0 when that is the legacy default stream

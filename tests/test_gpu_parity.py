@@ -332,3 +332,69 @@ def test_bounded_wait_reports_timeout(idg_mod, oracle_mod, cuda_device):
     with pytest.raises(idg_mod.IdgError) as e:
         c.plan.wait_selftest(0)
     assert e.value.status == 1
+
+
+def _small_obs(rng, L, nodes=9, n_t=10, n_ch=12):
+    enu = synth.stations_uniform_disk(rng, 8, 3000.0)
+    return synth.make_observation(enu, n_t, 2.0, np.linspace(140e6, 170e6, n_ch), 4, 4096, L, 18, 0.5,
+                                  aterm_nodes=nodes, name="small")
+
+
+@pytest.mark.parametrize("nodes,L", [(5, 64), (13, 96), (2, 128)])
+def test_aterm_node_counts(idg_mod, oracle_mod, cuda_device, nodes, L):
+    """A-term sampling grids other than 9 x 9 (Section 3.3 interpolation)."""
+    rng = np.random.default_rng(nodes)
+    obs = _small_obs(rng, L, nodes)
+    A = synth.aterms_random(rng, obs.n_intervals, obs.n_stations, nodes)
+    vis = synth.random_visibilities(rng, obs)
+    N = obs.grid_size
+    Grand = (rng.standard_normal((4, N, N)) + 1j * rng.standard_normal((4, N, N))) * 1e-3
+    c = Case(idg_mod, oracle_mod, obs, A, vis)
+    assert _rel(c.gpu_grid(), c.oracle_grid()) < GRID_TOL
+    assert _degrid_err(c.gpu_degrid(Grand), c.oracle_degrid(Grand)) < DEGRID_TOL
+
+
+def test_plans_with_different_node_counts_coexist(idg_mod, oracle_mod, cuda_device):
+    """A plan made after another with more A-term nodes must not shrink the
+    kernels' shared-memory limit below what the first plan needs."""
+    rng = np.random.default_rng(21)
+    big = _small_obs(rng, 96, 17)
+    A_big = synth.aterms_random(rng, big.n_intervals, big.n_stations, 17)
+    vis = synth.random_visibilities(rng, big)
+    c_big = Case(idg_mod, oracle_mod, big, A_big, vis)
+    small = _small_obs(rng, 96, 3)
+    c_small = Case(idg_mod, oracle_mod, small, synth.aterms_random(rng, small.n_intervals, small.n_stations, 3),
+                   synth.random_visibilities(rng, small))
+    N = big.grid_size
+    Grand = (rng.standard_normal((4, N, N)) + 1j * rng.standard_normal((4, N, N))) * 1e-3
+    assert _degrid_err(c_big.gpu_degrid(Grand), c_big.oracle_degrid(Grand)) < DEGRID_TOL
+    assert _degrid_err(c_small.gpu_degrid(Grand), c_small.oracle_degrid(Grand)) < DEGRID_TOL
+
+
+def test_user_taper(idg_mod, oracle_mod, cuda_device):
+    """IDG_TAPER_USER: the caller's taper samples replace the Kaiser-Bessel taper."""
+    import torch
+    rng = np.random.default_rng(5)
+    obs = _small_obs(rng, 64)
+    L = obs.subgrid_size
+    x = (np.arange(L) - L / 2) / L
+    taper = 0.54 + 0.46 * np.cos(2 * np.pi * x)          # a Hamming-like window, positive everywhere
+    A = synth.aterms_random(rng, obs.n_intervals, obs.n_stations, obs.aterm_nodes)
+    vis = synth.random_visibilities(rng, obs)
+    plan = idg_mod.Plan(obs, taper_user=taper)
+    geom = oracle_mod.Geometry(obs.grid_size, L, obs.kernel_padding, obs.image_size, taper_kind=1, taper_user=taper,
+                               aterm_nodes=obs.aterm_nodes)
+    ref_plan = oracle_mod.plan(geom, obs.uvw, obs.freqs, obs.aterm_offsets)
+    args = (geom, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets, ref_plan)
+    N = obs.grid_size
+    G = torch.zeros((4, N, N), dtype=torch.complex128, device="cuda")
+    plan.grid(torch.as_tensor(vis.astype(np.complex64)).cuda(), torch.as_tensor(A).cuda(), G)
+    plan.synchronize()
+    G_ref = oracle_mod.grid(*args, vis.astype(np.complex64).astype(np.complex128), A.astype(np.complex128))
+    assert _rel(G.cpu().numpy(), G_ref) < GRID_TOL
+    V = torch.empty(vis.shape, dtype=torch.complex64, device="cuda")
+    plan.degrid(torch.as_tensor(G_ref).cuda(), torch.as_tensor(A).cuda(), V)
+    plan.synchronize()
+    V_ref = oracle_mod.degrid(*args, G_ref, A.astype(np.complex128))
+    assert _degrid_err(V.cpu().numpy(), V_ref) < DEGRID_TOL
+    plan.close()

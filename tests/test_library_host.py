@@ -133,3 +133,17 @@ def test_wait_selftest_rejects_host_plans(idg_mod):
         assert e.value.status == 1
     finally:
         idg_mod.idg_plan_destroy(plan)
+
+
+def test_aterm_nodes_bounds(idg_mod):
+    obs = _brute.tiny_observation(seed=1)
+    for nodes, ok in ((1, False), (2, True), (25, True), (26, False)):
+        g, _ = idg_mod.make_geometry(obs.grid_size, obs.subgrid_size, obs.kernel_padding, obs.image_size,
+                                     aterm_nodes=nodes, flags=idg_mod.IDG_HOST_ONLY)
+        if ok:
+            idg_mod.idg_plan_destroy(idg_mod.idg_plan_create(g, obs.n_stations, obs.baselines, obs.uvw, obs.freqs,
+                                                             obs.aterm_offsets))
+        else:
+            with pytest.raises(idg_mod.IdgError) as e:
+                idg_mod.idg_plan_create(g, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets)
+            assert e.value.status == 1
