@@ -19,7 +19,7 @@
 // with two segments, each pixel pair gets one Z per segment and every lane
 // reads the Z of its own visibility's segment.
 // Phases use the same FP64 offset / exact anchor reduction / FP32 increment
-// scheme as the gridder.
+// scheme as the gridder, with one anchor per 16 pixels of a row.
 #include "kernels_common.cuh"
 
 namespace idg {
@@ -31,7 +31,7 @@ constexpr int kRangeBlocks = 8;   // pixel blocks per work unit (one per warp pe
 template <int L>
 struct DegridSmem {
   float4 z[2][kDegridSegs][kChunkBlocks][4][4];  // [buf][segment][block][pixel pair][pol] {Zr_a, Zr_b, Zi_a, Zi_b}
-  float4 g[2][kChunkBlocks][3];     // block geometry
+  float4 g[2][kChunkBlocks / 2][5]; // geometry of the 16-pixel phase-anchor blocks
   float4 coef[8][2][32];            // [vis group][half][lane]: (ah, bh, al, bl), (w, 2 pi a, 2 pi w, 0)
   float out[8][kDegridThreads];     // [component][visibility slot], accumulated with shared atomics
 };
@@ -90,7 +90,6 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
 #pragma unroll
     for (int c = 0; c < 8; ++c) S.out[c][tid] = 0.f;
   }
-  const float2 DI[4] = {{-4.f, -3.f}, {-2.f, -1.f}, {0.f, 1.f}, {2.f, 3.f}};
   const float2* Y = a.scratch + size_t(item.sg) * 4 * L * L;
 
   // prologue geometry: each thread builds one pixel pair (2 consecutive pixels) per chunk
@@ -151,9 +150,9 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
 #pragma unroll
     for (int p = 0; p < 4; ++p) S.z[buf][s][pb][pq][p] = zo[p];
     }
-    if (tid < kChunkBlocks * 3) {
-      const int b = tid / 3, c = tid % 3;
-      S.g[buf][b][c] = a.blk[size_t(chunk * kChunkBlocks + b) * 3 + c];
+    if (tid < kChunkBlocks / 2 * 5) {
+      const int b = tid / 5, c = tid % 5;
+      S.g[buf][b][c] = a.blk16[size_t(chunk * (kChunkBlocks / 2) + b) * 5 + c];
     }
   };
 
@@ -179,26 +178,30 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
         IM[p] = make_float2(0.f, 0.f);
       }
 #pragma unroll 1
-      for (int b = warp * kRangeBlocks; b < (warp + 1) * kRangeBlocks; ++b) {
-        const float4 g0 = S.g[buf][b][0], g1 = S.g[buf][b][1], g2 = S.g[buf][b][2];
-        const float n0 = g0.x, di0 = g2.y, dj0 = g2.z;
-        const float2 DN[4] = {{g0.y, g0.z}, {g0.w, g1.x}, {g1.y, g1.z}, {g1.w, g2.x}};
+      for (int b2 = warp * (kRangeBlocks / 2); b2 < (warp + 1) * (kRangeBlocks / 2); ++b2) {
+        // one phase anchor per 16 pixels (pixel 8 of the block): exact reduction there, FP32 increments
+        const float4* G = S.g[buf][b2];
+        const float4 g0 = G[0], g4 = G[4];
+        const float n0 = g0.x, di0 = g4.y, dj0 = g4.z;
         const float sh = fmaf(c0.x, di0, c0.y * dj0);
         const float d1 = __fsub_rn(sh, round_nearest(sh));
         const float lo = fmaf(c1.x, n0, fmaf(c0.z, di0, c0.w * dj0));
         float rr = __fadd_rn(d1, lo);
         rr = __fmul_rn(__fsub_rn(rr, round_nearest(rr)), kTwoPiF);
         const float2 R0 = make_float2(rr, rr);
+        const float* dn = reinterpret_cast<const float*>(G) + 1;  // dn[0..15]
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float2 ph = ffma2(CRR, DN[q], ffma2(ARR, DI[q], R0));
+        for (int q = 0; q < 8; ++q) {
+          const float2 DN = make_float2(dn[2 * q], dn[2 * q + 1]);
+          const float2 DI = make_float2(float(2 * q - 8), float(2 * q - 7));
+          const float2 ph = ffma2(CRR, DN, ffma2(ARR, DI, R0));
           float2 Cs, Sn;
           __sincosf(ph.x, &Sn.x, &Cs.x);
           __sincosf(ph.y, &Sn.y, &Cs.y);
           const float2 NS = make_float2(-Sn.x, -Sn.y);
 #pragma unroll
           for (int p = 0; p < 4; ++p) {
-            const float4 z = zs[b][q][p];
+            const float4 z = zs[2 * b2 + (q >> 2)][q & 3][p];
             const float2 ZR = make_float2(z.x, z.y), ZI = make_float2(z.z, z.w);
             // V += Z conj(e): re += Zr c + Zi s, im += Zi c - Zr s
             RE[p] = ffma2(ZR, Cs, RE[p]);

@@ -61,6 +61,7 @@ struct idg_plan {
   double* d_fscale = nullptr;
   float* d_taper = nullptr;
   float4* d_blk = nullptr;
+  float4* d_blk16 = nullptr;
   float2* d_twiddle = nullptr;
   SubgridDesc* d_sg = nullptr;
   SegmentDesc* d_seg = nullptr;
@@ -156,7 +157,7 @@ void free_device(idg_plan* p) {
   p->graph_degrid = {};
   void* ptrs[] = {p->d_uvw,    p->d_fscale, p->d_taper,   p->d_blk,     p->d_twiddle, p->d_sg,     p->d_seg,
                   p->d_gitems, p->d_ditems, p->d_scratch, p->d_records, p->d_status,  p->d_queue,
-                  p->d_adiag};
+                  p->d_adiag,  p->d_blk16};
   // stream-ordered frees: no device-wide synchronisation, so plans of other
   // streams keep running while this one is released
   for (void* q : ptrs)
@@ -165,6 +166,7 @@ void free_device(idg_plan* p) {
   p->d_fscale = nullptr;
   p->d_taper = nullptr;
   p->d_blk = nullptr;
+  p->d_blk16 = nullptr;
   p->d_twiddle = nullptr;
   p->d_sg = nullptr;
   p->d_seg = nullptr;
@@ -197,6 +199,31 @@ std::vector<float4> block_geometry(int L, double fov) {
       g[0] = make_float4(float(n0), dn[0], dn[1], dn[2]);
       g[1] = make_float4(dn[3], dn[4], dn[5], dn[6]);
       g[2] = make_float4(dn[7], float(ia - L / 2), float(j - L / 2), 0.f);
+    }
+  return t;
+}
+
+// Same for blocks of 16 pixels (the degridder's phase anchors), anchor at pixel 8:
+// [j][m][5] = (n0, dn[0..2]) (dn[3..6]) (dn[7..10]) (dn[11..14]) (dn[15], i_a - L/2, j - L/2, 0)
+std::vector<float4> block_geometry16(int L, double fov) {
+  const int bpr = L / 16;
+  std::vector<float4> t(size_t(L) * bpr * 5);
+  auto nprime = [&](int i, int j) {
+    const double l = double(i - L / 2) * fov / double(L), m = double(j - L / 2) * fov / double(L);
+    return std::sqrt(1.0 - l * l - m * m) - 1.0;
+  };
+  for (int j = 0; j < L; ++j)
+    for (int mb = 0; mb < bpr; ++mb) {
+      const int ia = mb * 16 + 8;
+      const double n0 = nprime(ia, j);
+      float dn[16];
+      for (int k = 0; k < 16; ++k) dn[k] = float(nprime(mb * 16 + k, j) - n0);
+      float4* g = &t[(size_t(j) * bpr + mb) * 5];
+      g[0] = make_float4(float(n0), dn[0], dn[1], dn[2]);
+      g[1] = make_float4(dn[3], dn[4], dn[5], dn[6]);
+      g[2] = make_float4(dn[7], dn[8], dn[9], dn[10]);
+      g[3] = make_float4(dn[11], dn[12], dn[13], dn[14]);
+      g[4] = make_float4(dn[15], float(ia - L / 2), float(j - L / 2), 0.f);
     }
   return t;
 }
@@ -377,6 +404,7 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     taper_d = kaiser_bessel_taper(L, g->taper_beta > 0.0 ? g->taper_beta : 0.35 * kPi * g->kernel_padding);
   std::vector<float> taper_f(taper_d.begin(), taper_d.end());
   std::vector<float4> blk = block_geometry(L, g->image_size);
+  std::vector<float4> blk16 = block_geometry16(L, g->image_size);
   std::vector<float2> tw(L);
   for (int m = 0; m < L; ++m) {
     const double ang = -2.0 * kPi * double(m) / double(L);
@@ -394,6 +422,7 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
   if (!e) e = upload(p, &p->d_fscale, fscale.data(), fscale.size());
   if (!e) e = upload(p, &p->d_taper, taper_f.data(), taper_f.size());
   if (!e) e = upload(p, &p->d_blk, blk.data(), blk.size());
+  if (!e) e = upload(p, &p->d_blk16, blk16.data(), blk16.size());
   if (!e) e = upload(p, &p->d_twiddle, tw.data(), tw.size());
   if (!e) e = upload(p, &p->d_sg, p->exec.data(), p->exec.size());
   if (!e) e = upload(p, &p->d_seg, p->part.segments.data(), p->part.segments.size());
@@ -556,7 +585,7 @@ idg_status idg_degrid(idg_plan* plan, const void* grid_c128, const void* aterms_
     da.seg = plan->d_seg;
     da.items = plan->d_ditems + b.di_offset;
     da.taper = plan->d_taper;
-    da.blk = plan->d_blk;
+    da.blk16 = plan->d_blk16;
     da.scratch = plan->d_scratch;
     da.g = kgeom(plan);
     e = timed(plan, kDegridder, [&] {

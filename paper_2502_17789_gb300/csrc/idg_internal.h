@@ -143,7 +143,7 @@ struct DegridArgs {
   const SegmentDesc* seg;
   const DegridItem* items;
   const float* taper;
-  const float4* blk;
+  const float4* blk16;        // [L][L/16][5] 16-pixel block geometry (n0, dn[16], anchor offsets)
   const float2* scratch;      // [batch][4][L][L] subgrid images Y
   KernelGeom g;
 };
