@@ -41,7 +41,8 @@ CSRC = os.path.join(ROOT, "paper_2502_17789_gb300", "csrc")
 # the capture that --record-traffic reads (one pass per launch, full-size workload)
 NCU_LAUNCH_LIST = ('ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum '
                    '--clock-control none -k regex:"gridder|fft|splitter|stage|aterm" -c 300 --csv '
-                   '--log-file launches.csv python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e')
+                   '--log-file launches.csv python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e '
+                   '--serving-requests 0')
 KERNEL_SOURCES = {"gridder": ["gridder.cu", "kernels_common.cuh", "idg_internal.h"],
                   "degridder": ["degridder.cu", "kernels_common.cuh", "idg_internal.h"]}
 
