@@ -686,11 +686,15 @@ idg_status idg_synchronize(idg_plan* plan) {
   if (plan->host_only) return IDG_OK;
   int e = int(cudaStreamSynchronize(plan->stream));
   if (e) return cuda_err(plan, e, "idg_synchronize");
+  // stream-ordered read (and reset) of the status word: no device-wide synchronisation
   int status = 0;
-  e = int(cudaMemcpy(&status, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  e = int(cudaMemcpyAsync(&status, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost, plan->stream));
+  if (!e) e = int(cudaStreamSynchronize(plan->stream));
   if (e) return cuda_err(plan, e, "idg_synchronize");
   if (status) {
-    cudaMemset(plan->d_status, 0, sizeof(int));
+    e = int(cudaMemsetAsync(plan->d_status, 0, sizeof(int), plan->stream));
+    if (!e) e = int(cudaStreamSynchronize(plan->stream));
+    if (e) return cuda_err(plan, e, "idg_synchronize");
     return set_err(plan, IDG_ERR_TIMEOUT, "a kernel gave up waiting for a bulk copy (bounded wait expired)");
   }
   return IDG_OK;
