@@ -12,6 +12,8 @@ Every function follows a passage of the paper (arXiv 2502.17789):
   degrid()  Section 2.5 prediction steps 3a-3c, Eq. 13 (adjoint reading)
   taper()   Section 4.2 Kaiser-Bessel taper
   dft2()    the subgrid Fourier transform of Eq. 8 (centred, unnormalised)
+  invert()  Section 2.5 imaging step 3, Eq. 11 with the single w = 0 layer
+  predict() Section 2.5 prediction step 2, Eq. 12 with w = 0 (adjoint reading)
 """
 from __future__ import annotations
 
@@ -226,3 +228,47 @@ def aterm_interp(A: np.ndarray, L: int) -> np.ndarray:
     if st != 0:
         raise OracleError(st, "aterm_interp")
     return out
+
+
+def _centre_signs(N: int) -> np.ndarray:
+    """(-1)^(x+y) on an N x N plane: with it, a plain FFT of even length N is
+    the centred transform sum_X f(X) e^{-+2 pi i (X - N/2)(p - N/2)/N}."""
+    s = (-1.0) ** np.arange(N)
+    return np.outer(s, s)
+
+
+def image_taper(geom: Geometry) -> np.ndarray:
+    """T(l_p) T(m_q) on the master image, l_p = (p - N/2) FOV/N ([q][p])."""
+    if geom.taper_kind != 0:
+        raise ValueError("the image-domain wrapper needs the Kaiser-Bessel taper")
+    t = taper(geom.grid_size, geom.beta)
+    return np.outer(t, t)
+
+
+def invert(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Plan, vis, aterms):
+    """Dirty image, complex128 [4][N][N] indexed [pol][q][p] at (l_p, m_q):
+    I = sum_{X,Y} G(X,Y) e^{+2 pi i (u_X l_p + v_Y m_q)} / (L^2 T(l_p) T(m_q)),
+    G the gridded visibilities.  The L^2 T T factor is what the gridder puts
+    on every image point (taper once per direction, unnormalised L x L
+    transforms); dividing it out is Eq. 11's 1/T correction."""
+    N, L = geom.grid_size, geom.subgrid_size
+    if N % 2:
+        raise ValueError("N must be even")
+    G = grid(geom, n_st, baselines, uvw, freqs, aterm_offsets, pl, vis, aterms)
+    S = _centre_signs(N)
+    img = np.fft.ifft2(G * S[None], axes=(-2, -1)) * float(N) * float(N) * S[None]
+    return img / (float(L) * float(L) * image_taper(geom)[None])
+
+
+def predict(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Plan, image, aterms):
+    """Visibilities of an image (the adjoint of invert): the model grid
+    G(X,Y) = sum_{p,q} I e^{-2 pi i (u_X l_p + v_Y m_q)} / (L^2 T(l_p) T(m_q)),
+    then degrid.  With the degridder's own taper this predicts Eq. 1 on
+    the image's pixels."""
+    N, L = geom.grid_size, geom.subgrid_size
+    if N % 2:
+        raise ValueError("N must be even")
+    S = _centre_signs(N)
+    src = np.asarray(image, np.complex128) / (float(L) * float(L) * image_taper(geom)[None])
+    G = np.fft.fft2(src * S[None], axes=(-2, -1)) * S[None]
+    return degrid(geom, n_st, baselines, uvw, freqs, aterm_offsets, pl, G, aterms)

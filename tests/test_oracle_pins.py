@@ -346,3 +346,74 @@ def test_degrid_off_grid_sources_within_aliasing_bound(oracle_mod):
         V = _degrid(oracle_mod, obs, geom, pl, G, A)
         want = L * L * _brute.measurement_equation(obs, A, l, m, np.eye(2))
         assert np.abs(V - want).max() / np.abs(want).max() < 1e-6
+
+
+# ---------------------------------------------------------------- image-domain wrapper (Eq. 11, Eq. 12)
+
+def _wrapper_args(obs, geom, pl):
+    return (geom, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets, pl)
+
+
+def test_invert_equals_direct_adjoint_on_the_subgrid_lattice(oracle_mod):
+    """On image pixels that coincide with subgrid pixel positions
+    (p - N/2 = (N/L)(i - L/2)) the dirty image is exactly the adjoint of
+    Eq. 1 with A-terms: the gridder's L^2 T_i T_j is divided out by the same
+    taper values.  The check is a direct sum over the visibilities."""
+    obs, geom, pl, A, vis = _problem(oracle_mod, seed=5)
+    N, L, fov = obs.grid_size, obs.subgrid_size, obs.image_size
+    img = oracle_mod.invert(*_wrapper_args(obs, geom, pl), vis, A)
+    r = N // L
+    worst = 0.0
+    for (i, j) in [(8, 8), (3, 11), (12, 2), (5, 7), (9, 14)]:
+        p, q = N // 2 + r * (i - L // 2), N // 2 + r * (j - L // 2)
+        l, m = (p - N // 2) * fov / N, (q - N // 2) * fov / N
+        want = _brute.dft_image(obs, vis, A, l, m).reshape(4)
+        worst = max(worst, np.abs(img[:, q, p] - want).max() / np.abs(want).max())
+    assert worst < 1e-9
+
+
+def test_predict_of_a_lattice_point_source_is_the_measurement_equation(oracle_mod):
+    """predict() of an image holding brightness B on one lattice pixel gives
+    Eq. 1 for a point source there, exactly."""
+    obs, geom, pl, A, _ = _problem(oracle_mod, seed=6)
+    N, L, fov = obs.grid_size, obs.subgrid_size, obs.image_size
+    r = N // L
+    B = np.array([[0.9, 0.1 + 0.3j], [0.1 - 0.3j, 1.4]])
+    for (i, j) in [(8, 8), (4, 10), (11, 5)]:
+        p, q = N // 2 + r * (i - L // 2), N // 2 + r * (j - L // 2)
+        img = np.zeros((4, N, N), complex)
+        img[:, q, p] = B.reshape(4)
+        V = oracle_mod.predict(*_wrapper_args(obs, geom, pl), img, A)
+        l, m = (p - N // 2) * fov / N, (q - N // 2) * fov / N
+        want = _brute.measurement_equation(obs, A, l, m, B)
+        assert _relerr(V, want) < 1e-10
+
+
+def test_predict_is_the_adjoint_of_invert(oracle_mod):
+    obs, geom, pl, A, vis = _problem(oracle_mod, seed=7)
+    N = obs.grid_size
+    rng = np.random.default_rng(3)
+    img = rng.standard_normal((4, N, N)) + 1j * rng.standard_normal((4, N, N))
+    lhs = np.vdot(oracle_mod.predict(*_wrapper_args(obs, geom, pl), img, A), vis)
+    rhs = np.vdot(img, oracle_mod.invert(*_wrapper_args(obs, geom, pl), vis, A))
+    assert abs(lhs - rhs) / abs(rhs) < 1e-11
+
+
+def test_invert_off_lattice_within_aliasing_bound(oracle_mod):
+    """Anywhere in the central 1/1.5 of the field the dirty image agrees with
+    the direct adjoint of Eq. 1 to the taper kernel's aliasing level (P = 18,
+    default beta)."""
+    obs = _tiny(seed=9, n_st=5, n_t=4, n_ch=3, N=1024, L=96, P=18, fov=0.5, diameter=400.0)
+    geom = _geom(oracle_mod, obs)
+    pl = oracle_mod.plan(geom, obs.uvw, obs.freqs, obs.aterm_offsets)
+    A = synth.aterms_identity(obs.n_intervals, obs.n_stations).astype(np.complex128)
+    rng = np.random.default_rng(4)
+    vis = rng.standard_normal(obs.uvw.shape[:2] + (obs.n_channels, 4)) \
+        + 1j * rng.standard_normal(obs.uvw.shape[:2] + (obs.n_channels, 4))
+    img = oracle_mod.invert(*_wrapper_args(obs, geom, pl), vis, A)
+    N, fov = obs.grid_size, obs.image_size
+    scale = np.abs(vis).sum()
+    for (p, q) in [(611, 433), (371, 660), (512, 301), (689, 689)]:
+        l, m = (p - N // 2) * fov / N, (q - N // 2) * fov / N
+        want = _brute.dft_image(obs, vis, A, l, m).reshape(4)
+        assert np.abs(img[:, q, p] - want).max() / scale < 1e-6
