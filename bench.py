@@ -42,7 +42,7 @@ CSRC = os.path.join(ROOT, "paper_2502_17789_gb300", "csrc")
 NCU_LAUNCH_LIST = ('ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum '
                    '--clock-control none -k regex:"gridder|fft|splitter|stage|aterm" -c 300 --csv '
                    '--log-file launches.csv python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e '
-                   '--serving-requests 0')
+                   '--serving-requests 0 --image-steps 0')
 KERNEL_SOURCES = {"gridder": ["gridder.cu", "kernels_common.cuh", "idg_internal.h"],
                   "degridder": ["degridder.cu", "kernels_common.cuh", "idg_internal.h"]}
 
@@ -71,6 +71,8 @@ def parse_args():
                     help="read an ncu launch list (--csv, with dram__bytes_read.sum and dram__bytes_write.sum) "
                          "of this command's default workload and store the per-launch DRAM bytes of the gridder "
                          "and degridder, keyed by the digest of their sources, in profiles/kernel_traffic.json")
+    ap.add_argument("--image-steps", type=int, default=2,
+                    help="timed invert + predict calls of the image-domain wrapper; 0 = skip")
     ap.add_argument("--serving-requests", type=int, default=24,
                     help="requests of the serving comparison (batched vs plain at 2x plain capacity); 0 = skip")
     ap.add_argument("--aterms", choices=["beam", "full"], default="beam",
@@ -367,6 +369,29 @@ def run_native(args):
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
     gpu_launches = int(sum(v[1] for v in prof.values()))
 
+    # image-domain wrapper (Eq. 11 / Eq. 12): invert = grid + master-grid transform + taper correction,
+    # predict = the reverse; one timed call each after an untimed one that makes the cuFFT plan
+    image_domain = None
+    if args.image_steps > 0:
+        img = torch.empty_like(G_out)
+        plan.invert(vis_d, A_d, G_out, img)
+        plan.predict(img, A_d, G_out, vis_pred)
+        torch.cuda.synchronize(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        inv_ms = pred_ms = 0.0
+        for _ in range(args.image_steps):
+            ev[0].record(stream)
+            plan.invert(vis_d, A_d, G_out, img)
+            ev[1].record(stream)
+            plan.predict(img, A_d, G_out, vis_pred)
+            ev[2].record(stream)
+            torch.cuda.synchronize(dev)
+            inv_ms += ev[0].elapsed_time(ev[1])
+            pred_ms += ev[1].elapsed_time(ev[2])
+        image_domain = {"invert_ms": inv_ms / args.image_steps, "predict_ms": pred_ms / args.image_steps,
+                        "image": f"complex128 [4][{N}][{N}]", "transform": "cuFFT Z2Z, 4 planes"}
+        del img
+
     # end to end through the C ABI with host buffers
     e2e = None
     if args.no_e2e:
@@ -440,7 +465,7 @@ def run_native(args):
                    "subgrids": st.n_subgrids, "segments": st.n_segments, "batches": st.n_batches,
                    "vis_pixels_per_direction": st.vis_pixels},
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches,
-        "kernels": kernels, "serving": serving,
+        "kernels": kernels, "image_domain": image_domain, "serving": serving,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -227,6 +227,43 @@ idg_status idg_profile_read(idg_plan* plan, double* ms, int64_t* launches);
 idg_status idg_grid_noalloc(idg_plan* plan, const void* vis_c64, const void* aterms_c64, void* grid_c128);
 
 /*
+ * idg_invert -- dirty image: Section 2.5 imaging step 3, Eq. 11 with the
+ * single w = 0 layer (subgrids here have w0 = 0).  Zeroes `grid`, grids the
+ * visibilities into it exactly as idg_grid, then writes
+ *   image[pol][q][p] = sum_{X,Y} grid[pol][Y][X] e^{+2 pi i (u_X l_p + v_Y m_q)}
+ *                      / (L^2 T(l_p) T(m_q)),
+ *   u_X = (X - N/2) / FOV,  l_p = (p - N/2) FOV / N  (likewise v, m),
+ * i.e. the adjoint of the measurement equation (Eq. 1) with A-terms on the
+ * N x N image, with the gridder's taper and unnormalised L x L transforms
+ * divided out.  Pixels where T is small (the outer part of the field) carry
+ * amplified errors; the paper images the central part of a padded field.
+ *   vis_c64    device complex64 [n_baselines][n_timesteps][n_channels][4], read
+ *   aterms_c64 device complex64 [n_intervals][n_stations][nodes][nodes][4], read
+ *   grid_c128  device complex128 [4][N][N], overwritten with the gridded uv plane
+ *   image_c128 device complex128 [4][N][N] (pol, m, l), written
+ * The master-grid transform is cuFFT (4 double-complex planes) on the plan's
+ * stream; the first call on a plan creates its cuFFT plan (allocates).
+ * IDG_ERR_UNSUPPORTED with IDG_TAPER_USER (its samples exist only on the
+ * subgrid lattice) or an odd grid size; otherwise as idg_grid.
+ */
+idg_status idg_invert(idg_plan* plan, const void* vis_c64, const void* aterms_c64, void* grid_c128,
+                      void* image_c128);
+
+/*
+ * idg_predict -- visibilities of an image: Section 2.5 prediction step 2,
+ * Eq. 12 with w = 0, in the adjoint reading of idg_invert:
+ *   grid[pol][Y][X] = sum_{p,q} image[pol][q][p] e^{-2 pi i (u_X l_p + v_Y m_q)}
+ *                     / (L^2 T(l_p) T(m_q)),
+ * then idg_degrid(grid) into vis (overwritten).  With the degridder's own
+ * taper this predicts Eq. 1 on the image pixels.
+ *   image_c128 device complex128 [4][N][N], read;  grid_c128 overwritten;
+ *   vis_c64    device complex64 [n_baselines][n_timesteps][n_channels][4], written.
+ * Errors as idg_invert.
+ */
+idg_status idg_predict(idg_plan* plan, const void* image_c128, const void* aterms_c64, void* grid_c128,
+                       void* vis_c64);
+
+/*
  * idg_wait_selftest -- exercise the bounded-wait error path.  No counterpart
  * in the paper.  Enqueues on the plan's stream one warp that waits on a
  * shared-memory mbarrier nothing completes; after limit_us microseconds

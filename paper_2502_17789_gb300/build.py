@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libidg.so")
-SOURCES = ["planner.cpp", "gridder.cu", "fft.cu", "degridder.cu", "idg_api.cu", "noalloc.cu"]
+SOURCES = ["planner.cpp", "gridder.cu", "fft.cu", "degridder.cu", "idg_api.cu", "noalloc.cu", "image.cu"]
 HEADERS = ["idg_internal.h", "kernels_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
@@ -47,7 +47,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     tmp = LIB + ".tmp"
-    r = subprocess.run([NVCC] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
+    # cuFFT (the master-grid transform of the image-domain wrapper), found at run time next to the toolkit
+    import shutil
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(shutil.which(NVCC) or NVCC))), "lib64")
+    r = subprocess.run([NVCC] + ARCH + ["-shared", "-o", tmp] + objs +
+                       ["-L" + cuda_lib, "-lcufft", "-Xlinker", "-rpath," + cuda_lib],
+                       capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

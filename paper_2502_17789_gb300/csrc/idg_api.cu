@@ -7,6 +7,7 @@
 // together and their adds into the master grid stay in L2).  Within a batch
 // the work items are ordered longest-first so the tail of the launch is
 // short.
+#include <cufft.h>
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -72,6 +73,10 @@ struct idg_plan {
   int* d_status = nullptr;      // kernel status word (timeouts)
   int* d_queue = nullptr;       // work-queue counters, 2 per batch (gridder, degridder)
   uint8_t* d_adiag = nullptr;   // [n_int][n_st] diagonal-A-term flags of the current call
+  // image-domain wrapper, made at its first use
+  cufftHandle fft = 0;
+  bool fft_ready = false;
+  double* d_inv_t = nullptr;    // [N] 1 / T(l_p), l_p = (p - N/2) FOV/N
   int64_t max_batch_vis = 0;
   int persistent_grid_blocks = 0, persistent_degrid_blocks = 0;  // > 0: persistent launches
   struct GraphCache {
@@ -157,7 +162,7 @@ void free_device(idg_plan* p) {
   p->graph_degrid = {};
   void* ptrs[] = {p->d_uvw,    p->d_fscale, p->d_taper,   p->d_blk,     p->d_twiddle, p->d_sg,     p->d_seg,
                   p->d_gitems, p->d_ditems, p->d_scratch, p->d_records, p->d_status,  p->d_queue,
-                  p->d_adiag,  p->d_blk16};
+                  p->d_adiag,  p->d_blk16, p->d_inv_t};
   // stream-ordered frees: no device-wide synchronisation, so plans of other
   // streams keep running while this one is released
   for (void* q : ptrs)
@@ -167,6 +172,7 @@ void free_device(idg_plan* p) {
   p->d_taper = nullptr;
   p->d_blk = nullptr;
   p->d_blk16 = nullptr;
+  p->d_inv_t = nullptr;
   p->d_twiddle = nullptr;
   p->d_sg = nullptr;
   p->d_seg = nullptr;
@@ -459,6 +465,8 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
 idg_status idg_plan_destroy(idg_plan* plan) {
   if (!plan) return IDG_OK;
   if (!plan->host_only) cudaStreamSynchronize(plan->stream);
+  if (plan->fft_ready) cufftDestroy(plan->fft);
+  plan->fft_ready = false;
   release_events(plan);
   free_device(plan);
   if (!plan->host_only) cudaStreamSynchronize(plan->stream);
@@ -679,6 +687,77 @@ idg_status idg_grid_graph(idg_plan* plan, const void* vis_c64, const void* aterm
 
 idg_status idg_degrid_graph(idg_plan* plan, const void* grid_c128, const void* aterms_c64, void* vis_c64) {
   return run_graph(plan, true, grid_c128, aterms_c64, vis_c64);
+}
+
+// ------------------------------------------------------------------ image-domain wrapper
+
+static idg_status fft_err(idg_plan* p, cufftResult r, const char* what) {
+  return set_err(p, IDG_ERR_CUDA, std::string(what) + ": cuFFT error " + std::to_string(int(r)));
+}
+
+// cuFFT plan for the 4 master-grid planes and the image taper table, made once per plan
+static idg_status ensure_image(idg_plan* p) {
+  if (p->host_only) return set_err(p, IDG_ERR_INVALID_ARG, "plan was created with IDG_HOST_ONLY");
+  if (p->geom.taper_kind != IDG_TAPER_KB)
+    return set_err(p, IDG_ERR_UNSUPPORTED, "the image-domain wrapper needs the Kaiser-Bessel taper");
+  if (p->N % 2) return set_err(p, IDG_ERR_UNSUPPORTED, "the image-domain wrapper needs an even grid size");
+  if (!p->fft_ready) {
+    int n[2] = {p->N, p->N};
+    cufftResult r = cufftPlanMany(&p->fft, 2, n, nullptr, 1, p->N * p->N, nullptr, 1, p->N * p->N, CUFFT_Z2Z, 4);
+    if (r != CUFFT_SUCCESS) return fft_err(p, r, "cufftPlanMany");
+    p->fft_ready = true;
+    const double beta = p->geom.taper_beta > 0.0 ? p->geom.taper_beta : 0.35 * kPi * p->geom.kernel_padding;
+    std::vector<double> inv = kaiser_bessel_taper(p->N, beta);
+    for (double& v : inv) v = 1.0 / v;
+    const int e = upload(p, &p->d_inv_t, inv.data(), inv.size());
+    if (e) return cuda_err(p, e, "image taper table");
+  }
+  const cufftResult r = cufftSetStream(p->fft, p->stream);
+  if (r != CUFFT_SUCCESS) return fft_err(p, r, "cufftSetStream");
+  return IDG_OK;
+}
+
+idg_status idg_invert(idg_plan* plan, const void* vis_c64, const void* aterms_c64, void* grid_c128,
+                      void* image_c128) {
+  if (!plan) return set_err(nullptr, IDG_ERR_INVALID_ARG, "plan is NULL");
+  idg_status st;
+  if ((st = check_buffer(plan, grid_c128, "grid")) || (st = check_buffer(plan, image_c128, "image")) ||
+      (st = ensure_image(plan)))
+    return st;
+  const int N = plan->N;
+  const double inv_l2 = 1.0 / (double(plan->L) * double(plan->L));
+  int e = int(cudaMemsetAsync(grid_c128, 0, size_t(4) * N * N * sizeof(double2), plan->stream));
+  if (e) return cuda_err(plan, e, "zeroing the grid");
+  if ((st = idg_grid(plan, vis_c64, aterms_c64, grid_c128))) return st;
+  double2* img = static_cast<double2*>(image_c128);
+  e = launch_sign_scale(static_cast<const double2*>(grid_c128), img, nullptr, 1.0, N, 4, plan->stream);
+  if (e) return cuda_err(plan, e, "centring signs");
+  const cufftResult r = cufftExecZ2Z(plan->fft, reinterpret_cast<cufftDoubleComplex*>(img),
+                                     reinterpret_cast<cufftDoubleComplex*>(img), CUFFT_INVERSE);
+  if (r != CUFFT_SUCCESS) return fft_err(plan, r, "cufftExecZ2Z");
+  e = launch_sign_scale(img, img, plan->d_inv_t, inv_l2, N, 4, plan->stream);
+  if (e) return cuda_err(plan, e, "taper correction");
+  return IDG_OK;
+}
+
+idg_status idg_predict(idg_plan* plan, const void* image_c128, const void* aterms_c64, void* grid_c128,
+                       void* vis_c64) {
+  if (!plan) return set_err(nullptr, IDG_ERR_INVALID_ARG, "plan is NULL");
+  idg_status st;
+  if ((st = check_buffer(plan, grid_c128, "grid")) || (st = check_buffer(plan, image_c128, "image")) ||
+      (st = ensure_image(plan)))
+    return st;
+  const int N = plan->N;
+  const double inv_l2 = 1.0 / (double(plan->L) * double(plan->L));
+  double2* g = static_cast<double2*>(grid_c128);
+  int e = launch_sign_scale(static_cast<const double2*>(image_c128), g, plan->d_inv_t, inv_l2, N, 4, plan->stream);
+  if (e) return cuda_err(plan, e, "taper correction");
+  const cufftResult r = cufftExecZ2Z(plan->fft, reinterpret_cast<cufftDoubleComplex*>(g),
+                                     reinterpret_cast<cufftDoubleComplex*>(g), CUFFT_FORWARD);
+  if (r != CUFFT_SUCCESS) return fft_err(plan, r, "cufftExecZ2Z");
+  e = launch_sign_scale(g, g, nullptr, 1.0, N, 4, plan->stream);
+  if (e) return cuda_err(plan, e, "centring signs");
+  return idg_degrid(plan, grid_c128, aterms_c64, vis_c64);
 }
 
 idg_status idg_synchronize(idg_plan* plan) {

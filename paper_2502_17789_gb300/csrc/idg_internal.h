@@ -162,6 +162,8 @@ int launch_gridder(int L, const GridArgs& a, int n_items, int persistent_blocks,
 int configure_gridder(int L, int* persistent_blocks);   // attributes + persistent grid size
 int configure_degridder(int L, int nodes, int* persistent_blocks);
 int launch_stage_records(int L, const StageArgs& a, int n_subgrids, void* stream);
+// out[k][y][x] = (-1)^(x+y) c w[y] w[x] in[k][y][x] over `planes` N x N complex128 planes (w may be null)
+int launch_sign_scale(const double2* in, double2* out, const double* w, double c, int N, int planes, void* stream);
 // one warp waits, bounded by limit_ns, on an mbarrier nothing completes; sets kStatusTimeout bit in *status
 int launch_wait_selftest(int* status, int64_t limit_ns, void* stream);
 // flags[i][s] = 1 when every node of A-term (interval i, station s) has zero off-diagonal entries

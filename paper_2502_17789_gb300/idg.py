@@ -26,7 +26,7 @@ IDG_DROP_OUT_OF_GRID, IDG_SPLIT_AT_ATERM_INTERVALS, IDG_HOST_ONLY, IDG_PERSISTEN
 # every function declared in include/idg.h
 EXPORTS = ["idg_plan_create", "idg_grid", "idg_degrid", "idg_grid_graph", "idg_degrid_graph", "idg_set_stream", "idg_plan_stats", "idg_plan_subgrids",
            "idg_plan_segments", "idg_subgrid_images", "idg_synchronize", "idg_profile_enable", "idg_profile_read",
-           "idg_grid_noalloc", "idg_wait_selftest", "idg_last_error",
+           "idg_grid_noalloc", "idg_invert", "idg_predict", "idg_wait_selftest", "idg_last_error",
            "idg_plan_destroy", "idg_abi_version"]
 KERNEL_CLASSES = ["gridder", "fft_adder", "splitter_ifft", "degridder", "stage", "aterm_flags"]
 
@@ -83,6 +83,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.idg_synchronize.argtypes = [P]
     lib.idg_grid_noalloc.argtypes = [P, P, P, P]
     lib.idg_wait_selftest.argtypes = [P, ctypes.c_int32]
+    lib.idg_invert.argtypes = [P, P, P, P, P]
+    lib.idg_predict.argtypes = [P, P, P, P, P]
     lib.idg_profile_enable.argtypes = [P, i32]
     lib.idg_profile_read.argtypes = [P, P, P]
     lib.idg_last_error.argtypes = [P]
@@ -134,6 +136,14 @@ def idg_grid(plan, vis_ptr, aterms_ptr, grid_ptr):
 
 def idg_grid_noalloc(plan, vis_ptr, aterms_ptr, grid_ptr):
     _check(load().idg_grid_noalloc(plan, vis_ptr, aterms_ptr, grid_ptr), "idg_grid_noalloc", plan)
+
+
+def idg_invert(plan, vis_ptr, aterms_ptr, grid_ptr, image_ptr):
+    _check(load().idg_invert(plan, vis_ptr, aterms_ptr, grid_ptr, image_ptr), "idg_invert", plan)
+
+
+def idg_predict(plan, image_ptr, aterms_ptr, grid_ptr, vis_ptr):
+    _check(load().idg_predict(plan, image_ptr, aterms_ptr, grid_ptr, vis_ptr), "idg_predict", plan)
 
 
 def idg_wait_selftest(plan, limit_us: int):
@@ -287,6 +297,16 @@ class Plan:
 
     def synchronize(self):
         idg_synchronize(self.handle)
+
+    def invert(self, vis, aterms, grid, image):
+        """Dirty image [4, N, N] (pol, m, l) of `vis`; `grid` receives the uv plane."""
+        idg_invert(self.handle, _dev_ptr(vis), _dev_ptr(aterms), _dev_ptr(grid), _dev_ptr(image))
+        return image
+
+    def predict(self, image, aterms, grid, vis):
+        """Visibilities of `image` [4, N, N]; `grid` receives the model uv plane."""
+        idg_predict(self.handle, _dev_ptr(image), _dev_ptr(aterms), _dev_ptr(grid), _dev_ptr(vis))
+        return vis
 
     def wait_selftest(self, limit_us: int = 20000):
         idg_wait_selftest(self.handle, limit_us)
