@@ -30,6 +30,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 FLAG_DROP = 1
 FLAG_SPLIT_INTERVALS = 2
+FLAG_W_LAYERS = 4
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsorted frequencies", 3: "uv out of grid",
           4: "w too large", 9: "capacity"}
@@ -64,9 +65,10 @@ def _load():
         P = ctypes.c_void_p
         i32, f64 = ctypes.c_int, ctypes.c_double
         lib.oracle_plan.argtypes = [i32, i32, i32, f64, i32, i32, i32, i32, P, P, P, i32,
-                                    P, i32, P, P, i32, P]
+                                    P, i32, P, P, i32, P, P, P]
         lib.oracle_plan.restype = i32
-        common = [i32, i32, i32, f64, i32, f64, P, i32, i32, i32, i32, i32, P, P, P, i32, P, i32, P, i32]
+        common = [i32, i32, i32, f64, i32, f64, P, i32, i32, i32, i32, i32, P, P, P, i32, P, i32, P, i32,
+                  P, f64, i32]
         lib.oracle_grid.argtypes = common + [P, P, P, P, P]
         lib.oracle_grid.restype = i32
         lib.oracle_degrid.argtypes = common + [P, P, P]
@@ -111,6 +113,18 @@ class Geometry:
 class Plan:
     subgrids: np.ndarray   # int32 [n_sg, 8]: b, t0, t1, c0, c1, x0, y0, dropped
     segments: np.ndarray   # int32 [n_seg, 4]: subgrid, interval, t_begin, t_end
+    layers: np.ndarray | None = None   # int32 [n_sg]: w layer k (w0 = k w_step); None = all 0
+    w_step: float = 0.0                # layer spacing 2 w_max, wavelengths
+
+    @property
+    def k_range(self) -> tuple[int, int]:
+        """(k_min, n_layers) of the non-dropped subgrids; (0, 1) without layers."""
+        if self.layers is None:
+            return 0, 1
+        keep = self.layers[self.subgrids[:, 7] == 0]
+        if keep.size == 0:
+            return 0, 1
+        return int(keep.min()), int(keep.max() - keep.min() + 1)
 
 
 def plan(geom: Geometry, uvw: np.ndarray, freqs: np.ndarray, aterm_offsets: np.ndarray) -> Plan:
@@ -127,17 +141,21 @@ def plan(geom: Geometry, uvw: np.ndarray, freqs: np.ndarray, aterm_offsets: np.n
     while True:
         sg = np.zeros((cap, 8), np.int32)
         seg = np.zeros((cap, 4), np.int32)
+        lay = np.zeros(cap, np.int32)
+        w_step = ctypes.c_double(0.0)
         nsg = ctypes.c_int(0)
         nseg = ctypes.c_int(0)
         st = lib.oracle_plan(geom.grid_size, geom.subgrid_size, geom.kernel_padding, geom.image_size,
                              geom.flags, n_bl, n_t, n_ch, _ptr(uvw), _ptr(freqs), _ptr(offs), n_int,
-                             _ptr(sg), cap, ctypes.byref(nsg), _ptr(seg), cap, ctypes.byref(nseg))
+                             _ptr(sg), cap, ctypes.byref(nsg), _ptr(seg), cap, ctypes.byref(nseg),
+                             _ptr(lay), ctypes.byref(w_step))
         if st == 9:
             cap *= 2
             continue
         if st != 0:
             raise OracleError(st, "plan")
-        return Plan(sg[: nsg.value].copy(), seg[: nseg.value].copy())
+        layers = lay[: nsg.value].copy() if geom.flags & FLAG_W_LAYERS else None
+        return Plan(sg[: nsg.value].copy(), seg[: nseg.value].copy(), layers, float(w_step.value))
 
 
 def _common(geom, baselines, uvw, freqs, aterm_offsets, pl, n_st):
@@ -148,11 +166,20 @@ def _common(geom, baselines, uvw, freqs, aterm_offsets, pl, n_st):
     sg = np.ascontiguousarray(pl.subgrids, dtype=np.int32)
     seg = np.ascontiguousarray(pl.segments, dtype=np.int32)
     n_bl, n_t, _ = uvw.shape
+    lay = None if pl.layers is None else np.ascontiguousarray(pl.layers, dtype=np.int32)
+    k_min, _ = pl.k_range
     args = [geom.grid_size, geom.subgrid_size, geom.kernel_padding, geom.image_size, geom.taper_kind,
             geom.beta, _ptr(tu), geom.aterm_nodes, n_st, n_bl, n_t, freqs.shape[0], _ptr(bl), _ptr(uvw),
-            _ptr(freqs), len(aterm_offsets) - 1, _ptr(sg), sg.shape[0], _ptr(seg), seg.shape[0]]
-    keep = (uvw, freqs, bl, tu, sg, seg)
+            _ptr(freqs), len(aterm_offsets) - 1, _ptr(sg), sg.shape[0], _ptr(seg), seg.shape[0],
+            _ptr(lay), pl.w_step, k_min]
+    keep = (uvw, freqs, bl, tu, sg, seg, lay)
     return args, keep
+
+
+def grid_shape(geom: Geometry, pl: Plan) -> tuple:
+    """[4][N][N] without w layers, [n_layers][4][N][N] with them."""
+    N = geom.grid_size
+    return (pl.k_range[1], 4, N, N) if pl.layers is not None else (4, N, N)
 
 
 def grid(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Plan, vis, aterms,
@@ -165,7 +192,8 @@ def grid(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Pl
     v = np.ascontiguousarray(vis, dtype=np.complex128)
     a = np.ascontiguousarray(aterms, dtype=np.complex128)
     N, L = geom.grid_size, geom.subgrid_size
-    g = np.zeros((4, N, N), np.complex128) if grid_in is None else np.array(grid_in, dtype=np.complex128, copy=True)
+    g = np.zeros(grid_shape(geom, pl), np.complex128) if grid_in is None else \
+        np.array(grid_in, dtype=np.complex128, copy=True)
     img = uv = None
     if want_subgrids:
         img = np.zeros((pl.subgrids.shape[0], 4, L, L), np.complex128)
@@ -245,30 +273,55 @@ def image_taper(geom: Geometry) -> np.ndarray:
     return np.outer(t, t)
 
 
+def _nprime_image(geom: Geometry) -> np.ndarray:
+    """n'(l_p, m_q) = sqrt(1 - l^2 - m^2) - 1 on the master image ([q][p])."""
+    N, fov = geom.grid_size, geom.image_size
+    l = (np.arange(N) - N // 2) * fov / N
+    return np.sqrt(1.0 - l[None, :] ** 2 - l[:, None] ** 2) - 1.0
+
+
 def invert(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Plan, vis, aterms):
     """Dirty image, complex128 [4][N][N] indexed [pol][q][p] at (l_p, m_q):
-    I = sum_{X,Y} G(X,Y) e^{+2 pi i (u_X l_p + v_Y m_q)} / (L^2 T(l_p) T(m_q)),
-    G the gridded visibilities.  The L^2 T T factor is what the gridder puts
-    on every image point (taper once per direction, unnormalised L x L
-    transforms); dividing it out is Eq. 11's 1/T correction."""
+    I = sum_layers e^{+2 pi i w0 n'} sum_{X,Y} G_w0(X,Y) e^{+2 pi i (u_X l_p + v_Y m_q)}
+        / (L^2 T(l_p) T(m_q)),
+    G_w0 the visibilities gridded onto layer w0 (Eq. 11; one layer w0 = 0
+    without w layers).  The L^2 T T factor is what the gridder puts on every
+    image point (taper once per direction, unnormalised L x L transforms);
+    dividing it out is Eq. 11's 1/T correction."""
     N, L = geom.grid_size, geom.subgrid_size
     if N % 2:
         raise ValueError("N must be even")
     G = grid(geom, n_st, baselines, uvw, freqs, aterm_offsets, pl, vis, aterms)
     S = _centre_signs(N)
-    img = np.fft.ifft2(G * S[None], axes=(-2, -1)) * float(N) * float(N) * S[None]
+    layers = G[None] if pl.layers is None else G
+    k_min, _ = pl.k_range
+    n1 = _nprime_image(geom)
+    img = np.zeros((4, N, N), np.complex128)
+    for li, Gl in enumerate(layers):
+        w0 = (k_min + li) * pl.w_step if pl.layers is not None else 0.0
+        part = np.fft.ifft2(Gl * S[None], axes=(-2, -1)) * float(N) * float(N) * S[None]
+        img += part * np.exp(2j * np.pi * w0 * n1)[None]
     return img / (float(L) * float(L) * image_taper(geom)[None])
 
 
 def predict(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Plan, image, aterms):
-    """Visibilities of an image (the adjoint of invert): the model grid
-    G(X,Y) = sum_{p,q} I e^{-2 pi i (u_X l_p + v_Y m_q)} / (L^2 T(l_p) T(m_q)),
-    then degrid.  With the degridder's own taper this predicts Eq. 1 on
-    the image's pixels."""
+    """Visibilities of an image (the adjoint of invert): each layer's model
+    grid G_w0(X,Y) = sum_{p,q} I e^{-2 pi i w0 n'} e^{-2 pi i (u_X l_p + v_Y m_q)}
+    / (L^2 T(l_p) T(m_q)) (Eq. 12), then degrid.  With the degridder's own
+    taper this predicts Eq. 1 on the image's pixels."""
     N, L = geom.grid_size, geom.subgrid_size
     if N % 2:
         raise ValueError("N must be even")
     S = _centre_signs(N)
     src = np.asarray(image, np.complex128) / (float(L) * float(L) * image_taper(geom)[None])
-    G = np.fft.fft2(src * S[None], axes=(-2, -1)) * S[None]
+    k_min, n_layers = pl.k_range
+    n1 = _nprime_image(geom)
+    G = np.zeros(grid_shape(geom, pl), np.complex128)
+    for li in range(n_layers):
+        w0 = (k_min + li) * pl.w_step if pl.layers is not None else 0.0
+        Gl = np.fft.fft2(src * np.exp(-2j * np.pi * w0 * n1)[None] * S[None], axes=(-2, -1)) * S[None]
+        if pl.layers is None:
+            G = Gl
+        else:
+            G[li] = Gl
     return degrid(geom, n_st, baselines, uvw, freqs, aterm_offsets, pl, G, aterms)

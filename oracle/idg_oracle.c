@@ -22,7 +22,8 @@
  *     n'_{ij} = sqrt(1-l^2-m^2) - 1                              (Eq. 1, Eq. 7)
  *   - Gridder (Eq. 10, step 2a of Section 2.5):
  *       X(i,j) = T_i T_j sum_g A_p,g^H [ sum_{k in g} V_k e^{+2 pi i phi_k} ] A_q,g
- *       phi_k = (u_k-u0) l_i + (v_k-v0) m_j + (w_k-w0) n'_{ij},  w0 = 0
+ *       phi_k = (u_k-u0) l_i + (v_k-v0) m_j + (w_k-w0) n'_{ij},
+ *     w0 = 0, or with w layers the subgrid's layer k w_step (Section 2.4)
  *     where g runs over the A-term intervals the subgrid covers (Section 3.3:
  *     the A-term is applied after the sum over visibilities that share it).
  *   - Subgrid FFT (step 2b), unnormalised, centred:
@@ -64,6 +65,7 @@ enum {
 /* planner flags */
 #define OR_FLAG_DROP 1
 #define OR_FLAG_SPLIT_INTERVALS 2
+#define OR_FLAG_W_LAYERS 4
 
 typedef double complex cplx;
 
@@ -170,7 +172,7 @@ static void or_herm(const cplx a[4], cplx h[4]) {
 /* ------------------------------------------------------------------ */
 
 typedef struct {
-  int b, blk, ts, te, c0, c1;
+  int b, blk, ts, te, c0, c1, layer;
 } or_sub;
 
 static int or_cmp_sub(const void* pa, const void* pb) {
@@ -188,7 +190,17 @@ typedef struct {
   const double* freqs;
   int n_t, N;
   double fov;
+  int layered;     /* w layers in use */
+  double w_step;   /* layer spacing 2 w_max (wavelengths) */
 } or_ctx;
+
+/* w layer of a visibility: the nearest multiple k of w_step (w0 = k w_step),
+ * so |w - w0| <= w_step / 2 = w_max; layer 0 when layers are off */
+static int or_layer(const or_ctx* cx, int b, int t, int c) {
+  if (!cx->layered) return 0;
+  double w = or_wavelengths(cx->uvw, cx->n_t, b, t, 2, cx->freqs[c]);
+  return (int)floor(w / cx->w_step + 0.5);
+}
 
 /* bounding-box extent test: does the set of (t,ch) points fit within `span`
  * pixels in both the u and the v direction? */
@@ -206,12 +218,14 @@ static int or_box_fits(const or_ctx* cx, int b, const int* ts, const int* cs, in
   return (xhi - xlo) <= span && (yhi - ylo) <= span;
 }
 
-/* every visibility of the subtable [ts,te) x [c0,c1) inside the box? */
-static int or_members_fit(const or_ctx* cx, int b, int ts, int te, int c0, int c1, double span) {
+/* every visibility of the subtable [ts,te) x [c0,c1) inside the box, and in
+ * layer k0? */
+static int or_members_fit(const or_ctx* cx, int b, int ts, int te, int c0, int c1, double span, int k0) {
   double xlo = 0, xhi = 0, ylo = 0, yhi = 0;
   int first = 1;
   for (int t = ts; t < te; ++t)
     for (int c = c0; c < c1; ++c) {
+      if (or_layer(cx, b, t, c) != k0) return 0;
       double f = cx->freqs[c];
       double x = or_pix(cx->uvw, cx->n_t, b, t, 0, f, cx->fov, cx->N);
       double y = or_pix(cx->uvw, cx->n_t, b, t, 1, f, cx->fov, cx->N);
@@ -244,14 +258,23 @@ static int or_members_fit(const or_ctx* cx, int b, int ts, int te, int c0, int c
  * outside [0, N-L] is an error, or is dropped with OR_FLAG_DROP.
  * Segments: one per A-term interval that intersects the subgrid's timesteps.
  * w check (reading of the Section 2.4 footnote): the w fringe across the
- * subgrid, |w| * max|grad n'| * FOV pixels, must not exceed P/2 - 1.
+ * subgrid, |w - w0| * max|grad n'| * FOV pixels, must not exceed P/2 - 1,
+ * i.e. |w - w0| <= w_max = (P/2 - 1) / (max|grad n'| FOV).  Without
+ * OR_FLAG_W_LAYERS every subgrid has w0 = 0 and a larger |w| is an error.
+ * With it (Section 2.4: the hybrid with w-stacking) w0 snaps to the nearest
+ * multiple of 2 w_max and every member of a subgrid shares that layer: the
+ * channel runs, the time growth (corners) and the final shrink (all members)
+ * also require the layer of the run's first visibility.
  *
  * out_sg: cap_sg rows of 8 ints {b, t0, t1, c0, c1, x0, y0, dropped}
  * out_seg: cap_seg rows of 4 ints {subgrid, interval, t_begin, t_end}
+ * out_layer (optional): per subgrid its layer k, w0 = k w_step
+ * w_step_out (optional): the layer spacing 2 w_max in wavelengths
  */
 int oracle_plan(int N, int L, int P, double fov, int flags, int n_bl, int n_t, int n_ch,
                 const double* uvw, const double* freqs, const int* aterm_offsets, int n_int,
-                int* out_sg, int cap_sg, int* n_sg_out, int* out_seg, int cap_seg, int* n_seg_out) {
+                int* out_sg, int cap_sg, int* n_sg_out, int* out_seg, int cap_seg, int* n_seg_out,
+                int* out_layer, double* w_step_out) {
   if (N <= 0 || L <= 0 || P < 0 || L > N || (N % 2) || (L % 2) || (P % 2) || n_bl < 0 || n_t < 0 ||
       n_ch < 0 || n_int < 1 || !(fov > 0.0))
     return OR_ERR_INVALID;
@@ -271,14 +294,18 @@ int oracle_plan(int N, int L, int P, double fov, int flags, int n_bl, int n_t, i
   /* w limit */
   double gmax = sqrt(r2max) / sqrt(1.0 - r2max);
   double wlim = 0.5 * P - 1.0;
-  for (int b = 0; b < n_bl; ++b)
+  const int layered = (flags & OR_FLAG_W_LAYERS) != 0;
+  const double w_step = 2.0 * (wlim / (gmax * fov));
+  if (w_step_out) *w_step_out = w_step;
+  if (layered && !(w_step > 0.0)) return OR_ERR_INVALID;
+  for (int b = 0; b < n_bl && !layered; ++b)
     for (int t = 0; t < n_t; ++t)
       for (int c = 0; c < n_ch; ++c) {
         double w = or_wavelengths(uvw, n_t, b, t, 2, freqs[c]);
         if (fabs(w) * gmax * fov > wlim) return OR_ERR_W_TOO_LARGE;
       }
 
-  or_ctx cx = {uvw, freqs, n_t, N, fov};
+  or_ctx cx = {uvw, freqs, n_t, N, fov, layered, w_step};
   int n_sg = 0, n_seg = 0;
   int stack_cap = 64;
   int* stack = (int*)malloc(sizeof(int) * 3 * stack_cap);
@@ -300,11 +327,13 @@ int oracle_plan(int N, int L, int P, double fov, int flags, int n_bl, int n_t, i
         int ts = stack[3 * sp], c0 = stack[3 * sp + 1], c1 = stack[3 * sp + 2];
         int c = c0;
         while (c < c1) {
+          int k0 = or_layer(&cx, b, ts, c);
           int hi = c + 1; /* range is [c, hi) */
           for (;;) {
             if (hi >= c1) break;
             int tt[2] = {ts, ts}, cc[2] = {c, hi};
             if (!or_box_fits(&cx, b, tt, cc, 2, (double)Sc)) break;
+            if (or_layer(&cx, b, ts, hi) != k0) break;
             ++hi;
           }
           int te = ts + 1;
@@ -312,14 +341,15 @@ int oracle_plan(int N, int L, int P, double fov, int flags, int n_bl, int n_t, i
             if (te >= tb) break;
             int tt[4] = {ts, ts, te, te}, cc[4] = {c, hi - 1, c, hi - 1};
             if (!or_box_fits(&cx, b, tt, cc, 4, (double)S)) break;
+            if (or_layer(&cx, b, te, c) != k0 || or_layer(&cx, b, te, hi - 1) != k0) break;
             ++te;
           }
-          while (te > ts + 1 && !or_members_fit(&cx, b, ts, te, c, hi, (double)S)) --te;
+          while (te > ts + 1 && !or_members_fit(&cx, b, ts, te, c, hi, (double)S, k0)) --te;
           if (n_list == list_cap) {
             list_cap *= 2;
             list = (or_sub*)realloc(list, sizeof(or_sub) * list_cap);
           }
-          or_sub s = {b, blk, ts, te, c, hi};
+          or_sub s = {b, blk, ts, te, c, hi, k0};
           list[n_list++] = s;
           if (te < tb) {
             if (sp == stack_cap) {
@@ -360,6 +390,7 @@ int oracle_plan(int N, int L, int P, double fov, int flags, int n_bl, int n_t, i
       int* row = out_sg + (size_t)n_sg * 8;
       row[0] = b; row[1] = s.ts; row[2] = s.te; row[3] = s.c0; row[4] = s.c1;
       row[5] = x0; row[6] = y0; row[7] = dropped;
+      if (out_layer) out_layer[n_sg] = s.layer;
       for (int a = 0; a < n_int; ++a) {
         int lo = aterm_offsets[a] > s.ts ? aterm_offsets[a] : s.ts;
         int hi = aterm_offsets[a + 1] < s.te ? aterm_offsets[a + 1] : s.te;
@@ -448,6 +479,9 @@ typedef struct {
   int n_sg;
   const int* seg;
   int n_seg;
+  const int* layer;  /* per subgrid w layer k (NULL: all 0) */
+  double w_step;     /* w0 = k w_step */
+  int k_min;         /* the master grid holds layers k_min .. k_min + n_layers - 1 */
 } or_job;
 
 /* n'(l,m) = sqrt(1 - l^2 - m^2) - 1 */
@@ -463,7 +497,7 @@ static void or_subgrid_image(const or_job* jb, int s, const cplx* vis, const cpl
   int p = jb->baselines[2 * b], q = jb->baselines[2 * b + 1];
   double u0 = (double)(x0 + L / 2 - N / 2) / jb->fov;
   double v0 = (double)(y0 + L / 2 - N / 2) / jb->fov;
-  double w0 = 0.0;
+  double w0 = jb->layer ? (double)jb->layer[s] * jb->w_step : 0.0;
   memset(X, 0, sizeof(cplx) * 4 * (size_t)L * L);
   for (int g = seg_first[s]; g < seg_first[s] + seg_count[s]; ++g) {
     const int* sr = jb->seg + (size_t)g * 4;
@@ -513,14 +547,17 @@ static void or_seg_index(const or_job* jb, int* seg_first, int* seg_count) {
  * vis: complex [n_bl][n_t][n_ch][4]; aterms: complex [n_int][n_st][nodes][nodes][4].
  * subgrid_images (optional): complex [n_sg][4][L][L], the subgrid images X
  * before the FFT; subgrid_uv (optional): the same after the FFT.
+ * With w layers (layer != NULL) subgrid s uses w0 = layer[s] w_step in its
+ * phase and is added into grid[layer[s] - k_min][4][N][N].
  */
 int oracle_grid(int N, int L, int P, double fov, int taper_kind, double beta, const double* taper_user,
                 int nodes, int n_st, int n_bl, int n_t, int n_ch, const int* baselines, const double* uvw,
                 const double* freqs, int n_int, const int* sg, int n_sg, const int* seg, int n_seg,
+                const int* layer, double w_step, int k_min,
                 const double* vis_ri, const double* aterms_ri, double* grid_ri, double* subgrid_images,
                 double* subgrid_uv) {
   or_job jb = {N, L, P, fov, taper_kind, beta, taper_user, nodes, n_st, n_bl, n_t, n_ch, baselines,
-               uvw, freqs, n_int, sg, n_sg, seg, n_seg};
+               uvw, freqs, n_int, sg, n_sg, seg, n_seg, layer, w_step, k_min};
   double* T = (double*)malloc(sizeof(double) * L);
   int st = oracle_taper(L, taper_kind, beta, taper_user, T);
   if (st) { free(T); return st; }
@@ -553,10 +590,11 @@ int oracle_grid(int N, int L, int P, double fov, int taper_kind, double beta, co
       const int* row = sg + (size_t)(s0 + k) * 8;
       if (row[7]) continue;
       int x0 = row[5], y0 = row[6];
+      cplx* gl = grid + (layer ? (size_t)(layer[s0 + k] - k_min) * 4 * N * N : 0);
       for (int e = 0; e < 4; ++e)
         for (int y = 0; y < L; ++y)
           for (int x = 0; x < L; ++x)
-            grid[((size_t)e * N + (y0 + y)) * N + (x0 + x)] += buf[(((size_t)k * 4 + e) * L + y) * L + x];
+            gl[((size_t)e * N + (y0 + y)) * N + (x0 + x)] += buf[(((size_t)k * 4 + e) * L + y) * L + x];
     }
   }
   free(buf);
@@ -570,14 +608,16 @@ int oracle_grid(int N, int L, int P, double fov, int taper_kind, double beta, co
 /*
  * oracle_degrid: predict visibilities from grid[4][N][N] (Eq. 13 read as the
  * adjoint of the gridder).  vis_out is overwritten; visibilities of dropped
- * subgrids are zero.
+ * subgrids are zero.  With w layers, subgrid s reads grid[layer[s] - k_min]
+ * and uses w0 = layer[s] w_step.
  */
 int oracle_degrid(int N, int L, int P, double fov, int taper_kind, double beta, const double* taper_user,
                   int nodes, int n_st, int n_bl, int n_t, int n_ch, const int* baselines, const double* uvw,
                   const double* freqs, int n_int, const int* sg, int n_sg, const int* seg, int n_seg,
+                  const int* layer, double w_step, int k_min,
                   const double* grid_ri, const double* aterms_ri, double* vis_ri) {
   or_job jb = {N, L, P, fov, taper_kind, beta, taper_user, nodes, n_st, n_bl, n_t, n_ch, baselines,
-               uvw, freqs, n_int, sg, n_sg, seg, n_seg};
+               uvw, freqs, n_int, sg, n_sg, seg, n_seg, layer, w_step, k_min};
   double* T = (double*)malloc(sizeof(double) * L);
   int st = oracle_taper(L, taper_kind, beta, taper_user, T);
   if (st) { free(T); return st; }
@@ -600,14 +640,15 @@ int oracle_degrid(int N, int L, int P, double fov, int taper_kind, double beta, 
     cplx* Y = (cplx*)malloc(sizeof(cplx) * 4 * plane);
     cplx* tmp = (cplx*)malloc(sizeof(cplx) * plane);
     /* splitter */
+    const cplx* gl = grid + (layer ? (size_t)(layer[s] - k_min) * 4 * N * N : 0);
     for (int e = 0; e < 4; ++e)
       for (int y = 0; y < L; ++y)
         for (int x = 0; x < L; ++x)
-          Yh[((size_t)e * L + y) * L + x] = grid[((size_t)e * N + (y0 + y)) * N + (x0 + x)];
+          Yh[((size_t)e * L + y) * L + x] = gl[((size_t)e * N + (y0 + y)) * N + (x0 + x)];
     for (int e = 0; e < 4; ++e) or_dft2_plane(L, F, Yh + e * plane, Y + e * plane, tmp);
     double u0 = (double)(x0 + L / 2 - N / 2) / fov;
     double v0 = (double)(y0 + L / 2 - N / 2) / fov;
-    double w0 = 0.0;
+    double w0 = layer ? (double)layer[s] * w_step : 0.0;
     for (int g = seg_first[s]; g < seg_first[s] + seg_count[s]; ++g) {
       const int* sr = seg + (size_t)g * 4;
       int a = sr[1], tb = sr[2], te = sr[3];

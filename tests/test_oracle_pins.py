@@ -417,3 +417,86 @@ def test_invert_off_lattice_within_aliasing_bound(oracle_mod):
         l, m = (p - N // 2) * fov / N, (q - N // 2) * fov / N
         want = _brute.dft_image(obs, vis, A, l, m).reshape(4)
         assert np.abs(img[:, q, p] - want).max() / scale < 1e-6
+
+
+# ---------------------------------------------------------------- w layers (Section 2.4, Eq. 11, Eq. 12)
+
+def _layered_problem(oracle_mod, seed=0, height=400.0, n_t=6, **kw):
+    """A strongly non-coplanar array: |w| well beyond w_max, so w0 = 0 alone
+    is rejected and the visibilities spread over several w layers."""
+    obs = _tiny(seed=seed, height=height, n_t=n_t, steps_per_interval=3, **kw)
+    rng = np.random.default_rng(seed + 11)
+    A = synth.aterms_random(rng, obs.n_intervals, obs.n_stations, obs.aterm_nodes).astype(np.complex128)
+    vis = synth.random_visibilities(rng, obs).astype(np.complex128)
+    geom = _geom(oracle_mod, obs, flags=oracle_mod.FLAG_W_LAYERS)
+    pl = oracle_mod.plan(geom, obs.uvw, obs.freqs, obs.aterm_offsets)
+    return obs, geom, pl, A, vis
+
+
+def test_w_layers_plan_invariants(oracle_mod):
+    obs, geom, pl, _, _ = _layered_problem(oracle_mod)
+    with pytest.raises(oracle_mod.OracleError) as e:
+        oracle_mod.plan(_geom(oracle_mod, obs), obs.uvw, obs.freqs, obs.aterm_offsets)
+    assert e.value.code == 4
+    assert pl.k_range[1] >= 3
+    _check_plan_invariants(obs, pl, False)
+    # w_max from the fringe limit of the Section 2.4 footnote, independently
+    r2 = 0.5 * obs.image_size ** 2
+    w_max = (obs.kernel_padding / 2 - 1) / (np.sqrt(r2 / (1 - r2)) * obs.image_size)
+    assert pl.w_step == pytest.approx(2 * w_max, rel=1e-14)
+    _, _, w = _brute.uvw_lambda(obs)
+    for s, (b, t0, t1, c0, c1, *_rest) in enumerate(pl.subgrids):
+        dw = w[b, t0:t1, c0:c1] - pl.layers[s] * pl.w_step
+        assert np.abs(dw).max() <= w_max * (1 + 1e-12)
+
+
+def test_w_layers_reduce_to_one_layer_when_coplanar(oracle_mod):
+    obs, geom, pl, A, vis = _problem(oracle_mod, seed=2)
+    g2 = _geom(oracle_mod, obs, flags=oracle_mod.FLAG_W_LAYERS)
+    p2 = oracle_mod.plan(g2, obs.uvw, obs.freqs, obs.aterm_offsets)
+    np.testing.assert_array_equal(p2.subgrids, pl.subgrids)
+    assert np.all(p2.layers == 0)
+    G1 = _grid(oracle_mod, obs, geom, pl, vis, A)
+    G2 = oracle_mod.grid(g2, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets, p2, vis, A)
+    assert G2.shape == (1,) + G1.shape and np.array_equal(G2[0], G1)
+
+
+def test_w_stacked_invert_equals_direct_adjoint_on_the_lattice(oracle_mod):
+    """With several w layers the dirty image on the subgrid lattice is still
+    exactly the adjoint of Eq. 1: each subgrid carries (w - w0) and the layer
+    transform multiplies by e^{2 pi i w0 n'} (Eq. 11)."""
+    obs, geom, pl, A, vis = _layered_problem(oracle_mod, seed=1)
+    N, L, fov = obs.grid_size, obs.subgrid_size, obs.image_size
+    img = oracle_mod.invert(*_wrapper_args(obs, geom, pl), vis, A)
+    r = N // L
+    worst = 0.0
+    for (i, j) in [(8, 8), (2, 13), (13, 3), (5, 6), (10, 12)]:
+        p, q = N // 2 + r * (i - L // 2), N // 2 + r * (j - L // 2)
+        l, m = (p - N // 2) * fov / N, (q - N // 2) * fov / N
+        want = _brute.dft_image(obs, vis, A, l, m).reshape(4)
+        worst = max(worst, np.abs(img[:, q, p] - want).max() / np.abs(want).max())
+    assert worst < 1e-9
+
+
+def test_w_stacked_predict_of_a_lattice_point_source(oracle_mod):
+    obs, geom, pl, A, _ = _layered_problem(oracle_mod, seed=3)
+    N, L, fov = obs.grid_size, obs.subgrid_size, obs.image_size
+    r = N // L
+    B = np.array([[1.1, -0.2j], [0.2j, 0.8]])
+    for (i, j) in [(8, 8), (3, 12), (12, 4)]:
+        p, q = N // 2 + r * (i - L // 2), N // 2 + r * (j - L // 2)
+        img = np.zeros((4, N, N), complex)
+        img[:, q, p] = B.reshape(4)
+        V = oracle_mod.predict(*_wrapper_args(obs, geom, pl), img, A)
+        l, m = (p - N // 2) * fov / N, (q - N // 2) * fov / N
+        assert _relerr(V, _brute.measurement_equation(obs, A, l, m, B)) < 1e-10
+
+
+def test_w_stacked_predict_is_the_adjoint_of_invert(oracle_mod):
+    obs, geom, pl, A, vis = _layered_problem(oracle_mod, seed=4)
+    N = obs.grid_size
+    rng = np.random.default_rng(5)
+    img = rng.standard_normal((4, N, N)) + 1j * rng.standard_normal((4, N, N))
+    lhs = np.vdot(oracle_mod.predict(*_wrapper_args(obs, geom, pl), img, A), vis)
+    rhs = np.vdot(img, oracle_mod.invert(*_wrapper_args(obs, geom, pl), vis, A))
+    assert abs(lhs - rhs) / abs(rhs) < 1e-11
