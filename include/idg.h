@@ -66,7 +66,9 @@ enum {
   IDG_DROP_OUT_OF_GRID = 1,         /* drop subgrids that leave the grid instead of failing */
   IDG_SPLIT_AT_ATERM_INTERVALS = 2, /* never let a subgrid span two A-term intervals (Section 3.3 as written) */
   IDG_HOST_ONLY = 4,                /* plan on the host only: no device memory, grid/degrid refused */
-  IDG_PERSISTENT = 8                /* persistent launches: #SMs x occupancy blocks drain a work queue */
+  IDG_PERSISTENT = 8,               /* persistent launches: #SMs x occupancy blocks drain a work queue */
+  IDG_W_LAYERS = 16                 /* w layers (Section 2.4): w0 snaps to multiples of 2 w_max instead of
+                                       rejecting |w| > w_max; grids hold one [4][N][N] plane set per layer */
 };
 
 typedef struct {
@@ -78,7 +80,8 @@ typedef struct {
   double taper_beta;
   const double* taper_user; /* host [L] taper samples at l_i = (i - L/2) FOV/L (IDG_TAPER_USER), copied */
   int32_t aterm_nodes;    /* nodes per axis of the A-term samples, 2 .. 25 */
-  int32_t flags;          /* IDG_DROP_OUT_OF_GRID | IDG_SPLIT_AT_ATERM_INTERVALS | IDG_HOST_ONLY | IDG_PERSISTENT */
+  int32_t flags;          /* IDG_DROP_OUT_OF_GRID | IDG_SPLIT_AT_ATERM_INTERVALS | IDG_HOST_ONLY | IDG_PERSISTENT
+                             | IDG_W_LAYERS */
 } idg_geometry;
 
 typedef struct {
@@ -95,6 +98,9 @@ typedef struct {
   int64_t vis_pixels;         /* sum over non-dropped subgrids of n_vis * L^2 */
   int32_t subgrid_size;
   int32_t batch_capacity;     /* subgrids per batch */
+  int32_t n_w_layers;         /* w layers of the master grid (1 without IDG_W_LAYERS) */
+  int32_t w_layer_min;        /* layer k of grid plane set 0; plane set i has w0 = (w_layer_min + i) w_layer_step */
+  double w_layer_step;        /* 2 w_max in wavelengths, w_max = (P/2 - 1) / (max|grad n'| FOV) */
 } idg_plan_stats_t;
 
 /*
@@ -124,7 +130,8 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
  * idg_grid -- imaging direction (Section 2.5 steps 2a-2c, Eq. 10, Eq. 6).
  *   vis_c64     device complex64 [n_baselines][n_timesteps][n_channels][4]
  *   aterms_c64  device complex64 [n_intervals][n_stations][nodes][nodes][4]
- *   grid_c128   device complex128 [4][N][N], ACCUMULATED INTO (+=)
+ *   grid_c128   device complex128 [n_w_layers][4][N][N] (see idg_plan_stats;
+ *               [4][N][N] without IDG_W_LAYERS), ACCUMULATED INTO (+=)
  * Dropped subgrids contribute nothing.  Asynchronous on the plan's stream.
  * Buffers must be 16-byte aligned.
  */
@@ -133,7 +140,7 @@ idg_status idg_grid(idg_plan* plan, const void* vis_c64, const void* aterms_c64,
 /*
  * idg_degrid -- prediction direction (Section 2.5 steps 3a-3c, Eq. 13 read
  * as the adjoint of idg_grid).
- *   grid_c128   device complex128 [4][N][N], read only
+ *   grid_c128   device complex128 [n_w_layers][4][N][N], read only
  *   aterms_c64  device complex64 [n_intervals][n_stations][nodes][nodes][4]
  *   vis_c64     device complex64 [n_baselines][n_timesteps][n_channels][4],
  *               OVERWRITTEN; visibilities of dropped subgrids are set to 0
@@ -166,6 +173,12 @@ idg_status idg_plan_stats(const idg_plan* plan, idg_plan_stats_t* out);
  *   n     receives the number of subgrids; rows beyond cap are not written
  */
 idg_status idg_plan_subgrids(const idg_plan* plan, int32_t* out, int64_t cap, int64_t* n);
+
+/*
+ * idg_plan_layers -- per subgrid, in plan order, its w layer k (w0 = k *
+ * w_layer_step; 0 without IDG_W_LAYERS).  out: host int32 [cap].
+ */
+idg_status idg_plan_layers(const idg_plan* plan, int32_t* out, int64_t cap, int64_t* n);
 
 /*
  * idg_plan_segments -- copy the segments to host memory.
@@ -239,8 +252,12 @@ idg_status idg_grid_noalloc(idg_plan* plan, const void* vis_c64, const void* ate
  * amplified errors; the paper images the central part of a padded field.
  *   vis_c64    device complex64 [n_baselines][n_timesteps][n_channels][4], read
  *   aterms_c64 device complex64 [n_intervals][n_stations][nodes][nodes][4], read
- *   grid_c128  device complex128 [4][N][N], overwritten with the gridded uv plane
+ *   grid_c128  device complex128 [n_w_layers][4][N][N]: with one layer at
+ *              w0 = 0 it receives the gridded uv plane; with several it is
+ *              work space (each layer is transformed in place)
  *   image_c128 device complex128 [4][N][N] (pol, m, l), written
+ * With w layers the image is the w-stacked sum of Eq. 11: each layer's
+ * transform times e^{+2 pi i w0 n'(l,m)}, n' = sqrt(1 - l^2 - m^2) - 1.
  * The master-grid transform is cuFFT (4 double-complex planes) on the plan's
  * stream; the first call on a plan creates its cuFFT plan (allocates).
  * IDG_ERR_UNSUPPORTED with IDG_TAPER_USER (its samples exist only on the
@@ -256,7 +273,8 @@ idg_status idg_invert(idg_plan* plan, const void* vis_c64, const void* aterms_c6
  *                     / (L^2 T(l_p) T(m_q)),
  * then idg_degrid(grid) into vis (overwritten).  With the degridder's own
  * taper this predicts Eq. 1 on the image pixels.
- *   image_c128 device complex128 [4][N][N], read;  grid_c128 overwritten;
+ *   image_c128 device complex128 [4][N][N], read;  grid_c128 [n_w_layers][4][N][N]
+ *   overwritten (layer w0 from image e^{-2 pi i w0 n'}, Eq. 12);
  *   vis_c64    device complex64 [n_baselines][n_timesteps][n_channels][4], written.
  * Errors as idg_invert.
  */

@@ -78,7 +78,7 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
       const double inv_l = 1.0 / double(L);
       const double dx = (r[0] * fs) * a.g.fov - double(sd.x0 + L / 2 - a.g.N / 2);
       const double dy = (r[1] * fs) * a.g.fov - double(sd.y0 + L / 2 - a.g.N / 2);
-      const double w = r[2] * fs;
+      const double w = r[2] * fs - subgrid_w0(a.g, sd);  // w - w0 (Section 2.4)
       const double aa = dx * inv_l, bb = dy * inv_l;
       const double dah = rint(aa * 65536.0) * (1.0 / 65536.0);
       const double dbh = rint(bb * 65536.0) * (1.0 / 65536.0);

@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(kFftThreads) fft_adder_kernel(const FftArgs a)
   __syncthreads();
   fft2d<L, -1>(buf, tw);
   if (MODE == 0) {
-    double* g = reinterpret_cast<double*>(a.grid) + (size_t(pol) * a.N * a.N) * 2;
+    // plane set of the subgrid's w layer, then the polarisation plane
+    double* g = reinterpret_cast<double*>(a.grid) + ((size_t(sd.layer) * 4 + pol) * a.N * a.N) * 2;
     for (int e = threadIdx.x; e < L * L; e += kFftThreads) {
       const int y = e / L, x = e - y * L;
       const float sgn = ((x + y) & 1) ? -1.f : 1.f;
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(kFftThreads) splitter_ifft_kernel(const FftArg
   const int sgi = blockIdx.x >> 2, pol = blockIdx.x & 3;
   const SubgridDesc sd = a.sg[sgi];
   for (int e = threadIdx.x; e < L; e += kFftThreads) tw[e] = a.twiddle[e];
-  const double2* g = a.grid + size_t(pol) * a.N * a.N;
+  const double2* g = a.grid + (size_t(sd.layer) * 4 + pol) * a.N * a.N;  // w layer, then polarisation
   for (int e = threadIdx.x; e < L * L; e += kFftThreads) {
     const int y = e / L, x = e - y * L;
     const double2 v = g[size_t(sd.y0 + y) * a.N + sd.x0 + x];

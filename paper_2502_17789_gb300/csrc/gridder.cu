@@ -46,7 +46,7 @@ __device__ __forceinline__ Slopes vis_slopes(const StageArgs& a, const SubgridDe
   const double fs = a.fscale[ch];
   const double dx = (r[0] * fs) * a.g.fov - off_x;
   const double dy = (r[1] * fs) * a.g.fov - off_y;
-  return {dx * inv_l, dy * inv_l, r[2] * fs};
+  return {dx * inv_l, dy * inv_l, r[2] * fs - subgrid_w0(a.g, sd)};  // w - w0 (Section 2.4)
 }
 
 // (head, tail) split of the slopes for the exact anchor reduction, plus the

@@ -46,6 +46,7 @@ struct idg_plan {
   idg_geometry geom{};
   int32_t n_st = 0, n_bl = 0, n_t = 0, n_ch = 0, n_int = 0;
   int32_t L = 0, N = 0;
+  int32_t k_min = 0, n_layers = 1;  // w layers of the master grid
   cudaStream_t stream = nullptr;
   bool host_only = false;
   Partition part;
@@ -255,7 +256,8 @@ namespace idg {
 
 bool plan_device_view(const idg_plan* p, PlanDeviceView* v) {
   if (!p || p->host_only || !v) return false;
-  v->g = KernelGeom{p->N, p->L, p->n_t, p->n_ch, p->n_st, p->geom.aterm_nodes, p->geom.image_size};
+  v->g = KernelGeom{p->N, p->L, p->n_t, p->n_ch, p->n_st, p->geom.aterm_nodes, p->geom.image_size,
+                    p->part.w_step, p->k_min};
   v->stream = p->stream;
   v->uvw = p->d_uvw;
   v->fscale = p->d_fscale;
@@ -328,6 +330,9 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     return st;
   }
   const int L = p->L;
+  // w layers held by the master grid: k_min .. k_min + n_layers - 1 over the kept subgrids
+  bool any = false;
+  int32_t k_lo = 0, k_hi = 0;
   for (const SubgridDesc& d : p->part.subgrids) {
     if (d.dropped) {
       ++p->n_sg_dropped;
@@ -335,8 +340,14 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     } else {
       p->exec.push_back(d);
       p->vis_pixels += int64_t(d.n_vis) * L * L;
+      k_lo = any ? std::min(k_lo, d.layer) : d.layer;
+      k_hi = any ? std::max(k_hi, d.layer) : d.layer;
+      any = true;
     }
   }
+  p->k_min = k_lo;
+  p->n_layers = k_hi - k_lo + 1;
+  for (SubgridDesc& d : p->exec) d.layer -= k_lo;  // device tables hold the grid plane set
   if (host_only) {
     *out = p;
     return IDG_OK;
@@ -481,7 +492,8 @@ idg_status idg_set_stream(idg_plan* plan, void* cuda_stream) {
 }
 
 static KernelGeom kgeom(const idg_plan* p) {
-  return KernelGeom{p->N, p->L, p->n_t, p->n_ch, p->n_st, p->geom.aterm_nodes, p->geom.image_size};
+  return KernelGeom{p->N, p->L, p->n_t, p->n_ch, p->n_st, p->geom.aterm_nodes, p->geom.image_size,
+                    p->part.w_step, p->k_min};
 }
 
 static StageArgs stage_args(const idg_plan* p, const Batch& b, const void* vis) {
@@ -725,17 +737,41 @@ idg_status idg_invert(idg_plan* plan, const void* vis_c64, const void* aterms_c6
       (st = ensure_image(plan)))
     return st;
   const int N = plan->N;
+  const size_t plane_set = size_t(4) * N * N;
   const double inv_l2 = 1.0 / (double(plan->L) * double(plan->L));
-  int e = int(cudaMemsetAsync(grid_c128, 0, size_t(4) * N * N * sizeof(double2), plan->stream));
+  const double fov = plan->geom.image_size;
+  int e = int(cudaMemsetAsync(grid_c128, 0, plane_set * plan->n_layers * sizeof(double2), plan->stream));
   if (e) return cuda_err(plan, e, "zeroing the grid");
   if ((st = idg_grid(plan, vis_c64, aterms_c64, grid_c128))) return st;
   double2* img = static_cast<double2*>(image_c128);
-  e = launch_sign_scale(static_cast<const double2*>(grid_c128), img, nullptr, 1.0, N, 4, plan->stream);
-  if (e) return cuda_err(plan, e, "centring signs");
-  const cufftResult r = cufftExecZ2Z(plan->fft, reinterpret_cast<cufftDoubleComplex*>(img),
-                                     reinterpret_cast<cufftDoubleComplex*>(img), CUFFT_INVERSE);
-  if (r != CUFFT_SUCCESS) return fft_err(plan, r, "cufftExecZ2Z");
-  e = launch_sign_scale(img, img, plan->d_inv_t, inv_l2, N, 4, plan->stream);
+  double2* grid = static_cast<double2*>(grid_c128);
+  auto inverse = [&](double2* x) {
+    return cufftExecZ2Z(plan->fft, reinterpret_cast<cufftDoubleComplex*>(x), reinterpret_cast<cufftDoubleComplex*>(x),
+                        CUFFT_INVERSE);
+  };
+  const bool single = plan->n_layers == 1 && plan->k_min == 0;
+  if (single) {
+    // one layer at w0 = 0: transform a signed copy, the gridded plane stays in `grid`
+    e = launch_image_pass(grid, img, nullptr, 1.0, 0.0, fov, N, kPassSign, plan->stream);
+    if (e) return cuda_err(plan, e, "centring signs");
+    const cufftResult r = inverse(img);
+    if (r != CUFFT_SUCCESS) return fft_err(plan, r, "cufftExecZ2Z");
+    e = launch_image_pass(img, img, plan->d_inv_t, inv_l2, 0.0, fov, N, kPassSign, plan->stream);
+    if (e) return cuda_err(plan, e, "taper correction");
+    return IDG_OK;
+  }
+  // w-stacking (Eq. 11): transform every layer in place, shift it from w0 to w = 0, sum
+  for (int li = 0; li < plan->n_layers; ++li) {
+    double2* gl = grid + plane_set * li;
+    const double w0 = double(plan->k_min + li) * plan->part.w_step;
+    e = launch_image_pass(gl, gl, nullptr, 1.0, 0.0, fov, N, kPassSign, plan->stream);
+    if (e) return cuda_err(plan, e, "centring signs");
+    const cufftResult r = inverse(gl);
+    if (r != CUFFT_SUCCESS) return fft_err(plan, r, "cufftExecZ2Z");
+    e = launch_image_pass(gl, img, nullptr, 1.0, w0, fov, N, kPassSign | (li ? kPassAccumulate : 0), plan->stream);
+    if (e) return cuda_err(plan, e, "w-stacking");
+  }
+  e = launch_image_pass(img, img, plan->d_inv_t, inv_l2, 0.0, fov, N, 0, plan->stream);
   if (e) return cuda_err(plan, e, "taper correction");
   return IDG_OK;
 }
@@ -748,15 +784,23 @@ idg_status idg_predict(idg_plan* plan, const void* image_c128, const void* aterm
       (st = ensure_image(plan)))
     return st;
   const int N = plan->N;
+  const size_t plane_set = size_t(4) * N * N;
   const double inv_l2 = 1.0 / (double(plan->L) * double(plan->L));
-  double2* g = static_cast<double2*>(grid_c128);
-  int e = launch_sign_scale(static_cast<const double2*>(image_c128), g, plan->d_inv_t, inv_l2, N, 4, plan->stream);
-  if (e) return cuda_err(plan, e, "taper correction");
-  const cufftResult r = cufftExecZ2Z(plan->fft, reinterpret_cast<cufftDoubleComplex*>(g),
-                                     reinterpret_cast<cufftDoubleComplex*>(g), CUFFT_FORWARD);
-  if (r != CUFFT_SUCCESS) return fft_err(plan, r, "cufftExecZ2Z");
-  e = launch_sign_scale(g, g, nullptr, 1.0, N, 4, plan->stream);
-  if (e) return cuda_err(plan, e, "centring signs");
+  const double fov = plan->geom.image_size;
+  const double2* img = static_cast<const double2*>(image_c128);
+  double2* grid = static_cast<double2*>(grid_c128);
+  // inverse w-stacking (Eq. 12): each layer's model grid from the image shifted to its w0
+  for (int li = 0; li < plan->n_layers; ++li) {
+    double2* gl = grid + plane_set * li;
+    const double w0 = double(plan->k_min + li) * plan->part.w_step;
+    int e = launch_image_pass(img, gl, plan->d_inv_t, inv_l2, -w0, fov, N, kPassSign, plan->stream);
+    if (e) return cuda_err(plan, e, "taper correction");
+    const cufftResult r = cufftExecZ2Z(plan->fft, reinterpret_cast<cufftDoubleComplex*>(gl),
+                                       reinterpret_cast<cufftDoubleComplex*>(gl), CUFFT_FORWARD);
+    if (r != CUFFT_SUCCESS) return fft_err(plan, r, "cufftExecZ2Z");
+    e = launch_image_pass(gl, gl, nullptr, 1.0, 0.0, fov, N, kPassSign, plan->stream);
+    if (e) return cuda_err(plan, e, "centring signs");
+  }
   return idg_degrid(plan, grid_c128, aterms_c64, vis_c64);
 }
 
@@ -834,6 +878,16 @@ idg_status idg_plan_stats(const idg_plan* plan, idg_plan_stats_t* out) {
   out->vis_pixels = plan->vis_pixels;
   out->subgrid_size = plan->L;
   out->batch_capacity = plan->batch_cap;
+  out->n_w_layers = plan->n_layers;
+  out->w_layer_min = plan->k_min;
+  out->w_layer_step = plan->part.w_step;
+  return IDG_OK;
+}
+
+idg_status idg_plan_layers(const idg_plan* plan, int32_t* out, int64_t cap, int64_t* n) {
+  if (!plan || !n || (cap > 0 && !out)) return set_err(nullptr, IDG_ERR_INVALID_ARG, "NULL argument");
+  *n = int64_t(plan->part.subgrids.size());
+  for (int64_t s = 0; s < std::min<int64_t>(cap, *n); ++s) out[s] = plan->part.subgrids[s].layer;
   return IDG_OK;
 }
 

@@ -25,7 +25,7 @@ struct SubgridDesc {
   int32_t dropped;
   int32_t plan_index;            // position in plan order
   int32_t rec_offset;            // first staged record of this subgrid within its batch
-  int32_t pad1;
+  int32_t layer;                 // w layer: k (w0 = k w_step) in the partition, k - k_min on the device
 };
 static_assert(sizeof(SubgridDesc) == 64, "SubgridDesc layout");
 
@@ -73,6 +73,7 @@ struct PlanInput {
 struct Partition {
   std::vector<SubgridDesc> subgrids;  // plan order
   std::vector<SegmentDesc> segments;
+  double w_step = 0.0;                // w layer spacing 2 w_max (wavelengths)
 };
 
 // Returns IDG_OK or an error status with a message in `err`.
@@ -86,7 +87,14 @@ std::vector<double> kaiser_bessel_taper(int L, double beta);
 struct KernelGeom {
   int32_t N, L, n_t, n_ch, n_st, nodes;
   double fov;
+  double w_step;   // w layer spacing; a subgrid's w0 = (k_min + layer) * w_step
+  int32_t k_min;
 };
+
+// w0 of a subgrid (its w layer; 0 without layers)
+__host__ __device__ inline double subgrid_w0(const KernelGeom& g, const SubgridDesc& d) {
+  return double(g.k_min + d.layer) * g.w_step;
+}
 
 // Staged visibility record, 8 float4 = 128 bytes (written by the staging
 // kernel, streamed by the gridder with bulk copies):
@@ -162,8 +170,12 @@ int launch_gridder(int L, const GridArgs& a, int n_items, int persistent_blocks,
 int configure_gridder(int L, int* persistent_blocks);   // attributes + persistent grid size
 int configure_degridder(int L, int nodes, int* persistent_blocks);
 int launch_stage_records(int L, const StageArgs& a, int n_subgrids, void* stream);
-// out[k][y][x] = (-1)^(x+y) c w[y] w[x] in[k][y][x] over `planes` N x N complex128 planes (w may be null)
-int launch_sign_scale(const double2* in, double2* out, const double* w, double c, int N, int planes, void* stream);
+// element-wise pass over the 4 N x N complex128 planes of one w layer (image-domain wrapper):
+// out (+)= in * c * w[x] w[y] * (-1)^(x+y) * e^{i 2 pi w0 n'(x,y)}; w may be null
+constexpr int kPassSign = 1;        // apply (-1)^(x+y)
+constexpr int kPassAccumulate = 2;  // add into out
+int launch_image_pass(const double2* in, double2* out, const double* w, double c, double w0, double fov, int N,
+                      int flags, void* stream);
 // one warp waits, bounded by limit_ns, on an mbarrier nothing completes; sets kStatusTimeout bit in *status
 int launch_wait_selftest(int* status, int64_t limit_ns, void* stream);
 // flags[i][s] = 1 when every node of A-term (interval i, station s) has zero off-diagonal entries

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(ROWS * L / 8, (ROWS * L / 8) <= 128 ? 3 : 2)
         const double fs = a.fscale[ch];
         const double dx = (r[0] * fs) * a.g.fov - off_x;
         const double dy = (r[1] * fs) * a.g.fov - off_y;
-        const double w = r[2] * fs;
+        const double w = r[2] * fs - subgrid_w0(a.g, sd);  // w - w0 (Section 2.4)
         const double aa = dx * inv_l, bb = dy * inv_l;
         const double ah = rint(aa * 65536.0) * (1.0 / 65536.0);
         const double bh = rint(bb * 65536.0) * (1.0 / 65536.0);

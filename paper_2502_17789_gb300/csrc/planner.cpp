@@ -17,7 +17,12 @@
 //   4. emit it; its later timesteps become a new pending subtable
 //   subgrids are ordered by (baseline, block, t_start, c_lo)
 //   corner x0 = floor((xi_min + xi_max) / 2) - L/2, likewise y0
-//   w check: |w| * max|grad n'| * FOV <= P/2 - 1 (footnote of Section 2.4)
+//   w check: |w - w0| * max|grad n'| * FOV <= P/2 - 1 (footnote of Section 2.4),
+//   i.e. |w - w0| <= w_max.  Without IDG_W_LAYERS w0 = 0 and a larger |w| is
+//   an error; with it (the hybrid with w-stacking of Section 2.4) w0 is the
+//   nearest multiple k of w_step = 2 w_max and every member of a subgrid
+//   shares the layer k of the run's first visibility (checked on the channel
+//   run's ends, the time growth's corners and in the final shrink).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -32,13 +37,14 @@ struct Pending {
   int32_t ts, c_lo, c_hi;
 };
 struct Run {
-  int32_t blk, ts, te, c_lo, c_hi;
+  int32_t blk, ts, te, c_lo, c_hi, layer;
 };
 
-// Pixel coordinates of every visibility of one baseline, [t][ch].
+// Pixel coordinates (and w layers) of every visibility of one baseline, [t][ch].
 class BaselinePixels {
  public:
-  BaselinePixels(const PlanInput& in, int b) : n_ch_(in.n_ch), xi_(size_t(in.n_t) * in.n_ch), eta_(xi_.size()) {
+  BaselinePixels(const PlanInput& in, int b, double w_step)
+      : n_ch_(in.n_ch), xi_(size_t(in.n_t) * in.n_ch), eta_(xi_.size()), layer_(w_step > 0.0 ? xi_.size() : 0) {
     const double half = double(in.N / 2);
     for (int t = 0; t < in.n_t; ++t) {
       const double* r = in.uvw + (size_t(b) * in.n_t + t) * 3;
@@ -48,11 +54,23 @@ class BaselinePixels {
         const double v = (r[1] * f) / kSpeedOfLight;
         xi_[size_t(t) * n_ch_ + c] = u * in.fov + half;
         eta_[size_t(t) * n_ch_ + c] = v * in.fov + half;
+        if (w_step > 0.0) {
+          const double w = (r[2] * f) / kSpeedOfLight;
+          layer_[size_t(t) * n_ch_ + c] = int32_t(std::floor(w / w_step + 0.5));
+        }
       }
     }
   }
   double xi(int t, int c) const { return xi_[size_t(t) * n_ch_ + c]; }
   double eta(int t, int c) const { return eta_[size_t(t) * n_ch_ + c]; }
+  int32_t layer(int t, int c) const { return layer_.empty() ? 0 : layer_[size_t(t) * n_ch_ + c]; }
+  bool same_layer(int ts, int te, int c_lo, int c_hi, int32_t k) const {
+    if (layer_.empty()) return true;
+    for (int t = ts; t < te; ++t)
+      for (int c = c_lo; c < c_hi; ++c)
+        if (layer(t, c) != k) return false;
+    return true;
+  }
 
   // Extent of a set of (t, c) points along u and v.
   template <size_t K>
@@ -86,6 +104,7 @@ class BaselinePixels {
  private:
   int n_ch_;
   std::vector<double> xi_, eta_;
+  std::vector<int32_t> layer_;
 };
 
 }  // namespace
@@ -122,7 +141,11 @@ idg_status partition(const PlanInput& in, Partition* out, std::string* err) {
   const double r2 = 0.5 * in.fov * in.fov;
   const double grad = std::sqrt(r2) / std::sqrt(1.0 - r2);
   const double w_limit = 0.5 * in.P - 1.0;
-  for (int b = 0; b < in.n_bl; ++b)
+  const bool layered = (in.flags & IDG_W_LAYERS) != 0;
+  const double w_step = 2.0 * (w_limit / (grad * in.fov));
+  if (layered && !(w_step > 0.0)) return fail(IDG_ERR_INVALID_ARG, "w layers need kernel_padding > 2");
+  out->w_step = layered ? w_step : 0.0;
+  for (int b = 0; b < in.n_bl && !layered; ++b)
     for (int t = 0; t < in.n_t; ++t) {
       const double wm = in.uvw[(size_t(b) * in.n_t + t) * 3 + 2];
       for (int c = 0; c < in.n_ch; ++c) {
@@ -142,7 +165,7 @@ idg_status partition(const PlanInput& in, Partition* out, std::string* err) {
   std::vector<Pending> todo;
   for (int b = 0; b < in.n_bl; ++b) {
     if (in.n_t == 0 || in.n_ch == 0) break;
-    const BaselinePixels px(in, b);
+    const BaselinePixels px(in, b, layered ? w_step : 0.0);
     runs.clear();
     const int n_blocks = split ? in.n_int : 1;
     for (int blk = 0; blk < n_blocks; ++blk) {
@@ -154,24 +177,29 @@ idg_status partition(const PlanInput& in, Partition* out, std::string* err) {
         const Pending cur = todo.back();
         todo.pop_back();
         for (int lo = cur.c_lo; lo < cur.c_hi;) {
+          const int32_t k0 = px.layer(cur.ts, lo);
           int hi = lo + 1;
           while (hi < cur.c_hi) {
             const int ts2[2] = {cur.ts, cur.ts}, cs2[2] = {lo, hi};
             if (!px.within(ts2, cs2, double(Sc))) break;
+            if (px.layer(cur.ts, hi) != k0) break;
             ++hi;
           }
           int te = cur.ts + 1;
           while (te < tb) {
             const int ts4[4] = {cur.ts, cur.ts, te, te}, cs4[4] = {lo, hi - 1, lo, hi - 1};
             if (!px.within(ts4, cs4, double(S))) break;
+            if (px.layer(te, lo) != k0 || px.layer(te, hi - 1) != k0) break;
             ++te;
           }
           while (te > cur.ts + 1) {
             const auto bx = px.box(cur.ts, te, lo, hi);
-            if ((bx.xmax - bx.xmin) <= double(S) && (bx.ymax - bx.ymin) <= double(S)) break;
+            if ((bx.xmax - bx.xmin) <= double(S) && (bx.ymax - bx.ymin) <= double(S) &&
+                px.same_layer(cur.ts, te, lo, hi, k0))
+              break;
             --te;
           }
-          runs.push_back(Run{blk, cur.ts, te, lo, hi});
+          runs.push_back(Run{blk, cur.ts, te, lo, hi, k0});
           if (te < tb) todo.push_back(Pending{te, lo, hi});
           lo = hi;
         }
@@ -195,6 +223,7 @@ idg_status partition(const PlanInput& in, Partition* out, std::string* err) {
       d.x0 = int32_t(std::floor((bx.xmin + bx.xmax) / 2.0)) - in.L / 2;
       d.y0 = int32_t(std::floor((bx.ymin + bx.ymax) / 2.0)) - in.L / 2;
       d.n_vis = (r.te - r.ts) * (r.c_hi - r.c_lo);
+      d.layer = r.layer;
       d.plan_index = int32_t(out->subgrids.size());
       const bool outside = d.x0 < 0 || d.y0 < 0 || d.x0 > in.N - in.L || d.y0 > in.N - in.L;
       if (outside) {

@@ -21,11 +21,11 @@ STATUS_NAMES = {0: "IDG_OK", 1: "IDG_ERR_INVALID_ARG", 2: "IDG_ERR_UNSORTED_FREQ
                 4: "IDG_ERR_W_TOO_LARGE", 5: "IDG_ERR_OOM", 6: "IDG_ERR_CUDA", 7: "IDG_ERR_TIMEOUT",
                 8: "IDG_ERR_UNSUPPORTED"}
 IDG_TAPER_KB, IDG_TAPER_USER = 0, 1
-IDG_DROP_OUT_OF_GRID, IDG_SPLIT_AT_ATERM_INTERVALS, IDG_HOST_ONLY, IDG_PERSISTENT = 1, 2, 4, 8
+IDG_DROP_OUT_OF_GRID, IDG_SPLIT_AT_ATERM_INTERVALS, IDG_HOST_ONLY, IDG_PERSISTENT, IDG_W_LAYERS = 1, 2, 4, 8, 16
 
 # every function declared in include/idg.h
 EXPORTS = ["idg_plan_create", "idg_grid", "idg_degrid", "idg_grid_graph", "idg_degrid_graph", "idg_set_stream", "idg_plan_stats", "idg_plan_subgrids",
-           "idg_plan_segments", "idg_subgrid_images", "idg_synchronize", "idg_profile_enable", "idg_profile_read",
+           "idg_plan_segments", "idg_plan_layers", "idg_subgrid_images", "idg_synchronize", "idg_profile_enable", "idg_profile_read",
            "idg_grid_noalloc", "idg_invert", "idg_predict", "idg_wait_selftest", "idg_last_error",
            "idg_plan_destroy", "idg_abi_version"]
 KERNEL_CLASSES = ["gridder", "fft_adder", "splitter_ifft", "degridder", "stage", "aterm_flags"]
@@ -49,7 +49,8 @@ class PlanStats(ctypes.Structure):
                 ("n_vis_dropped", ctypes.c_int64), ("n_subgrids_dropped", ctypes.c_int64),
                 ("n_grid_items", ctypes.c_int64), ("n_degrid_items", ctypes.c_int64), ("n_batches", ctypes.c_int64),
                 ("occupancy_hist", ctypes.c_int64 * 16), ("device_bytes", ctypes.c_int64),
-                ("vis_pixels", ctypes.c_int64), ("subgrid_size", ctypes.c_int32), ("batch_capacity", ctypes.c_int32)]
+                ("vis_pixels", ctypes.c_int64), ("subgrid_size", ctypes.c_int32), ("batch_capacity", ctypes.c_int32),
+                ("n_w_layers", ctypes.c_int32), ("w_layer_min", ctypes.c_int32), ("w_layer_step", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -79,6 +80,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.idg_plan_stats.argtypes = [P, ctypes.POINTER(PlanStats)]
     lib.idg_plan_subgrids.argtypes = [P, P, i64, ctypes.POINTER(i64)]
     lib.idg_plan_segments.argtypes = [P, P, i64, ctypes.POINTER(i64)]
+    lib.idg_plan_layers.argtypes = [P, P, i64, ctypes.POINTER(i64)]
     lib.idg_subgrid_images.argtypes = [P, P, P, i32, P]
     lib.idg_synchronize.argtypes = [P]
     lib.idg_grid_noalloc.argtypes = [P, P, P, P]
@@ -179,6 +181,16 @@ def idg_plan_subgrids(plan) -> np.ndarray:
     out = np.zeros((max(n.value, 1), 8), np.int32)
     _check(lib.idg_plan_subgrids(plan, _np_ptr(out), n.value, ctypes.byref(n)), "idg_plan_subgrids", plan)
     return out[: n.value]
+
+
+def idg_plan_layers(plan) -> np.ndarray:
+    """int32 [n_subgrids]: each subgrid's w layer k (w0 = k * w_layer_step)."""
+    lib = load()
+    n = ctypes.c_int64(0)
+    _check(lib.idg_plan_layers(plan, None, 0, ctypes.byref(n)), "idg_plan_layers", plan)
+    out = np.zeros(n.value, np.int32)
+    _check(lib.idg_plan_layers(plan, _np_ptr(out), n.value, ctypes.byref(n)), "idg_plan_layers", plan)
+    return out
 
 
 def idg_plan_segments(plan) -> np.ndarray:
@@ -325,6 +337,16 @@ class Plan:
 
     def segments(self) -> np.ndarray:
         return idg_plan_segments(self.handle)
+
+    def layers(self) -> np.ndarray:
+        return idg_plan_layers(self.handle)
+
+    def grid_shape(self) -> tuple:
+        """Shape of the master grid this plan grids into: [n_w_layers, 4, N, N],
+        or [4, N, N] for a plan without IDG_W_LAYERS."""
+        st = self.stats()
+        N = self.geometry.grid_size
+        return (int(st.n_w_layers), 4, N, N) if self.geometry.flags & IDG_W_LAYERS else (4, N, N)
 
     def close(self):
         if getattr(self, "handle", None) is not None:

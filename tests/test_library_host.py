@@ -147,3 +147,36 @@ def test_aterm_nodes_bounds(idg_mod):
             with pytest.raises(idg_mod.IdgError) as e:
                 idg_mod.idg_plan_create(g, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets)
             assert e.value.status == 1
+
+
+def _non_coplanar(seed, n_st=16, height=300.0, **kw):
+    """An array with station heights of a few hundred metres: |w| exceeds
+    the single-layer limit, so planning needs w layers."""
+    obs = synth.config(2, seed=seed, n_stations=n_st, n_timesteps=24, **kw)
+    rng = np.random.default_rng(seed + 50)
+    enu = obs.enu.copy()
+    enu[:, 2] = rng.normal(0.0, height, enu.shape[0])
+    return synth.make_observation(enu, obs.n_timesteps, 2.0, obs.freqs, 4, obs.grid_size, obs.subgrid_size,
+                                  obs.kernel_padding, obs.image_size, name="non-coplanar")
+
+
+@pytest.mark.parametrize("seed,L", [(0, 96), (1, 64), (2, 128)])
+def test_planner_w_layers_bit_exact(idg_mod, oracle_mod, seed, L):
+    obs = _non_coplanar(seed)
+    with pytest.raises(idg_mod.IdgError) as e:
+        _host_plan(idg_mod, obs, 0, L)
+    assert e.value.status == 4
+    ref = _oracle_plan(oracle_mod, obs, oracle_mod.FLAG_W_LAYERS, L)
+    g, _ = idg_mod.make_geometry(obs.grid_size, L, obs.kernel_padding, obs.image_size, aterm_nodes=obs.aterm_nodes,
+                                 flags=idg_mod.IDG_W_LAYERS | idg_mod.IDG_HOST_ONLY)
+    h = idg_mod.idg_plan_create(g, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets)
+    try:
+        np.testing.assert_array_equal(idg_mod.idg_plan_subgrids(h), ref.subgrids)
+        np.testing.assert_array_equal(idg_mod.idg_plan_segments(h), ref.segments)
+        np.testing.assert_array_equal(idg_mod.idg_plan_layers(h), ref.layers)
+        st = idg_mod.idg_plan_stats(h)
+        k_min, n_layers = ref.k_range
+        assert (st.w_layer_min, st.n_w_layers) == (k_min, n_layers) and n_layers >= 3
+        assert st.w_layer_step == ref.w_step
+    finally:
+        idg_mod.idg_plan_destroy(h)
