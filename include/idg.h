@@ -224,8 +224,10 @@ idg_status idg_profile_read(idg_plan* plan, double* ms, int64_t* launches);
 /*
  * idg_grid_noalloc -- idg_grid without allocating memory.  No counterpart in
  * the paper: it serves callers that cannot call cudaMalloc at the point where
- * they grid (for example while a CUDA graph is being captured, or inside an
- * allocation-free real-time pipeline).  Same arguments and result as
+ * they grid -- real-time pipelines that reserve all memory at start-up
+ * (cudaMalloc / cudaFree may synchronise the device and take unbounded time)
+ * and hosts whose device memory belongs to another allocator.  Same arguments
+ * and result as
  * idg_grid, on a device plan; the subgrid images live in one static 32 MiB
  * device buffer compiled into the library (held on every GPU that loads it
  * until the process exits) instead of the plan's scratch, and subgrids are

@@ -1,12 +1,14 @@
 // idg_grid_noalloc: gridding that allocates no memory per call.
 //
 // Some callers cannot allocate device memory at the point where they grid:
-// code running while a CUDA graph is being captured (an allocation there is
-// an error or ends up in the graph), allocation-free real-time pipelines, or
-// hosts whose memory pool is owned by someone else.  This entry point grids
-// with an existing device plan but keeps its subgrid images in a fixed
-// static device buffer instead of plan- or call-owned scratch; it calls no
-// cudaMalloc, cudaFree or other allocating routine.
+// real-time pipelines that reserve all memory at start-up and forbid
+// allocation afterwards (cudaMalloc and cudaFree may synchronise the device
+// and take unbounded time), and hosts whose device memory is owned by
+// another allocator (a framework's caching pool) with no room left for a
+// second one.  This entry point grids with an existing device plan but keeps
+// its subgrid images in a fixed static device buffer instead of plan- or
+// call-owned scratch; it calls no cudaMalloc, cudaFree or other allocating
+// routine.
 //
 // The buffer (kNoAllocScratchBytes) lives as long as the library is loaded
 // on every GPU that loads it.  Subgrids are gridded in sub-batches whose

@@ -1,7 +1,8 @@
 """idg_grid_noalloc: the gridding entry point for callers that cannot
-allocate device memory where they grid (for example during CUDA graph
-capture).  It keeps its subgrid images in a static device buffer; its result
-must match idg_grid's.  This file is collected last on purpose."""
+allocate device memory where they grid (real-time pipelines that reserve all
+memory at start-up, hosts whose device memory belongs to another allocator).
+It keeps its subgrid images in a static device buffer; its result must match
+idg_grid's on two calls in a row.  This file is collected last on purpose."""
 import numpy as np
 import pytest
 
