@@ -181,18 +181,18 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
       for (int b2 = warp * (kRangeBlocks / 2); b2 < (warp + 1) * (kRangeBlocks / 2); ++b2) {
         // one phase anchor per 16 pixels (pixel 8 of the block): exact reduction there, FP32 increments
         const float4* G = S.g[buf][b2];
-        const float4 g0 = G[0], g4 = G[4];
-        const float n0 = g0.x, di0 = g4.y, dj0 = g4.z;
+        const float4 g0 = G[0];
+        const float n0 = g0.x, di0 = g0.y, dj0 = g0.z;
         const float sh = fmaf(c0.x, di0, c0.y * dj0);
         const float d1 = __fsub_rn(sh, round_nearest(sh));
         const float lo = fmaf(c1.x, n0, fmaf(c0.z, di0, c0.w * dj0));
         float rr = __fadd_rn(d1, lo);
         rr = __fmul_rn(__fsub_rn(rr, round_nearest(rr)), kTwoPiF);
         const float2 R0 = make_float2(rr, rr);
-        const float* dn = reinterpret_cast<const float*>(G) + 1;  // dn[0..15]
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const float2 DN = make_float2(dn[2 * q], dn[2 * q + 1]);
+          const float4 dn4 = G[1 + (q >> 1)];  // n' increments of pixels 4(q/2) .. 4(q/2)+3
+          const float2 DN = (q & 1) ? make_float2(dn4.z, dn4.w) : make_float2(dn4.x, dn4.y);
           const float2 DI = make_float2(float(2 * q - 8), float(2 * q - 7));
           const float2 ph = ffma2(CRR, DN, ffma2(ARR, DI, R0));
           float2 Cs, Sn;

@@ -274,8 +274,8 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
           // exact, then two range reductions) plus FP32 per-pixel increments
           const float4 cf = rec[6];
           const float4 g0 = __ldg(bg), g1 = __ldg(bg + 1), g2 = __ldg(bg + 2);
-          const float n0 = g0.x, di0 = g2.y, dj0 = g2.z;
-          const float2 DNB[4] = {{g0.y, g0.z}, {g0.w, g1.x}, {g1.y, g1.z}, {g1.w, g2.x}};
+          const float n0 = g0.x, di0 = g0.y, dj0 = g0.z;
+          const float2 DNB[4] = {{g1.x, g1.y}, {g1.z, g1.w}, {g2.x, g2.y}, {g2.z, g2.w}};
           float2 DN[C::QN];
 #pragma unroll
           for (int q = 0; q < C::QN; ++q) DN[q] = C::PX == 8 ? DNB[q] : (hq ? DNB[q + 2] : DNB[q]);
@@ -319,8 +319,13 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
 #pragma unroll
           for (int q = 0; q < C::QN; ++q) {
             RE[p][q] = ffma2(VRR[p], Cs[q], RE[p][q]);
-            RE[p][q] = ffma2(NVI[p], Sn[q], RE[p][q]);
             IM[p][q] = ffma2(VRR[p], Sn[q], IM[p][q]);
+          }
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < C::QN; ++q) {
+            RE[p][q] = ffma2(NVI[p], Sn[q], RE[p][q]);
             IM[p][q] = ffma2(VII[p], Cs[q], IM[p][q]);
           }
       }
@@ -484,7 +489,7 @@ int gridder_rows(int L) {
   switch (L) {
     case 32: return 32;
     case 64: return 16;
-    case 96: return 16;
+    case 96: return 8;
     case 128: return 8;
     default: return 0;
   }
@@ -494,7 +499,7 @@ int launch_gridder(int L, const GridArgs& a, int n_items, int persistent_blocks,
   switch (L) {
     case 32: return launch_gridder_t<32, 32>(a, n_items, persistent_blocks, stream);
     case 64: return launch_gridder_t<64, 16>(a, n_items, persistent_blocks, stream);
-    case 96: return launch_gridder_t<96, 16>(a, n_items, persistent_blocks, stream);
+    case 96: return launch_gridder_t<96, 8>(a, n_items, persistent_blocks, stream);
     case 128: return launch_gridder_t<128, 8>(a, n_items, persistent_blocks, stream);
     default: return int(cudaErrorInvalidValue);
   }
@@ -504,7 +509,7 @@ int configure_gridder(int L, int* persistent_blocks) {
   switch (L) {
     case 32: return configure_gridder_t<32, 32>(persistent_blocks);
     case 64: return configure_gridder_t<64, 16>(persistent_blocks);
-    case 96: return configure_gridder_t<96, 16>(persistent_blocks);
+    case 96: return configure_gridder_t<96, 8>(persistent_blocks);
     case 128: return configure_gridder_t<128, 8>(persistent_blocks);
     default: return int(cudaErrorInvalidValue);
   }

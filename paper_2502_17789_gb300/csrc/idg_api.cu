@@ -188,7 +188,8 @@ void free_device(idg_plan* p) {
 
 // Block geometry table, FP64 -> FP32: for each row j and block ib of 8
 // pixels, n'(anchor) and n'(pixel) - n'(anchor) (anchor = pixel 4 of the
-// block), plus the anchor offsets (i_a - L/2, j - L/2).
+// block), plus the anchor offsets (i_a - L/2, j - L/2):
+// [j][ib][3] = (n0, i_a - L/2, j - L/2, 0) (dn[0..3]) (dn[4..7]).
 std::vector<float4> block_geometry(int L, double fov) {
   const int tpr = L / 8;
   std::vector<float4> t(size_t(L) * tpr * 3);
@@ -203,15 +204,16 @@ std::vector<float4> block_geometry(int L, double fov) {
       float dn[8];
       for (int k = 0; k < 8; ++k) dn[k] = float(nprime(ib * 8 + k, j) - n0);
       float4* g = &t[(size_t(j) * tpr + ib) * 3];
-      g[0] = make_float4(float(n0), dn[0], dn[1], dn[2]);
-      g[1] = make_float4(dn[3], dn[4], dn[5], dn[6]);
-      g[2] = make_float4(dn[7], float(ia - L / 2), float(j - L / 2), 0.f);
+      g[0] = make_float4(float(n0), float(ia - L / 2), float(j - L / 2), 0.f);
+      g[1] = make_float4(dn[0], dn[1], dn[2], dn[3]);
+      g[2] = make_float4(dn[4], dn[5], dn[6], dn[7]);
     }
   return t;
 }
 
 // Same for blocks of 16 pixels (the degridder's phase anchors), anchor at pixel 8:
-// [j][m][5] = (n0, dn[0..2]) (dn[3..6]) (dn[7..10]) (dn[11..14]) (dn[15], i_a - L/2, j - L/2, 0)
+// [j][m][5] = (n0, i_a - L/2, j - L/2, 0) (dn[0..3]) (dn[4..7]) (dn[8..11]) (dn[12..15]): the
+// increments sit in aligned float4s so pixel pairs load as register pairs
 std::vector<float4> block_geometry16(int L, double fov) {
   const int bpr = L / 16;
   std::vector<float4> t(size_t(L) * bpr * 5);
@@ -226,11 +228,8 @@ std::vector<float4> block_geometry16(int L, double fov) {
       float dn[16];
       for (int k = 0; k < 16; ++k) dn[k] = float(nprime(mb * 16 + k, j) - n0);
       float4* g = &t[(size_t(j) * bpr + mb) * 5];
-      g[0] = make_float4(float(n0), dn[0], dn[1], dn[2]);
-      g[1] = make_float4(dn[3], dn[4], dn[5], dn[6]);
-      g[2] = make_float4(dn[7], dn[8], dn[9], dn[10]);
-      g[3] = make_float4(dn[11], dn[12], dn[13], dn[14]);
-      g[4] = make_float4(dn[15], float(ia - L / 2), float(j - L / 2), 0.f);
+      g[0] = make_float4(float(n0), float(ia - L / 2), float(j - L / 2), 0.f);
+      for (int q = 0; q < 4; ++q) g[1 + q] = make_float4(dn[4 * q], dn[4 * q + 1], dn[4 * q + 2], dn[4 * q + 3]);
     }
   return t;
 }

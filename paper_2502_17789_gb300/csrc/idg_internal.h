@@ -134,7 +134,7 @@ struct GridArgs {
   const SegmentDesc* seg;     // global segment table
   const GridItem* items;
   const float* taper;         // [L]
-  const float4* blk;          // [L][L/8][3] block geometry (n0, dn[8], anchor offsets)
+  const float4* blk;          // [L][L/8][3] block geometry (n0, anchor offsets) (dn[0..3]) (dn[4..7])
   float2* scratch;            // [batch][4][L][L]
   KernelGeom g;
 };
@@ -151,7 +151,7 @@ struct DegridArgs {
   const SegmentDesc* seg;
   const DegridItem* items;
   const float* taper;
-  const float4* blk16;        // [L][L/16][5] 16-pixel block geometry (n0, dn[16], anchor offsets)
+  const float4* blk16;        // [L][L/16][5] 16-pixel block geometry (n0, anchor offsets) (dn[0..15])
   const float2* scratch;      // [batch][4][L][L] subgrid images Y
   KernelGeom g;
 };

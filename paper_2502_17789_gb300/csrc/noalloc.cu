@@ -83,8 +83,8 @@ __global__ void __launch_bounds__(ROWS * L / 8, (ROWS * L / 8) <= 128 ? 3 : 2)
   const float4* bg = a.blk + (size_t(j) * TPR + ib) * 3;
   const float4 g0 = bg[0], g1 = bg[1], g2 = bg[2];
   const float n0 = g0.x;
-  const float2 DN[4] = {{g0.y, g0.z}, {g0.w, g1.x}, {g1.y, g1.z}, {g1.w, g2.x}};
-  const float di0 = g2.y, dj0 = g2.z;
+  const float2 DN[4] = {{g1.x, g1.y}, {g1.z, g1.w}, {g2.x, g2.y}, {g2.z, g2.w}};
+  const float di0 = g0.y, dj0 = g0.z;
   const float2 DI[4] = {{-4.f, -3.f}, {-2.f, -1.f}, {0.f, 1.f}, {2.f, 3.f}};
   const int nc = sd.c1 - sd.c0;
   const double inv_l = 1.0 / double(L);
