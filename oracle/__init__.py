@@ -12,7 +12,8 @@ Every function follows a passage of the paper (arXiv 2502.17789):
   degrid()  Section 2.5 prediction steps 3a-3c, Eq. 13 (adjoint reading)
   taper()   Section 4.2 Kaiser-Bessel taper
   dft2()    the subgrid Fourier transform of Eq. 8 (centred, unnormalised)
-  invert()  Section 2.5 imaging step 3, Eq. 11 with the single w = 0 layer
+  invert()  Section 2.5 imaging step 3, Eq. 11 (w-stacked over the w layers),
+            optionally with the A-term power normalisation of Section 3.3
   predict() Section 2.5 prediction step 2, Eq. 12 with w = 0 (adjoint reading)
 """
 from __future__ import annotations
@@ -69,7 +70,7 @@ def _load():
         lib.oracle_plan.restype = i32
         common = [i32, i32, i32, f64, i32, f64, P, i32, i32, i32, i32, i32, P, P, P, i32, P, i32, P, i32,
                   P, f64, i32]
-        lib.oracle_grid.argtypes = common + [P, P, P, P, P]
+        lib.oracle_grid.argtypes = common + [P, P, P, P, P, i32, P]
         lib.oracle_grid.restype = i32
         lib.oracle_degrid.argtypes = common + [P, P, P]
         lib.oracle_degrid.restype = i32
@@ -183,10 +184,15 @@ def grid_shape(geom: Geometry, pl: Plan) -> tuple:
 
 
 def grid(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Plan, vis, aterms,
-         grid_in=None, want_subgrids: bool = False):
+         grid_in=None, want_subgrids: bool = False, normalize: bool = False):
     """Grid visibilities (complex [n_bl][n_t][n_ch][4]) with A-terms
     (complex [n_int][n_st][nodes][nodes][4]) onto a complex128 [4][N][N] grid.
-    Returns grid (and the subgrid images before / after the FFT if asked)."""
+    Returns grid (and the subgrid images before / after the FFT if asked).
+    normalize: A-term power normalisation (Section 3.3): every segment's
+    corrected image is divided per pixel by f = ||A_p^H A_q||_F; the result
+    is then (grid, weights) (plus the subgrid images if asked), weights
+    float64 [L*L + 1] = sum n_seg / f on the subgrid lattice ([j][i]
+    flattened) and sum n_seg in the last slot."""
     lib = _load()
     args, keep = _common(geom, baselines, uvw, freqs, aterm_offsets, pl, n_st)
     v = np.ascontiguousarray(vis, dtype=np.complex128)
@@ -198,11 +204,29 @@ def grid(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Pl
     if want_subgrids:
         img = np.zeros((pl.subgrids.shape[0], 4, L, L), np.complex128)
         uv = np.zeros_like(img)
-    st = lib.oracle_grid(*args, _ptr(v), _ptr(a), _ptr(g), _ptr(img), _ptr(uv))
+    w = np.zeros(L * L + 1, np.float64) if normalize else None
+    st = lib.oracle_grid(*args, _ptr(v), _ptr(a), _ptr(g), _ptr(img), _ptr(uv), int(normalize), _ptr(w))
     if st != 0:
         raise OracleError(st, "grid")
     del keep
-    return (g, img, uv) if want_subgrids else g
+    out = (g, w) if normalize else (g,)
+    if want_subgrids:
+        out = out + (img, uv)
+    return out if len(out) > 1 else g
+
+
+def lattice_to_image(values: np.ndarray, N: int, L: int) -> np.ndarray:
+    """Bilinear interpolation of a [L][L] map on the subgrid lattice
+    (l_i = (i - L/2) FOV/L) to the N x N image (l_p = (p - N/2) FOV/N), i.e.
+    at the fractional lattice index (p - N/2) L/N + L/2; beyond the last
+    lattice point the map is extended flat.  Returns [q][p]."""
+    v = np.asarray(values, np.float64).reshape(L, L)
+    f = (np.arange(N) - N // 2) * (L / N) + L // 2
+    i0 = np.clip(np.floor(f).astype(int), 0, L - 2)
+    fr = np.clip(f - i0, 0.0, 1.0)
+    # along i (columns) then j (rows)
+    rows = v[:, i0] * (1.0 - fr)[None, :] + v[:, i0 + 1] * fr[None, :]          # [j][p]
+    return rows[i0, :] * (1.0 - fr)[:, None] + rows[i0 + 1, :] * fr[:, None]    # [q][p]
 
 
 def degrid(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Plan, grid_arr, aterms):
@@ -280,18 +304,26 @@ def _nprime_image(geom: Geometry) -> np.ndarray:
     return np.sqrt(1.0 - l[None, :] ** 2 - l[:, None] ** 2) - 1.0
 
 
-def invert(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Plan, vis, aterms):
+def invert(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Plan, vis, aterms,
+           normalize: bool = False):
     """Dirty image, complex128 [4][N][N] indexed [pol][q][p] at (l_p, m_q):
     I = sum_layers e^{+2 pi i w0 n'} sum_{X,Y} G_w0(X,Y) e^{+2 pi i (u_X l_p + v_Y m_q)}
         / (L^2 T(l_p) T(m_q)),
     G_w0 the visibilities gridded onto layer w0 (Eq. 11; one layer w0 = 0
     without w layers).  The L^2 T T factor is what the gridder puts on every
     image point (taper once per direction, unnormalised L x L transforms);
-    dividing it out is Eq. 11's 1/T correction."""
+    dividing it out is Eq. 11's 1/T correction.
+    normalize (Section 3.3): the gridding divides every segment by
+    f = ||A_p^H A_q||_F and the image is then divided by the weighted
+    average of that factor, W = (sum n_seg / f) / (sum n_seg) on the subgrid
+    lattice, interpolated to the image pixels (lattice_to_image)."""
     N, L = geom.grid_size, geom.subgrid_size
     if N % 2:
         raise ValueError("N must be even")
-    G = grid(geom, n_st, baselines, uvw, freqs, aterm_offsets, pl, vis, aterms)
+    if normalize:
+        G, W = grid(geom, n_st, baselines, uvw, freqs, aterm_offsets, pl, vis, aterms, normalize=True)
+    else:
+        G = grid(geom, n_st, baselines, uvw, freqs, aterm_offsets, pl, vis, aterms)
     S = _centre_signs(N)
     layers = G[None] if pl.layers is None else G
     k_min, _ = pl.k_range
@@ -301,7 +333,10 @@ def invert(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: 
         w0 = (k_min + li) * pl.w_step if pl.layers is not None else 0.0
         part = np.fft.ifft2(Gl * S[None], axes=(-2, -1)) * float(N) * float(N) * S[None]
         img += part * np.exp(2j * np.pi * w0 * n1)[None]
-    return img / (float(L) * float(L) * image_taper(geom)[None])
+    img = img / (float(L) * float(L) * image_taper(geom)[None])
+    if normalize:
+        img = img / lattice_to_image(W[: L * L] / W[L * L], N, L)[None]
+    return img
 
 
 def predict(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Plan, image, aterms):

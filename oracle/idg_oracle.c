@@ -488,9 +488,17 @@ typedef struct {
 static double or_nprime(double l, double m) { return sqrt(1.0 - l * l - m * m) - 1.0; }
 
 /* subgrid image X (Eq. 10 with the deferred A-term of Section 3.3), all 4
- * polarisations, layout [pol][j][i] */
+ * polarisations, layout [pol][j][i].
+ * With normalize (the A-term power normalisation of Section 3.3): each
+ * segment's corrected image A_p^H X A_q is divided, pixel by pixel, by the
+ * Frobenius norm f = ||A_p^H A_q||_F of the product of the two matrices the
+ * gridder applies (A_1^{-1} (A_2^{-1})^H in the paper's notation, where the
+ * caller passes inverse terms), and wsub[j L + i] accumulates n_seg / f,
+ * n_seg the segment's visibility count.  A pixel with f = 0 contributes
+ * nothing and no weight. */
 static void or_subgrid_image(const or_job* jb, int s, const cplx* vis, const cplx* aterms,
-                             const double* T, const int* seg_first, const int* seg_count, cplx* X) {
+                             const double* T, const int* seg_first, const int* seg_count, cplx* X,
+                             int normalize, double* wsub) {
   const int L = jb->L, N = jb->N, nodes = jb->nodes;
   const int* row = jb->sg + (size_t)s * 8;
   int b = row[0], c0 = row[3], c1 = row[4], x0 = row[5], y0 = row[6];
@@ -528,6 +536,19 @@ static void or_subgrid_image(const or_job* jb, int s, const cplx* vis, const cpl
         or_mul(acc, Aqi, M);
         or_mul(ApH, M, E);
         double tt = T[i] * T[j];
+        if (normalize) {
+          cplx Pm[4];
+          or_mul(ApH, Aqi, Pm);
+          double f2 = 0.0;
+          for (int e4 = 0; e4 < 4; ++e4) f2 += creal(Pm[e4]) * creal(Pm[e4]) + cimag(Pm[e4]) * cimag(Pm[e4]);
+          double f = sqrt(f2);
+          if (f > 0.0) {
+            tt /= f;
+            wsub[(size_t)j * L + i] += (double)((te - tb) * (c1 - c0)) / f;
+          } else {
+            tt = 0.0;
+          }
+        }
         for (int e4 = 0; e4 < 4; ++e4) X[((size_t)e4 * L + j) * L + i] += tt * E[e4];
       }
   }
@@ -549,13 +570,16 @@ static void or_seg_index(const or_job* jb, int* seg_first, int* seg_count) {
  * before the FFT; subgrid_uv (optional): the same after the FFT.
  * With w layers (layer != NULL) subgrid s uses w0 = layer[s] w_step in its
  * phase and is added into grid[layer[s] - k_min][4][N][N].
+ * normalize: A-term power normalisation (see or_subgrid_image); weights
+ * (needed with normalize) double [L*L + 1] accumulates, over the non-dropped
+ * subgrids, sum n_seg / f per subgrid pixel and in its last slot sum n_seg.
  */
 int oracle_grid(int N, int L, int P, double fov, int taper_kind, double beta, const double* taper_user,
                 int nodes, int n_st, int n_bl, int n_t, int n_ch, const int* baselines, const double* uvw,
                 const double* freqs, int n_int, const int* sg, int n_sg, const int* seg, int n_seg,
                 const int* layer, double w_step, int k_min,
                 const double* vis_ri, const double* aterms_ri, double* grid_ri, double* subgrid_images,
-                double* subgrid_uv) {
+                double* subgrid_uv, int normalize, double* weights) {
   or_job jb = {N, L, P, fov, taper_kind, beta, taper_user, nodes, n_st, n_bl, n_t, n_ch, baselines,
                uvw, freqs, n_int, sg, n_sg, seg, n_seg, layer, w_step, k_min};
   double* T = (double*)malloc(sizeof(double) * L);
@@ -569,16 +593,25 @@ int oracle_grid(int N, int L, int P, double fov, int taper_kind, double beta, co
   const cplx* aterms = (const cplx*)aterms_ri;
   cplx* grid = (cplx*)grid_ri;
   const size_t plane = (size_t)L * L;
+  if (normalize && !weights) {
+    free(T);
+    free(seg_first);
+    free(seg_count);
+    free(F);
+    return OR_ERR_INVALID;
+  }
   const int batch = 64;
   cplx* buf = (cplx*)malloc(sizeof(cplx) * 4 * plane * batch);
+  double* wbuf = (double*)calloc(plane * batch, sizeof(double));
   for (int s0 = 0; s0 < n_sg; s0 += batch) {
     int nb = n_sg - s0 < batch ? n_sg - s0 : batch;
+    memset(wbuf, 0, sizeof(double) * plane * batch);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int k = 0; k < nb; ++k) {
       int s = s0 + k;
       cplx* X = (cplx*)malloc(sizeof(cplx) * 4 * plane);
       cplx* tmp = (cplx*)malloc(sizeof(cplx) * plane);
-      or_subgrid_image(&jb, s, vis, aterms, T, seg_first, seg_count, X);
+      or_subgrid_image(&jb, s, vis, aterms, T, seg_first, seg_count, X, normalize, wbuf + (size_t)k * plane);
       if (subgrid_images) memcpy((cplx*)subgrid_images + (size_t)s * 4 * plane, X, sizeof(cplx) * 4 * plane);
       for (int e = 0; e < 4; ++e) or_dft2_plane(L, F, X + e * plane, buf + ((size_t)k * 4 + e) * plane, tmp);
       if (subgrid_uv) memcpy((cplx*)subgrid_uv + (size_t)s * 4 * plane, buf + (size_t)k * 4 * plane, sizeof(cplx) * 4 * plane);
@@ -595,8 +628,15 @@ int oracle_grid(int N, int L, int P, double fov, int taper_kind, double beta, co
         for (int y = 0; y < L; ++y)
           for (int x = 0; x < L; ++x)
             gl[((size_t)e * N + (y0 + y)) * N + (x0 + x)] += buf[(((size_t)k * 4 + e) * L + y) * L + x];
+      if (normalize) {
+        for (size_t e = 0; e < plane; ++e) weights[e] += wbuf[(size_t)k * plane + e];
+        int c0 = row[3], c1 = row[4];
+        for (int g = seg_first[s0 + k]; g < seg_first[s0 + k] + seg_count[s0 + k]; ++g)
+          weights[plane] += (double)((seg[(size_t)g * 4 + 3] - seg[(size_t)g * 4 + 2]) * (c1 - c0));
+      }
     }
   }
+  free(wbuf);
   free(buf);
   free(F);
   free(seg_first);

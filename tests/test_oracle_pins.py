@@ -500,3 +500,94 @@ def test_w_stacked_predict_is_the_adjoint_of_invert(oracle_mod):
     lhs = np.vdot(oracle_mod.predict(*_wrapper_args(obs, geom, pl), img, A), vis)
     rhs = np.vdot(img, oracle_mod.invert(*_wrapper_args(obs, geom, pl), vis, A))
     assert abs(lhs - rhs) / abs(rhs) < 1e-11
+
+
+# ---------------------------------------------------------------- A-term power normalisation (Section 3.3)
+
+def _segment_norms(obs, pl, A, l, m):
+    """Per plan segment: (visibility count, f = ||A_p^H A_q||_F at (l, m)),
+    with A interpolated by numpy (tests/_brute.bilinear_at)."""
+    out = []
+    for (s, a, tb, te) in pl.segments:
+        b, _, _, c0, c1, _, _, dropped = [int(z) for z in pl.subgrids[s]]
+        if dropped:
+            continue
+        p, q = obs.baselines[b]
+        Ap = _brute.bilinear_at(A[a, p], obs.image_size, l, m)
+        Aq = _brute.bilinear_at(A[a, q], obs.image_size, l, m)
+        out.append(((te - tb) * (c1 - c0), np.linalg.norm(Ap.conj().T @ Aq)))
+    return out
+
+
+def test_normalised_weights_are_the_segment_frobenius_norms(oracle_mod):
+    """The weight map is sum over segments of n_seg / ||A_p^H A_q||_F at every
+    subgrid lattice point, and its last slot the number of visibilities."""
+    obs, geom, pl, A, vis = _problem(oracle_mod, seed=11)
+    L, fov = obs.subgrid_size, obs.image_size
+    _, W = _grid(oracle_mod, obs, geom, pl, vis, A, normalize=True)
+    assert W[L * L] == obs.n_baselines * obs.n_timesteps * obs.n_channels
+    worst = 0.0
+    for (i, j) in [(0, 0), (8, 8), (3, 11), (15, 2), (9, 14)]:
+        l, m = (i - L // 2) * fov / L, (j - L // 2) * fov / L
+        want = sum(n / f for n, f in _segment_norms(obs, pl, A, l, m))
+        worst = max(worst, abs(W[j * L + i] - want) / want)
+    assert worst < 1e-12
+
+
+def test_normalised_invert_on_the_lattice_is_the_weighted_direct_adjoint(oracle_mod):
+    """On the subgrid lattice the normalised dirty image is
+      [sum_seg adj_seg(l,m) / f_seg(l,m)] / [(sum_seg n_seg / f_seg(l,m)) / sum n_seg],
+    adj_seg the adjoint of Eq. 1 over the segment's visibilities (a direct sum)."""
+    obs, geom, pl, A, vis = _problem(oracle_mod, seed=12)
+    N, L, fov = obs.grid_size, obs.subgrid_size, obs.image_size
+    img = oracle_mod.invert(*_wrapper_args(obs, geom, pl), vis, A, normalize=True)
+    u, v, w = _brute.uvw_lambda(obs)
+    n_tot = obs.n_baselines * obs.n_timesteps * obs.n_channels
+    r = N // L
+    worst = 0.0
+    for (i, j) in [(8, 8), (3, 11), (12, 2), (5, 7)]:
+        p, q = N // 2 + r * (i - L // 2), N // 2 + r * (j - L // 2)
+        l, m = (p - N // 2) * fov / N, (q - N // 2) * fov / N
+        n1 = np.sqrt(1.0 - l * l - m * m) - 1.0
+        num = np.zeros((2, 2), np.complex128)
+        den = 0.0
+        for (s, a, tb, te) in pl.segments:
+            b, _, _, c0, c1 = [int(z) for z in pl.subgrids[s][:5]]
+            pa, qa = obs.baselines[b]
+            Ap = _brute.bilinear_at(A[a, pa], fov, l, m)
+            Aq = _brute.bilinear_at(A[a, qa], fov, l, m)
+            f = np.linalg.norm(Ap.conj().T @ Aq)
+            ph = np.exp(2j * np.pi * (u[b, tb:te, c0:c1] * l + v[b, tb:te, c0:c1] * m + w[b, tb:te, c0:c1] * n1))
+            S = np.einsum("tc,tce->e", ph, vis[b, tb:te, c0:c1]).reshape(2, 2)
+            num += Ap.conj().T @ S @ Aq / f
+            den += (te - tb) * (c1 - c0) / f
+        want = (num / (den / n_tot)).reshape(4)
+        worst = max(worst, np.abs(img[:, q, p] - want).max() / np.abs(want).max())
+    assert worst < 1e-9
+
+
+def test_normalisation_is_a_no_op_for_identity_aterms(oracle_mod):
+    """Identity A-terms: f = sqrt(2) everywhere, so the normalised image
+    equals the plain one."""
+    obs, geom, pl, _, vis = _problem(oracle_mod, seed=13)
+    A = synth.aterms_identity(obs.n_intervals, obs.n_stations, obs.aterm_nodes).astype(np.complex128)
+    plain = oracle_mod.invert(*_wrapper_args(obs, geom, pl), vis, A)
+    norm = oracle_mod.invert(*_wrapper_args(obs, geom, pl), vis, A, normalize=True)
+    assert _relerr(norm, plain) < 1e-12
+    L = obs.subgrid_size
+    _, W = _grid(oracle_mod, obs, geom, pl, vis, A, normalize=True)
+    assert np.allclose(W[: L * L], W[L * L] / np.sqrt(2.0), rtol=1e-13, atol=0)
+
+
+def test_lattice_to_image_reproduces_bilinear_fields(oracle_mod):
+    """A map that is bilinear in (l, m) on the lattice is reproduced exactly at
+    every image pixel inside the lattice, and extended flat beyond it."""
+    N, L = 64, 16
+    li = np.arange(L) - L // 2
+    field = 2.0 + 0.3 * li[None, :] - 0.1 * li[:, None] + 0.01 * li[None, :] * li[:, None]   # [j][i]
+    img = oracle_mod.lattice_to_image(field, N, L)
+    x = (np.arange(N) - N // 2) * (L / N)        # lattice offset of pixel p
+    inside = x <= L // 2 - 1
+    want = 2.0 + 0.3 * x[None, :] - 0.1 * x[:, None] + 0.01 * x[None, :] * x[:, None]
+    assert np.allclose(img[np.ix_(inside, inside)], want[np.ix_(inside, inside)], rtol=0, atol=1e-12)
+    assert np.allclose(img[:, -1], img[:, np.flatnonzero(inside)[-1]])
