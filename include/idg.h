@@ -67,8 +67,11 @@ enum {
   IDG_SPLIT_AT_ATERM_INTERVALS = 2, /* never let a subgrid span two A-term intervals (Section 3.3 as written) */
   IDG_HOST_ONLY = 4,                /* plan on the host only: no device memory, grid/degrid refused */
   IDG_PERSISTENT = 8,               /* persistent launches: #SMs x occupancy blocks drain a work queue */
-  IDG_W_LAYERS = 16                 /* w layers (Section 2.4): w0 snaps to multiples of 2 w_max instead of
+  IDG_W_LAYERS = 16,                /* w layers (Section 2.4): w0 snaps to multiples of 2 w_max instead of
                                        rejecting |w| > w_max; grids hold one [4][N][N] plane set per layer */
+  IDG_NORMALIZE_ATERM = 32          /* A-term power normalisation (Section 3.3): the gridder divides each
+                                       segment's corrected image by ||A_p^H A_q||_F per pixel and the plan
+                                       accumulates the weights idg_invert corrects the image with */
 };
 
 typedef struct {
@@ -81,7 +84,7 @@ typedef struct {
   const double* taper_user; /* host [L] taper samples at l_i = (i - L/2) FOV/L (IDG_TAPER_USER), copied */
   int32_t aterm_nodes;    /* nodes per axis of the A-term samples, 2 .. 25 */
   int32_t flags;          /* IDG_DROP_OUT_OF_GRID | IDG_SPLIT_AT_ATERM_INTERVALS | IDG_HOST_ONLY | IDG_PERSISTENT
-                             | IDG_W_LAYERS */
+                             | IDG_W_LAYERS | IDG_NORMALIZE_ATERM */
 } idg_geometry;
 
 typedef struct {
@@ -134,6 +137,10 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
  *               [4][N][N] without IDG_W_LAYERS), ACCUMULATED INTO (+=)
  * Dropped subgrids contribute nothing.  Asynchronous on the plan's stream.
  * Buffers must be 16-byte aligned.
+ * With IDG_NORMALIZE_ATERM (Section 3.3) each segment's corrected image
+ * A_p^H X A_q is divided, at every subgrid pixel, by f = ||A_p^H A_q||_F of
+ * the two interpolated matrices (a pixel with f = 0 contributes nothing),
+ * and the plan's weights (idg_aterm_weights) accumulate n_seg / f there.
  */
 idg_status idg_grid(idg_plan* plan, const void* vis_c64, const void* aterms_c64, void* grid_c128);
 
@@ -199,6 +206,21 @@ idg_status idg_subgrid_images(idg_plan* plan, const void* vis_c64, const void* a
                               void* out_c64);
 
 /*
+ * idg_aterm_weights -- the A-term power weights of a plan made with
+ * IDG_NORMALIZE_ATERM (Section 3.3: the image is corrected by the weighted
+ * average of the normalisation factor over all subgrids).
+ *   out    host float64 [L*L + 1]: at subgrid pixel (i, j), out[j*L + i] =
+ *          sum over the gridded segments of n_seg / ||A_p^H A_q||_F at
+ *          (l_i, m_j); out[L*L] = sum of n_seg (the gridded visibilities).
+ *          Accumulated by every idg_grid (and idg_invert) since the last reset.
+ *   reset  != 0: zero the weights after reading them
+ * The image correction is out / out[L*L] interpolated to the image pixels,
+ * as idg_invert applies it.  Synchronises the plan's stream.
+ * IDG_ERR_INVALID_ARG for plans without the flag or a NULL out.
+ */
+idg_status idg_aterm_weights(idg_plan* plan, double* out, int32_t reset);
+
+/*
  * idg_synchronize -- wait for the plan's stream and report device-side
  * failures of earlier calls: IDG_ERR_TIMEOUT if a kernel gave up a bounded
  * wait (the call's results are then incomplete), IDG_ERR_CUDA on an
@@ -236,7 +258,8 @@ idg_status idg_profile_read(idg_plan* plan, double* ms, int64_t* launches);
  *     per device, with that device current): make it before any capture;
  *   - every call shares the buffer: calls that overlap on the GPU (other
  *     streams or threads) race; the buffer keeps the last call's contents;
- *   - IDG_ERR_UNSUPPORTED if one subgrid image would not fit the buffer,
+ *   - IDG_ERR_UNSUPPORTED if one subgrid image would not fit the buffer or
+ *     the plan normalises its A-terms (IDG_NORMALIZE_ATERM),
  *     IDG_ERR_INVALID_ARG for host-only plans or NULL / misaligned buffers.
  */
 idg_status idg_grid_noalloc(idg_plan* plan, const void* vis_c64, const void* aterms_c64, void* grid_c128);
@@ -262,6 +285,13 @@ idg_status idg_grid_noalloc(idg_plan* plan, const void* vis_c64, const void* ate
  * transform times e^{+2 pi i w0 n'(l,m)}, n' = sqrt(1 - l^2 - m^2) - 1.
  * The master-grid transform is cuFFT (4 double-complex planes) on the plan's
  * stream; the first call on a plan creates its cuFFT plan (allocates).
+ * With IDG_NORMALIZE_ATERM the plan's weights are zeroed first, the
+ * gridding is normalised (idg_grid) and the image is then divided by the
+ * weighted average of the normalisation factor, W = weights / (sum n_seg) on
+ * the subgrid lattice, interpolated bilinearly to image pixel (p, q) at the
+ * fractional lattice index ((p - N/2) L/N + L/2, (q - N/2) L/N + L/2) and
+ * extended flat beyond the last lattice point.  idg_predict does not
+ * normalise (it stays the adjoint of the plain invert).
  * IDG_ERR_UNSUPPORTED with IDG_TAPER_USER (its samples exist only on the
  * subgrid lattice) or an odd grid size; otherwise as idg_grid.
  */

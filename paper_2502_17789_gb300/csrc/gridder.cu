@@ -26,7 +26,9 @@
 //    pixel instead of a sine and a cosine.  The 4-polarisation complex
 //    multiply-accumulate runs as packed f32x2 FMAs over pixel pairs.  After each A-term segment the
 //    thread applies A_p^H X A_q, the taper and the centring sign and adds
-//    the result into its private columns of a shared-memory image sum.
+//    the result into its private columns of a shared-memory image sum
+//    (with the A-term power normalisation, divided by ||A_p^H A_q||_F per
+//    pixel, whose weights n_seg / f go to the plan's weight map).
 #include "kernels_common.cuh"
 
 namespace idg {
@@ -191,9 +193,10 @@ __device__ __forceinline__ void cursor_advance(ChunkCursor& cur, const SegmentDe
 // One work item.  `cg` counts the chunks this block has consumed so far (it
 // selects the buffer and the mbarrier phase, and carries over between the
 // items of a persistent block).  Returns false if a bounded wait expired.
-template <int L, int ROWS>
+// NORM: A-term power normalisation (a.aweights set)
+template <int L, int ROWS, bool NORM>
 __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, uint32_t& cg, float4* s_rec,
-                                             float* s_acc, uint64_t* s_bar) {
+                                             float* s_acc, float* s_w, uint64_t* s_bar) {
   using C = GridCfg<L, ROWS>;
   const GridItem item = a.items[item_idx];
   const SubgridDesc sd = a.sg[item.sg];
@@ -257,6 +260,10 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
     cc = {0, s0.k_begin, s0.k_end};
   }
   bool first_seg = true;
+  if constexpr (NORM) {
+#pragma unroll
+    for (int px = 0; px < C::PX; ++px) s_w[px * C::NT + tid] = 0.f;
+  }
   for (int c = 0; c < n_chunks; ++c) {
     const uint32_t cc_g = cg + uint32_t(c);
     const int buf = int(cc_g & 1);
@@ -373,7 +380,24 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
           const Jones Aqj = interp_jones_ldg(Aq, nodes, wx, wy);
           E = jmul_ah(Apj, jmul(X, Aqj));
         }
-        const float wgt = a.taper[i] * tj * (((i + j) & 1) ? -1.f : 1.f);
+        float wgt = a.taper[i] * tj * (((i + j) & 1) ? -1.f : 1.f);
+        if constexpr (NORM) {
+          // A-term power normalisation (Section 3.3): divide by f = ||A_p^H A_q||_F
+          float f2;
+          if (diag) {
+            const JonesDiag P = interp_diag_ldg(Ap, nodes, wx, wy), Q = interp_diag_ldg(Aq, nodes, wx, wy);
+            f2 = (P.d0.re * P.d0.re + P.d0.im * P.d0.im) * (Q.d0.re * Q.d0.re + Q.d0.im * Q.d0.im) +
+                 (P.d1.re * P.d1.re + P.d1.im * P.d1.im) * (Q.d1.re * Q.d1.re + Q.d1.im * Q.d1.im);
+          } else {
+            const Jones M = jmul_ah(interp_jones_ldg(Ap, nodes, wx, wy), interp_jones_ldg(Aq, nodes, wx, wy));
+            f2 = 0.f;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) f2 += M.m[e].re * M.m[e].re + M.m[e].im * M.m[e].im;
+          }
+          const float inv_f = f2 > 0.f ? rsqrtf(f2) : 0.f;
+          wgt *= inv_f;
+          s_w[px * C::NT + tid] += float(seg.k_end - seg.k_begin) * inv_f;
+        }
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
           float* acc = s_acc + (px * 8 + 2 * p) * C::NT + tid;
@@ -398,6 +422,12 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
     cursor_advance<C::VC>(cc, a.seg, sd.seg_begin, sd.seg_count);
   }
 
+  // ---- A-term weights of this thread's pixels, and the subgrid's visibility count once
+  if (NORM && n_chunks > 0) {
+#pragma unroll 1
+    for (int px = 0; px < C::PX; ++px) atomicAdd(&a.aweights[size_t(j) * L + i0 + px], double(s_w[px * C::NT + tid]));
+    if (item.tile == 0 && tid == 0) atomicAdd(&a.aweights[size_t(L) * L], double(sd.n_vis));
+  }
   // ---- write the subgrid image rows: [sg][pol][j][i]
   if (n_chunks > 0) {
 #pragma unroll
@@ -419,14 +449,16 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
 // PERSIST = false: one item per block (block index, LPT order).
 // PERSIST = true: #SMs x occupancy blocks pull items from the work-queue
 // counter a.queue until the n_items are drained.
-template <int L, int ROWS, bool PERSIST>
+// NORM: with the A-term power normalisation.
+template <int L, int ROWS, bool PERSIST, bool NORM>
 __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
     gridder_kernel(const GridArgs a) {
   using C = GridCfg<L, ROWS>;
   extern __shared__ float4 smem[];
   float4* s_rec = smem;                                                        // [2][VC][8]
   float* s_acc = reinterpret_cast<float*>(s_rec + 2 * C::VC * kRecordFloat4);  // [8 PX][NT]
-  uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_acc + 8 * C::PX * C::NT);    // [2]
+  float* s_w = s_acc + 8 * C::PX * C::NT;                                      // [PX][NT] A-term weights
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_w + C::PX * C::NT);          // [2]
   int* s_item = reinterpret_cast<int*>(s_bar + 2);
   if (threadIdx.x == 0) {
     mbar_init(&s_bar[0], 1);
@@ -436,14 +468,14 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
   __syncthreads();
   uint32_t cg = 0;
   if constexpr (!PERSIST) {
-    gridder_item<L, ROWS>(a, blockIdx.x, cg, s_rec, s_acc, s_bar);
+    gridder_item<L, ROWS, NORM>(a, blockIdx.x, cg, s_rec, s_acc, s_w, s_bar);
   } else {
   for (;;) {
     if (threadIdx.x == 0) *s_item = atomicAdd(a.queue, 1);
     __syncthreads();
     const int it = *s_item;
     if (it >= a.n_items) return;
-    if (!gridder_item<L, ROWS>(a, it, cg, s_rec, s_acc, s_bar)) return;
+    if (!gridder_item<L, ROWS, NORM>(a, it, cg, s_rec, s_acc, s_w, s_bar)) return;
     __syncthreads();  // shared buffers and s_item free for the next item
   }
   }
@@ -452,19 +484,23 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
 template <int L, int ROWS>
 static size_t gridder_smem() {
   using C = GridCfg<L, ROWS>;
-  return sizeof(float4) * 2 * C::VC * kRecordFloat4 + sizeof(float) * 8 * C::PX * C::NT + 2 * sizeof(uint64_t) + 16;
+  return sizeof(float4) * 2 * C::VC * kRecordFloat4 + sizeof(float) * 9 * C::PX * C::NT + 2 * sizeof(uint64_t) + 16;
 }
 
 template <int L, int ROWS>
 static int configure_gridder_t(int* persistent_blocks) {
   using C = GridCfg<L, ROWS>;
   const int smem = int(gridder_smem<L, ROWS>());
-  cudaError_t e = cudaFuncSetAttribute(gridder_kernel<L, ROWS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(gridder_kernel<L, ROWS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const void* fns[4] = {reinterpret_cast<const void*>(gridder_kernel<L, ROWS, false, false>),
+                        reinterpret_cast<const void*>(gridder_kernel<L, ROWS, true, false>),
+                        reinterpret_cast<const void*>(gridder_kernel<L, ROWS, false, true>),
+                        reinterpret_cast<const void*>(gridder_kernel<L, ROWS, true, true>)};
+  cudaError_t e = cudaSuccess;
+  for (const void* fn : fns)
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   int per_sm = 0, dev = 0, sms = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gridder_kernel<L, ROWS, true>, C::NT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gridder_kernel<L, ROWS, true, false>, C::NT, smem);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   *persistent_blocks = per_sm * sms;
@@ -476,11 +512,19 @@ static int launch_gridder_t(const GridArgs& a, int n_items, int persistent_block
   using C = GridCfg<L, ROWS>;
   const size_t smem = gridder_smem<L, ROWS>();
   if (n_items <= 0) return 0;
-  if (persistent_blocks > 0)
-    gridder_kernel<L, ROWS, true>
-        <<<persistent_blocks < n_items ? persistent_blocks : n_items, C::NT, smem, cudaStream_t(stream)>>>(a);
-  else
-    gridder_kernel<L, ROWS, false><<<n_items, C::NT, smem, cudaStream_t(stream)>>>(a);
+  const int pb = persistent_blocks < n_items ? persistent_blocks : n_items;
+  cudaStream_t st = cudaStream_t(stream);
+  if (a.aweights) {
+    if (persistent_blocks > 0)
+      gridder_kernel<L, ROWS, true, true><<<pb, C::NT, smem, st>>>(a);
+    else
+      gridder_kernel<L, ROWS, false, true><<<n_items, C::NT, smem, st>>>(a);
+  } else {
+    if (persistent_blocks > 0)
+      gridder_kernel<L, ROWS, true, false><<<pb, C::NT, smem, st>>>(a);
+    else
+      gridder_kernel<L, ROWS, false, false><<<n_items, C::NT, smem, st>>>(a);
+  }
   return int(cudaGetLastError());
 }
 

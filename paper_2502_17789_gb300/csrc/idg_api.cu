@@ -74,6 +74,7 @@ struct idg_plan {
   int* d_status = nullptr;      // kernel status word (timeouts)
   int* d_queue = nullptr;       // work-queue counters, 2 per batch (gridder, degridder)
   uint8_t* d_adiag = nullptr;   // [n_int][n_st] diagonal-A-term flags of the current call
+  double* d_aweights = nullptr; // [L*L + 1] A-term power weights (IDG_NORMALIZE_ATERM)
   // image-domain wrapper, made at its first use
   cufftHandle fft = 0;
   bool fft_ready = false;
@@ -163,7 +164,7 @@ void free_device(idg_plan* p) {
   p->graph_degrid = {};
   void* ptrs[] = {p->d_uvw,    p->d_fscale, p->d_taper,   p->d_blk,     p->d_twiddle, p->d_sg,     p->d_seg,
                   p->d_gitems, p->d_ditems, p->d_scratch, p->d_records, p->d_status,  p->d_queue,
-                  p->d_adiag,  p->d_blk16, p->d_inv_t};
+                  p->d_adiag,  p->d_blk16, p->d_inv_t, p->d_aweights};
   // stream-ordered frees: no device-wide synchronisation, so plans of other
   // streams keep running while this one is released
   for (void* q : ptrs)
@@ -184,6 +185,7 @@ void free_device(idg_plan* p) {
   p->d_status = nullptr;
   p->d_queue = nullptr;
   p->d_adiag = nullptr;
+  p->d_aweights = nullptr;
 }
 
 // Block geometry table, FP64 -> FP32: for each row j and block ib of 8
@@ -266,6 +268,7 @@ bool plan_device_view(const idg_plan* p, PlanDeviceView* v) {
   v->sg = p->d_sg;
   v->n_sg = int32_t(p->exec.size());
   v->seg = p->d_seg;
+  v->flags = p->geom.flags;
   return true;
 }
 
@@ -460,6 +463,12 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     e = int(cudaMallocAsync(reinterpret_cast<void**>(&p->d_queue), sizeof(int) * 2 * p->batches.size(), p->stream));
     if (!e) p->device_bytes += int64_t(sizeof(int) * 2 * p->batches.size());
   }
+  if (!e && (g->flags & IDG_NORMALIZE_ATERM)) {
+    const size_t wb = (size_t(L) * L + 1) * sizeof(double);
+    e = int(cudaMallocAsync(reinterpret_cast<void**>(&p->d_aweights), wb, p->stream));
+    if (!e) e = int(cudaMemsetAsync(p->d_aweights, 0, wb, p->stream));
+    if (!e) p->device_bytes += int64_t(wb);
+  }
   if (!e) e = int(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
   if (!e) e = int(cudaStreamSynchronize(p->stream));
   if (e) {
@@ -521,6 +530,7 @@ static GridArgs grid_args(const idg_plan* p, const Batch& b, const void* vis, co
   ga.taper = p->d_taper;
   ga.blk = p->d_blk;
   ga.scratch = p->d_scratch;
+  ga.aweights = p->d_aweights;
   ga.g = kgeom(p);
   return ga;
 }
@@ -741,7 +751,18 @@ idg_status idg_invert(idg_plan* plan, const void* vis_c64, const void* aterms_c6
   const double fov = plan->geom.image_size;
   int e = int(cudaMemsetAsync(grid_c128, 0, plane_set * plan->n_layers * sizeof(double2), plan->stream));
   if (e) return cuda_err(plan, e, "zeroing the grid");
+  if (plan->d_aweights) {
+    e = int(cudaMemsetAsync(plan->d_aweights, 0, (size_t(plan->L) * plan->L + 1) * sizeof(double), plan->stream));
+    if (e) return cuda_err(plan, e, "zeroing the A-term weights");
+  }
   if ((st = idg_grid(plan, vis_c64, aterms_c64, grid_c128))) return st;
+  // A-term power correction (Section 3.3), after the taper correction
+  auto weight_correction = [&]() -> idg_status {
+    if (!plan->d_aweights) return IDG_OK;
+    const int ew = launch_weight_correction(static_cast<double2*>(image_c128), plan->d_aweights, N, plan->L,
+                                            plan->stream);
+    return ew ? cuda_err(plan, ew, "A-term weight correction") : IDG_OK;
+  };
   double2* img = static_cast<double2*>(image_c128);
   double2* grid = static_cast<double2*>(grid_c128);
   auto inverse = [&](double2* x) {
@@ -757,7 +778,7 @@ idg_status idg_invert(idg_plan* plan, const void* vis_c64, const void* aterms_c6
     if (r != CUFFT_SUCCESS) return fft_err(plan, r, "cufftExecZ2Z");
     e = launch_image_pass(img, img, plan->d_inv_t, inv_l2, 0.0, fov, N, kPassSign, plan->stream);
     if (e) return cuda_err(plan, e, "taper correction");
-    return IDG_OK;
+    return weight_correction();
   }
   // w-stacking (Eq. 11): transform every layer in place, shift it from w0 to w = 0, sum
   for (int li = 0; li < plan->n_layers; ++li) {
@@ -772,7 +793,7 @@ idg_status idg_invert(idg_plan* plan, const void* vis_c64, const void* aterms_c6
   }
   e = launch_image_pass(img, img, plan->d_inv_t, inv_l2, 0.0, fov, N, 0, plan->stream);
   if (e) return cuda_err(plan, e, "taper correction");
-  return IDG_OK;
+  return weight_correction();
 }
 
 idg_status idg_predict(idg_plan* plan, const void* image_c128, const void* aterms_c64, void* grid_c128,
@@ -801,6 +822,17 @@ idg_status idg_predict(idg_plan* plan, const void* image_c128, const void* aterm
     if (e) return cuda_err(plan, e, "centring signs");
   }
   return idg_degrid(plan, grid_c128, aterms_c64, vis_c64);
+}
+
+idg_status idg_aterm_weights(idg_plan* plan, double* out, int32_t reset) {
+  if (!plan) return set_err(nullptr, IDG_ERR_INVALID_ARG, "plan is NULL");
+  if (!plan->d_aweights || !out)
+    return set_err(plan, IDG_ERR_INVALID_ARG, "idg_aterm_weights needs a plan made with IDG_NORMALIZE_ATERM and an output");
+  const size_t bytes = (size_t(plan->L) * plan->L + 1) * sizeof(double);
+  int e = int(cudaMemcpyAsync(out, plan->d_aweights, bytes, cudaMemcpyDeviceToHost, plan->stream));
+  if (!e && reset) e = int(cudaMemsetAsync(plan->d_aweights, 0, bytes, plan->stream));
+  if (!e) e = int(cudaStreamSynchronize(plan->stream));
+  return e ? cuda_err(plan, e, "idg_aterm_weights") : IDG_OK;
 }
 
 idg_status idg_synchronize(idg_plan* plan) {

@@ -136,6 +136,7 @@ struct GridArgs {
   const float* taper;         // [L]
   const float4* blk;          // [L][L/8][3] block geometry (n0, anchor offsets) (dn[0..3]) (dn[4..7])
   float2* scratch;            // [batch][4][L][L]
+  double* aweights;           // A-term power weights [L*L + 1] (IDG_NORMALIZE_ATERM), else NULL
   KernelGeom g;
 };
 
@@ -174,6 +175,9 @@ int launch_stage_records(int L, const StageArgs& a, int n_subgrids, void* stream
 // out (+)= in * c * w[x] w[y] * (-1)^(x+y) * e^{i 2 pi w0 n'(x,y)}; w may be null
 constexpr int kPassSign = 1;        // apply (-1)^(x+y)
 constexpr int kPassAccumulate = 2;  // add into out
+// image /= W(p, q) with W the A-term weight map [L*L + 1] (sum n_seg / f,
+// then sum n_seg) averaged and interpolated bilinearly from the subgrid lattice
+int launch_weight_correction(double2* image, const double* aweights, int N, int L, void* stream);
 int launch_image_pass(const double2* in, double2* out, const double* w, double c, double w0, double fov, int N,
                       int flags, void* stream);
 // one warp waits, bounded by limit_ns, on an mbarrier nothing completes; sets kStatusTimeout bit in *status
@@ -202,6 +206,7 @@ struct PlanDeviceView {
   const SubgridDesc* sg;   // non-dropped subgrids, execution order
   int32_t n_sg;
   const SegmentDesc* seg;
+  int32_t flags;           // the plan's IDG_* flags
 };
 bool plan_device_view(const idg_plan* plan, PlanDeviceView* out);
 idg_status plan_set_error(const idg_plan* plan, idg_status st, const char* msg);

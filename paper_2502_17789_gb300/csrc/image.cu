@@ -3,7 +3,8 @@
 // transforms.  With (-1)^(x+y) on both sides, a plain FFT of even length N is
 // the centred transform sum_X f(X) e^{-+2 pi i (X - N/2)(p - N/2)/N}; each w
 // layer's image is multiplied by e^{+2 pi i w0 n'(l,m)} (w-stacking); the
-// taper correction divides by L^2 T(l_p) T(m_q).
+// taper correction divides by L^2 T(l_p) T(m_q); with the A-term power
+// normalisation of Section 3.3 a last pass divides by the averaged weights.
 #include "kernels_common.cuh"
 
 namespace idg {
@@ -57,6 +58,56 @@ int launch_image_pass(const double2* in, double2* out, const double* w, double c
   const int blocks = int(want < int64_t(sms) * 8 ? want : int64_t(sms) * 8);
   if (blocks <= 0) return 0;
   image_pass_kernel<<<blocks, 256, 0, cudaStream_t(stream)>>>(in, out, w, c, w0, fov, N, flags);
+  return int(cudaGetLastError());
+}
+
+// A-term power correction (Section 3.3): divide every image pixel by the
+// visibility-weighted average of the normalisation factor, W = aw[j L + i] /
+// aw[L L] on the subgrid lattice (l_i = (i - L/2) FOV/L), interpolated
+// bilinearly at the fractional lattice index (p - N/2) L/N + L/2 (flat beyond
+// the last lattice point).  A zero W (no visibilities) leaves the pixel.
+__global__ void __launch_bounds__(256) weight_correction_kernel(double2* img, const double* aw, int N, int L) {
+  const int64_t npix = int64_t(N) * N;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const double total = aw[int64_t(L) * L];
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < npix; e += stride) {
+    const int x = int(e % N), y = int(e / N);
+    auto lattice = [&](int p, int* i0, double* fr) {
+      const double f = double(p - N / 2) * (double(L) / double(N)) + double(L / 2);
+      int i = int(floor(f));
+      i = i < 0 ? 0 : (i > L - 2 ? L - 2 : i);
+      double r = f - double(i);
+      *i0 = i;
+      *fr = r < 0.0 ? 0.0 : (r > 1.0 ? 1.0 : r);
+    };
+    int i0, j0;
+    double fx, fy;
+    lattice(x, &i0, &fx);
+    lattice(y, &j0, &fy);
+    const double* r0 = aw + int64_t(j0) * L + i0;
+    const double* r1 = r0 + L;
+    const double wv = ((1.0 - fx) * r0[0] + fx * r0[1]) * (1.0 - fy) + ((1.0 - fx) * r1[0] + fx * r1[1]) * fy;
+    if (!(wv > 0.0) || !(total > 0.0)) continue;
+    const double c = total / wv;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      double2 v = img[int64_t(k) * npix + e];
+      v.x *= c;
+      v.y *= c;
+      img[int64_t(k) * npix + e] = v;
+    }
+  }
+}
+
+int launch_weight_correction(double2* image, const double* aweights, int N, int L, void* stream) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return int(e);
+  const int64_t want = (int64_t(N) * N + 255) / 256;
+  const int blocks = int(want < int64_t(sms) * 8 ? want : int64_t(sms) * 8);
+  if (blocks <= 0) return 0;
+  weight_correction_kernel<<<blocks, 256, 0, cudaStream_t(stream)>>>(image, aweights, N, L);
   return int(cudaGetLastError());
 }
 

@@ -22,11 +22,12 @@ STATUS_NAMES = {0: "IDG_OK", 1: "IDG_ERR_INVALID_ARG", 2: "IDG_ERR_UNSORTED_FREQ
                 8: "IDG_ERR_UNSUPPORTED"}
 IDG_TAPER_KB, IDG_TAPER_USER = 0, 1
 IDG_DROP_OUT_OF_GRID, IDG_SPLIT_AT_ATERM_INTERVALS, IDG_HOST_ONLY, IDG_PERSISTENT, IDG_W_LAYERS = 1, 2, 4, 8, 16
+IDG_NORMALIZE_ATERM = 32
 
 # every function declared in include/idg.h
 EXPORTS = ["idg_plan_create", "idg_grid", "idg_degrid", "idg_grid_graph", "idg_degrid_graph", "idg_set_stream", "idg_plan_stats", "idg_plan_subgrids",
            "idg_plan_segments", "idg_plan_layers", "idg_subgrid_images", "idg_synchronize", "idg_profile_enable", "idg_profile_read",
-           "idg_grid_noalloc", "idg_invert", "idg_predict", "idg_wait_selftest", "idg_last_error",
+           "idg_grid_noalloc", "idg_invert", "idg_predict", "idg_wait_selftest", "idg_aterm_weights", "idg_last_error",
            "idg_plan_destroy", "idg_abi_version"]
 KERNEL_CLASSES = ["gridder", "fft_adder", "splitter_ifft", "degridder", "stage", "aterm_flags"]
 
@@ -85,6 +86,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.idg_synchronize.argtypes = [P]
     lib.idg_grid_noalloc.argtypes = [P, P, P, P]
     lib.idg_wait_selftest.argtypes = [P, ctypes.c_int32]
+    lib.idg_aterm_weights.argtypes = [P, P, i32]
     lib.idg_invert.argtypes = [P, P, P, P, P]
     lib.idg_predict.argtypes = [P, P, P, P, P]
     lib.idg_profile_enable.argtypes = [P, i32]
@@ -319,6 +321,15 @@ class Plan:
         """Visibilities of `image` [4, N, N]; `grid` receives the model uv plane."""
         idg_predict(self.handle, _dev_ptr(image), _dev_ptr(aterms), _dev_ptr(grid), _dev_ptr(vis))
         return vis
+
+    def aterm_weights(self, reset: bool = False) -> np.ndarray:
+        """A-term power weights of a plan made with IDG_NORMALIZE_ATERM:
+        float64 [L*L + 1], sum n_seg / ||A_p^H A_q||_F per subgrid pixel
+        ([j][i] flattened) and sum n_seg last (see idg_aterm_weights)."""
+        L = self.geometry.subgrid_size
+        out = np.zeros(L * L + 1, np.float64)
+        _check(load().idg_aterm_weights(self.handle, _np_ptr(out), int(bool(reset))), "idg_aterm_weights", self.handle)
+        return out
 
     def wait_selftest(self, limit_us: int = 20000):
         idg_wait_selftest(self.handle, limit_us)

@@ -180,3 +180,20 @@ def test_planner_w_layers_bit_exact(idg_mod, oracle_mod, seed, L):
         assert st.w_layer_step == ref.w_step
     finally:
         idg_mod.idg_plan_destroy(h)
+
+
+def test_aterm_weights_need_a_device_plan_with_the_flag(idg_mod):
+    """idg_aterm_weights reads the weights of IDG_NORMALIZE_ATERM device
+    plans; a host-only plan (even with the flag) has none."""
+    import ctypes
+    import numpy as np
+    obs = _brute.tiny_observation(seed=2)
+    g, _ = idg_mod.make_geometry(obs.grid_size, obs.subgrid_size, obs.kernel_padding, obs.image_size,
+                                 flags=idg_mod.IDG_HOST_ONLY | idg_mod.IDG_NORMALIZE_ATERM)
+    plan = idg_mod.idg_plan_create(g, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets)
+    try:
+        out = np.zeros(obs.subgrid_size ** 2 + 1)
+        st = idg_mod.load().idg_aterm_weights(plan, out.ctypes.data_as(ctypes.c_void_p), 0)
+        assert st == 1 and not out.any()
+    finally:
+        idg_mod.idg_plan_destroy(plan)
