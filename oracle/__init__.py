@@ -32,6 +32,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 FLAG_DROP = 1
 FLAG_SPLIT_INTERVALS = 2
 FLAG_W_LAYERS = 4
+FLAG_STOKES_I = 8   # one Stokes-I plane instead of the 4 correlation planes (oracle-side flag; the planner ignores it)
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsorted frequencies", 3: "uv out of grid",
           4: "w too large", 9: "capacity"}
@@ -69,7 +70,7 @@ def _load():
                                     P, i32, P, P, i32, P, P, P]
         lib.oracle_plan.restype = i32
         common = [i32, i32, i32, f64, i32, f64, P, i32, i32, i32, i32, i32, P, P, P, i32, P, i32, P, i32,
-                  P, f64, i32]
+                  P, f64, i32, i32]
         lib.oracle_grid.argtypes = common + [P, P, P, P, P, i32, P]
         lib.oracle_grid.restype = i32
         lib.oracle_degrid.argtypes = common + [P, P, P]
@@ -172,15 +173,22 @@ def _common(geom, baselines, uvw, freqs, aterm_offsets, pl, n_st):
     args = [geom.grid_size, geom.subgrid_size, geom.kernel_padding, geom.image_size, geom.taper_kind,
             geom.beta, _ptr(tu), geom.aterm_nodes, n_st, n_bl, n_t, freqs.shape[0], _ptr(bl), _ptr(uvw),
             _ptr(freqs), len(aterm_offsets) - 1, _ptr(sg), sg.shape[0], _ptr(seg), seg.shape[0],
-            _ptr(lay), pl.w_step, k_min]
+            _ptr(lay), pl.w_step, k_min, n_pol(geom)]
     keep = (uvw, freqs, bl, tu, sg, seg, lay)
     return args, keep
 
 
+def n_pol(geom: Geometry) -> int:
+    """Planes of the master grid and the image: 4 correlations, or 1 with
+    FLAG_STOKES_I (I = (XX + YY) / 2; an unpolarised model predicts XX = YY = I)."""
+    return 1 if geom.flags & FLAG_STOKES_I else 4
+
+
 def grid_shape(geom: Geometry, pl: Plan) -> tuple:
-    """[4][N][N] without w layers, [n_layers][4][N][N] with them."""
-    N = geom.grid_size
-    return (pl.k_range[1], 4, N, N) if pl.layers is not None else (4, N, N)
+    """[npol][N][N] without w layers, [n_layers][npol][N][N] with them
+    (npol = 4, or 1 with FLAG_STOKES_I)."""
+    N, npol = geom.grid_size, n_pol(geom)
+    return (pl.k_range[1], npol, N, N) if pl.layers is not None else (npol, N, N)
 
 
 def grid(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Plan, vis, aterms,
@@ -202,7 +210,7 @@ def grid(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Pl
         np.array(grid_in, dtype=np.complex128, copy=True)
     img = uv = None
     if want_subgrids:
-        img = np.zeros((pl.subgrids.shape[0], 4, L, L), np.complex128)
+        img = np.zeros((pl.subgrids.shape[0], n_pol(geom), L, L), np.complex128)
         uv = np.zeros_like(img)
     w = np.zeros(L * L + 1, np.float64) if normalize else None
     st = lib.oracle_grid(*args, _ptr(v), _ptr(a), _ptr(g), _ptr(img), _ptr(uv), int(normalize), _ptr(w))
@@ -230,7 +238,8 @@ def lattice_to_image(values: np.ndarray, N: int, L: int) -> np.ndarray:
 
 
 def degrid(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Plan, grid_arr, aterms):
-    """Predict visibilities complex128 [n_bl][n_t][n_ch][4] from a [4][N][N] grid."""
+    """Predict visibilities complex128 [n_bl][n_t][n_ch][4] from a [npol][N][N]
+    grid (4 correlation planes, or the Stokes-I plane with FLAG_STOKES_I)."""
     lib = _load()
     args, keep = _common(geom, baselines, uvw, freqs, aterm_offsets, pl, n_st)
     gr = np.ascontiguousarray(grid_arr, dtype=np.complex128)
@@ -306,7 +315,7 @@ def _nprime_image(geom: Geometry) -> np.ndarray:
 
 def invert(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: Plan, vis, aterms,
            normalize: bool = False):
-    """Dirty image, complex128 [4][N][N] indexed [pol][q][p] at (l_p, m_q):
+    """Dirty image, complex128 [npol][N][N] indexed [pol][q][p] at (l_p, m_q):
     I = sum_layers e^{+2 pi i w0 n'} sum_{X,Y} G_w0(X,Y) e^{+2 pi i (u_X l_p + v_Y m_q)}
         / (L^2 T(l_p) T(m_q)),
     G_w0 the visibilities gridded onto layer w0 (Eq. 11; one layer w0 = 0
@@ -328,7 +337,7 @@ def invert(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: 
     layers = G[None] if pl.layers is None else G
     k_min, _ = pl.k_range
     n1 = _nprime_image(geom)
-    img = np.zeros((4, N, N), np.complex128)
+    img = np.zeros((n_pol(geom), N, N), np.complex128)
     for li, Gl in enumerate(layers):
         w0 = (k_min + li) * pl.w_step if pl.layers is not None else 0.0
         part = np.fft.ifft2(Gl * S[None], axes=(-2, -1)) * float(N) * float(N) * S[None]

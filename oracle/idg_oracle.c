@@ -570,6 +570,9 @@ static void or_seg_index(const or_job* jb, int* seg_first, int* seg_count) {
  * before the FFT; subgrid_uv (optional): the same after the FFT.
  * With w layers (layer != NULL) subgrid s uses w0 = layer[s] w_step in its
  * phase and is added into grid[layer[s] - k_min][4][N][N].
+ * npol: 4 (correlation planes) or 1 (Stokes I): with 1 the grid holds
+ * one plane per layer, I = (XX + YY) / 2 of each corrected subgrid image,
+ * and the subgrid image outputs hold that one plane.
  * normalize: A-term power normalisation (see or_subgrid_image); weights
  * (needed with normalize) double [L*L + 1] accumulates, over the non-dropped
  * subgrids, sum n_seg / f per subgrid pixel and in its last slot sum n_seg.
@@ -577,7 +580,7 @@ static void or_seg_index(const or_job* jb, int* seg_first, int* seg_count) {
 int oracle_grid(int N, int L, int P, double fov, int taper_kind, double beta, const double* taper_user,
                 int nodes, int n_st, int n_bl, int n_t, int n_ch, const int* baselines, const double* uvw,
                 const double* freqs, int n_int, const int* sg, int n_sg, const int* seg, int n_seg,
-                const int* layer, double w_step, int k_min,
+                const int* layer, double w_step, int k_min, int npol,
                 const double* vis_ri, const double* aterms_ri, double* grid_ri, double* subgrid_images,
                 double* subgrid_uv, int normalize, double* weights) {
   or_job jb = {N, L, P, fov, taper_kind, beta, taper_user, nodes, n_st, n_bl, n_t, n_ch, baselines,
@@ -593,7 +596,7 @@ int oracle_grid(int N, int L, int P, double fov, int taper_kind, double beta, co
   const cplx* aterms = (const cplx*)aterms_ri;
   cplx* grid = (cplx*)grid_ri;
   const size_t plane = (size_t)L * L;
-  if (normalize && !weights) {
+  if ((npol != 1 && npol != 4) || (normalize && !weights)) {
     free(T);
     free(seg_first);
     free(seg_count);
@@ -612,9 +615,11 @@ int oracle_grid(int N, int L, int P, double fov, int taper_kind, double beta, co
       cplx* X = (cplx*)malloc(sizeof(cplx) * 4 * plane);
       cplx* tmp = (cplx*)malloc(sizeof(cplx) * plane);
       or_subgrid_image(&jb, s, vis, aterms, T, seg_first, seg_count, X, normalize, wbuf + (size_t)k * plane);
-      if (subgrid_images) memcpy((cplx*)subgrid_images + (size_t)s * 4 * plane, X, sizeof(cplx) * 4 * plane);
-      for (int e = 0; e < 4; ++e) or_dft2_plane(L, F, X + e * plane, buf + ((size_t)k * 4 + e) * plane, tmp);
-      if (subgrid_uv) memcpy((cplx*)subgrid_uv + (size_t)s * 4 * plane, buf + (size_t)k * 4 * plane, sizeof(cplx) * 4 * plane);
+      if (npol == 1) /* Stokes I = (XX + YY) / 2 of the corrected image */
+        for (size_t e = 0; e < plane; ++e) X[e] = 0.5 * (X[e] + X[3 * plane + e]);
+      if (subgrid_images) memcpy((cplx*)subgrid_images + (size_t)s * npol * plane, X, sizeof(cplx) * npol * plane);
+      for (int e = 0; e < npol; ++e) or_dft2_plane(L, F, X + e * plane, buf + ((size_t)k * 4 + e) * plane, tmp);
+      if (subgrid_uv) memcpy((cplx*)subgrid_uv + (size_t)s * npol * plane, buf + (size_t)k * 4 * plane, sizeof(cplx) * npol * plane);
       free(tmp);
       free(X);
     }
@@ -623,8 +628,8 @@ int oracle_grid(int N, int L, int P, double fov, int taper_kind, double beta, co
       const int* row = sg + (size_t)(s0 + k) * 8;
       if (row[7]) continue;
       int x0 = row[5], y0 = row[6];
-      cplx* gl = grid + (layer ? (size_t)(layer[s0 + k] - k_min) * 4 * N * N : 0);
-      for (int e = 0; e < 4; ++e)
+      cplx* gl = grid + (layer ? (size_t)(layer[s0 + k] - k_min) * npol * N * N : 0);
+      for (int e = 0; e < npol; ++e)
         for (int y = 0; y < L; ++y)
           for (int x = 0; x < L; ++x)
             gl[((size_t)e * N + (y0 + y)) * N + (x0 + x)] += buf[(((size_t)k * 4 + e) * L + y) * L + x];
@@ -649,15 +654,17 @@ int oracle_grid(int N, int L, int P, double fov, int taper_kind, double beta, co
  * oracle_degrid: predict visibilities from grid[4][N][N] (Eq. 13 read as the
  * adjoint of the gridder).  vis_out is overwritten; visibilities of dropped
  * subgrids are zero.  With w layers, subgrid s reads grid[layer[s] - k_min]
- * and uses w0 = layer[s] w_step.
+ * and uses w0 = layer[s] w_step.  npol = 1: the grid holds Stokes I and the
+ * model is unpolarised, Y = Y_I times the 2x2 identity (XX = YY = I).
  */
 int oracle_degrid(int N, int L, int P, double fov, int taper_kind, double beta, const double* taper_user,
                   int nodes, int n_st, int n_bl, int n_t, int n_ch, const int* baselines, const double* uvw,
                   const double* freqs, int n_int, const int* sg, int n_sg, const int* seg, int n_seg,
-                  const int* layer, double w_step, int k_min,
+                  const int* layer, double w_step, int k_min, int npol,
                   const double* grid_ri, const double* aterms_ri, double* vis_ri) {
   or_job jb = {N, L, P, fov, taper_kind, beta, taper_user, nodes, n_st, n_bl, n_t, n_ch, baselines,
                uvw, freqs, n_int, sg, n_sg, seg, n_seg, layer, w_step, k_min};
+  if (npol != 1 && npol != 4) return OR_ERR_INVALID;
   double* T = (double*)malloc(sizeof(double) * L);
   int st = oracle_taper(L, taper_kind, beta, taper_user, T);
   if (st) { free(T); return st; }
@@ -680,12 +687,18 @@ int oracle_degrid(int N, int L, int P, double fov, int taper_kind, double beta, 
     cplx* Y = (cplx*)malloc(sizeof(cplx) * 4 * plane);
     cplx* tmp = (cplx*)malloc(sizeof(cplx) * plane);
     /* splitter */
-    const cplx* gl = grid + (layer ? (size_t)(layer[s] - k_min) * 4 * N * N : 0);
-    for (int e = 0; e < 4; ++e)
+    const cplx* gl = grid + (layer ? (size_t)(layer[s] - k_min) * npol * N * N : 0);
+    for (int e = 0; e < npol; ++e)
       for (int y = 0; y < L; ++y)
         for (int x = 0; x < L; ++x)
           Yh[((size_t)e * L + y) * L + x] = gl[((size_t)e * N + (y0 + y)) * N + (x0 + x)];
-    for (int e = 0; e < 4; ++e) or_dft2_plane(L, F, Yh + e * plane, Y + e * plane, tmp);
+    for (int e = 0; e < npol; ++e) or_dft2_plane(L, F, Yh + e * plane, Y + e * plane, tmp);
+    if (npol == 1) /* Stokes-I model: Y = Y_I times the 2x2 identity */
+      for (size_t e = 0; e < plane; ++e) {
+        Y[plane + e] = 0.0;
+        Y[2 * plane + e] = 0.0;
+        Y[3 * plane + e] = Y[e];
+      }
     double u0 = (double)(x0 + L / 2 - N / 2) / fov;
     double v0 = (double)(y0 + L / 2 - N / 2) / fov;
     double w0 = layer ? (double)layer[s] * w_step : 0.0;

@@ -591,3 +591,60 @@ def test_lattice_to_image_reproduces_bilinear_fields(oracle_mod):
     want = 2.0 + 0.3 * x[None, :] - 0.1 * x[:, None] + 0.01 * x[None, :] * x[:, None]
     assert np.allclose(img[np.ix_(inside, inside)], want[np.ix_(inside, inside)], rtol=0, atol=1e-12)
     assert np.allclose(img[:, -1], img[:, np.flatnonzero(inside)[-1]])
+
+
+# ---------------------------------------------------------------- Stokes I (one image plane)
+
+def _stokes_geom(oracle_mod, obs, geom):
+    return oracle_mod.Geometry(geom.grid_size, geom.subgrid_size, geom.kernel_padding, geom.image_size,
+                               aterm_nodes=geom.aterm_nodes, flags=geom.flags | oracle_mod.FLAG_STOKES_I)
+
+
+def test_stokes_i_invert_on_the_lattice_is_half_the_trace_of_the_direct_adjoint(oracle_mod):
+    """With one Stokes-I plane the dirty image on the subgrid lattice is
+    (XX + YY) / 2 of the adjoint of Eq. 1 with A-terms (a direct sum)."""
+    obs, geom, pl, A, vis = _problem(oracle_mod, seed=21)
+    gi = _stokes_geom(oracle_mod, obs, geom)
+    N, L, fov = obs.grid_size, obs.subgrid_size, obs.image_size
+    img = oracle_mod.invert(gi, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets, pl, vis, A)
+    assert img.shape == (1, N, N)
+    r = N // L
+    worst = 0.0
+    for (i, j) in [(8, 8), (3, 11), (12, 2), (5, 7)]:
+        p, q = N // 2 + r * (i - L // 2), N // 2 + r * (j - L // 2)
+        l, m = (p - N // 2) * fov / N, (q - N // 2) * fov / N
+        adj = _brute.dft_image(obs, vis, A, l, m)
+        want = 0.5 * (adj[0, 0] + adj[1, 1])
+        worst = max(worst, abs(img[0, q, p] - want) / abs(want))
+    assert worst < 1e-9
+
+
+def test_stokes_i_predict_of_a_lattice_point_source_is_the_measurement_equation(oracle_mod):
+    """An unpolarised point source S on one lattice pixel of the Stokes-I
+    image predicts Eq. 1 with brightness S times the identity."""
+    obs, geom, pl, A, _ = _problem(oracle_mod, seed=22)
+    gi = _stokes_geom(oracle_mod, obs, geom)
+    N, L, fov = obs.grid_size, obs.subgrid_size, obs.image_size
+    r = N // L
+    for (i, j, S) in [(8, 8, 1.3), (4, 10, 0.7)]:
+        p, q = N // 2 + r * (i - L // 2), N // 2 + r * (j - L // 2)
+        img = np.zeros((1, N, N), complex)
+        img[0, q, p] = S
+        V = oracle_mod.predict(gi, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets, pl, img, A)
+        l, m = (p - N // 2) * fov / N, (q - N // 2) * fov / N
+        want = _brute.measurement_equation(obs, A, l, m, S * np.eye(2))
+        assert _relerr(V, want) < 1e-10
+
+
+def test_stokes_i_pair_is_adjoint_up_to_one_half(oracle_mod):
+    """invert takes (XX + YY) / 2 while predict puts I on XX and YY, so
+    <predict(img), v> = 2 <img, invert(v)>."""
+    obs, geom, pl, A, vis = _problem(oracle_mod, seed=23)
+    gi = _stokes_geom(oracle_mod, obs, geom)
+    N = obs.grid_size
+    rng = np.random.default_rng(5)
+    img = rng.standard_normal((1, N, N)) + 1j * rng.standard_normal((1, N, N))
+    args = (gi, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets, pl)
+    lhs = np.vdot(oracle_mod.predict(*args, img, A), vis)
+    rhs = np.vdot(img, oracle_mod.invert(*args, vis, A))
+    assert abs(lhs - 2.0 * rhs) / abs(lhs) < 1e-11
