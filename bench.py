@@ -73,6 +73,8 @@ def parse_args():
                          "and degridder, keyed by the digest of their sources, in profiles/kernel_traffic.json")
     ap.add_argument("--image-steps", type=int, default=2,
                     help="timed invert + predict calls of the image-domain wrapper; 0 = skip")
+    ap.add_argument("--stokes-steps", type=int, default=5,
+                    help="timed grid + degrid steps of the same workload in Stokes-I mode (one grid plane); 0 = skip")
     ap.add_argument("--serving-requests", type=int, default=24,
                     help="requests of the serving comparison (batched vs plain at 2x plain capacity); 0 = skip")
     ap.add_argument("--aterms", choices=["beam", "full"], default="beam",
@@ -392,6 +394,39 @@ def run_native(args):
                         "image": f"complex128 [4][{N}][{N}]", "transform": "cuFFT Z2Z, 4 planes"}
         del img
 
+    # the same workload imaged in Stokes I (IDG_STOKES_I): one grid plane, a quarter of the subgrid
+    # transforms, adder and splitter work; the phasor sums still carry the 4 correlations
+    stokes_i = None
+    if args.stokes_steps > 0:
+        plan_i = idg.Plan(obs, flags=idg.IDG_STOKES_I, stream=stream.cuda_stream)
+        Gi_model = torch.zeros(plan_i.grid_shape(), dtype=torch.complex128, device=dev)
+        plan_i.grid(vis_d, A_d, Gi_model)
+        Gi_out = torch.empty_like(Gi_model)
+
+        def step_i():
+            Gi_out.zero_()
+            plan_i.grid(vis_d, A_d, Gi_out)
+            plan_i.degrid(Gi_model, A_d, vis_pred)
+
+        for _ in range(2):
+            step_i()
+        torch.cuda.synchronize(dev)
+        plan_i.profile(True)
+        plan_i.profile_read()
+        e0.record(stream)
+        for _ in range(args.stokes_steps):
+            step_i()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        si_ms = e0.elapsed_time(e1)
+        prof_i = plan_i.profile_read()
+        plan_i.close()
+        stokes_i = {"value": 2.0 * obs.n_vis * args.stokes_steps / (si_ms * 1e-3), "unit": UNIT,
+                    "ms_per_step": si_ms / args.stokes_steps, "steps": args.stokes_steps,
+                    "grid": f"complex128 [1][{N}][{N}]",
+                    "kernels": {k: {"ms_per_step": v[0] / args.stokes_steps} for k, v in prof_i.items()}}
+        del Gi_model, Gi_out
+
     # end to end through the C ABI with host buffers
     e2e = None
     if args.no_e2e:
@@ -465,7 +500,7 @@ def run_native(args):
                    "subgrids": st.n_subgrids, "segments": st.n_segments, "batches": st.n_batches,
                    "vis_pixels_per_direction": st.vis_pixels},
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches,
-        "kernels": kernels, "image_domain": image_domain, "serving": serving,
+        "kernels": kernels, "image_domain": image_domain, "stokes_i": stokes_i, "serving": serving,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -505,7 +540,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": obs.name, "n_vis": obs.n_vis},
+            "data": "synthetic", "config": {"workload": workload_description(args.workload, obs), "n_vis": obs.n_vis},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

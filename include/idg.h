@@ -69,9 +69,13 @@ enum {
   IDG_PERSISTENT = 8,               /* persistent launches: #SMs x occupancy blocks drain a work queue */
   IDG_W_LAYERS = 16,                /* w layers (Section 2.4): w0 snaps to multiples of 2 w_max instead of
                                        rejecting |w| > w_max; grids hold one [4][N][N] plane set per layer */
-  IDG_NORMALIZE_ATERM = 32          /* A-term power normalisation (Section 3.3): the gridder divides each
+  IDG_NORMALIZE_ATERM = 32,         /* A-term power normalisation (Section 3.3): the gridder divides each
                                        segment's corrected image by ||A_p^H A_q||_F per pixel and the plan
                                        accumulates the weights idg_invert corrects the image with */
+  IDG_STOKES_I = 64                 /* Stokes-I imaging: grids and images hold one plane, I = (XX + YY)/2 of
+                                       each corrected subgrid image; prediction takes an unpolarised model
+                                       (XX = YY = I, XY = YX = 0); the grid, FFT, adder and splitter work
+                                       on a quarter of the planes */
 };
 
 typedef struct {
@@ -84,7 +88,7 @@ typedef struct {
   const double* taper_user; /* host [L] taper samples at l_i = (i - L/2) FOV/L (IDG_TAPER_USER), copied */
   int32_t aterm_nodes;    /* nodes per axis of the A-term samples, 2 .. 25 */
   int32_t flags;          /* IDG_DROP_OUT_OF_GRID | IDG_SPLIT_AT_ATERM_INTERVALS | IDG_HOST_ONLY | IDG_PERSISTENT
-                             | IDG_W_LAYERS | IDG_NORMALIZE_ATERM */
+                             | IDG_W_LAYERS | IDG_NORMALIZE_ATERM | IDG_STOKES_I */
 } idg_geometry;
 
 typedef struct {
@@ -104,6 +108,7 @@ typedef struct {
   int32_t n_w_layers;         /* w layers of the master grid (1 without IDG_W_LAYERS) */
   int32_t w_layer_min;        /* layer k of grid plane set 0; plane set i has w0 = (w_layer_min + i) w_layer_step */
   double w_layer_step;        /* 2 w_max in wavelengths, w_max = (P/2 - 1) / (max|grad n'| FOV) */
+  int32_t n_pol;              /* planes per layer of grids and images: 4, or 1 with IDG_STOKES_I */
 } idg_plan_stats_t;
 
 /*
@@ -133,9 +138,12 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
  * idg_grid -- imaging direction (Section 2.5 steps 2a-2c, Eq. 10, Eq. 6).
  *   vis_c64     device complex64 [n_baselines][n_timesteps][n_channels][4]
  *   aterms_c64  device complex64 [n_intervals][n_stations][nodes][nodes][4]
- *   grid_c128   device complex128 [n_w_layers][4][N][N] (see idg_plan_stats;
- *               [4][N][N] without IDG_W_LAYERS), ACCUMULATED INTO (+=)
+ *   grid_c128   device complex128 [n_w_layers][n_pol][N][N] (see idg_plan_stats;
+ *               [n_pol][N][N] without IDG_W_LAYERS; n_pol = 4, or 1 with
+ *               IDG_STOKES_I), ACCUMULATED INTO (+=)
  * Dropped subgrids contribute nothing.  Asynchronous on the plan's stream.
+ * With IDG_STOKES_I the one plane receives I = (XX + YY) / 2 of every
+ * corrected subgrid image (the visibilities still carry 4 correlations).
  * Buffers must be 16-byte aligned.
  * With IDG_NORMALIZE_ATERM (Section 3.3) each segment's corrected image
  * A_p^H X A_q is divided, at every subgrid pixel, by f = ||A_p^H A_q||_F of
@@ -147,7 +155,8 @@ idg_status idg_grid(idg_plan* plan, const void* vis_c64, const void* aterms_c64,
 /*
  * idg_degrid -- prediction direction (Section 2.5 steps 3a-3c, Eq. 13 read
  * as the adjoint of idg_grid).
- *   grid_c128   device complex128 [n_w_layers][4][N][N], read only
+ *   grid_c128   device complex128 [n_w_layers][n_pol][N][N], read only; with
+ *               IDG_STOKES_I an unpolarised model, XX = YY = I, XY = YX = 0
  *   aterms_c64  device complex64 [n_intervals][n_stations][nodes][nodes][4]
  *   vis_c64     device complex64 [n_baselines][n_timesteps][n_channels][4],
  *               OVERWRITTEN; visibilities of dropped subgrids are set to 0
@@ -198,7 +207,7 @@ idg_status idg_plan_segments(const idg_plan* plan, int32_t* out, int64_t cap, in
  * (Section 2.5 step 2a, or 2a+2b with stage = 1).
  *   stage 0: subgrid images X(i,j) after the phasor sum, A-term and taper
  *   stage 1: the same after the centred subgrid FFT, Vhat(x,y)
- *   out_c64: device complex64 [n_subgrids][4][L][L] in plan order, written;
+ *   out_c64: device complex64 [n_subgrids][n_pol][L][L] in plan order, written;
  *            rows of dropped subgrids are zero
  * Does not touch any grid.  Asynchronous on the plan's stream.
  */
@@ -259,7 +268,8 @@ idg_status idg_profile_read(idg_plan* plan, double* ms, int64_t* launches);
  *   - every call shares the buffer: calls that overlap on the GPU (other
  *     streams or threads) race; the buffer keeps the last call's contents;
  *   - IDG_ERR_UNSUPPORTED if one subgrid image would not fit the buffer or
- *     the plan normalises its A-terms (IDG_NORMALIZE_ATERM),
+ *     the plan normalises its A-terms (IDG_NORMALIZE_ATERM) or images
+ *     Stokes I (IDG_STOKES_I),
  *     IDG_ERR_INVALID_ARG for host-only plans or NULL / misaligned buffers.
  */
 idg_status idg_grid_noalloc(idg_plan* plan, const void* vis_c64, const void* aterms_c64, void* grid_c128);
@@ -277,10 +287,10 @@ idg_status idg_grid_noalloc(idg_plan* plan, const void* vis_c64, const void* ate
  * amplified errors; the paper images the central part of a padded field.
  *   vis_c64    device complex64 [n_baselines][n_timesteps][n_channels][4], read
  *   aterms_c64 device complex64 [n_intervals][n_stations][nodes][nodes][4], read
- *   grid_c128  device complex128 [n_w_layers][4][N][N]: with one layer at
+ *   grid_c128  device complex128 [n_w_layers][n_pol][N][N]: with one layer at
  *              w0 = 0 it receives the gridded uv plane; with several it is
  *              work space (each layer is transformed in place)
- *   image_c128 device complex128 [4][N][N] (pol, m, l), written
+ *   image_c128 device complex128 [n_pol][N][N] (pol, m, l), written
  * With w layers the image is the w-stacked sum of Eq. 11: each layer's
  * transform times e^{+2 pi i w0 n'(l,m)}, n' = sqrt(1 - l^2 - m^2) - 1.
  * The master-grid transform is cuFFT (4 double-complex planes) on the plan's
@@ -305,7 +315,7 @@ idg_status idg_invert(idg_plan* plan, const void* vis_c64, const void* aterms_c6
  *                     / (L^2 T(l_p) T(m_q)),
  * then idg_degrid(grid) into vis (overwritten).  With the degridder's own
  * taper this predicts Eq. 1 on the image pixels.
- *   image_c128 device complex128 [4][N][N], read;  grid_c128 [n_w_layers][4][N][N]
+ *   image_c128 device complex128 [n_pol][N][N], read;  grid_c128 [n_w_layers][n_pol][N][N]
  *   overwritten (layer w0 from image e^{-2 pi i w0 n'}, Eq. 12);
  *   vis_c64    device complex64 [n_baselines][n_timesteps][n_channels][4], written.
  * Errors as idg_invert.

@@ -100,6 +100,14 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
   auto load_y = [&](int chunk) {
     const int bidx = chunk * kChunkBlocks + pb;
     const int j = bidx / TPR, i = (bidx % TPR) * 8 + 2 * pq;
+    if (a.g.npol == 1) {
+      // Stokes-I model: Y = Y_I times the 2x2 identity (XX = YY = I)
+      const float4 v = *reinterpret_cast<const float4*>(Y + size_t(j) * L + i);
+      ya[0] = ya[3] = make_float2(v.x, v.y);
+      yb[0] = yb[3] = make_float2(v.z, v.w);
+      ya[1] = ya[2] = yb[1] = yb[2] = make_float2(0.f, 0.f);
+      return;
+    }
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
       const float4 v = *reinterpret_cast<const float4*>(Y + (size_t(p) * L + j) * L + i);

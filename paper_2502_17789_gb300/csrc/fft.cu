@@ -9,7 +9,7 @@
 // degridder's prologue (-1)^(i+j) after the inverse transform.
 //
 // One block transforms one polarisation plane of one subgrid (L x L complex
-// FP32) in shared memory: row transforms then column transforms, each a
+// FP32; 4 correlation planes, or the one Stokes-I plane) in shared memory: row transforms then column transforms, each a
 // Stockham autosort sequence of radix-4/2/3 stages.  Every stage reads its
 // butterflies into registers, synchronises, and writes them back, so one
 // L x L buffer suffices.
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_adder_kernel(const FftArgs a)
   extern __shared__ float2 sbuf[];
   float2* buf = sbuf;
   float2* tw = sbuf + L * L;
-  const int sgi = blockIdx.x >> 2, pol = blockIdx.x & 3;
+  const int sgi = blockIdx.x / a.npol, pol = blockIdx.x % a.npol;
   const SubgridDesc sd = a.sg[sgi];
   float2* plane = a.scratch + (size_t(sgi) * 4 + pol) * L * L;
   for (int e = threadIdx.x; e < L; e += kFftThreads) tw[e] = a.twiddle[e];
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_adder_kernel(const FftArgs a)
   fft2d<L, -1>(buf, tw);
   if (MODE == 0) {
     // plane set of the subgrid's w layer, then the polarisation plane
-    double* g = reinterpret_cast<double*>(a.grid) + ((size_t(sd.layer) * 4 + pol) * a.N * a.N) * 2;
+    double* g = reinterpret_cast<double*>(a.grid) + ((size_t(sd.layer) * a.npol + pol) * a.N * a.N) * 2;
     for (int e = threadIdx.x; e < L * L; e += kFftThreads) {
       const int y = e / L, x = e - y * L;
       const float sgn = ((x + y) & 1) ? -1.f : 1.f;
@@ -188,10 +188,10 @@ __global__ void __launch_bounds__(kFftThreads) splitter_ifft_kernel(const FftArg
   extern __shared__ float2 sbuf[];
   float2* buf = sbuf;
   float2* tw = sbuf + L * L;
-  const int sgi = blockIdx.x >> 2, pol = blockIdx.x & 3;
+  const int sgi = blockIdx.x / a.npol, pol = blockIdx.x % a.npol;
   const SubgridDesc sd = a.sg[sgi];
   for (int e = threadIdx.x; e < L; e += kFftThreads) tw[e] = a.twiddle[e];
-  const double2* g = a.grid + (size_t(sd.layer) * 4 + pol) * a.N * a.N;  // w layer, then polarisation
+  const double2* g = a.grid + (size_t(sd.layer) * a.npol + pol) * a.N * a.N;  // w layer, then polarisation
   for (int e = threadIdx.x; e < L * L; e += kFftThreads) {
     const int y = e / L, x = e - y * L;
     const double2 v = g[size_t(sd.y0 + y) * a.N + sd.x0 + x];
@@ -207,11 +207,11 @@ __global__ void __launch_bounds__(kFftThreads) splitter_ifft_kernel(const FftArg
 
 // plan-order export of subgrid images for inspection, undoing (-1)^(x+y)
 template <int L>
-__global__ void export_kernel(const SubgridDesc* sg, const float2* scratch, float2* out) {
-  const int sgi = blockIdx.x >> 2, pol = blockIdx.x & 3;
+__global__ void export_kernel(const SubgridDesc* sg, const float2* scratch, float2* out, int npol) {
+  const int sgi = blockIdx.x / npol, pol = blockIdx.x % npol;
   const int dst_sg = sg[sgi].plan_index;
   const float2* src = scratch + (size_t(sgi) * 4 + pol) * L * L;
-  float2* dst = out + (size_t(dst_sg) * 4 + pol) * L * L;
+  float2* dst = out + (size_t(dst_sg) * npol + pol) * L * L;
   for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
     const int y = e / L, x = e - y * L;
     const float sgn = ((x + y) & 1) ? -1.f : 1.f;
@@ -250,23 +250,23 @@ template <int L>
 static int fft_adder_t(const FftArgs& a, int n, int mode, void* stream) {
   if (n <= 0) return 0;
   if (mode == 0)
-    fft_adder_kernel<L, 0><<<n * 4, kFftThreads, fft_smem<L>(), cudaStream_t(stream)>>>(a);
+    fft_adder_kernel<L, 0><<<n * a.npol, kFftThreads, fft_smem<L>(), cudaStream_t(stream)>>>(a);
   else
-    fft_adder_kernel<L, 1><<<n * 4, kFftThreads, fft_smem<L>(), cudaStream_t(stream)>>>(a);
+    fft_adder_kernel<L, 1><<<n * a.npol, kFftThreads, fft_smem<L>(), cudaStream_t(stream)>>>(a);
   return int(cudaGetLastError());
 }
 
 template <int L>
 static int splitter_t(const FftArgs& a, int n, void* stream) {
   if (n <= 0) return 0;
-  splitter_ifft_kernel<L><<<n * 4, kFftThreads, fft_smem<L>(), cudaStream_t(stream)>>>(a);
+  splitter_ifft_kernel<L><<<n * a.npol, kFftThreads, fft_smem<L>(), cudaStream_t(stream)>>>(a);
   return int(cudaGetLastError());
 }
 
 template <int L>
-static int export_t(const SubgridDesc* sg, const float2* scratch, float2* out, int n, void* stream) {
+static int export_t(const SubgridDesc* sg, const float2* scratch, float2* out, int n, int npol, void* stream) {
   if (n <= 0) return 0;
-  export_kernel<L><<<n * 4, 256, 0, cudaStream_t(stream)>>>(sg, scratch, out);
+  export_kernel<L><<<n * npol, 256, 0, cudaStream_t(stream)>>>(sg, scratch, out, npol);
   return int(cudaGetLastError());
 }
 
@@ -290,12 +290,13 @@ int launch_splitter_ifft(int L, const FftArgs& a, int n, void* stream) {
   }
 }
 
-int launch_export_subgrids(int L, const SubgridDesc* sg, const float2* scratch, float2* out, int n, void* stream) {
+int launch_export_subgrids(int L, const SubgridDesc* sg, const float2* scratch, float2* out, int n, int npol,
+                           void* stream) {
   switch (L) {
-    case 32: return export_t<32>(sg, scratch, out, n, stream);
-    case 64: return export_t<64>(sg, scratch, out, n, stream);
-    case 96: return export_t<96>(sg, scratch, out, n, stream);
-    case 128: return export_t<128>(sg, scratch, out, n, stream);
+    case 32: return export_t<32>(sg, scratch, out, n, npol, stream);
+    case 64: return export_t<64>(sg, scratch, out, n, npol, stream);
+    case 96: return export_t<96>(sg, scratch, out, n, npol, stream);
+    case 128: return export_t<128>(sg, scratch, out, n, npol, stream);
     default: return int(cudaErrorInvalidValue);
   }
 }

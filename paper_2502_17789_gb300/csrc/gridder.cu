@@ -428,8 +428,19 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
     for (int px = 0; px < C::PX; ++px) atomicAdd(&a.aweights[size_t(j) * L + i0 + px], double(s_w[px * C::NT + tid]));
     if (item.tile == 0 && tid == 0) atomicAdd(&a.aweights[size_t(L) * L], double(sd.n_vis));
   }
-  // ---- write the subgrid image rows: [sg][pol][j][i]
-  if (n_chunks > 0) {
+  // ---- write the subgrid image rows: [sg][pol][j][i]; in Stokes-I mode only
+  // plane 0, I = (XX + YY) / 2
+  if (n_chunks > 0 && a.g.npol == 1) {
+    float4* dst = reinterpret_cast<float4*>(a.scratch + (size_t(item.sg) * 4 * L + j) * L + i0);
+#pragma unroll
+    for (int h = 0; h < C::QN; ++h) {
+      const int px = 2 * h;
+      auto half_trace = [&](int q, int c) {
+        return 0.5f * (s_acc[(q * 8 + c) * C::NT + tid] + s_acc[(q * 8 + 6 + c) * C::NT + tid]);
+      };
+      dst[h] = make_float4(half_trace(px, 0), half_trace(px, 1), half_trace(px + 1, 0), half_trace(px + 1, 1));
+    }
+  } else if (n_chunks > 0) {
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
       float4* dst = reinterpret_cast<float4*>(a.scratch + ((size_t(item.sg) * 4 + p) * L + j) * L + i0);

@@ -47,6 +47,7 @@ struct idg_plan {
   int32_t n_st = 0, n_bl = 0, n_t = 0, n_ch = 0, n_int = 0;
   int32_t L = 0, N = 0;
   int32_t k_min = 0, n_layers = 1;  // w layers of the master grid
+  int32_t npol = 4;                  // master-grid planes per layer: 4, or 1 with IDG_STOKES_I
   cudaStream_t stream = nullptr;
   bool host_only = false;
   Partition part;
@@ -349,6 +350,7 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
   }
   p->k_min = k_lo;
   p->n_layers = k_hi - k_lo + 1;
+  p->npol = (g->flags & IDG_STOKES_I) ? 1 : 4;
   for (SubgridDesc& d : p->exec) d.layer -= k_lo;  // device tables hold the grid plane set
   if (host_only) {
     *out = p;
@@ -500,8 +502,10 @@ idg_status idg_set_stream(idg_plan* plan, void* cuda_stream) {
 }
 
 static KernelGeom kgeom(const idg_plan* p) {
-  return KernelGeom{p->N, p->L, p->n_t, p->n_ch, p->n_st, p->geom.aterm_nodes, p->geom.image_size,
-                    p->part.w_step, p->k_min};
+  KernelGeom g{p->N, p->L, p->n_t, p->n_ch, p->n_st, p->geom.aterm_nodes, p->geom.image_size, p->part.w_step,
+               p->k_min};
+  g.npol = p->npol;
+  return g;
 }
 
 static StageArgs stage_args(const idg_plan* p, const Batch& b, const void* vis) {
@@ -565,7 +569,8 @@ idg_status idg_grid(idg_plan* plan, const void* vis_c64, const void* aterms_c64,
       return launch_gridder(L, ga, b.gi_count, plan->persistent_grid_blocks, plan->stream);
     });
     if (e) return cuda_err(plan, e, "gridder launch");
-    FftArgs fa{plan->d_sg + b.sg_offset, plan->d_scratch, static_cast<double2*>(grid_c128), plan->d_twiddle, plan->N};
+    FftArgs fa{plan->d_sg + b.sg_offset, plan->d_scratch, static_cast<double2*>(grid_c128), plan->d_twiddle, plan->N,
+               plan->npol};
     e = timed(plan, kFftAdder, [&] { return launch_fft_adder(L, fa, b.sg_count, 0, plan->stream); });
     if (e) return cuda_err(plan, e, "fft/adder launch");
   }
@@ -599,7 +604,7 @@ idg_status idg_degrid(idg_plan* plan, const void* grid_c128, const void* aterms_
   for (size_t bi = 0; bi < plan->batches.size(); ++bi) {
     const Batch& b = plan->batches[bi];
     FftArgs fa{plan->d_sg + b.sg_offset, plan->d_scratch, const_cast<double2*>(static_cast<const double2*>(grid_c128)),
-               plan->d_twiddle, plan->N};
+               plan->d_twiddle, plan->N, plan->npol};
     int e = timed(plan, kSplitter, [&] { return launch_splitter_ifft(L, fa, b.sg_count, plan->stream); });
     if (e) return cuda_err(plan, e, "splitter/ifft launch");
     DegridArgs da{};
@@ -635,7 +640,7 @@ idg_status idg_subgrid_images(idg_plan* plan, const void* vis_c64, const void* a
       (st = check_buffer(plan, out_c64, "out")))
     return st;
   const int L = plan->L;
-  const size_t total = plan->part.subgrids.size() * size_t(4) * L * L * sizeof(float2);
+  const size_t total = plan->part.subgrids.size() * size_t(plan->npol) * L * L * sizeof(float2);
   int e = int(cudaMemsetAsync(out_c64, 0, total, plan->stream));
   if (e) return cuda_err(plan, e, "zeroing output");
   e = timed(plan, kFlags, [&] {
@@ -650,12 +655,12 @@ idg_status idg_subgrid_images(idg_plan* plan, const void* vis_c64, const void* a
     e = launch_gridder(L, ga, b.gi_count, 0, plan->stream);
     if (e) return cuda_err(plan, e, "gridder launch");
     if (stage == 1) {
-      FftArgs fa{plan->d_sg + b.sg_offset, plan->d_scratch, nullptr, plan->d_twiddle, plan->N};
+      FftArgs fa{plan->d_sg + b.sg_offset, plan->d_scratch, nullptr, plan->d_twiddle, plan->N, plan->npol};
       e = launch_fft_adder(L, fa, b.sg_count, 1, plan->stream);
       if (e) return cuda_err(plan, e, "fft launch");
     }
     e = launch_export_subgrids(L, plan->d_sg + b.sg_offset, plan->d_scratch, static_cast<float2*>(out_c64),
-                               b.sg_count, plan->stream);
+                               b.sg_count, plan->npol, plan->stream);
     if (e) return cuda_err(plan, e, "export launch");
   }
   return IDG_OK;
@@ -724,7 +729,8 @@ static idg_status ensure_image(idg_plan* p) {
   if (p->N % 2) return set_err(p, IDG_ERR_UNSUPPORTED, "the image-domain wrapper needs an even grid size");
   if (!p->fft_ready) {
     int n[2] = {p->N, p->N};
-    cufftResult r = cufftPlanMany(&p->fft, 2, n, nullptr, 1, p->N * p->N, nullptr, 1, p->N * p->N, CUFFT_Z2Z, 4);
+    cufftResult r =
+        cufftPlanMany(&p->fft, 2, n, nullptr, 1, p->N * p->N, nullptr, 1, p->N * p->N, CUFFT_Z2Z, p->npol);
     if (r != CUFFT_SUCCESS) return fft_err(p, r, "cufftPlanMany");
     p->fft_ready = true;
     const double beta = p->geom.taper_beta > 0.0 ? p->geom.taper_beta : 0.35 * kPi * p->geom.kernel_padding;
@@ -746,7 +752,7 @@ idg_status idg_invert(idg_plan* plan, const void* vis_c64, const void* aterms_c6
       (st = ensure_image(plan)))
     return st;
   const int N = plan->N;
-  const size_t plane_set = size_t(4) * N * N;
+  const size_t plane_set = size_t(plan->npol) * N * N;
   const double inv_l2 = 1.0 / (double(plan->L) * double(plan->L));
   const double fov = plan->geom.image_size;
   int e = int(cudaMemsetAsync(grid_c128, 0, plane_set * plan->n_layers * sizeof(double2), plan->stream));
@@ -759,7 +765,7 @@ idg_status idg_invert(idg_plan* plan, const void* vis_c64, const void* aterms_c6
   // A-term power correction (Section 3.3), after the taper correction
   auto weight_correction = [&]() -> idg_status {
     if (!plan->d_aweights) return IDG_OK;
-    const int ew = launch_weight_correction(static_cast<double2*>(image_c128), plan->d_aweights, N, plan->L,
+    const int ew = launch_weight_correction(plan->npol, static_cast<double2*>(image_c128), plan->d_aweights, N, plan->L,
                                             plan->stream);
     return ew ? cuda_err(plan, ew, "A-term weight correction") : IDG_OK;
   };
@@ -772,11 +778,11 @@ idg_status idg_invert(idg_plan* plan, const void* vis_c64, const void* aterms_c6
   const bool single = plan->n_layers == 1 && plan->k_min == 0;
   if (single) {
     // one layer at w0 = 0: transform a signed copy, the gridded plane stays in `grid`
-    e = launch_image_pass(grid, img, nullptr, 1.0, 0.0, fov, N, kPassSign, plan->stream);
+    e = launch_image_pass(plan->npol, grid, img, nullptr, 1.0, 0.0, fov, N, kPassSign, plan->stream);
     if (e) return cuda_err(plan, e, "centring signs");
     const cufftResult r = inverse(img);
     if (r != CUFFT_SUCCESS) return fft_err(plan, r, "cufftExecZ2Z");
-    e = launch_image_pass(img, img, plan->d_inv_t, inv_l2, 0.0, fov, N, kPassSign, plan->stream);
+    e = launch_image_pass(plan->npol, img, img, plan->d_inv_t, inv_l2, 0.0, fov, N, kPassSign, plan->stream);
     if (e) return cuda_err(plan, e, "taper correction");
     return weight_correction();
   }
@@ -784,14 +790,14 @@ idg_status idg_invert(idg_plan* plan, const void* vis_c64, const void* aterms_c6
   for (int li = 0; li < plan->n_layers; ++li) {
     double2* gl = grid + plane_set * li;
     const double w0 = double(plan->k_min + li) * plan->part.w_step;
-    e = launch_image_pass(gl, gl, nullptr, 1.0, 0.0, fov, N, kPassSign, plan->stream);
+    e = launch_image_pass(plan->npol, gl, gl, nullptr, 1.0, 0.0, fov, N, kPassSign, plan->stream);
     if (e) return cuda_err(plan, e, "centring signs");
     const cufftResult r = inverse(gl);
     if (r != CUFFT_SUCCESS) return fft_err(plan, r, "cufftExecZ2Z");
-    e = launch_image_pass(gl, img, nullptr, 1.0, w0, fov, N, kPassSign | (li ? kPassAccumulate : 0), plan->stream);
+    e = launch_image_pass(plan->npol, gl, img, nullptr, 1.0, w0, fov, N, kPassSign | (li ? kPassAccumulate : 0), plan->stream);
     if (e) return cuda_err(plan, e, "w-stacking");
   }
-  e = launch_image_pass(img, img, plan->d_inv_t, inv_l2, 0.0, fov, N, 0, plan->stream);
+  e = launch_image_pass(plan->npol, img, img, plan->d_inv_t, inv_l2, 0.0, fov, N, 0, plan->stream);
   if (e) return cuda_err(plan, e, "taper correction");
   return weight_correction();
 }
@@ -804,7 +810,7 @@ idg_status idg_predict(idg_plan* plan, const void* image_c128, const void* aterm
       (st = ensure_image(plan)))
     return st;
   const int N = plan->N;
-  const size_t plane_set = size_t(4) * N * N;
+  const size_t plane_set = size_t(plan->npol) * N * N;
   const double inv_l2 = 1.0 / (double(plan->L) * double(plan->L));
   const double fov = plan->geom.image_size;
   const double2* img = static_cast<const double2*>(image_c128);
@@ -813,12 +819,12 @@ idg_status idg_predict(idg_plan* plan, const void* image_c128, const void* aterm
   for (int li = 0; li < plan->n_layers; ++li) {
     double2* gl = grid + plane_set * li;
     const double w0 = double(plan->k_min + li) * plan->part.w_step;
-    int e = launch_image_pass(img, gl, plan->d_inv_t, inv_l2, -w0, fov, N, kPassSign, plan->stream);
+    int e = launch_image_pass(plan->npol, img, gl, plan->d_inv_t, inv_l2, -w0, fov, N, kPassSign, plan->stream);
     if (e) return cuda_err(plan, e, "taper correction");
     const cufftResult r = cufftExecZ2Z(plan->fft, reinterpret_cast<cufftDoubleComplex*>(gl),
                                        reinterpret_cast<cufftDoubleComplex*>(gl), CUFFT_FORWARD);
     if (r != CUFFT_SUCCESS) return fft_err(plan, r, "cufftExecZ2Z");
-    e = launch_image_pass(gl, gl, nullptr, 1.0, 0.0, fov, N, kPassSign, plan->stream);
+    e = launch_image_pass(plan->npol, gl, gl, nullptr, 1.0, 0.0, fov, N, kPassSign, plan->stream);
     if (e) return cuda_err(plan, e, "centring signs");
   }
   return idg_degrid(plan, grid_c128, aterms_c64, vis_c64);
@@ -910,6 +916,7 @@ idg_status idg_plan_stats(const idg_plan* plan, idg_plan_stats_t* out) {
   out->subgrid_size = plan->L;
   out->batch_capacity = plan->batch_cap;
   out->n_w_layers = plan->n_layers;
+  out->n_pol = plan->npol;
   out->w_layer_min = plan->k_min;
   out->w_layer_step = plan->part.w_step;
   return IDG_OK;

@@ -89,6 +89,7 @@ struct KernelGeom {
   double fov;
   double w_step;   // w layer spacing; a subgrid's w0 = (k_min + layer) * w_step
   int32_t k_min;
+  int32_t npol = 4;  // master-grid planes: 4 correlations, or 1 (Stokes I = (XX + YY) / 2)
 };
 
 // w0 of a subgrid (its w layer; 0 without layers)
@@ -160,9 +161,10 @@ struct DegridArgs {
 struct FftArgs {
   const SubgridDesc* sg;   // batch subgrid table
   float2* scratch;         // [batch][4][L][L]
-  double2* grid;           // [4][N][N] (adder: +=, splitter: read)
+  double2* grid;           // [layers][npol][N][N] (adder: +=, splitter: read)
   const float2* twiddle;   // [L] e^{-2 pi i m / L}
   int32_t N;
+  int32_t npol = 4;        // planes per subgrid transformed and added / split (4, or 1 for Stokes I)
 };
 
 // Launchers (return cudaError_t as int).  `n` is the item or subgrid count.
@@ -177,8 +179,8 @@ constexpr int kPassSign = 1;        // apply (-1)^(x+y)
 constexpr int kPassAccumulate = 2;  // add into out
 // image /= W(p, q) with W the A-term weight map [L*L + 1] (sum n_seg / f,
 // then sum n_seg) averaged and interpolated bilinearly from the subgrid lattice
-int launch_weight_correction(double2* image, const double* aweights, int N, int L, void* stream);
-int launch_image_pass(const double2* in, double2* out, const double* w, double c, double w0, double fov, int N,
+int launch_weight_correction(int npol, double2* image, const double* aweights, int N, int L, void* stream);
+int launch_image_pass(int npol, const double2* in, double2* out, const double* w, double c, double w0, double fov, int N,
                       int flags, void* stream);
 // one warp waits, bounded by limit_ns, on an mbarrier nothing completes; sets kStatusTimeout bit in *status
 int launch_wait_selftest(int* status, int64_t limit_ns, void* stream);
@@ -190,7 +192,7 @@ int launch_fft_adder(int L, const FftArgs& a, int n_subgrids, int mode, void* st
 int launch_splitter_ifft(int L, const FftArgs& a, int n_subgrids, void* stream);
 // copy a batch of subgrid images to plan order with the (-1)^(x+y) centring undone
 int launch_export_subgrids(int L, const SubgridDesc* sg, const float2* scratch, float2* out, int n_subgrids,
-                           void* stream);
+                           int npol, void* stream);
 int configure_kernels(int L);  // one-time attributes (dynamic shared memory opt-in)
 
 // Read-only view of a device plan's tables, for entry points defined outside

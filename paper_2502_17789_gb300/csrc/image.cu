@@ -9,14 +9,14 @@
 
 namespace idg {
 
-// For every pixel (x, y) of N x N and each of the 4 polarisation planes:
+// For every pixel (x, y) of N x N and each of the npol polarisation planes:
 //   v = in * c * w[x] w[y] * (kPassSign ? (-1)^(x+y) : 1) * e^{i 2 pi w0 n'(x,y)}
 //   out = kPassAccumulate ? out + v : v
 // with n' = sqrt(1 - l^2 - m^2) - 1 at l = (x - N/2) FOV/N, m likewise (the
 // phase only when w0 != 0; sincospi keeps it accurate for large w0 n').
 // One thread per pixel, grid-stride; 16 bytes read (and written) per element.
-__global__ void __launch_bounds__(256) image_pass_kernel(const double2* in, double2* out, const double* w, double c,
-                                                         double w0, double fov, int N, int flags) {
+__global__ void __launch_bounds__(256) image_pass_kernel(int npol, const double2* in, double2* out, const double* w,
+                                                         double c, double w0, double fov, int N, int flags) {
   const int64_t npix = int64_t(N) * N;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < npix; e += stride) {
@@ -33,8 +33,8 @@ __global__ void __launch_bounds__(256) image_pass_kernel(const double2* in, doub
       pr = f * co;
       pi = f * s;
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
+#pragma unroll 4
+    for (int k = 0; k < npol; ++k) {
       const int64_t idx = int64_t(k) * npix + e;
       const double2 v = in[idx];
       double2 r = make_double2(v.x * pr - v.y * pi, v.x * pi + v.y * pr);
@@ -48,8 +48,8 @@ __global__ void __launch_bounds__(256) image_pass_kernel(const double2* in, doub
   }
 }
 
-int launch_image_pass(const double2* in, double2* out, const double* w, double c, double w0, double fov, int N,
-                      int flags, void* stream) {
+int launch_image_pass(int npol, const double2* in, double2* out, const double* w, double c, double w0, double fov,
+                      int N, int flags, void* stream) {
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -57,7 +57,7 @@ int launch_image_pass(const double2* in, double2* out, const double* w, double c
   const int64_t want = (int64_t(N) * N + 255) / 256;
   const int blocks = int(want < int64_t(sms) * 8 ? want : int64_t(sms) * 8);
   if (blocks <= 0) return 0;
-  image_pass_kernel<<<blocks, 256, 0, cudaStream_t(stream)>>>(in, out, w, c, w0, fov, N, flags);
+  image_pass_kernel<<<blocks, 256, 0, cudaStream_t(stream)>>>(npol, in, out, w, c, w0, fov, N, flags);
   return int(cudaGetLastError());
 }
 
@@ -66,7 +66,8 @@ int launch_image_pass(const double2* in, double2* out, const double* w, double c
 // aw[L L] on the subgrid lattice (l_i = (i - L/2) FOV/L), interpolated
 // bilinearly at the fractional lattice index (p - N/2) L/N + L/2 (flat beyond
 // the last lattice point).  A zero W (no visibilities) leaves the pixel.
-__global__ void __launch_bounds__(256) weight_correction_kernel(double2* img, const double* aw, int N, int L) {
+__global__ void __launch_bounds__(256) weight_correction_kernel(int npol, double2* img, const double* aw, int N,
+                                                                int L) {
   const int64_t npix = int64_t(N) * N;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   const double total = aw[int64_t(L) * L];
@@ -89,8 +90,8 @@ __global__ void __launch_bounds__(256) weight_correction_kernel(double2* img, co
     const double wv = ((1.0 - fx) * r0[0] + fx * r0[1]) * (1.0 - fy) + ((1.0 - fx) * r1[0] + fx * r1[1]) * fy;
     if (!(wv > 0.0) || !(total > 0.0)) continue;
     const double c = total / wv;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
+#pragma unroll 4
+    for (int k = 0; k < npol; ++k) {
       double2 v = img[int64_t(k) * npix + e];
       v.x *= c;
       v.y *= c;
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(256) weight_correction_kernel(double2* img, co
   }
 }
 
-int launch_weight_correction(double2* image, const double* aweights, int N, int L, void* stream) {
+int launch_weight_correction(int npol, double2* image, const double* aweights, int N, int L, void* stream) {
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -107,7 +108,7 @@ int launch_weight_correction(double2* image, const double* aweights, int N, int 
   const int64_t want = (int64_t(N) * N + 255) / 256;
   const int blocks = int(want < int64_t(sms) * 8 ? want : int64_t(sms) * 8);
   if (blocks <= 0) return 0;
-  weight_correction_kernel<<<blocks, 256, 0, cudaStream_t(stream)>>>(image, aweights, N, L);
+  weight_correction_kernel<<<blocks, 256, 0, cudaStream_t(stream)>>>(npol, image, aweights, N, L);
   return int(cudaGetLastError());
 }
 

@@ -248,8 +248,9 @@ extern "C" idg_status idg_grid_noalloc(idg_plan* plan, const void* vis_c64, cons
   for (const void* p : ptrs)
     if (!p || reinterpret_cast<uintptr_t>(p) % 16)
       return plan_set_error(plan, IDG_ERR_INVALID_ARG, "idg_grid_noalloc: NULL or misaligned buffer");
-  if (v.flags & IDG_NORMALIZE_ATERM)
-    return plan_set_error(plan, IDG_ERR_UNSUPPORTED, "idg_grid_noalloc does not normalise A-terms (IDG_NORMALIZE_ATERM)");
+  if (v.flags & (IDG_NORMALIZE_ATERM | IDG_STOKES_I))
+    return plan_set_error(plan, IDG_ERR_UNSUPPORTED,
+                          "idg_grid_noalloc grids the 4 correlation planes without A-term normalisation");
   const size_t per_sg = size_t(4) * v.g.L * v.g.L * sizeof(float2);
   if (per_sg > kNoAllocScratchBytes)
     return plan_set_error(plan, IDG_ERR_UNSUPPORTED,

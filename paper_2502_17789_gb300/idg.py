@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "IDG_OK", 1: "IDG_ERR_INVALID_ARG", 2: "IDG_ERR_UNSORTED_FREQ
                 8: "IDG_ERR_UNSUPPORTED"}
 IDG_TAPER_KB, IDG_TAPER_USER = 0, 1
 IDG_DROP_OUT_OF_GRID, IDG_SPLIT_AT_ATERM_INTERVALS, IDG_HOST_ONLY, IDG_PERSISTENT, IDG_W_LAYERS = 1, 2, 4, 8, 16
-IDG_NORMALIZE_ATERM = 32
+IDG_NORMALIZE_ATERM, IDG_STOKES_I = 32, 64
 
 # every function declared in include/idg.h
 EXPORTS = ["idg_plan_create", "idg_grid", "idg_degrid", "idg_grid_graph", "idg_degrid_graph", "idg_set_stream", "idg_plan_stats", "idg_plan_subgrids",
@@ -51,7 +51,8 @@ class PlanStats(ctypes.Structure):
                 ("n_grid_items", ctypes.c_int64), ("n_degrid_items", ctypes.c_int64), ("n_batches", ctypes.c_int64),
                 ("occupancy_hist", ctypes.c_int64 * 16), ("device_bytes", ctypes.c_int64),
                 ("vis_pixels", ctypes.c_int64), ("subgrid_size", ctypes.c_int32), ("batch_capacity", ctypes.c_int32),
-                ("n_w_layers", ctypes.c_int32), ("w_layer_min", ctypes.c_int32), ("w_layer_step", ctypes.c_double)]
+                ("n_w_layers", ctypes.c_int32), ("w_layer_min", ctypes.c_int32), ("w_layer_step", ctypes.c_double),
+                ("n_pol", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -301,7 +302,8 @@ class Plan:
     def subgrid_images(self, vis, aterms, stage: int):
         import torch
         L = self.geometry.subgrid_size
-        out = torch.empty((self.stats().n_subgrids, 4, L, L), dtype=torch.complex64, device=vis.device)
+        st = self.stats()
+        out = torch.empty((st.n_subgrids, st.n_pol, L, L), dtype=torch.complex64, device=vis.device)
         idg_subgrid_images(self.handle, _dev_ptr(vis), _dev_ptr(aterms), stage, _dev_ptr(out))
         return out
 
@@ -353,11 +355,16 @@ class Plan:
         return idg_plan_layers(self.handle)
 
     def grid_shape(self) -> tuple:
-        """Shape of the master grid this plan grids into: [n_w_layers, 4, N, N],
-        or [4, N, N] for a plan without IDG_W_LAYERS."""
+        """Shape of the master grid this plan grids into: [n_w_layers, n_pol, N, N],
+        or [n_pol, N, N] for a plan without IDG_W_LAYERS (n_pol = 4, or 1 with
+        IDG_STOKES_I)."""
         st = self.stats()
-        N = self.geometry.grid_size
-        return (int(st.n_w_layers), 4, N, N) if self.geometry.flags & IDG_W_LAYERS else (4, N, N)
+        N, npol = self.geometry.grid_size, int(st.n_pol)
+        return (int(st.n_w_layers), npol, N, N) if self.geometry.flags & IDG_W_LAYERS else (npol, N, N)
+
+    def image_shape(self) -> tuple:
+        """Shape of the images of invert / predict: [n_pol, N, N]."""
+        return (int(self.stats().n_pol), self.geometry.grid_size, self.geometry.grid_size)
 
     def close(self):
         if getattr(self, "handle", None) is not None:
