@@ -20,6 +20,8 @@
 // reads the Z of its own visibility's segment.
 // Phases use the same FP64 offset / exact anchor reduction / FP32 increment
 // scheme as the gridder, with one anchor per 16 pixels of a row.
+#include <type_traits>
+
 #include "kernels_common.cuh"
 
 namespace idg {
@@ -66,6 +68,8 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
       }
     }
   }
+  const unsigned all_segs = n_seg == 2 ? 3u : 1u;
+  const bool two_pol = a.g.npol == 1 && (diag & all_segs) == all_segs;
   // visibility slot tid: FP64 offsets -> FP32 phase coefficients (zeros for empty slots)
   {
     const int nc = sd.c1 - sd.c0;
@@ -173,7 +177,12 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
     const int buf = chunk & 1;
     const bool more = chunk + 1 < NCH;
     if (more) load_y(chunk + 1);
-    // warp `warp` sums pixel blocks [warp*8, warp*8+8) of the chunk for every visibility group
+    // warp `warp` sums pixel blocks [warp*8, warp*8+8) of the chunk for every
+    // visibility group, over all four correlations (NP = 4) or, for a
+    // Stokes-I model seen through diagonal A-terms, XX and YY only (NP = 2:
+    // Z01 = Z10 = 0, so the predicted XY and YX are zero)
+    auto sum_chunk = [&](auto np_tag) {
+    constexpr int NP = decltype(np_tag)::value;
     for (int g = 0; g < n_vg; ++g) {
       const float4 c0 = S.coef[g][0][lane], c1 = S.coef[g][1][lane];
       // Z of this lane's segment (lanes of one group may straddle the two segments)
@@ -208,7 +217,8 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
           __sincosf(ph.y, &Sn.y, &Cs.y);
           const float2 NS = make_float2(-Sn.x, -Sn.y);
 #pragma unroll
-          for (int p = 0; p < 4; ++p) {
+          for (int pi = 0; pi < NP; ++pi) {
+            const int p = NP == 4 ? pi : 3 * pi;
             const float4 z = zs[2 * b2 + (q >> 2)][q & 3][p];
             const float2 ZR = make_float2(z.x, z.y), ZI = make_float2(z.z, z.w);
             // V += Z conj(e): re += Zr c + Zi s, im += Zi c - Zr s
@@ -221,11 +231,17 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
       }
       const int slot = g * 32 + lane;
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
+      for (int pi = 0; pi < NP; ++pi) {
+        const int p = NP == 4 ? pi : 3 * pi;
         atomicAdd(&S.out[2 * p][slot], RE[p].x + RE[p].y);
         atomicAdd(&S.out[2 * p + 1][slot], IM[p].x + IM[p].y);
       }
     }
+    };
+    if (two_pol)
+      sum_chunk(std::integral_constant<int, 2>{});
+    else
+      sum_chunk(std::integral_constant<int, 4>{});
     if (more) build_z(chunk + 1, buf ^ 1);
     __syncthreads();
   }

@@ -29,6 +29,8 @@
 //    the result into its private columns of a shared-memory image sum
 //    (with the A-term power normalisation, divided by ||A_p^H A_q||_F per
 //    pixel, whose weights n_seg / f go to the plan's weight map).
+#include <type_traits>
+
 #include "kernels_common.cuh"
 
 namespace idg {
@@ -269,7 +271,16 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
     const int buf = int(cc_g & 1);
     const bool ok = mbar_wait_bounded(&s_bar[buf], (cc_g >> 1) & 1);
     const int nv = imin(C::VC, cc.end - cc.k);
-    if (ok) {
+    // Stokes I with both stations' A-terms of this chunk's segment diagonal:
+    // I = (conj(p0) X00 q0 + conj(p1) X11 q1) / 2 needs only the XX and YY sums
+    bool two_pol = false;
+    if (a.g.npol == 1) {
+      const SegmentDesc sg = a.seg[sd.seg_begin + cc.seg];
+      two_pol = a.adiag[sg.interval * a.g.n_st + sd.p] && a.adiag[sg.interval * a.g.n_st + sd.q];
+    }
+    // the record loop, for all four correlations (NP = 4) or XX and YY only (NP = 2)
+    auto records = [&](auto np_tag) {
+      constexpr int NP = decltype(np_tag)::value;
       const float4* rb = s_rec + buf * C::VC * kRecordFloat4;
 #pragma unroll 1
       for (int v = 0; v < nv; ++v) {
@@ -322,20 +333,28 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
         const float2 VII[4] = {{f0.z, f0.w}, {f2.x, f2.y}, {f3.z, f3.w}, {f5.x, f5.y}};
         const float2 NVI[4] = {{f1.x, f1.y}, {f2.z, f2.w}, {f4.x, f4.y}, {f5.z, f5.w}};
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
+        for (int pi = 0; pi < NP; ++pi)
 #pragma unroll
           for (int q = 0; q < C::QN; ++q) {
+            const int p = NP == 4 ? pi : 3 * pi;  // NP = 2: correlations 0 (XX) and 3 (YY)
             RE[p][q] = ffma2(VRR[p], Cs[q], RE[p][q]);
             IM[p][q] = ffma2(VRR[p], Sn[q], IM[p][q]);
           }
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
+        for (int pi = 0; pi < NP; ++pi)
 #pragma unroll
           for (int q = 0; q < C::QN; ++q) {
+            const int p = NP == 4 ? pi : 3 * pi;
             RE[p][q] = ffma2(NVI[p], Sn[q], RE[p][q]);
             IM[p][q] = ffma2(VII[p], Cs[q], IM[p][q]);
           }
       }
+    };
+    if (ok) {
+      if (two_pol)
+        records(std::integral_constant<int, 2>{});
+      else
+        records(std::integral_constant<int, 4>{});
     }
     // every thread is done with this buffer: refill it with chunk c + 2
     if (__syncthreads_or(!ok)) {

@@ -12,10 +12,15 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
-def _setup(idg_mod, oracle_mod, seed=0, flags=0, oflags=0, obs=None):
+def _setup(idg_mod, oracle_mod, seed=0, flags=0, oflags=0, obs=None, diagonal=None):
     obs = obs or synth.config(2, seed=seed, n_stations=14, n_timesteps=12, n_channels=16)
     rng = np.random.default_rng(seed + 1)
     A = synth.aterms_random(rng, obs.n_intervals, obs.n_stations, obs.aterm_nodes)
+    if diagonal == "all":
+        A[..., 1:3] = 0.0
+    elif diagonal == "mixed":      # diagonal Jones matrices for every other (interval, station)
+        A[::2, ::2, ..., 1:3] = 0.0
+        A[1::2, 1::2, ..., 1:3] = 0.0
     vis = synth.random_visibilities(rng, obs).astype(np.complex64)
     plan = idg_mod.Plan(obs, flags=idg_mod.IDG_STOKES_I | flags)
     geom = oracle_mod.Geometry(obs.grid_size, obs.subgrid_size, obs.kernel_padding, obs.image_size,
@@ -25,10 +30,12 @@ def _setup(idg_mod, oracle_mod, seed=0, flags=0, oflags=0, obs=None):
     return obs, A, vis, plan, geom, pl, args
 
 
-@pytest.mark.parametrize("persistent", [False, True])
-def test_stokes_i_grid_and_degrid(idg_mod, oracle_mod, cuda_device, persistent):
+@pytest.mark.parametrize("persistent,diagonal", [(False, None), (True, None), (False, "all"), (True, "mixed")])
+def test_stokes_i_grid_and_degrid(idg_mod, oracle_mod, cuda_device, persistent, diagonal):
+    """Full-Jones, diagonal and mixed A-terms: with diagonal ones the kernels
+    sum only XX and YY (the predicted XY and YX are zero)."""
     import torch
-    obs, A, vis, plan, geom, pl, args = _setup(idg_mod, oracle_mod,
+    obs, A, vis, plan, geom, pl, args = _setup(idg_mod, oracle_mod, diagonal=diagonal,
                                                 flags=idg_mod.IDG_PERSISTENT if persistent else 0)
     N = obs.grid_size
     assert plan.grid_shape() == (1, N, N) and plan.stats().n_pol == 1
@@ -48,6 +55,8 @@ def test_stokes_i_grid_and_degrid(idg_mod, oracle_mod, cuda_device, persistent):
     V_ref = oracle_mod.degrid(*args, Gr, A.astype(np.complex128))
     derr = np.sqrt(np.mean(np.abs(V.cpu().numpy() - V_ref) ** 2)) / np.abs(V_ref).max()
     assert derr < TOL, derr
+    if diagonal == "all":
+        assert not V.cpu().numpy()[..., 1:3].any()
     plan.close()
 
 
