@@ -439,7 +439,7 @@ def run_native(args):
     e2e = None
     if args.no_e2e:
         args.e2e_steps = 0
-    need_host = args.e2e_steps > 0 or (rank == 0 and not args.no_cpu_baseline)
+    need_host = args.e2e_steps > 0 or (rank == 0 and world == 1 and not args.no_cpu_baseline)
     vis_h = vis_d.cpu().pin_memory() if need_host else None
     gmodel_h = G_model.cpu().pin_memory() if need_host else None
     if args.e2e_steps > 0:
@@ -499,7 +499,7 @@ def run_native(args):
         del vis_in, gmodel_in, gout_d, vpred_d, gout_h, vpred_h
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the oracle baseline runs at N = 1 only
         cpu = cpu_baseline(obs, A_d.cpu().numpy(), vis_h.numpy(), gmodel_h.numpy(), args.cpu_seconds)
 
     # the serving form (continuous batching) beside the plain one-request-at-a-time form, on a Poisson stream
