@@ -47,7 +47,7 @@ CSRC = os.path.join(ROOT, "paper_2502_17789_gb300", "csrc")
 NCU_LAUNCH_LIST = ('ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum '
                    '--clock-control none -k regex:"gridder|fft|splitter|stage|aterm" -c 300 --csv '
                    '--log-file launches.csv python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e '
-                   '--serving-requests 0 --image-steps 0')
+                   '--serving-requests 0 --image-steps 0 --stokes-steps 0')
 KERNEL_SOURCES = {"gridder": ["gridder.cu", "kernels_common.cuh", "idg_internal.h"],
                   "degridder": ["degridder.cu", "kernels_common.cuh", "idg_internal.h"]}
 

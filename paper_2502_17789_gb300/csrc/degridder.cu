@@ -32,7 +32,9 @@ constexpr int kRangeBlocks = 8;   // pixel blocks per work unit (one per warp pe
 
 template <int L>
 struct DegridSmem {
-  float4 z[2][kDegridSegs][kChunkBlocks][4][4];  // [buf][segment][block][pixel pair][pol] {Zr_a, Zr_b, Zi_a, Zi_b}
+  // [buf][segment][pol][block][pixel pair] {Zr_a, Zr_b, Zi_a, Zi_b}: the prologue's thread t writes
+  // element t of each pol plane, so a warp's stores are contiguous (no bank conflicts)
+  float4 z[2][kDegridSegs][4][kChunkBlocks][4];
   float4 g[2][kChunkBlocks / 2][5]; // geometry of the 16-pixel phase-anchor blocks
   float4 coef[8][2][32];            // [vis group][half][lane]: (ah, bh, al, bl), (w, 2 pi a, 2 pi w, 0)
   float out[8][kDegridThreads];     // [component][visibility slot], accumulated with shared atomics
@@ -160,7 +162,7 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
       }
     }
 #pragma unroll
-    for (int p = 0; p < 4; ++p) S.z[buf][s][pb][pq][p] = zo[p];
+    for (int p = 0; p < 4; ++p) S.z[buf][s][p][pb][pq] = zo[p];
     }
     if (tid < kChunkBlocks / 2 * 5) {
       const int b = tid / 5, c = tid % 5;
@@ -186,7 +188,7 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
     for (int g = 0; g < n_vg; ++g) {
       const float4 c0 = S.coef[g][0][lane], c1 = S.coef[g][1][lane];
       // Z of this lane's segment (lanes of one group may straddle the two segments)
-      const float4(*zs)[4][4] = S.z[buf][g * 32 + lane >= n0 ? 1 : 0];
+      const float4(*zs)[kChunkBlocks][4] = S.z[buf][g * 32 + lane >= n0 ? 1 : 0];
       const float2 ARR = make_float2(c1.y, c1.y), CRR = make_float2(c1.z, c1.z);
       float2 RE[4], IM[4];
 #pragma unroll
@@ -219,7 +221,7 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
 #pragma unroll
           for (int pi = 0; pi < NP; ++pi) {
             const int p = NP == 4 ? pi : 3 * pi;
-            const float4 z = zs[2 * b2 + (q >> 2)][q & 3][p];
+            const float4 z = zs[p][2 * b2 + (q >> 2)][q & 3];
             const float2 ZR = make_float2(z.x, z.y), ZI = make_float2(z.z, z.w);
             // V += Z conj(e): re += Zr c + Zi s, im += Zi c - Zr s
             RE[p] = ffma2(ZR, Cs, RE[p]);
