@@ -5,7 +5,8 @@ mixed-precision report with a 1000-source degrid -> grid round trip.
 At full size the oracle checks sampled outputs it can compute one subgrid at
 a time (degridded visibilities of a seeded, occupancy-stratified sample of
 subgrids); the full grid is checked through identities that hold at any
-size: the DC invariant and the adjoint identity."""
+size: the DC invariant and the adjoint identity, and Stokes-I mode against
+the four-correlation path."""
 import numpy as np
 import pytest
 
@@ -117,6 +118,51 @@ def test_full_size_grid_identities(mwa_full):
     lhs = torch.vdot(V_d.reshape(-1).to(torch.complex128), mwa_full["vis_d"].reshape(-1).to(torch.complex128))
     rhs = torch.vdot(R.reshape(-1), G_d.reshape(-1))
     assert abs(complex(lhs) - complex(rhs)) / abs(complex(rhs)) < GRID_TOL
+
+
+def test_full_size_stokes_i_against_four_correlations(mwa_full, idg_mod):
+    """Stokes-I mode (one grid plane) on the full workload, against the
+    four-correlation path of the same observation through identities that
+    hold at any size: the I grid is (G_XX + G_YY)/2 of the four-plane grid
+    (subgrid FFT and adder are linear), and the visibilities predicted from a
+    model I plane equal the four-plane prediction of the model XX = YY = I,
+    XY = YX = 0; the beam x screen A-terms are diagonal, so the predicted XY
+    and YX are exactly zero."""
+    import torch
+    obs, A_d, vis_d = mwa_full["obs"], mwa_full["A_d"], mwa_full["vis_d"]
+    N = obs.grid_size
+    plan4 = mwa_full["plan"]
+    plan1 = idg_mod.Plan(obs, flags=idg_mod.IDG_STOKES_I)
+    try:
+        assert plan1.grid_shape() == (1, N, N)
+        G4 = torch.zeros((4, N, N), dtype=torch.complex128, device="cuda")
+        plan4.grid(vis_d, A_d, G4)
+        plan4.synchronize()
+        GI = torch.zeros((1, N, N), dtype=torch.complex128, device="cuda")
+        plan1.grid(vis_d, A_d, GI)
+        plan1.synchronize()
+        want = 0.5 * (G4[0] + G4[3])
+        err = float(torch.linalg.vector_norm(GI[0] - want) / torch.linalg.vector_norm(want))
+        assert err < GRID_TOL, err
+        del G4, GI, want
+        g = torch.Generator(device="cuda")
+        g.manual_seed(13)
+        I = torch.randn((1, N, N), dtype=torch.complex128, device="cuda", generator=g)
+        Gm = torch.zeros((4, N, N), dtype=torch.complex128, device="cuda")
+        Gm[0] = I[0]
+        Gm[3] = I[0]
+        V4 = torch.empty_like(vis_d)
+        VI = torch.empty_like(vis_d)
+        plan4.degrid(Gm, A_d, V4)
+        plan4.synchronize()
+        plan1.degrid(I, A_d, VI)
+        plan1.synchronize()
+        d = (VI - V4).to(torch.complex128)
+        err = float(torch.sqrt(torch.mean(d.abs() ** 2)) / V4.abs().max())
+        assert err < DEGRID_TOL, err
+        assert not bool(VI[..., 1:3].any())
+    finally:
+        plan1.close()
 
 
 def test_mixed_precision_round_trip(idg_mod, oracle_mod, cuda_device):
