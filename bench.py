@@ -16,7 +16,8 @@ L2, so no flush is needed between steps.
 The e2e leg measures the same steps through the C ABI with the inputs in
 pinned host memory and the results read back every step; the copies run on
 two copy streams with double buffers, overlapping the kernels of the
-neighbouring steps.
+neighbouring steps, and within a step the model grid's copy overlaps the
+gridding and the output grid's copy the degridding.
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 build) on a bounded sample of the same workload.
@@ -450,8 +451,11 @@ def run_native(args):
         vpred_d = [torch.empty_like(vis_d) for _ in range(2)]
         gout_h = [torch.empty(G_model.shape, dtype=G_model.dtype, pin_memory=True) for _ in range(2)]
         vpred_h = [torch.empty(vis_d.shape, dtype=vis_d.dtype, pin_memory=True) for _ in range(2)]
-        ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("in_ready", "done", "out_copied")}
+        ev = {k: [torch.cuda.Event() for _ in range(2)]
+              for k in ("vis_ready", "gm_ready", "grid_done", "done", "grid_copied", "out_copied")}
 
+        # per step: the gridder needs only the visibilities and the degridder only the model grid, so the
+        # model grid's copy overlaps the gridding and the output grid's copy overlaps the degridding
         def e2e_steps(n, first=None):
             for k in range(n):
                 b = k % 2
@@ -459,20 +463,29 @@ def run_native(args):
                     if k == 0 and first is not None:
                         first.record(h2d)
                     if k >= 2:
-                        h2d.wait_event(ev["done"][b])        # step k-2 no longer reads these inputs
+                        h2d.wait_event(ev["grid_done"][b])   # step k-2 no longer reads vis_in[b]
                     vis_in[b].copy_(vis_h, non_blocking=True)
+                    ev["vis_ready"][b].record(h2d)
+                    if k >= 2:
+                        h2d.wait_event(ev["done"][b])        # ... nor gmodel_in[b]
                     gmodel_in[b].copy_(gmodel_h, non_blocking=True)
-                    ev["in_ready"][b].record(h2d)
-                stream.wait_event(ev["in_ready"][b])
+                    ev["gm_ready"][b].record(h2d)
+                stream.wait_event(ev["vis_ready"][b])
                 if k >= 2:
-                    stream.wait_event(ev["out_copied"][b])   # step k-2's results have left these buffers
+                    stream.wait_event(ev["grid_copied"][b])  # step k-2's grid has left gout_d[b]
                 gout_d[b].zero_()
                 plan.grid(vis_in[b], A_d, gout_d[b])
+                ev["grid_done"][b].record(stream)
+                stream.wait_event(ev["gm_ready"][b])
+                if k >= 2:
+                    stream.wait_event(ev["out_copied"][b])   # step k-2's visibilities have left vpred_d[b]
                 plan.degrid(gmodel_in[b], A_d, vpred_d[b])
                 ev["done"][b].record(stream)
                 with torch.cuda.stream(d2h):
-                    d2h.wait_event(ev["done"][b])
+                    d2h.wait_event(ev["grid_done"][b])
                     gout_h[b].copy_(gout_d[b], non_blocking=True)
+                    ev["grid_copied"][b].record(d2h)
+                    d2h.wait_event(ev["done"][b])
                     vpred_h[b].copy_(vpred_d[b], non_blocking=True)
                     ev["out_copied"][b].record(d2h)
             return ev["out_copied"][(n - 1) % 2]
@@ -494,8 +507,9 @@ def run_native(args):
                "h2d_bytes_per_step": int(vis_h.numel() * 8 + gmodel_h.numel() * 16),
                "d2h_bytes_per_step": int(gout_h[0].numel() * 16 + vpred_h[0].numel() * 8),
                "ms_per_step": e2e_ms / args.e2e_steps,
-               "copies": "pinned host buffers; H2D and D2H on two copy streams, double-buffered, overlapping "
-                         "the previous / next step's kernels"}
+               "copies": "pinned host buffers; H2D and D2H on two copy streams, double-buffered; the model "
+                         "grid's H2D overlaps the gridding, the output grid's D2H the degridding, and the "
+                         "neighbouring steps' copies the kernels"}
         del vis_in, gmodel_in, gout_d, vpred_d, gout_h, vpred_h
 
     cpu = None
