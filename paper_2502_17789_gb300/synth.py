@@ -5,7 +5,7 @@ frequencies, A-term samples, point-source skies and the visibilities those
 skies produce.  It holds none of the gridding / degridding arithmetic, and it
 is the only code shared by the GPU path's tests and the oracle's tests.
 
-Recipes (stated again in the design doc):
+Recipes:
   * stations on a flat array at the MWA latitude (-26.703 deg), pointing at
     declination -27 deg, hour angle centred on transit; uvw from the textbook
     ENU -> equatorial -> (u,v,w) rotation (Thompson, Moran & Swenson, ch. 4);
@@ -131,7 +131,7 @@ def config(idx: int, seed: int = 0, subgrid_size: int | None = None, n_stations:
         n_ch = n_channels or 8
         freqs = 150e6 + 1e6 * np.arange(n_ch)
         return make_observation(enu, n_t, 8.0, freqs, max(n_t, 1), 512, subgrid_size or 32, 12, 0.35,
-                                name="cfg1-small")
+                                name="small-32-stations")
     if idx in (2, 3):
         n_st = n_stations or 128
         enu = stations_uniform_disk(rng, n_st, 3000.0)
@@ -139,7 +139,7 @@ def config(idx: int, seed: int = 0, subgrid_size: int | None = None, n_stations:
         n_ch = n_channels or 24
         freqs = np.linspace(140e6, 170e6, n_ch)
         return make_observation(enu, n_t, 2.0, freqs, 4, 4096, subgrid_size or 96, 18, 0.5,
-                                name="cfg2-mwa-like" if idx == 2 else "cfg3-mixed-precision")
+                                name="mwa-like-128-stations" if idx == 2 else "mixed-precision-1000-sources")
     if idx == 4:
         n_st = n_stations or 256
         enu = stations_lognormal(rng, n_st, 300.0, 1.0, 3000.0)
@@ -147,7 +147,7 @@ def config(idx: int, seed: int = 0, subgrid_size: int | None = None, n_stations:
         n_ch = n_channels or 30
         freqs = np.linspace(140e6, 170e6, n_ch)
         return make_observation(enu, n_t, 0.5, freqs, 8, 8192, subgrid_size or 96, 18, 0.5,
-                                name="cfg4-uneven")
+                                name="uneven-256-stations")
     raise ValueError(f"unknown workload {idx}")
 
 

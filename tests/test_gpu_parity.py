@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
 the same seeded inputs.
 
-Tolerances (benchmark spec, restated in the design doc):
+Tolerances (FP32 path against the FP64 oracle):
   gridder   ||G_gpu - G_oracle||_2 / ||G_oracle||_2 <= 1e-5 over all 4 planes
   degridder rms_k |V_gpu - V_oracle| / max_k |V_oracle| <= 1e-5
   plans     bit-exact
@@ -108,7 +108,7 @@ def test_subgrid_images_match_oracle(idg_mod, oracle_mod, cuda_device, L):
 
 # ------------------------------------------------------------------ grid / degrid parity
 
-def test_cfg1_full_grid_and_degrid(idg_mod, oracle_mod, cuda_device):
+def test_small_workload_full_grid_and_degrid(idg_mod, oracle_mod, cuda_device):
     """Workload 1 at full size: 32 stations, 16 x 8 s, 8 channels, 512^2 grid,
     L = 32, identity A-terms, point-source sky plus noise."""
     obs = synth.config(1, seed=0)
@@ -126,7 +126,7 @@ def test_cfg1_full_grid_and_degrid(idg_mod, oracle_mod, cuda_device):
 
 
 @pytest.mark.parametrize("L,split", [(32, False), (64, True), (96, False), (96, True), (128, False)])
-def test_reduced_cfg2_random_aterms(idg_mod, oracle_mod, cuda_device, L, split):
+def test_reduced_mwa_like_random_aterms(idg_mod, oracle_mod, cuda_device, L, split):
     """Random full-Jones A-terms, several intervals, ragged chunk tails."""
     obs = synth.config(2, n_stations=10, n_timesteps=13, n_channels=17)
     A, vis = _random_problem(100 + L, obs, n_int=4)

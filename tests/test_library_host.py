@@ -50,11 +50,11 @@ def _oracle_plan(oracle_mod, obs, flags=0, L=None):
 
 
 CASES = [
-    ("cfg1", lambda: synth.config(1), None),
-    ("cfg1-L64", lambda: synth.config(1), 64),
-    ("cfg2-reduced", lambda: synth.config(2, n_stations=40, n_timesteps=20), None),
-    ("cfg2-reduced-L128", lambda: synth.config(2, n_stations=30, n_timesteps=16), 128),
-    ("cfg4-reduced", lambda: synth.config(4, n_stations=48, n_timesteps=40), 64),
+    ("small", lambda: synth.config(1), None),
+    ("small-L64", lambda: synth.config(1), 64),
+    ("mwa-like-reduced", lambda: synth.config(2, n_stations=40, n_timesteps=20), None),
+    ("mwa-like-reduced-L128", lambda: synth.config(2, n_stations=30, n_timesteps=16), 128),
+    ("uneven-reduced", lambda: synth.config(4, n_stations=48, n_timesteps=40), 64),
 ]
 
 
