@@ -18,6 +18,10 @@
 namespace idg {
 
 constexpr int kFftThreads = 512;
+// Blocks per SM the register budget is sized for: two for L <= 96 (a plane of
+// at most 74 KB of shared memory, so two blocks fit and one block's global
+// loads and atomics overlap the other's transform), one for L = 128 (132 KB).
+constexpr int fft_min_blocks(int L) { return L <= 96 ? 2 : 1; }
 
 // radix sequence per supported size
 template <int L>
@@ -151,7 +155,7 @@ __device__ __forceinline__ void fft2d(float2* buf, const float2* tw) {
 // grid-direction: transform the gridder's subgrid image and add it into the
 // FP64 master grid (mode 0) or leave the transform in scratch (mode 1)
 template <int L, int MODE>
-__global__ void __launch_bounds__(kFftThreads) fft_adder_kernel(const FftArgs a) {
+__global__ void __launch_bounds__(kFftThreads, fft_min_blocks(L)) fft_adder_kernel(const FftArgs a) {
   extern __shared__ float2 sbuf[];
   float2* buf = sbuf;
   float2* tw = sbuf + L * L;
@@ -184,7 +188,7 @@ __global__ void __launch_bounds__(kFftThreads) fft_adder_kernel(const FftArgs a)
 // degrid-direction: copy the subgrid's footprint out of the master grid
 // (FP64 -> FP32, times (-1)^(x+y)) and inverse-transform it into scratch
 template <int L>
-__global__ void __launch_bounds__(kFftThreads) splitter_ifft_kernel(const FftArgs a) {
+__global__ void __launch_bounds__(kFftThreads, fft_min_blocks(L)) splitter_ifft_kernel(const FftArgs a) {
   extern __shared__ float2 sbuf[];
   float2* buf = sbuf;
   float2* tw = sbuf + L * L;
@@ -233,6 +237,13 @@ static int configure_t() {
     e = cudaFuncSetAttribute(fft_adder_kernel<L, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(splitter_ifft_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  // shared memory is what bounds these kernels' occupancy: ask for the largest carveout
+  const void* fns[3] = {reinterpret_cast<const void*>(fft_adder_kernel<L, 0>),
+                        reinterpret_cast<const void*>(fft_adder_kernel<L, 1>),
+                        reinterpret_cast<const void*>(splitter_ifft_kernel<L>)};
+  for (const void* fn : fns)
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, int(cudaSharedmemCarveoutMaxShared));
   return int(e);
 }
 
