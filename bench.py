@@ -19,6 +19,10 @@ two copy streams with double buffers, overlapping the kernels of the
 neighbouring steps, and within a step the model grid's copy overlaps the
 gridding and the output grid's copy the degridding.
 
+Further legs on the same device: Stokes-I mode, w layers (the same array
+with station heights of 50 m rms), the A-term power normalisation (grid and
+invert), the image-domain wrapper and the serving comparison.
+
 --impl reference times the FP64 CPU oracle (the reference arm of this
 build) on a bounded sample of the same workload.
 """
@@ -48,7 +52,7 @@ CSRC = os.path.join(ROOT, "paper_2502_17789_gb300", "csrc")
 NCU_LAUNCH_LIST = ('ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum '
                    '--clock-control none -k regex:"gridder|fft|splitter|stage|aterm" -c 300 --csv '
                    '--log-file launches.csv python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e '
-                   '--serving-requests 0 --image-steps 0 --stokes-steps 0')
+                   '--serving-requests 0 --image-steps 0 --stokes-steps 0 --wlayer-steps 0 --normalize-steps 0')
 KERNEL_SOURCES = {"gridder": ["gridder.cu", "kernels_common.cuh", "idg_internal.h"],
                   "degridder": ["degridder.cu", "kernels_common.cuh", "idg_internal.h"]}
 
@@ -81,6 +85,12 @@ def parse_args():
                     help="timed invert + predict calls of the image-domain wrapper; 0 = skip")
     ap.add_argument("--stokes-steps", type=int, default=5,
                     help="timed grid + degrid steps of the same workload in Stokes-I mode (one grid plane); 0 = skip")
+    ap.add_argument("--wlayer-steps", type=int, default=3,
+                    help="timed grid + degrid steps with w layers (IDG_W_LAYERS) on the same array with station "
+                         "heights of 50 m rms; 0 = skip")
+    ap.add_argument("--normalize-steps", type=int, default=3,
+                    help="timed grid and invert calls with the A-term power normalisation "
+                         "(IDG_NORMALIZE_ATERM) on the same workload; 0 = skip")
     ap.add_argument("--serving-requests", type=int, default=24,
                     help="requests of the serving comparison (batched vs plain at 2x plain capacity); 0 = skip")
     ap.add_argument("--aterms", choices=["beam", "full"], default="beam",
@@ -297,7 +307,7 @@ def run_native(args):
     import torch.distributed as dist
 
     from paper_2502_17789_gb300 import build as libbuild
-    from paper_2502_17789_gb300 import idg, parallel
+    from paper_2502_17789_gb300 import idg, parallel, synth
 
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
@@ -433,6 +443,75 @@ def run_native(args):
                     "kernels": {k: {"ms_per_step": v[0] / args.stokes_steps} for k, v in prof_i.items()}}
         del Gi_model, Gi_out
 
+    def timed(fn, n):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / n
+
+    # w layers (IDG_W_LAYERS, Section 2.4 with w-stacking): the same 128-station disk with station
+    # heights of 50 m rms, so |w| spans several layers of 2 w_max; the visibilities and A-terms of the
+    # main workload have the same shapes and are reused (their values do not change the work)
+    w_layers = None
+    if args.wlayer_steps > 0 and args.workload == 2 and args.stations is None and args.timesteps is None:
+        rng_w = np.random.default_rng(1)
+        enu = synth.stations_uniform_disk(rng_w, obs.n_stations, 3000.0)
+        enu[:, 2] = rng_w.normal(0.0, 50.0, enu.shape[0])
+        obs_w = synth.make_observation(enu, obs.n_timesteps, 2.0, obs.freqs, 4, obs.grid_size, obs.subgrid_size,
+                                       obs.kernel_padding, obs.image_size, name="mwa-like-128-stations-50m-heights")
+        plan_w = idg.Plan(obs_w, flags=idg.IDG_W_LAYERS, stream=stream.cuda_stream)
+        st_w = plan_w.stats()
+        Gw_model = torch.zeros(plan_w.grid_shape(), dtype=torch.complex128, device=dev)
+        plan_w.grid(vis_d, A_d, Gw_model)
+        Gw_out = torch.empty_like(Gw_model)
+
+        def step_w():
+            Gw_out.zero_()
+            plan_w.grid(vis_d, A_d, Gw_out)
+            plan_w.degrid(Gw_model, A_d, vis_pred)
+
+        plan_w.profile(True)
+        plan_w.profile_read()
+        w_ms = timed(step_w, args.wlayer_steps)
+        prof_w = plan_w.profile_read()
+        w_layers = {"value": 2.0 * obs_w.n_vis / (w_ms * 1e-3), "unit": UNIT, "ms_per_step": w_ms,
+                    "steps": args.wlayer_steps, "n_w_layers": int(st_w.n_w_layers),
+                    "w_layer_step_wavelengths": float(st_w.w_layer_step), "subgrids": int(st_w.n_subgrids),
+                    "grid": f"complex128 [{int(st_w.n_w_layers)}][4][{N}][{N}]",
+                    "array": "the 128-station 3 km disk with station heights of 50 m rms",
+                    "kernels": {k: {"ms_per_step": v[0] / (args.wlayer_steps + 1)} for k, v in prof_w.items()}}
+        plan_w.close()
+        del Gw_model, Gw_out
+
+    # A-term power normalisation (IDG_NORMALIZE_ATERM, Section 3.3): gridding with the per-pixel
+    # 1/||A_p^H A_q||_F and the weight map, and the normalised invert (grid, transform, taper and
+    # weight correction), against the plain gridder and invert of the same workload above
+    normalized = None
+    if args.normalize_steps > 0:
+        plan_n = idg.Plan(obs, flags=idg.IDG_NORMALIZE_ATERM, stream=stream.cuda_stream)
+        Gn = torch.empty_like(G_out)
+
+        def grid_n():
+            Gn.zero_()
+            plan_n.grid(vis_d, A_d, Gn)
+
+        plan_n.profile(True)
+        plan_n.profile_read()
+        n_grid_ms = timed(grid_n, args.normalize_steps)
+        prof_n = plan_n.profile_read()
+        img_n = torch.empty_like(G_out)
+        n_inv_ms = timed(lambda: plan_n.invert(vis_d, A_d, Gn, img_n), args.normalize_steps)
+        normalized = {"grid_ms": n_grid_ms, "gridder_ms": prof_n["gridder"][0] / (args.normalize_steps + 1),
+                      "plain_gridder_ms": kernels["gridder"]["ms_per_step"], "invert_ms": n_inv_ms,
+                      "plain_invert_ms": image_domain["invert_ms"] if image_domain else None,
+                      "steps": args.normalize_steps}
+        plan_n.close()
+        del Gn, img_n
+
     # end to end through the C ABI with host buffers: every step copies its inputs (visibilities and model
     # grid) from pinned host memory and reads its results (grid and predicted visibilities) back.  The
     # copies run on two copy streams with double-buffered device buffers, so step k+1's inputs and step
@@ -545,7 +624,8 @@ def run_native(args):
                    "subgrids": st.n_subgrids, "segments": st.n_segments, "batches": st.n_batches,
                    "vis_pixels_per_direction": st.vis_pixels},
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches,
-        "kernels": kernels, "image_domain": image_domain, "stokes_i": stokes_i, "serving": serving,
+        "kernels": kernels, "image_domain": image_domain, "stokes_i": stokes_i, "w_layers": w_layers,
+        "normalized": normalized, "serving": serving,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

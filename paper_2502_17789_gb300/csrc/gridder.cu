@@ -391,28 +391,29 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
           X.m[p].re = (px & 1) ? RE[p][q].y : RE[p][q].x;
           X.m[p].im = (px & 1) ? IM[p][q].y : IM[p][q].x;
         }
+        // f2 = ||A_p^H A_q||_F^2 for the A-term power normalisation (Section 3.3),
+        // from the same interpolated A-terms
         Jones E;
+        float f2 = 0.f;
         if (diag) {
-          E = jdiag_ah_x_b(interp_diag_ldg(Ap, nodes, wx, wy), X, interp_diag_ldg(Aq, nodes, wx, wy));
+          const JonesDiag P = interp_diag_ldg(Ap, nodes, wx, wy), Q = interp_diag_ldg(Aq, nodes, wx, wy);
+          E = jdiag_ah_x_b(P, X, Q);
+          if constexpr (NORM)
+            f2 = (P.d0.re * P.d0.re + P.d0.im * P.d0.im) * (Q.d0.re * Q.d0.re + Q.d0.im * Q.d0.im) +
+                 (P.d1.re * P.d1.re + P.d1.im * P.d1.im) * (Q.d1.re * Q.d1.re + Q.d1.im * Q.d1.im);
         } else {
           const Jones Apj = interp_jones_ldg(Ap, nodes, wx, wy);
           const Jones Aqj = interp_jones_ldg(Aq, nodes, wx, wy);
           E = jmul_ah(Apj, jmul(X, Aqj));
-        }
-        float wgt = a.taper[i] * tj * (((i + j) & 1) ? -1.f : 1.f);
-        if constexpr (NORM) {
-          // A-term power normalisation (Section 3.3): divide by f = ||A_p^H A_q||_F
-          float f2;
-          if (diag) {
-            const JonesDiag P = interp_diag_ldg(Ap, nodes, wx, wy), Q = interp_diag_ldg(Aq, nodes, wx, wy);
-            f2 = (P.d0.re * P.d0.re + P.d0.im * P.d0.im) * (Q.d0.re * Q.d0.re + Q.d0.im * Q.d0.im) +
-                 (P.d1.re * P.d1.re + P.d1.im * P.d1.im) * (Q.d1.re * Q.d1.re + Q.d1.im * Q.d1.im);
-          } else {
-            const Jones M = jmul_ah(interp_jones_ldg(Ap, nodes, wx, wy), interp_jones_ldg(Aq, nodes, wx, wy));
-            f2 = 0.f;
+          if constexpr (NORM) {
+            const Jones M = jmul_ah(Apj, Aqj);
 #pragma unroll
             for (int e = 0; e < 4; ++e) f2 += M.m[e].re * M.m[e].re + M.m[e].im * M.m[e].im;
           }
+        }
+        float wgt = a.taper[i] * tj * (((i + j) & 1) ? -1.f : 1.f);
+        if constexpr (NORM) {
+          // divide by f = ||A_p^H A_q||_F
           const float inv_f = f2 > 0.f ? rsqrtf(f2) : 0.f;
           wgt *= inv_f;
           s_w[px * C::NT + tid] += float(seg.k_end - seg.k_begin) * inv_f;
