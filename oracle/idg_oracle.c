@@ -40,8 +40,8 @@
  *     [-FOV/2, FOV/2]^2 and interpolated bilinearly to the subgrid pixels.
  *
  * The partitioner follows Section 3.1 (subtables of the time x channel table
- * of one baseline, checked by their corners); the exact reading of
- * "comfortably" and of the time extension is documented at oracle_plan().
+ * of one baseline, checked by their corners); the exact reading of the
+ * fit-with-margin rule and of the time extension is documented at oracle_plan().
  */
 #include <complex.h>
 #include <math.h>
@@ -244,7 +244,7 @@ static int or_members_fit(const or_ctx* cx, int b, int ts, int te, int c0, int c
  * Reading of Section 3.1 (the paper gives the idea, not the constants):
  *   S  = L - P - 4           admissible pixel span of one subgrid (the -4
  *                            absorbs the flooring of the subgrid centre)
- *   G  = max(2, floor(S/4))  room left to grow in time ("comfortably")
+ *   G  = max(2, floor(S/4))  room left to grow in time (the fit margin)
  *   Sc = S - G               span allowed when splitting channels
  * For each baseline and each time block (the whole baseline, or each A-term
  * interval when OR_FLAG_SPLIT_INTERVALS is set) a LIFO stack of pending

@@ -11,7 +11,7 @@
 //   span S = L - P - 4, growth margin G = max(2, S/4), channel span Sc = S - G
 //   1. pending subtables (t_start, c_lo, c_hi) start as (block start, 0, n_ch)
 //   2. at t_start, cut [c_lo, c_hi) into maximal runs whose end channels lie
-//      within Sc pixels in u and in v ("comfortably")
+//      within Sc pixels in u and in v (fit with a margin left for time growth)
 //   3. extend each run in time while its four corner visibilities stay within
 //      S pixels, then shrink while any member falls outside S
 //   4. emit it; its later timesteps become a new pending subtable
