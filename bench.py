@@ -385,6 +385,15 @@ def run_native(args):
     if clocks.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = round(achieved / (peak_tflops * clocks["sm_mhz"] / sm_max), 4)
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
+    # the paper's kernel rates (Section 5.3: gridder 480 and degridder 400 M visibilities/s on an A100 at
+    # 32 x 32 subgrids), beside this run's; a visibility costs L^2 pixel updates, so the per
+    # visibility x pixel rates are the ones that compare across subgrid sizes
+    paper_context = {"hardware": "NVIDIA A100 SXM 40 GB", "subgrid_size": 32,
+                     "gridder_vis_per_s": 480e6, "degridder_vis_per_s": 400e6,
+                     "gridder_vispx_per_s": 480e6 * 32 * 32, "degridder_vispx_per_s": 400e6 * 32 * 32,
+                     "this_gridder_vispx_per_s": vispx / (prof["gridder"][0] * 1e-3),
+                     "this_degridder_vispx_per_s": vispx / (prof["degridder"][0] * 1e-3),
+                     "note": "context, not a target: the paper's dataset and visibility count differ"}
     gpu_launches = int(sum(v[1] for v in prof.values()))
 
     # image-domain wrapper (Eq. 11 / Eq. 12): invert = grid + master-grid transform + taper correction,
@@ -624,7 +633,7 @@ def run_native(args):
                    "subgrids": st.n_subgrids, "segments": st.n_segments, "batches": st.n_batches,
                    "vis_pixels_per_direction": st.vis_pixels},
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches,
-        "kernels": kernels, "image_domain": image_domain, "stokes_i": stokes_i, "w_layers": w_layers,
+        "kernels": kernels, "image_domain": image_domain, "paper_context": paper_context, "stokes_i": stokes_i, "w_layers": w_layers,
         "normalized": normalized, "serving": serving,
     }
     if rank == 0:
