@@ -167,7 +167,7 @@ struct GridCfg {
   static constexpr int QN = PX / 2;      // pixel pairs per thread
   static constexpr int TPR = L / PX;     // threads per row
   static constexpr int NT = ROWS * TPR;  // threads per block
-  static constexpr int VC = 64;          // records per chunk
+  static constexpr int VC = 48;          // records per chunk
   static constexpr int MINB = NT <= 128 ? 3 : (NT <= 192 ? 2 : 1);
   static_assert(L % 8 == 0 && L % ROWS == 0 && (PX == 4 || PX == 8), "gridder shape");
 };
