@@ -3,7 +3,7 @@
 This package wraps ``idg_oracle.c`` (plain double-precision C, OpenMP over
 subgrids) with ctypes.  It is the independent reference that the GPU library
 is checked against.  Only the test suite, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` may import it; the library never does, and it
+CPU-baseline leg and reference arm of ``bench.py`` may import it; the library never does, and it
 imports nothing from the library.
 
 Every function follows a passage of the paper (arXiv 2502.17789):
