@@ -4,9 +4,8 @@
  * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
  * reference that the GPU library is checked against.  Only the test suite,
  * the smoke check and the CPU-baseline leg and reference arm of the
- * benchmark load it.  It
- * shares no code, header, table or helper with the CUDA library, and the
- * library never calls it.
+ * benchmark load it.  It shares no code, header, table or helper with the
+ * CUDA library, and the library never calls it.
  *
  * Everything here is double precision (the paper fixes no precision for the
  * reference; Section 4.1 compares against an FP64 direct transform).
