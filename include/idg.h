@@ -128,6 +128,10 @@ typedef struct {
  * IDG_ERR_INVALID_ARG, IDG_ERR_UNSUPPORTED, IDG_ERR_OOM or IDG_ERR_CUDA.
  * Device memory comes from the stream-ordered allocator (cudaMallocAsync on
  * cuda_stream).  Synchronises the stream (uploads the plan tables).
+ * Subgrids run in batches whose subgrid images fit a scratch buffer of
+ * 1 GiB, or of the byte count in the environment variable
+ * IDG_SCRATCH_BYTES read at plan creation (the plan's statistics give the
+ * batch count and its device bytes).
  */
 idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stations, int32_t n_baselines,
                            int32_t n_timesteps, int32_t n_channels, const int32_t* baselines,
