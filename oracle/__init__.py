@@ -67,10 +67,10 @@ def _load():
         P = ctypes.c_void_p
         i32, f64 = ctypes.c_int, ctypes.c_double
         lib.oracle_plan.argtypes = [i32, i32, i32, f64, i32, i32, i32, i32, P, P, P, i32,
-                                    P, i32, P, P, i32, P, P, P]
+                                    P, i32, P, P, i32, P, P, P, P]
         lib.oracle_plan.restype = i32
         common = [i32, i32, i32, f64, i32, f64, P, i32, i32, i32, i32, i32, P, P, P, i32, P, i32, P, i32,
-                  P, f64, i32, i32]
+                  P, P, f64, i32, i32]
         lib.oracle_grid.argtypes = common + [P, P, P, P, P, i32, P]
         lib.oracle_grid.restype = i32
         lib.oracle_degrid.argtypes = common + [P, P, P]
@@ -115,8 +115,13 @@ class Geometry:
 class Plan:
     subgrids: np.ndarray   # int32 [n_sg, 8]: b, t0, t1, c0, c1, x0, y0, dropped
     segments: np.ndarray   # int32 [n_seg, 4]: subgrid, interval, t_begin, t_end
-    layers: np.ndarray | None = None   # int32 [n_sg]: w layer k (w0 = k w_step); None = all 0
-    w_step: float = 0.0                # layer spacing 2 w_max, wavelengths
+    layers: np.ndarray | None = None   # int32 [n_sg]: w layer k (w0 = (k + 1/2) w_step); None: no layers, w0 = 0
+    w_step: float = 0.0                # layer width 2 w_max, wavelengths
+    conj: np.ndarray | None = None     # int32 [n_sg]: 1 = the subgrid holds mirrored rows (w < 0; V^H at -uvw)
+
+    def w0(self, k: int) -> float:
+        """w0 of layer k: (2k + 1) w_max = (k + 1/2) w_step (Section 2.4); 0 without layers."""
+        return (k + 0.5) * self.w_step if self.layers is not None else 0.0
 
     @property
     def k_range(self) -> tuple[int, int]:
@@ -144,20 +149,23 @@ def plan(geom: Geometry, uvw: np.ndarray, freqs: np.ndarray, aterm_offsets: np.n
         sg = np.zeros((cap, 8), np.int32)
         seg = np.zeros((cap, 4), np.int32)
         lay = np.zeros(cap, np.int32)
+        cj = np.zeros(cap, np.int32)
         w_step = ctypes.c_double(0.0)
         nsg = ctypes.c_int(0)
         nseg = ctypes.c_int(0)
         st = lib.oracle_plan(geom.grid_size, geom.subgrid_size, geom.kernel_padding, geom.image_size,
                              geom.flags, n_bl, n_t, n_ch, _ptr(uvw), _ptr(freqs), _ptr(offs), n_int,
                              _ptr(sg), cap, ctypes.byref(nsg), _ptr(seg), cap, ctypes.byref(nseg),
-                             _ptr(lay), ctypes.byref(w_step))
+                             _ptr(lay), _ptr(cj), ctypes.byref(w_step))
         if st == 9:
             cap *= 2
             continue
         if st != 0:
             raise OracleError(st, "plan")
-        layers = lay[: nsg.value].copy() if geom.flags & FLAG_W_LAYERS else None
-        return Plan(sg[: nsg.value].copy(), seg[: nseg.value].copy(), layers, float(w_step.value))
+        layered = bool(geom.flags & FLAG_W_LAYERS)
+        layers = lay[: nsg.value].copy() if layered else None
+        conj = cj[: nsg.value].copy() if layered else None
+        return Plan(sg[: nsg.value].copy(), seg[: nseg.value].copy(), layers, float(w_step.value), conj)
 
 
 def _common(geom, baselines, uvw, freqs, aterm_offsets, pl, n_st):
@@ -169,12 +177,13 @@ def _common(geom, baselines, uvw, freqs, aterm_offsets, pl, n_st):
     seg = np.ascontiguousarray(pl.segments, dtype=np.int32)
     n_bl, n_t, _ = uvw.shape
     lay = None if pl.layers is None else np.ascontiguousarray(pl.layers, dtype=np.int32)
+    cj = None if pl.conj is None else np.ascontiguousarray(pl.conj, dtype=np.int32)
     k_min, _ = pl.k_range
     args = [geom.grid_size, geom.subgrid_size, geom.kernel_padding, geom.image_size, geom.taper_kind,
             geom.beta, _ptr(tu), geom.aterm_nodes, n_st, n_bl, n_t, freqs.shape[0], _ptr(bl), _ptr(uvw),
             _ptr(freqs), len(aterm_offsets) - 1, _ptr(sg), sg.shape[0], _ptr(seg), seg.shape[0],
-            _ptr(lay), pl.w_step, k_min, n_pol(geom)]
-    keep = (uvw, freqs, bl, tu, sg, seg, lay)
+            _ptr(lay), _ptr(cj), pl.w_step, k_min, n_pol(geom)]
+    keep = (uvw, freqs, bl, tu, sg, seg, lay, cj)
     return args, keep
 
 
@@ -319,7 +328,10 @@ def invert(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: 
     I = sum_layers e^{+2 pi i w0 n'} sum_{X,Y} G_w0(X,Y) e^{+2 pi i (u_X l_p + v_Y m_q)}
         / (L^2 T(l_p) T(m_q)),
     G_w0 the visibilities gridded onto layer w0 (Eq. 11; one layer w0 = 0
-    without w layers).  The L^2 T T factor is what the gridder puts on every
+    without w layers).  With w layers the rows of negative w are gridded as
+    their mirrors (V^H at -uvw, Section 2.4 footnote), so each contributes
+    the conjugate transpose of its own term: the Hermitian part of the image
+    is that of the visibilities as given.  The L^2 T T factor is what the gridder puts on every
     image point (taper once per direction, unnormalised L x L transforms);
     dividing it out is Eq. 11's 1/T correction.
     normalize (Section 3.3): the gridding divides every segment by
@@ -339,7 +351,7 @@ def invert(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl: 
     n1 = _nprime_image(geom)
     img = np.zeros((n_pol(geom), N, N), np.complex128)
     for li, Gl in enumerate(layers):
-        w0 = (k_min + li) * pl.w_step if pl.layers is not None else 0.0
+        w0 = pl.w0(k_min + li)
         part = np.fft.ifft2(Gl * S[None], axes=(-2, -1)) * float(N) * float(N) * S[None]
         img += part * np.exp(2j * np.pi * w0 * n1)[None]
     img = img / (float(L) * float(L) * image_taper(geom)[None])
@@ -362,7 +374,7 @@ def predict(geom: Geometry, n_st: int, baselines, uvw, freqs, aterm_offsets, pl:
     n1 = _nprime_image(geom)
     G = np.zeros(grid_shape(geom, pl), np.complex128)
     for li in range(n_layers):
-        w0 = (k_min + li) * pl.w_step if pl.layers is not None else 0.0
+        w0 = pl.w0(k_min + li)
         Gl = np.fft.fft2(src * np.exp(-2j * np.pi * w0 * n1)[None] * S[None], axes=(-2, -1)) * S[None]
         if pl.layers is None:
             G = Gl

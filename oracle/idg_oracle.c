@@ -23,9 +23,15 @@
  *   - Gridder (Eq. 10, step 2a of Section 2.5):
  *       X(i,j) = T_i T_j sum_g A_p,g^H [ sum_{k in g} V_k e^{+2 pi i phi_k} ] A_q,g
  *       phi_k = (u_k-u0) l_i + (v_k-v0) m_j + (w_k-w0) n'_{ij},
- *     w0 = 0, or with w layers the subgrid's layer k w_step (Section 2.4)
- *     where g runs over the A-term intervals the subgrid covers (Section 3.3:
- *     the A-term is applied after the sum over visibilities that share it).
+ *     w0 = 0, or with w layers the subgrid's layer w0 = (2k+1) w_max
+ *     (Section 2.4), where g runs over the A-term intervals the subgrid covers
+ *     (Section 3.3: the A-term is applied after the sum over visibilities
+ *     that share it).
+ *   - w layers (Section 2.4 and its footnote): a timestep row (b, t) whose w
+ *     is negative is gridded as its mirror, the visibility V^H of baseline
+ *     (q, p) at (-u, -v, -w), since V(u,v,w) = V(-u,-v,-w)^H; so every
+ *     gridded w >= 0 and the layers are {w_max, 3 w_max, 5 w_max, ...}.  The
+ *     degridder predicts the mirror and returns its conjugate transpose.
  *   - Subgrid FFT (step 2b), unnormalised, centred:
  *       Vhat(x,y) = sum_{ij} X(i,j) e^{-2 pi i [(x-L/2)(i-L/2)+(y-L/2)(j-L/2)]/L}
  *   - Adder (step 2c, Eq. 6): G[pol][y0+y][x0+x] += Vhat(x,y)
@@ -73,16 +79,25 @@ typedef double complex cplx;
 /* coordinates                                                          */
 /* ------------------------------------------------------------------ */
 
-/* pixel coordinate along u (axis 0) or v (axis 1): ((uvw*f)/c)*FOV + N/2 */
-static double or_pix(const double* uvw, int n_t, int b, int t, int axis,
+/* pixel coordinate along u (axis 0) or v (axis 1): ((sgn*uvw*f)/c)*FOV + N/2,
+ * sgn = -1 for a mirrored row (w layers), else +1 */
+static double or_pix(const double* uvw, int n_t, int b, int t, int axis, double sgn,
                      double f, double fov, int N) {
-  double u_m = uvw[((size_t)b * n_t + t) * 3 + axis];
+  double u_m = sgn * uvw[((size_t)b * n_t + t) * 3 + axis];
   double u_l = (u_m * f) / OR_SPEED_OF_LIGHT;
   return u_l * fov + (double)(N / 2);
 }
 
-static double or_wavelengths(const double* uvw, int n_t, int b, int t, int axis, double f) {
-  return (uvw[((size_t)b * n_t + t) * 3 + axis] * f) / OR_SPEED_OF_LIGHT;
+static double or_wavelengths(const double* uvw, int n_t, int b, int t, int axis, double sgn, double f) {
+  return (sgn * uvw[((size_t)b * n_t + t) * 3 + axis] * f) / OR_SPEED_OF_LIGHT;
+}
+
+/* conjugate transpose of a 2x2 visibility, the mirror's value V^H */
+static void or_vis_herm(const double complex* V, double complex out[4]) {
+  out[0] = conj(V[0]);
+  out[1] = conj(V[2]);
+  out[2] = conj(V[1]);
+  out[3] = conj(V[3]);
 }
 
 /* ------------------------------------------------------------------ */
@@ -172,7 +187,7 @@ static void or_herm(const cplx a[4], cplx h[4]) {
 /* ------------------------------------------------------------------ */
 
 typedef struct {
-  int b, blk, ts, te, c0, c1, layer;
+  int b, blk, ts, te, c0, c1, key;
 } or_sub;
 
 static int or_cmp_sub(const void* pa, const void* pb) {
@@ -191,15 +206,24 @@ typedef struct {
   int n_t, N;
   double fov;
   int layered;     /* w layers in use */
-  double w_step;   /* layer spacing 2 w_max (wavelengths) */
+  double w_step;   /* layer width 2 w_max (wavelengths) */
 } or_ctx;
 
-/* w layer of a visibility: the nearest multiple k of w_step (w0 = k w_step),
- * so |w - w0| <= w_step / 2 = w_max; layer 0 when layers are off */
+/* -1 when row (b, t) is mirrored (w layers and w < 0), else +1 */
+static double or_sign(const or_ctx* cx, int b, int t) {
+  return cx->layered && cx->uvw[((size_t)b * cx->n_t + t) * 3 + 2] < 0.0 ? -1.0 : 1.0;
+}
+
+/* w layer key of a visibility: 2k + m, m = 1 for a mirrored row, and k the
+ * layer of its gridded w' = |w| >= 0: k = floor(w' / (2 w_max)), so that
+ * w0 = (2k+1) w_max and |w' - w0| <= w_max.  Members of one subgrid share
+ * the key (one layer, one side).  0 when layers are off. */
 static int or_layer(const or_ctx* cx, int b, int t, int c) {
   if (!cx->layered) return 0;
-  double w = or_wavelengths(cx->uvw, cx->n_t, b, t, 2, cx->freqs[c]);
-  return (int)floor(w / cx->w_step + 0.5);
+  double sgn = or_sign(cx, b, t);
+  double w = or_wavelengths(cx->uvw, cx->n_t, b, t, 2, sgn, cx->freqs[c]);
+  int k = (int)floor(w / cx->w_step);
+  return 2 * k + (sgn < 0.0 ? 1 : 0);
 }
 
 /* bounding-box extent test: does the set of (t,ch) points fit within `span`
@@ -208,8 +232,9 @@ static int or_box_fits(const or_ctx* cx, int b, const int* ts, const int* cs, in
   double xlo = 0, xhi = 0, ylo = 0, yhi = 0;
   for (int n = 0; n < npts; ++n) {
     double f = cx->freqs[cs[n]];
-    double x = or_pix(cx->uvw, cx->n_t, b, ts[n], 0, f, cx->fov, cx->N);
-    double y = or_pix(cx->uvw, cx->n_t, b, ts[n], 1, f, cx->fov, cx->N);
+    double sgn = or_sign(cx, b, ts[n]);
+    double x = or_pix(cx->uvw, cx->n_t, b, ts[n], 0, sgn, f, cx->fov, cx->N);
+    double y = or_pix(cx->uvw, cx->n_t, b, ts[n], 1, sgn, f, cx->fov, cx->N);
     if (n == 0 || x < xlo) xlo = x;
     if (n == 0 || x > xhi) xhi = x;
     if (n == 0 || y < ylo) ylo = y;
@@ -227,8 +252,9 @@ static int or_members_fit(const or_ctx* cx, int b, int ts, int te, int c0, int c
     for (int c = c0; c < c1; ++c) {
       if (or_layer(cx, b, t, c) != k0) return 0;
       double f = cx->freqs[c];
-      double x = or_pix(cx->uvw, cx->n_t, b, t, 0, f, cx->fov, cx->N);
-      double y = or_pix(cx->uvw, cx->n_t, b, t, 1, f, cx->fov, cx->N);
+      double sgn = or_sign(cx, b, t);
+      double x = or_pix(cx->uvw, cx->n_t, b, t, 0, sgn, f, cx->fov, cx->N);
+      double y = or_pix(cx->uvw, cx->n_t, b, t, 1, sgn, f, cx->fov, cx->N);
       if (first || x < xlo) xlo = x;
       if (first || x > xhi) xhi = x;
       if (first || y < ylo) ylo = y;
@@ -261,20 +287,25 @@ static int or_members_fit(const or_ctx* cx, int b, int ts, int te, int c0, int c
  * subgrid, |w - w0| * max|grad n'| * FOV pixels, must not exceed P/2 - 1,
  * i.e. |w - w0| <= w_max = (P/2 - 1) / (max|grad n'| FOV).  Without
  * OR_FLAG_W_LAYERS every subgrid has w0 = 0 and a larger |w| is an error.
- * With it (Section 2.4: the hybrid with w-stacking) w0 snaps to the nearest
- * multiple of 2 w_max and every member of a subgrid shares that layer: the
- * channel runs, the time growth (corners) and the final shrink (all members)
- * also require the layer of the run's first visibility.
+ * With it (Section 2.4: the hybrid with w-stacking) rows with w < 0 are
+ * mirrored (footnote of Section 2.4; see the conventions above), the gridded
+ * w' >= 0 falls in layer k = floor(w' / (2 w_max)) with w0 = (2k+1) w_max,
+ * one of {w_max, 3 w_max, 5 w_max, ...}, and every member of a subgrid
+ * shares the layer and the side (mirrored or not) of the run's first
+ * visibility: the channel runs, the time growth (corners) and the final
+ * shrink (all members) also require it.  Pixel coordinates of mirrored rows
+ * are those of (-u, -v).
  *
  * out_sg: cap_sg rows of 8 ints {b, t0, t1, c0, c1, x0, y0, dropped}
  * out_seg: cap_seg rows of 4 ints {subgrid, interval, t_begin, t_end}
- * out_layer (optional): per subgrid its layer k, w0 = k w_step
- * w_step_out (optional): the layer spacing 2 w_max in wavelengths
+ * out_layer (optional): per subgrid its layer k, w0 = (k + 1/2) w_step
+ * out_conj (optional): per subgrid 1 if it holds mirrored rows, else 0
+ * w_step_out (optional): the layer width 2 w_max in wavelengths
  */
 int oracle_plan(int N, int L, int P, double fov, int flags, int n_bl, int n_t, int n_ch,
                 const double* uvw, const double* freqs, const int* aterm_offsets, int n_int,
                 int* out_sg, int cap_sg, int* n_sg_out, int* out_seg, int cap_seg, int* n_seg_out,
-                int* out_layer, double* w_step_out) {
+                int* out_layer, int* out_conj, double* w_step_out) {
   if (N <= 0 || L <= 0 || P < 0 || L > N || (N % 2) || (L % 2) || (P % 2) || n_bl < 0 || n_t < 0 ||
       n_ch < 0 || n_int < 1 || !(fov > 0.0))
     return OR_ERR_INVALID;
@@ -301,7 +332,7 @@ int oracle_plan(int N, int L, int P, double fov, int flags, int n_bl, int n_t, i
   for (int b = 0; b < n_bl && !layered; ++b)
     for (int t = 0; t < n_t; ++t)
       for (int c = 0; c < n_ch; ++c) {
-        double w = or_wavelengths(uvw, n_t, b, t, 2, freqs[c]);
+        double w = or_wavelengths(uvw, n_t, b, t, 2, 1.0, freqs[c]);
         if (fabs(w) * gmax * fov > wlim) return OR_ERR_W_TOO_LARGE;
       }
 
@@ -365,14 +396,15 @@ int oracle_plan(int N, int L, int P, double fov, int flags, int n_bl, int n_t, i
     qsort(list, n_list, sizeof(or_sub), or_cmp_sub);
     for (int n = 0; n < n_list; ++n) {
       or_sub s = list[n];
-      /* exact bounding box of the members */
+      /* exact bounding box of the members (mirrored coordinates for mirrored rows) */
       double xlo = 0, xhi = 0, ylo = 0, yhi = 0;
       int first = 1;
       for (int t = s.ts; t < s.te; ++t)
         for (int c = s.c0; c < s.c1; ++c) {
           double f = freqs[c];
-          double x = or_pix(uvw, n_t, b, t, 0, f, fov, N);
-          double y = or_pix(uvw, n_t, b, t, 1, f, fov, N);
+          double sgn = or_sign(&cx, b, t);
+          double x = or_pix(uvw, n_t, b, t, 0, sgn, f, fov, N);
+          double y = or_pix(uvw, n_t, b, t, 1, sgn, f, fov, N);
           if (first || x < xlo) xlo = x;
           if (first || x > xhi) xhi = x;
           if (first || y < ylo) ylo = y;
@@ -390,7 +422,8 @@ int oracle_plan(int N, int L, int P, double fov, int flags, int n_bl, int n_t, i
       int* row = out_sg + (size_t)n_sg * 8;
       row[0] = b; row[1] = s.ts; row[2] = s.te; row[3] = s.c0; row[4] = s.c1;
       row[5] = x0; row[6] = y0; row[7] = dropped;
-      if (out_layer) out_layer[n_sg] = s.layer;
+      if (out_layer) out_layer[n_sg] = s.key >> 1;
+      if (out_conj) out_conj[n_sg] = s.key & 1;
       for (int a = 0; a < n_int; ++a) {
         int lo = aterm_offsets[a] > s.ts ? aterm_offsets[a] : s.ts;
         int hi = aterm_offsets[a + 1] < s.te ? aterm_offsets[a + 1] : s.te;
@@ -479,8 +512,9 @@ typedef struct {
   int n_sg;
   const int* seg;
   int n_seg;
-  const int* layer;  /* per subgrid w layer k (NULL: all 0) */
-  double w_step;     /* w0 = k w_step */
+  const int* layer;  /* per subgrid w layer k (NULL: no layers, w0 = 0) */
+  const int* conj;   /* per subgrid 1 = mirrored rows (NULL: none) */
+  double w_step;     /* w0 = (k + 1/2) w_step */
   int k_min;         /* the master grid holds layers k_min .. k_min + n_layers - 1 */
 } or_job;
 
@@ -502,10 +536,13 @@ static void or_subgrid_image(const or_job* jb, int s, const cplx* vis, const cpl
   const int L = jb->L, N = jb->N, nodes = jb->nodes;
   const int* row = jb->sg + (size_t)s * 8;
   int b = row[0], c0 = row[3], c1 = row[4], x0 = row[5], y0 = row[6];
-  int p = jb->baselines[2 * b], q = jb->baselines[2 * b + 1];
+  /* a mirrored subgrid grids V^H of baseline (q, p) at (-u, -v, -w) */
+  int mirrored = jb->conj ? jb->conj[s] : 0;
+  double sgn = mirrored ? -1.0 : 1.0;
+  int p = jb->baselines[2 * b + (mirrored ? 1 : 0)], q = jb->baselines[2 * b + (mirrored ? 0 : 1)];
   double u0 = (double)(x0 + L / 2 - N / 2) / jb->fov;
   double v0 = (double)(y0 + L / 2 - N / 2) / jb->fov;
-  double w0 = jb->layer ? (double)jb->layer[s] * jb->w_step : 0.0;
+  double w0 = jb->layer ? ((double)jb->layer[s] + 0.5) * jb->w_step : 0.0;
   memset(X, 0, sizeof(cplx) * 4 * (size_t)L * L);
   for (int g = seg_first[s]; g < seg_first[s] + seg_count[s]; ++g) {
     const int* sr = jb->seg + (size_t)g * 4;
@@ -521,13 +558,16 @@ static void or_subgrid_image(const or_job* jb, int s, const cplx* vis, const cpl
         for (int t = tb; t < te; ++t)
           for (int c = c0; c < c1; ++c) {
             double f = jb->freqs[c];
-            double u = or_wavelengths(jb->uvw, jb->n_t, b, t, 0, f);
-            double v = or_wavelengths(jb->uvw, jb->n_t, b, t, 1, f);
-            double w = or_wavelengths(jb->uvw, jb->n_t, b, t, 2, f);
+            double u = or_wavelengths(jb->uvw, jb->n_t, b, t, 0, sgn, f);
+            double v = or_wavelengths(jb->uvw, jb->n_t, b, t, 1, sgn, f);
+            double w = or_wavelengths(jb->uvw, jb->n_t, b, t, 2, sgn, f);
             double phi = (u - u0) * l + (v - v0) * m + (w - w0) * n1;
             cplx e = cexp(I * 2.0 * OR_PI * phi);
             const cplx* V = vis + (((size_t)b * jb->n_t + t) * jb->n_ch + c) * 4;
-            for (int e4 = 0; e4 < 4; ++e4) acc[e4] += V[e4] * e;
+            cplx Vm[4];
+            if (mirrored) or_vis_herm(V, Vm);
+            else memcpy(Vm, V, sizeof Vm);
+            for (int e4 = 0; e4 < 4; ++e4) acc[e4] += Vm[e4] * e;
           }
         cplx Api[4], Aqi[4], ApH[4], M[4], E[4];
         or_interp(Ap, nodes, L, i, j, Api);
@@ -568,8 +608,9 @@ static void or_seg_index(const or_job* jb, int* seg_first, int* seg_count) {
  * vis: complex [n_bl][n_t][n_ch][4]; aterms: complex [n_int][n_st][nodes][nodes][4].
  * subgrid_images (optional): complex [n_sg][4][L][L], the subgrid images X
  * before the FFT; subgrid_uv (optional): the same after the FFT.
- * With w layers (layer != NULL) subgrid s uses w0 = layer[s] w_step in its
- * phase and is added into grid[layer[s] - k_min][4][N][N].
+ * With w layers (layer != NULL) subgrid s uses w0 = (layer[s] + 1/2) w_step
+ * in its phase and is added into grid[layer[s] - k_min][4][N][N]; conj
+ * (optional) marks the mirrored subgrids.
  * npol: 4 (correlation planes) or 1 (Stokes I): with 1 the grid holds
  * one plane per layer, I = (XX + YY) / 2 of each corrected subgrid image,
  * and the subgrid image outputs hold that one plane.
@@ -580,11 +621,11 @@ static void or_seg_index(const or_job* jb, int* seg_first, int* seg_count) {
 int oracle_grid(int N, int L, int P, double fov, int taper_kind, double beta, const double* taper_user,
                 int nodes, int n_st, int n_bl, int n_t, int n_ch, const int* baselines, const double* uvw,
                 const double* freqs, int n_int, const int* sg, int n_sg, const int* seg, int n_seg,
-                const int* layer, double w_step, int k_min, int npol,
+                const int* layer, const int* conj, double w_step, int k_min, int npol,
                 const double* vis_ri, const double* aterms_ri, double* grid_ri, double* subgrid_images,
                 double* subgrid_uv, int normalize, double* weights) {
   or_job jb = {N, L, P, fov, taper_kind, beta, taper_user, nodes, n_st, n_bl, n_t, n_ch, baselines,
-               uvw, freqs, n_int, sg, n_sg, seg, n_seg, layer, w_step, k_min};
+               uvw, freqs, n_int, sg, n_sg, seg, n_seg, layer, conj, w_step, k_min};
   double* T = (double*)malloc(sizeof(double) * L);
   int st = oracle_taper(L, taper_kind, beta, taper_user, T);
   if (st) { free(T); return st; }
@@ -654,16 +695,18 @@ int oracle_grid(int N, int L, int P, double fov, int taper_kind, double beta, co
  * oracle_degrid: predict visibilities from grid[4][N][N] (Eq. 13 read as the
  * adjoint of the gridder).  vis_out is overwritten; visibilities of dropped
  * subgrids are zero.  With w layers, subgrid s reads grid[layer[s] - k_min]
- * and uses w0 = layer[s] w_step.  npol = 1: the grid holds Stokes I and the
+ * and uses w0 = (layer[s] + 1/2) w_step; a mirrored subgrid predicts the
+ * mirror (baseline (q, p) at (-u, -v, -w)) and stores its conjugate
+ * transpose.  npol = 1: the grid holds Stokes I and the
  * model is unpolarised, Y = Y_I times the 2x2 identity (XX = YY = I).
  */
 int oracle_degrid(int N, int L, int P, double fov, int taper_kind, double beta, const double* taper_user,
                   int nodes, int n_st, int n_bl, int n_t, int n_ch, const int* baselines, const double* uvw,
                   const double* freqs, int n_int, const int* sg, int n_sg, const int* seg, int n_seg,
-                  const int* layer, double w_step, int k_min, int npol,
+                  const int* layer, const int* conj, double w_step, int k_min, int npol,
                   const double* grid_ri, const double* aterms_ri, double* vis_ri) {
   or_job jb = {N, L, P, fov, taper_kind, beta, taper_user, nodes, n_st, n_bl, n_t, n_ch, baselines,
-               uvw, freqs, n_int, sg, n_sg, seg, n_seg, layer, w_step, k_min};
+               uvw, freqs, n_int, sg, n_sg, seg, n_seg, layer, conj, w_step, k_min};
   if (npol != 1 && npol != 4) return OR_ERR_INVALID;
   double* T = (double*)malloc(sizeof(double) * L);
   int st = oracle_taper(L, taper_kind, beta, taper_user, T);
@@ -682,7 +725,9 @@ int oracle_degrid(int N, int L, int P, double fov, int taper_kind, double beta, 
     const int* row = sg + (size_t)s * 8;
     if (row[7]) continue;
     int b = row[0], c0 = row[3], c1 = row[4], x0 = row[5], y0 = row[6];
-    int p = baselines[2 * b], q = baselines[2 * b + 1];
+    int mirrored = conj ? conj[s] : 0;
+    double sgn = mirrored ? -1.0 : 1.0;
+    int p = baselines[2 * b + (mirrored ? 1 : 0)], q = baselines[2 * b + (mirrored ? 0 : 1)];
     cplx* Yh = (cplx*)malloc(sizeof(cplx) * 4 * plane);
     cplx* Y = (cplx*)malloc(sizeof(cplx) * 4 * plane);
     cplx* tmp = (cplx*)malloc(sizeof(cplx) * plane);
@@ -701,7 +746,7 @@ int oracle_degrid(int N, int L, int P, double fov, int taper_kind, double beta, 
       }
     double u0 = (double)(x0 + L / 2 - N / 2) / fov;
     double v0 = (double)(y0 + L / 2 - N / 2) / fov;
-    double w0 = layer ? (double)layer[s] * w_step : 0.0;
+    double w0 = layer ? ((double)layer[s] + 0.5) * w_step : 0.0;
     for (int g = seg_first[s]; g < seg_first[s] + seg_count[s]; ++g) {
       const int* sr = seg + (size_t)g * 4;
       int a = sr[1], tb = sr[2], te = sr[3];
@@ -724,9 +769,9 @@ int oracle_degrid(int N, int L, int P, double fov, int taper_kind, double beta, 
       for (int t = tb; t < te; ++t)
         for (int c = c0; c < c1; ++c) {
           double f = freqs[c];
-          double u = or_wavelengths(uvw, n_t, b, t, 0, f);
-          double v = or_wavelengths(uvw, n_t, b, t, 1, f);
-          double w = or_wavelengths(uvw, n_t, b, t, 2, f);
+          double u = or_wavelengths(uvw, n_t, b, t, 0, sgn, f);
+          double v = or_wavelengths(uvw, n_t, b, t, 1, sgn, f);
+          double w = or_wavelengths(uvw, n_t, b, t, 2, sgn, f);
           cplx acc[4] = {0, 0, 0, 0};
           for (int j = 0; j < L; ++j)
             for (int i = 0; i < L; ++i) {
@@ -738,7 +783,8 @@ int oracle_degrid(int N, int L, int P, double fov, int taper_kind, double beta, 
               for (int e4 = 0; e4 < 4; ++e4) acc[e4] += Zp[e4] * e;
             }
           cplx* V = vis + (((size_t)b * n_t + t) * n_ch + c) * 4;
-          for (int e4 = 0; e4 < 4; ++e4) V[e4] = acc[e4];
+          if (mirrored) or_vis_herm(acc, V);
+          else for (int e4 = 0; e4 < 4; ++e4) V[e4] = acc[e4];
         }
       free(Z);
     }

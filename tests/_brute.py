@@ -144,3 +144,22 @@ def convolutional_grid(obs, pl, vis, aterms, T, w0=0.0):
                     K = np.einsum("Yj,Xi,jirc->rcYX", ey, ex, M * wph[..., None, None])
                     G[:, y0:y0 + L, x0:x0 + L] += K.reshape(4, L, L)
     return G
+
+
+def mirrored_set(obs, vis):
+    """The visibility set as gridded with w layers (Section 2.4 footnote,
+    V(u,v,w) = V(-u,-v,-w)^H): every timestep row with w < 0 is replaced by
+    its mirror, the conjugate transpose of V on baseline (q, p) at -uvw.
+    Returned as an observation with twice the baselines -- the originals
+    keep the rows of w >= 0, the appended reversed baselines hold the
+    mirrored rows -- and its visibilities (zero where a row is absent), so
+    that dft_image and measurement_equation apply unchanged."""
+    import copy
+    neg = obs.uvw[..., 2] < 0.0                                           # [bl, t]
+    o2 = copy.copy(obs)
+    o2.baselines = np.concatenate([obs.baselines, obs.baselines[:, ::-1]]).astype(np.int32)
+    o2.uvw = np.concatenate([obs.uvw, -obs.uvw])
+    v = np.asarray(vis, np.complex128)
+    herm = v.reshape(v.shape[:3] + (2, 2)).conj().swapaxes(-1, -2).reshape(v.shape)
+    v2 = np.concatenate([np.where(neg[..., None, None], 0.0, v), np.where(neg[..., None, None], herm, 0.0)])
+    return o2, v2

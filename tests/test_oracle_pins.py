@@ -123,6 +123,26 @@ def test_plan_handworked_golden(oracle_mod):
     np.testing.assert_array_equal(pl.subgrids, np.array(tc["expected"], np.int32))
 
 
+def _shrink_case_uvw(gd):
+    sc = gd["shrink_case"]
+    xi = np.array(sc["xi"])
+    uvw = np.zeros((1, xi.size, 3))
+    uvw[0, :, 0] = (xi - gd["geometry"]["N"] / 2) * synth.SPEED_OF_LIGHT / sc["f0"]
+    return uvw, np.array([sc["f0"]]), np.array([0, xi.size], np.int32)
+
+
+def test_plan_shrink_golden(oracle_mod):
+    """The final shrink of a time run (Section 3.1 checks only the corners
+    while growing): a track whose corners with the first row all fit but
+    whose rows 2 and 3 are 23 pixels apart; the hand-worked split is [0,3)
+    and [3,6), so a shrink one row short or one row too far fails."""
+    gd = _golden()
+    g = gd["geometry"]
+    uvw, freqs, offs = _shrink_case_uvw(gd)
+    pl = oracle_mod.plan(oracle_mod.Geometry(g["N"], g["L"], g["P"], g["fov"]), uvw, freqs, offs)
+    np.testing.assert_array_equal(pl.subgrids, np.array(gd["shrink_case"]["expected"], np.int32))
+
+
 def _check_plan_invariants(obs, pl, split):
     N, L, P, fov = obs.grid_size, obs.subgrid_size, obs.kernel_padding, obs.image_size
     u, v, _ = _brute.uvw_lambda(obs)
@@ -434,53 +454,100 @@ def _layered_problem(oracle_mod, seed=0, height=400.0, n_t=6, **kw):
     return obs, geom, pl, A, vis
 
 
+def _w_prime(obs):
+    """Per (baseline, timestep): the side (True = mirrored, w < 0) and the
+    gridded coordinates (u', v', w') = sign * (u, v, w) in wavelengths."""
+    u, v, w = _brute.uvw_lambda(obs)
+    neg = obs.uvw[..., 2] < 0.0
+    sgn = np.where(neg, -1.0, 1.0)[..., None]
+    return neg, sgn * u, sgn * v, sgn * w
+
+
 def test_w_layers_plan_invariants(oracle_mod):
+    """Section 2.4: rows with w < 0 are mirrored, every gridded w' >= 0 sits
+    within w_max of its subgrid's layer w0 = (2k+1) w_max, a subgrid holds one
+    layer and one side, and the mirrored members lie inside their subgrid at
+    their mirrored (u', v') pixel coordinates."""
     obs, geom, pl, _, _ = _layered_problem(oracle_mod)
     with pytest.raises(oracle_mod.OracleError) as e:
         oracle_mod.plan(_geom(oracle_mod, obs), obs.uvw, obs.freqs, obs.aterm_offsets)
     assert e.value.code == 4
-    assert pl.k_range[1] >= 3
-    _check_plan_invariants(obs, pl, False)
+    assert pl.k_range[1] >= 2
     # w_max from the fringe limit of the Section 2.4 footnote, independently
     r2 = 0.5 * obs.image_size ** 2
     w_max = (obs.kernel_padding / 2 - 1) / (np.sqrt(r2 / (1 - r2)) * obs.image_size)
     assert pl.w_step == pytest.approx(2 * w_max, rel=1e-14)
-    _, _, w = _brute.uvw_lambda(obs)
-    for s, (b, t0, t1, c0, c1, *_rest) in enumerate(pl.subgrids):
-        dw = w[b, t0:t1, c0:c1] - pl.layers[s] * pl.w_step
-        assert np.abs(dw).max() <= w_max * (1 + 1e-12)
+    neg, u2, v2, w2 = _w_prime(obs)
+    assert neg.any() and (~neg).any(), "the problem needs rows on both sides"
+    N, L, P, fov = obs.grid_size, obs.subgrid_size, obs.kernel_padding, obs.image_size
+    count = np.zeros((obs.n_baselines, obs.n_timesteps, obs.n_channels), int)
+    for s, (b, t0, t1, c0, c1, x0, y0, dropped) in enumerate(pl.subgrids):
+        count[b, t0:t1, c0:c1] += 1
+        assert np.all(neg[b, t0:t1] == bool(pl.conj[s])), "one side per subgrid"
+        w0 = (2 * pl.layers[s] + 1) * w_max
+        assert pl.layers[s] >= 0
+        assert np.abs(w2[b, t0:t1, c0:c1] - w0).max() <= w_max * (1 + 1e-12)
+        xs = u2[b, t0:t1, c0:c1] * fov + N // 2
+        ys = v2[b, t0:t1, c0:c1] * fov + N // 2
+        assert (xs - x0).min() >= P / 2 and (xs - x0).max() <= L - 1 - P / 2
+        assert (ys - y0).min() >= P / 2 and (ys - y0).max() <= L - 1 - P / 2
+    assert np.all(count == 1), "every visibility belongs to exactly one subgrid"
 
 
-def test_w_layers_reduce_to_one_layer_when_coplanar(oracle_mod):
+def test_w_layers_of_a_coplanar_array_are_one_layer_at_w_max(oracle_mod):
+    """A nearly coplanar array has every |w| < 2 w_max: all subgrids fall in
+    the first layer of the paper's set, w0 = w_max, on either side."""
     obs, geom, pl, A, vis = _problem(oracle_mod, seed=2)
     g2 = _geom(oracle_mod, obs, flags=oracle_mod.FLAG_W_LAYERS)
     p2 = oracle_mod.plan(g2, obs.uvw, obs.freqs, obs.aterm_offsets)
-    np.testing.assert_array_equal(p2.subgrids, pl.subgrids)
-    assert np.all(p2.layers == 0)
-    G1 = _grid(oracle_mod, obs, geom, pl, vis, A)
+    assert np.all(p2.layers == 0) and p2.k_range == (0, 1)
+    neg, *_ = _w_prime(obs)
+    assert neg.any() and (~neg).any()
+    assert p2.w0(0) == pytest.approx(0.5 * p2.w_step)
     G2 = oracle_mod.grid(g2, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets, p2, vis, A)
-    assert G2.shape == (1,) + G1.shape and np.array_equal(G2[0], G1)
+    assert G2.shape == (1, 4, obs.grid_size, obs.grid_size)
+
+
+def _herm(img):
+    """Hermitian part (B + B^H)/2 of a [4][...] image of 2x2 matrices."""
+    m = np.moveaxis(np.asarray(img).reshape((2, 2) + np.shape(img)[1:]), (0, 1), (-2, -1))
+    h = 0.5 * (m + np.conj(np.swapaxes(m, -1, -2)))
+    return np.moveaxis(h, (-2, -1), (0, 1)).reshape(np.shape(img))
 
 
 def test_w_stacked_invert_equals_direct_adjoint_on_the_lattice(oracle_mod):
-    """With several w layers the dirty image on the subgrid lattice is still
-    exactly the adjoint of Eq. 1: each subgrid carries (w - w0) and the layer
-    transform multiplies by e^{2 pi i w0 n'} (Eq. 11)."""
+    """With w layers the dirty image on the subgrid lattice is exactly the
+    adjoint of Eq. 1 over the mirrored visibility set (each row of w < 0
+    replaced by V^H of baseline (q, p) at -uvw): every subgrid carries
+    (w' - w0) and each layer transform multiplies by e^{2 pi i w0 n'}
+    (Eq. 11).  Its Hermitian part equals that of the direct adjoint of the
+    visibilities as given, which the mirror cannot change (the footnote's
+    symmetry)."""
     obs, geom, pl, A, vis = _layered_problem(oracle_mod, seed=1)
+    assert pl.conj.any() and not pl.conj.all()
     N, L, fov = obs.grid_size, obs.subgrid_size, obs.image_size
     img = oracle_mod.invert(*_wrapper_args(obs, geom, pl), vis, A)
+    o2, v2 = _brute.mirrored_set(obs, vis)
     r = N // L
-    worst = 0.0
+    worst = worst_h = 0.0
     for (i, j) in [(8, 8), (2, 13), (13, 3), (5, 6), (10, 12)]:
         p, q = N // 2 + r * (i - L // 2), N // 2 + r * (j - L // 2)
         l, m = (p - N // 2) * fov / N, (q - N // 2) * fov / N
-        want = _brute.dft_image(obs, vis, A, l, m).reshape(4)
+        want = _brute.dft_image(o2, v2, A, l, m).reshape(4)
         worst = max(worst, np.abs(img[:, q, p] - want).max() / np.abs(want).max())
+        direct = _brute.dft_image(obs, vis, A, l, m).reshape(4, 1)
+        worst_h = max(worst_h, np.abs(_herm(img[:, q, p].reshape(4, 1)) - _herm(direct)).max() / np.abs(direct).max())
     assert worst < 1e-9
+    assert worst_h < 1e-9
 
 
 def test_w_stacked_predict_of_a_lattice_point_source(oracle_mod):
+    """A point source of Hermitian brightness on the lattice predicts Eq. 1
+    for every visibility, mirrored rows included: the degridder predicts the
+    mirror and returns its conjugate transpose, which for Hermitian B is the
+    visibility itself."""
     obs, geom, pl, A, _ = _layered_problem(oracle_mod, seed=3)
+    assert pl.conj.any() and not pl.conj.all()
     N, L, fov = obs.grid_size, obs.subgrid_size, obs.image_size
     r = N // L
     B = np.array([[1.1, -0.2j], [0.2j, 0.8]])
@@ -494,12 +561,29 @@ def test_w_stacked_predict_of_a_lattice_point_source(oracle_mod):
 
 
 def test_w_stacked_predict_is_the_adjoint_of_invert(oracle_mod):
+    """The mirror conjugates, so with w layers the pair is adjoint in the
+    real inner product Re<x, y> (conjugation is real-linear)."""
     obs, geom, pl, A, vis = _layered_problem(oracle_mod, seed=4)
+    assert pl.conj.any()
     N = obs.grid_size
     rng = np.random.default_rng(5)
     img = rng.standard_normal((4, N, N)) + 1j * rng.standard_normal((4, N, N))
-    lhs = np.vdot(oracle_mod.predict(*_wrapper_args(obs, geom, pl), img, A), vis)
-    rhs = np.vdot(img, oracle_mod.invert(*_wrapper_args(obs, geom, pl), vis, A))
+    lhs = np.vdot(oracle_mod.predict(*_wrapper_args(obs, geom, pl), img, A), vis).real
+    rhs = np.vdot(img, oracle_mod.invert(*_wrapper_args(obs, geom, pl), vis, A)).real
+    assert abs(lhs - rhs) / abs(rhs) < 1e-11
+
+
+def test_w_layered_degrid_is_the_adjoint_of_grid(oracle_mod):
+    """Gridding and degridding with mirrored subgrids on layered grids are
+    adjoint in the real inner product."""
+    obs, geom, pl, A, vis = _layered_problem(oracle_mod, seed=6)
+    assert pl.conj.any()
+    args = (geom, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets, pl)
+    G = oracle_mod.grid(*args, vis, A)
+    rng = np.random.default_rng(7)
+    R = rng.standard_normal(G.shape) + 1j * rng.standard_normal(G.shape)
+    lhs = np.vdot(oracle_mod.degrid(*args, R, A), vis).real
+    rhs = np.vdot(R, G).real
     assert abs(lhs - rhs) / abs(rhs) < 1e-11
 
 
