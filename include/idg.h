@@ -67,8 +67,11 @@ enum {
   IDG_SPLIT_AT_ATERM_INTERVALS = 2, /* never let a subgrid span two A-term intervals (Section 3.3 as written) */
   IDG_HOST_ONLY = 4,                /* plan on the host only: no device memory, grid/degrid refused */
   IDG_PERSISTENT = 8,               /* persistent launches: #SMs x occupancy blocks drain a work queue */
-  IDG_W_LAYERS = 16,                /* w layers (Section 2.4): w0 snaps to multiples of 2 w_max instead of
-                                       rejecting |w| > w_max; grids hold one [4][N][N] plane set per layer */
+  IDG_W_LAYERS = 16,                /* w layers (Section 2.4): rows (baseline, timestep) with w < 0 are taken
+                                       as their mirrors V^H of baseline (q, p) at (-u, -v, -w) (the footnote's
+                                       V(u,v,w) = V(-u,-v,-w)^H), and each subgrid sits on one layer
+                                       w0 in {w_max, 3 w_max, 5 w_max, ...} instead of rejecting
+                                       |w| > w_max; grids hold one [n_pol][N][N] plane set per layer */
   IDG_NORMALIZE_ATERM = 32,         /* A-term power normalisation (Section 3.3): the gridder divides each
                                        segment's corrected image by ||A_p^H A_q||_F per pixel and the plan
                                        accumulates the weights idg_invert corrects the image with */
@@ -106,8 +109,9 @@ typedef struct {
   int32_t subgrid_size;
   int32_t batch_capacity;     /* subgrids per batch */
   int32_t n_w_layers;         /* w layers of the master grid (1 without IDG_W_LAYERS) */
-  int32_t w_layer_min;        /* layer k of grid plane set 0; plane set i has w0 = (w_layer_min + i) w_layer_step */
-  double w_layer_step;        /* 2 w_max in wavelengths, w_max = (P/2 - 1) / (max|grad n'| FOV) */
+  int32_t w_layer_min;        /* layer k of grid plane set 0; plane set i has w0 = (w_layer_min + i + 1/2)
+                                 w_layer_step, i.e. layer k sits at w0 = (2k + 1) w_max */
+  double w_layer_step;        /* layer width 2 w_max in wavelengths, w_max = (P/2 - 1) / (max|grad n'| FOV) */
   int32_t n_pol;              /* planes per layer of grids and images: 4, or 1 with IDG_STOKES_I */
 } idg_plan_stats_t;
 
@@ -195,8 +199,12 @@ idg_status idg_plan_stats(const idg_plan* plan, idg_plan_stats_t* out);
 idg_status idg_plan_subgrids(const idg_plan* plan, int32_t* out, int64_t cap, int64_t* n);
 
 /*
- * idg_plan_layers -- per subgrid, in plan order, its w layer k (w0 = k *
- * w_layer_step; 0 without IDG_W_LAYERS).  out: host int32 [cap].
+ * idg_plan_layers -- per subgrid, in plan order, its w layer (Section 2.4).
+ *   out   host int32 [cap][2] rows {k, mirrored}: w0 = (k + 1/2) w_layer_step
+ *         = (2k + 1) w_max, and mirrored = 1 when the subgrid holds rows of
+ *         w < 0 gridded as their mirrors (V^H of baseline (q, p) at -uvw);
+ *         {0, 0} for every subgrid without IDG_W_LAYERS (w0 = 0 then)
+ *   n     receives the number of subgrids; rows beyond cap are not written
  */
 idg_status idg_plan_layers(const idg_plan* plan, int32_t* out, int64_t cap, int64_t* n);
 
@@ -268,7 +276,9 @@ idg_status idg_profile_read(idg_plan* plan, double* ms, int64_t* launches);
  * until the process exits) instead of the plan's scratch, and subgrids are
  * processed in sub-batches that fit it.  Calls no allocating routine.
  *   - the first call on a device looks up the buffer's device address (once
- *     per device, with that device current): make it before any capture;
+ *     per device, with that device current) and keeps it for the life of the
+ *     process: make that call before any capture, and do not reset the device
+ *     (cudaDeviceReset) between calls;
  *   - every call shares the buffer: calls that overlap on the GPU (other
  *     streams or threads) race; the buffer keeps the last call's contents;
  *   - IDG_ERR_UNSUPPORTED if one subgrid image would not fit the buffer or

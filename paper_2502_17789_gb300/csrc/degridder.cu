@@ -80,7 +80,7 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
       const int k = item.k_begin + tid;
       const int t = sd.t0 + k / nc, ch = sd.c0 + k % nc;
       const double* r = a.uvw + (size_t(sd.b) * a.g.n_t + t) * 3;
-      const double fs = a.fscale[ch];
+      const double fs = subgrid_sign(sd) * a.fscale[ch];  // a mirrored subgrid predicts (-u, -v, -w)
       const double inv_l = 1.0 / double(L);
       const double dx = (r[0] * fs) * a.g.fov - double(sd.x0 + L / 2 - a.g.N / 2);
       const double dy = (r[1] * fs) * a.g.fov - double(sd.y0 + L / 2 - a.g.N / 2);
@@ -254,8 +254,11 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
     const int k = item.k_begin + tid;
     const int t = sd.t0 + k / nc, ch = sd.c0 + k % nc;
     const size_t vidx = (size_t(sd.b) * a.g.n_t + t) * a.g.n_ch + ch;
-    a.vis[2 * vidx] = make_float4(S.out[0][tid], S.out[1][tid], S.out[2][tid], S.out[3][tid]);
-    a.vis[2 * vidx + 1] = make_float4(S.out[4][tid], S.out[5][tid], S.out[6][tid], S.out[7][tid]);
+    float4 v0 = make_float4(S.out[0][tid], S.out[1][tid], S.out[2][tid], S.out[3][tid]);
+    float4 v1 = make_float4(S.out[4][tid], S.out[5][tid], S.out[6][tid], S.out[7][tid]);
+    if (sd.flags & kSubgridMirrored) mirror_values(v0, v1);  // the visibility is the mirror's V^H
+    a.vis[2 * vidx] = v0;
+    a.vis[2 * vidx + 1] = v1;
   }
 }
 

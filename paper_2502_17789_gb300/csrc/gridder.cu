@@ -47,7 +47,7 @@ __device__ __forceinline__ Slopes vis_slopes(const StageArgs& a, const SubgridDe
   const double off_x = double(sd.x0 + L / 2 - a.g.N / 2);
   const double off_y = double(sd.y0 + L / 2 - a.g.N / 2);
   const double* r = a.uvw + (size_t(sd.b) * a.g.n_t + t) * 3;
-  const double fs = a.fscale[ch];
+  const double fs = subgrid_sign(sd) * a.fscale[ch];  // a mirrored subgrid sees (-u, -v, -w)
   const double dx = (r[0] * fs) * a.g.fov - off_x;
   const double dy = (r[1] * fs) * a.g.fov - off_y;
   return {dx * inv_l, dy * inv_l, r[2] * fs - subgrid_w0(a.g, sd)};  // w - w0 (Section 2.4)
@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(256) stage_records_kernel(const StageArgs a, i
   for (int k = threadIdx.x; k < sd.n_vis; k += blockDim.x) {
     const int t = sd.t0 + k / nc, cc = k % nc, ch = sd.c0 + cc;
     const size_t vidx = (size_t(sd.b) * a.g.n_t + t) * a.g.n_ch + ch;
-    const float4 v0 = a.vis[2 * vidx], v1 = a.vis[2 * vidx + 1];
+    float4 v0 = a.vis[2 * vidx], v1 = a.vis[2 * vidx + 1];
+    if (sd.flags & kSubgridMirrored) mirror_values(v0, v1);
     float4* rec = a.records + (size_t(sd.rec_offset) + k) * kRecordFloat4;
     rec[0] = make_float4(v0.x, v0.x, v0.y, v0.y);
     rec[1] = make_float4(-v0.y, -v0.y, v0.z, v0.z);

@@ -337,10 +337,17 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
   bool any = false;
   int32_t k_lo = 0, k_hi = 0;
   for (const SubgridDesc& d : p->part.subgrids) {
-    if (d.dropped) {
+    if (d.flags & kSubgridDropped) {
       ++p->n_sg_dropped;
       p->n_vis_dropped += d.n_vis;
     } else {
+      // the kernels write a subgrid's image after its last segment: every
+      // kept subgrid has members and at least one segment
+      if (d.seg_count < 1 || d.n_vis < 1) {
+        set_err(nullptr, IDG_ERR_INVALID_ARG, "internal: a subgrid without members or segments");
+        delete p;
+        return IDG_ERR_INVALID_ARG;
+      }
       p->exec.push_back(d);
       p->vis_pixels += int64_t(d.n_vis) * L * L;
       k_lo = any ? std::min(k_lo, d.layer) : d.layer;
@@ -775,7 +782,7 @@ idg_status idg_invert(idg_plan* plan, const void* vis_c64, const void* aterms_c6
     return cufftExecZ2Z(plan->fft, reinterpret_cast<cufftDoubleComplex*>(x), reinterpret_cast<cufftDoubleComplex*>(x),
                         CUFFT_INVERSE);
   };
-  const bool single = plan->n_layers == 1 && plan->k_min == 0;
+  const bool single = (plan->geom.flags & IDG_W_LAYERS) == 0;
   if (single) {
     // one layer at w0 = 0: transform a signed copy, the gridded plane stays in `grid`
     e = launch_image_pass(plan->npol, grid, img, nullptr, 1.0, 0.0, fov, N, kPassSign, plan->stream);
@@ -789,7 +796,7 @@ idg_status idg_invert(idg_plan* plan, const void* vis_c64, const void* aterms_c6
   // w-stacking (Eq. 11): transform every layer in place, shift it from w0 to w = 0, sum
   for (int li = 0; li < plan->n_layers; ++li) {
     double2* gl = grid + plane_set * li;
-    const double w0 = double(plan->k_min + li) * plan->part.w_step;
+    const double w0 = (double(plan->k_min + li) + 0.5) * plan->part.w_step;
     e = launch_image_pass(plan->npol, gl, gl, nullptr, 1.0, 0.0, fov, N, kPassSign, plan->stream);
     if (e) return cuda_err(plan, e, "centring signs");
     const cufftResult r = inverse(gl);
@@ -818,7 +825,7 @@ idg_status idg_predict(idg_plan* plan, const void* image_c128, const void* aterm
   // inverse w-stacking (Eq. 12): each layer's model grid from the image shifted to its w0
   for (int li = 0; li < plan->n_layers; ++li) {
     double2* gl = grid + plane_set * li;
-    const double w0 = double(plan->k_min + li) * plan->part.w_step;
+    const double w0 = (double(plan->k_min + li) + 0.5) * plan->part.w_step;
     int e = launch_image_pass(plan->npol, img, gl, plan->d_inv_t, inv_l2, -w0, fov, N, kPassSign, plan->stream);
     if (e) return cuda_err(plan, e, "taper correction");
     const cufftResult r = cufftExecZ2Z(plan->fft, reinterpret_cast<cufftDoubleComplex*>(gl),
@@ -925,7 +932,11 @@ idg_status idg_plan_stats(const idg_plan* plan, idg_plan_stats_t* out) {
 idg_status idg_plan_layers(const idg_plan* plan, int32_t* out, int64_t cap, int64_t* n) {
   if (!plan || !n || (cap > 0 && !out)) return set_err(nullptr, IDG_ERR_INVALID_ARG, "NULL argument");
   *n = int64_t(plan->part.subgrids.size());
-  for (int64_t s = 0; s < std::min<int64_t>(cap, *n); ++s) out[s] = plan->part.subgrids[s].layer;
+  for (int64_t s = 0; s < std::min<int64_t>(cap, *n); ++s) {
+    const SubgridDesc& d = plan->part.subgrids[s];
+    out[2 * s] = d.layer;
+    out[2 * s + 1] = (d.flags & kSubgridMirrored) ? 1 : 0;
+  }
   return IDG_OK;
 }
 
@@ -934,7 +945,7 @@ idg_status idg_plan_subgrids(const idg_plan* plan, int32_t* out, int64_t cap, in
   *n = int64_t(plan->part.subgrids.size());
   for (int64_t s = 0; s < std::min<int64_t>(cap, *n); ++s) {
     const SubgridDesc& d = plan->part.subgrids[s];
-    const int32_t row[8] = {d.b, d.t0, d.t1, d.c0, d.c1, d.x0, d.y0, d.dropped};
+    const int32_t row[8] = {d.b, d.t0, d.t1, d.c0, d.c1, d.x0, d.y0, (d.flags & kSubgridDropped) ? 1 : 0};
     std::memcpy(out + s * 8, row, sizeof row);
   }
   return IDG_OK;

@@ -22,12 +22,20 @@ struct SubgridDesc {
   int32_t x0, y0;
   int32_t seg_begin, seg_count;  // into the segment table
   int32_t n_vis;
-  int32_t dropped;
+  int32_t flags;                 // kSubgridDropped | kSubgridMirrored
   int32_t plan_index;            // position in plan order
   int32_t rec_offset;            // first staged record of this subgrid within its batch
-  int32_t layer;                 // w layer: k (w0 = k w_step) in the partition, k - k_min on the device
+  int32_t layer;                 // w layer: k (w0 = (k + 1/2) w_step) in the partition, k - k_min on the device
 };
 static_assert(sizeof(SubgridDesc) == 64, "SubgridDesc layout");
+
+// SubgridDesc::flags
+constexpr int32_t kSubgridDropped = 1;   // outside the grid (IDG_DROP_OUT_OF_GRID): not gridded, degrids to 0
+// w layers (Section 2.4, footnote): the subgrid holds rows with w < 0, taken
+// as their mirrors V^H at (-u, -v, -w) on baseline (q, p); p and q of the
+// descriptor are already swapped, the kernels negate uvw and conjugate-
+// transpose the values they read (gridder) or write (degridder)
+constexpr int32_t kSubgridMirrored = 2;
 
 // The part of a subgrid that shares one A-term interval (Section 3.3).
 // Members are enumerated t-major: k = (t - t0) * (c1 - c0) + (c - c0).
@@ -73,7 +81,7 @@ struct PlanInput {
 struct Partition {
   std::vector<SubgridDesc> subgrids;  // plan order
   std::vector<SegmentDesc> segments;
-  double w_step = 0.0;                // w layer spacing 2 w_max (wavelengths)
+  double w_step = 0.0;                // w layer width 2 w_max (wavelengths)
 };
 
 // Returns IDG_OK or an error status with a message in `err`.
@@ -87,14 +95,19 @@ std::vector<double> kaiser_bessel_taper(int L, double beta);
 struct KernelGeom {
   int32_t N, L, n_t, n_ch, n_st, nodes;
   double fov;
-  double w_step;   // w layer spacing; a subgrid's w0 = (k_min + layer) * w_step
+  double w_step;   // w layer width 2 w_max; a subgrid's w0 = (k_min + layer + 1/2) * w_step
   int32_t k_min;
   int32_t npol = 4;  // master-grid planes: 4 correlations, or 1 (Stokes I = (XX + YY) / 2)
 };
 
-// w0 of a subgrid (its w layer; 0 without layers)
+// w0 of a subgrid: (2k+1) w_max on layer k, one of {w_max, 3 w_max, ...}
+// (Section 2.4); 0 without layers (w_step = 0)
 __host__ __device__ inline double subgrid_w0(const KernelGeom& g, const SubgridDesc& d) {
-  return double(g.k_min + d.layer) * g.w_step;
+  return (double(g.k_min + d.layer) + 0.5) * g.w_step;
+}
+// -1 for a mirrored subgrid (its members' uvw are negated), else +1
+__host__ __device__ inline double subgrid_sign(const SubgridDesc& d) {
+  return (d.flags & kSubgridMirrored) ? -1.0 : 1.0;
 }
 
 // Staged visibility record, 8 float4 = 128 bytes (written by the staging

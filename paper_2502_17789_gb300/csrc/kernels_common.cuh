@@ -195,6 +195,14 @@ __device__ __forceinline__ Jones jdiag_a_y_bh(const JonesDiag& P, const Jones& Y
 
 __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
 
+// V -> V^H for a visibility stored as 2 float4 (XX, XY) (YX, YY): the value a
+// mirrored row carries (Section 2.4 footnote, V(u,v,w) = V(-u,-v,-w)^H)
+__device__ __forceinline__ void mirror_values(float4& v0, float4& v1) {
+  const float4 a = v0, b = v1;
+  v0 = make_float4(a.x, -a.y, b.x, -b.y);
+  v1 = make_float4(a.z, -a.w, b.z, -b.w);
+}
+
 // ---------------------------------------------------------------- async bulk copies (TMA, 1-D)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

@@ -107,9 +107,10 @@ __global__ void __launch_bounds__(ROWS * L / 8, (ROWS * L / 8) <= 128 ? 3 : 2)
         const int k = kc + tid;
         const int t = sd.t0 + k / nc, ch = sd.c0 + k % nc;
         const size_t vidx = (size_t(sd.b) * a.g.n_t + t) * a.g.n_ch + ch;
-        const float4 v0 = a.vis[2 * vidx], v1 = a.vis[2 * vidx + 1];
+        float4 v0 = a.vis[2 * vidx], v1 = a.vis[2 * vidx + 1];
+        if (sd.flags & kSubgridMirrored) mirror_values(v0, v1);
         const double* r = a.uvw + (size_t(sd.b) * a.g.n_t + t) * 3;
-        const double fs = a.fscale[ch];
+        const double fs = subgrid_sign(sd) * a.fscale[ch];  // a mirrored subgrid sees (-u, -v, -w)
         const double dx = (r[0] * fs) * a.g.fov - off_x;
         const double dy = (r[1] * fs) * a.g.fov - off_y;
         const double w = r[2] * fs - subgrid_w0(a.g, sd);  // w - w0 (Section 2.4)

@@ -19,9 +19,14 @@
 //   corner x0 = floor((xi_min + xi_max) / 2) - L/2, likewise y0
 //   w check: |w - w0| * max|grad n'| * FOV <= P/2 - 1 (footnote of Section 2.4),
 //   i.e. |w - w0| <= w_max.  Without IDG_W_LAYERS w0 = 0 and a larger |w| is
-//   an error; with it (the hybrid with w-stacking of Section 2.4) w0 is the
-//   nearest multiple k of w_step = 2 w_max and every member of a subgrid
-//   shares the layer k of the run's first visibility (checked on the channel
+//   an error.  With it (the hybrid with w-stacking of Section 2.4) a row
+//   (baseline, timestep) with w < 0 is mirrored -- the visibility V^H of
+//   baseline (q, p) at (-u, -v, -w), since V(u,v,w) = V(-u,-v,-w)^H (the
+//   footnote's way of halving the layers) -- so every gridded w' >= 0; its
+//   layer is k = floor(w' / w_step), w_step = 2 w_max, with w0 = (2k+1) w_max,
+//   the set {w_max, 3 w_max, 5 w_max, ...}.  Pixel coordinates of mirrored
+//   rows are those of (-u, -v), and every member of a subgrid shares the
+//   layer and the side of the run's first visibility (checked on the channel
 //   run's ends, the time growth's corners and in the final shrink).
 #include <algorithm>
 #include <cmath>
@@ -40,7 +45,9 @@ struct Run {
   int32_t blk, ts, te, c_lo, c_hi, layer;
 };
 
-// Pixel coordinates (and w layers) of every visibility of one baseline, [t][ch].
+// Pixel coordinates (and w layer keys) of every visibility of one baseline,
+// [t][ch].  With w layers the key is 2k + m (k the layer, m = 1 on a
+// mirrored row), so equal keys mean one layer and one side.
 class BaselinePixels {
  public:
   BaselinePixels(const PlanInput& in, int b, double w_step)
@@ -48,15 +55,17 @@ class BaselinePixels {
     const double half = double(in.N / 2);
     for (int t = 0; t < in.n_t; ++t) {
       const double* r = in.uvw + (size_t(b) * in.n_t + t) * 3;
+      const bool mirror = w_step > 0.0 && r[2] < 0.0;
+      const double sgn = mirror ? -1.0 : 1.0;
       for (int c = 0; c < in.n_ch; ++c) {
         const double f = in.freqs[c];
-        const double u = (r[0] * f) / kSpeedOfLight;
-        const double v = (r[1] * f) / kSpeedOfLight;
+        const double u = (sgn * r[0] * f) / kSpeedOfLight;
+        const double v = (sgn * r[1] * f) / kSpeedOfLight;
         xi_[size_t(t) * n_ch_ + c] = u * in.fov + half;
         eta_[size_t(t) * n_ch_ + c] = v * in.fov + half;
         if (w_step > 0.0) {
-          const double w = (r[2] * f) / kSpeedOfLight;
-          layer_[size_t(t) * n_ch_ + c] = int32_t(std::floor(w / w_step + 0.5));
+          const double w = (sgn * r[2] * f) / kSpeedOfLight;
+          layer_[size_t(t) * n_ch_ + c] = 2 * int32_t(std::floor(w / w_step)) + (mirror ? 1 : 0);
         }
       }
     }
@@ -213,9 +222,10 @@ idg_status partition(const PlanInput& in, Partition* out, std::string* err) {
     for (const Run& r : runs) {
       const auto bx = px.box(r.ts, r.te, r.c_lo, r.c_hi);
       SubgridDesc d{};
+      const bool mirror = (r.layer & 1) != 0;  // stations swap on the mirror (q, p)
       d.b = b;
-      d.p = in.baselines[2 * b];
-      d.q = in.baselines[2 * b + 1];
+      d.p = in.baselines[2 * b + (mirror ? 1 : 0)];
+      d.q = in.baselines[2 * b + (mirror ? 0 : 1)];
       d.t0 = r.ts;
       d.t1 = r.te;
       d.c0 = r.c_lo;
@@ -223,7 +233,8 @@ idg_status partition(const PlanInput& in, Partition* out, std::string* err) {
       d.x0 = int32_t(std::floor((bx.xmin + bx.xmax) / 2.0)) - in.L / 2;
       d.y0 = int32_t(std::floor((bx.ymin + bx.ymax) / 2.0)) - in.L / 2;
       d.n_vis = (r.te - r.ts) * (r.c_hi - r.c_lo);
-      d.layer = r.layer;
+      d.layer = r.layer >> 1;
+      d.flags = mirror ? kSubgridMirrored : 0;
       d.plan_index = int32_t(out->subgrids.size());
       const bool outside = d.x0 < 0 || d.y0 < 0 || d.x0 > in.N - in.L || d.y0 > in.N - in.L;
       if (outside) {
@@ -232,7 +243,7 @@ idg_status partition(const PlanInput& in, Partition* out, std::string* err) {
                         "outside the %d-pixel grid", b, r.ts, r.te, r.c_lo, r.c_hi, d.x0, d.y0, in.N);
           return fail(IDG_ERR_UV_OUT_OF_GRID, msg);
         }
-        d.dropped = 1;
+        d.flags |= kSubgridDropped;
       }
       d.seg_begin = int32_t(out->segments.size());
       for (int a = 0; a < in.n_int; ++a) {

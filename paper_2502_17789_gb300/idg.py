@@ -187,13 +187,14 @@ def idg_plan_subgrids(plan) -> np.ndarray:
 
 
 def idg_plan_layers(plan) -> np.ndarray:
-    """int32 [n_subgrids]: each subgrid's w layer k (w0 = k * w_layer_step)."""
+    """int32 [n_subgrids, 2]: per subgrid its w layer k (w0 = (k + 1/2) *
+    w_layer_step) and 1 if it holds mirrored rows (w < 0, gridded as V^H at -uvw)."""
     lib = load()
     n = ctypes.c_int64(0)
     _check(lib.idg_plan_layers(plan, None, 0, ctypes.byref(n)), "idg_plan_layers", plan)
-    out = np.zeros(n.value, np.int32)
+    out = np.zeros((max(n.value, 1), 2), np.int32)
     _check(lib.idg_plan_layers(plan, _np_ptr(out), n.value, ctypes.byref(n)), "idg_plan_layers", plan)
-    return out
+    return out[: n.value]
 
 
 def idg_plan_segments(plan) -> np.ndarray:

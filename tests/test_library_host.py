@@ -173,10 +173,11 @@ def test_planner_w_layers_bit_exact(idg_mod, oracle_mod, seed, L):
     try:
         np.testing.assert_array_equal(idg_mod.idg_plan_subgrids(h), ref.subgrids)
         np.testing.assert_array_equal(idg_mod.idg_plan_segments(h), ref.segments)
-        np.testing.assert_array_equal(idg_mod.idg_plan_layers(h), ref.layers)
+        np.testing.assert_array_equal(idg_mod.idg_plan_layers(h), np.stack([ref.layers, ref.conj], axis=1))
+        assert ref.conj.any() and not ref.conj.all()
         st = idg_mod.idg_plan_stats(h)
         k_min, n_layers = ref.k_range
-        assert (st.w_layer_min, st.n_w_layers) == (k_min, n_layers) and n_layers >= 3
+        assert (st.w_layer_min, st.n_w_layers) == (k_min, n_layers) and n_layers >= 2
         assert st.w_layer_step == ref.w_step
     finally:
         idg_mod.idg_plan_destroy(h)
@@ -197,3 +198,22 @@ def test_aterm_weights_need_a_device_plan_with_the_flag(idg_mod):
         assert st == 1 and not out.any()
     finally:
         idg_mod.idg_plan_destroy(plan)
+
+
+def test_planner_shrink_golden(idg_mod):
+    """The library planner's final shrink on the hand-worked track of
+    tests/golden/planner_handworked.json (Section 3.1: corners checked while
+    growing, every member after): [0,3) and [3,6)."""
+    import json
+    gd = json.load(open(os.path.join(ROOT, "tests", "golden", "planner_handworked.json")))
+    g, sc = gd["geometry"], gd["shrink_case"]
+    xi = np.array(sc["xi"])
+    uvw = np.zeros((1, xi.size, 3))
+    uvw[0, :, 0] = (xi - g["N"] / 2) * synth.SPEED_OF_LIGHT / sc["f0"]
+    geo, _ = idg_mod.make_geometry(g["N"], g["L"], g["P"], g["fov"], flags=idg_mod.IDG_HOST_ONLY)
+    h = idg_mod.idg_plan_create(geo, 2, np.array([[0, 1]], np.int32), uvw, np.array([sc["f0"]]),
+                                np.array([0, xi.size], np.int32))
+    try:
+        np.testing.assert_array_equal(idg_mod.idg_plan_subgrids(h), np.array(sc["expected"], np.int32))
+    finally:
+        idg_mod.idg_plan_destroy(h)
