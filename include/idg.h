@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define IDG_ABI_VERSION 1
+#define IDG_ABI_VERSION 2
 
 typedef struct idg_plan idg_plan; /* opaque, owned by the library */
 
@@ -92,6 +92,11 @@ typedef struct {
   int32_t aterm_nodes;    /* nodes per axis of the A-term samples, 2 .. 25 */
   int32_t flags;          /* IDG_DROP_OUT_OF_GRID | IDG_SPLIT_AT_ATERM_INTERVALS | IDG_HOST_ONLY | IDG_PERSISTENT
                              | IDG_W_LAYERS | IDG_NORMALIZE_ATERM | IDG_STOKES_I */
+  int32_t degrid_channels; /* degridder channels per lane: 1, 2 or 4, or 0 for the default.  With C > 1 a
+                              lane predicts C consecutive channels of one timestep, the first by sine and
+                              cosine, the others by rotation with the channel-step phasor (the phase is
+                              linear in frequency, Eq. 7); it needs uniformly spaced channels and falls back
+                              to 1 otherwise (idg_plan_stats reports the value in use) */
 } idg_geometry;
 
 typedef struct {
@@ -113,6 +118,7 @@ typedef struct {
                                  w_layer_step, i.e. layer k sits at w0 = (2k + 1) w_max */
   double w_layer_step;        /* layer width 2 w_max in wavelengths, w_max = (P/2 - 1) / (max|grad n'| FOV) */
   int32_t n_pol;              /* planes per layer of grids and images: 4, or 1 with IDG_STOKES_I */
+  int32_t degrid_channels;    /* channels per degridder lane in use */
 } idg_plan_stats_t;
 
 /*

@@ -5,56 +5,109 @@
 // where Y is the uncentred inverse subgrid FFT of the split-out grid
 // footprint (the splitter applied (-1)^(x+y)).
 //
-// Work item = up to 256 visibilities of one or two consecutive segments of
-// a subgrid (one A-term each), in groups of 32 (one per lane); pairing
-// segments fills the lanes that a lone segment of, say, 40 visibilities
-// would leave idle.  The block walks the subgrid in chunks of 64 pixel
-// blocks (8 consecutive pixels of a row each, 512 pixels).  Within a chunk,
-// warp w sums pixel blocks [8w, 8w+8) for every visibility group in turn and
-// adds its partial sums into a shared-memory accumulator with shared-memory
-// atomics, so all warps stay busy whatever the segment size.  Z of the next
-// chunk is built while the current chunk is summed: its Y values are loaded
-// into registers before the phasor sum and turned into Z (A-term prologue)
-// after it, into the other half of a double buffer, one barrier per chunk;
-// with two segments, each pixel pair gets one Z per segment and every lane
-// reads the Z of its own visibility's segment.
+// Work item = up to kDegridLanes lanes of one or two consecutive segments of
+// a subgrid (one A-term each), in groups of 32 (one per warp lane); pairing
+// segments fills the lanes that a lone segment would leave idle.  A lane
+// holds a channel group: up to C consecutive channels of one timestep row
+// (C = 1: one visibility).  The phase is linear in frequency (Eq. 7 with
+// u = u_m f / c), so with uniform channel spacing the lane evaluates the
+// phasor of its first channel and the phasor of the channel step with
+// __sincosf and reaches the others by rotation, one complex multiply per
+// pixel each; every Z value it loads serves its C visibilities.  A row's
+// nc channels are split into G = ceil(nc / C) groups of balanced size.
+// The block walks the subgrid in chunks of pixel blocks (8 consecutive
+// pixels of a row each; 512 pixels per chunk, 256 with C = 4).  Within a chunk, warp w sums pixel
+// blocks [8w, 8w+8) for every lane group in turn and adds its partial sums
+// into a shared-memory accumulator with shared-memory atomics, so all warps
+// stay busy whatever the segment size.  Z of the next chunk is built while
+// the current chunk is summed: its Y values are loaded into registers before
+// the phasor sum and turned into Z (A-term prologue) after it, into the other
+// half of a double buffer, one barrier per chunk; with two segments, each
+// pixel pair gets one Z per segment and every lane reads the Z of its own
+// segment.
 // Phases use the same FP64 offset / exact anchor reduction / FP32 increment
-// scheme as the gridder, with one anchor per 16 pixels of a row.
+// scheme as the gridder, with one anchor per 16 pixels of a row, for the
+// first channel and for the channel step alike.
 #include <type_traits>
 
 #include "kernels_common.cuh"
 
 namespace idg {
 
-constexpr int kDegridThreads = 256;
-constexpr int kChunkBlocks = 64;  // pixel blocks (of 8) per chunk = 512 pixels
-constexpr int kRangeBlocks = 8;   // pixel blocks per work unit (one per warp per visibility group)
+constexpr int kRangeBlocks = 8;   // pixel blocks (of 8 pixels) per work unit (one per warp per lane group)
 
-template <int L>
+// Launch shape per channels-per-lane C: W warps per block, each summing 8
+// pixel blocks of every chunk, so a chunk is 8 W blocks (64 W pixels).  With
+// C = 4 the 4 sets of accumulators need more registers than 16 warps per SM
+// leave, so that variant runs 4-warp blocks, 3 per SM (12 warps).
+__host__ __device__ constexpr int degrid_warps(int C) { return C >= 4 ? 4 : 8; }
+__host__ __device__ constexpr int degrid_threads(int C) { return 32 * degrid_warps(C); }
+__host__ __device__ constexpr int degrid_min_blocks(int C) { return C >= 4 ? 3 : 2; }
+
+template <int C>
 struct DegridSmem {
+  static constexpr int LN = degrid_lanes(C);         // lanes per item
+  static constexpr int CB = 8 * degrid_warps(C);     // pixel blocks per chunk
   // [buf][segment][pol][block][pixel pair] {Zr_a, Zr_b, Zi_a, Zi_b}: the prologue's thread t writes
   // element t of each pol plane, so a warp's stores are contiguous (no bank conflicts)
-  float4 z[2][kDegridSegs][4][kChunkBlocks][4];
-  float4 g[2][kChunkBlocks / 2][5]; // geometry of the 16-pixel phase-anchor blocks
-  float4 coef[8][2][32];            // [vis group][half][lane]: (ah, bh, al, bl), (w, 2 pi a, 2 pi w, 0)
-  float out[8][kDegridThreads];     // [component][visibility slot], accumulated with shared atomics
+  float4 z[2][kDegridSegs][4][CB][4];
+  float4 g[2][CB / 2][5];  // geometry of the 16-pixel phase-anchor blocks
+  // [lane group][k][lane]: k = 0, 1 first channel (ah, bh, al, bl), (w, 2 pi a, 2 pi w, 0);
+  // k = 2, 3 the channel step in the same form (C > 1)
+  float4 coef[LN / 32][C > 1 ? 4 : 2][32];
+  float out[8][C][LN];  // [component][channel of the group][lane], accumulated with shared atomics
 };
 
-template <int L>
-__device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx, DegridSmem<L>& S, float2* s_A) {
+// Phase slopes of (row t, channel ch) of a subgrid in turns per pixel, and
+// w - w0 in turns (Section 2.4), from FP64 uvw (negated on a mirrored subgrid)
+__device__ __forceinline__ void degrid_slopes(const DegridArgs& a, const SubgridDesc& sd, int L, int t, int ch,
+                                              double& aa, double& bb, double& w) {
+  const double* r = a.uvw + (size_t(sd.b) * a.g.n_t + t) * 3;
+  const double fs = subgrid_sign(sd) * a.fscale[ch];  // a mirrored subgrid predicts (-u, -v, -w)
+  const double inv_l = 1.0 / double(L);
+  aa = ((r[0] * fs) * a.g.fov - double(sd.x0 + L / 2 - a.g.N / 2)) * inv_l;
+  bb = ((r[1] * fs) * a.g.fov - double(sd.y0 + L / 2 - a.g.N / 2)) * inv_l;
+  w = r[2] * fs - subgrid_w0(a.g, sd);
+}
+
+// (head, tail) split of the slopes for the exact anchor reduction
+__device__ __forceinline__ void degrid_coef(double aa, double bb, double w, float4& c0, float4& c1) {
+  const double ah = rint(aa * 65536.0) * (1.0 / 65536.0);
+  const double bh = rint(bb * 65536.0) * (1.0 / 65536.0);
+  c0 = make_float4(float(ah), float(bh), float(aa - ah), float(bb - bh));
+  c1 = make_float4(float(w), float(kTwoPi * aa), float(kTwoPi * w), 0.f);
+}
+
+// anchor phase in radians, reduced to [-pi, pi]: head part exact, then two range reductions
+__device__ __forceinline__ float anchor_phase(float4 c0, float4 c1, float n0, float di0, float dj0) {
+  const float sh = fmaf(c0.x, di0, c0.y * dj0);
+  const float d1 = __fsub_rn(sh, round_nearest(sh));
+  const float lo = fmaf(c1.x, n0, fmaf(c0.z, di0, c0.w * dj0));
+  const float rr = __fadd_rn(d1, lo);
+  return __fmul_rn(__fsub_rn(rr, round_nearest(rr)), kTwoPiF);
+}
+
+template <int L, int C>
+__device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx, DegridSmem<C>& S, float2* s_A) {
   constexpr int TPR = L / 8;
   constexpr int NBLK = L * L / 8;
+  constexpr int NT = degrid_threads(C);
+  constexpr int kChunkBlocks = DegridSmem<C>::CB;
   constexpr int NCH = NBLK / kChunkBlocks;
-  static_assert(NBLK % kChunkBlocks == 0 && kChunkBlocks == 8 * kRangeBlocks, "chunking");
+  constexpr int LN = DegridSmem<C>::LN;
+  static_assert(NBLK % kChunkBlocks == 0 && kChunkBlocks == degrid_warps(C) * kRangeBlocks, "chunking");
+  static_assert(LN <= NT && NT == 4 * kChunkBlocks, "one thread per lane and per pixel pair in the prologue");
   const DegridItem item = a.items[item_idx];
   const SubgridDesc sd = a.sg[item.sg];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nv = item.k_end - item.k_begin;
-  const int n0 = item.k_mid - item.k_begin;          // visibilities of the first segment
+  const int nl = item.k_end - item.k_begin;          // lanes (channel groups) of the item
+  const int n0 = item.k_mid - item.k_begin;          // lanes of the first segment
   const int n_seg = item.k_mid < item.k_end ? 2 : 1;
-  const int n_vg = (nv + 31) >> 5;  // groups of 32 visibilities, 1..8
+  const int n_vg = (nl + 31) >> 5;  // groups of 32 lanes
   const int nodes = a.g.nodes;
   const int nA = nodes * nodes * 4;
+  const int nc = sd.c1 - sd.c0;
+  const int G = (nc + C - 1) / C;  // channel groups per row
   // per segment, uniform over the block: both stations' A-terms diagonal -> quarter of the Jones work
   unsigned diag = 0;  // bit s: segment s
 #pragma unroll
@@ -64,7 +117,7 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
       if (a.adiag[seg.interval * a.g.n_st + sd.p] && a.adiag[seg.interval * a.g.n_st + sd.q]) diag |= 1u << s;
       const float2* Ap = a.aterms + (size_t(seg.interval) * a.g.n_st + sd.p) * nA;
       const float2* Aq = a.aterms + (size_t(seg.interval) * a.g.n_st + sd.q) * nA;
-      for (int e = tid; e < nA; e += kDegridThreads) {
+      for (int e = tid; e < nA; e += NT) {
         s_A[2 * s * nA + e] = Ap[e];
         s_A[(2 * s + 1) * nA + e] = Aq[e];
       }
@@ -72,34 +125,41 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
   }
   const unsigned all_segs = n_seg == 2 ? 3u : 1u;
   const bool two_pol = a.g.npol == 1 && (diag & all_segs) == all_segs;
-  // visibility slot tid: FP64 offsets -> FP32 phase coefficients (zeros for empty slots)
-  {
-    const int nc = sd.c1 - sd.c0;
-    float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
-    if (tid < nv) {
-      const int k = item.k_begin + tid;
-      const int t = sd.t0 + k / nc, ch = sd.c0 + k % nc;
-      const double* r = a.uvw + (size_t(sd.b) * a.g.n_t + t) * 3;
-      const double fs = subgrid_sign(sd) * a.fscale[ch];  // a mirrored subgrid predicts (-u, -v, -w)
-      const double inv_l = 1.0 / double(L);
-      const double dx = (r[0] * fs) * a.g.fov - double(sd.x0 + L / 2 - a.g.N / 2);
-      const double dy = (r[1] * fs) * a.g.fov - double(sd.y0 + L / 2 - a.g.N / 2);
-      const double w = r[2] * fs - subgrid_w0(a.g, sd);  // w - w0 (Section 2.4)
-      const double aa = dx * inv_l, bb = dy * inv_l;
-      const double dah = rint(aa * 65536.0) * (1.0 / 65536.0);
-      const double dbh = rint(bb * 65536.0) * (1.0 / 65536.0);
-      c0 = make_float4(float(dah), float(dbh), float(aa - dah), float(bb - dbh));
-      c1 = make_float4(float(w), float(kTwoPi * aa), float(kTwoPi * w), 0.f);
+  // lane tid: row and channel range of its group; FP64 offsets -> FP32 phase
+  // coefficients of its first channel and of the channel step (zeros for empty lanes)
+  int my_t = 0, my_c = 0, my_n = 0;
+  if (tid < LN) {
+    float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0, c2 = c0, c3 = c0;
+    if (tid < nl) {
+      const int gidx = item.k_begin + tid;
+      const int row = gidx / G, gi = gidx - row * G;
+      my_t = sd.t0 + row;
+      my_c = sd.c0 + (gi * nc) / G;
+      my_n = sd.c0 + ((gi + 1) * nc) / G - my_c;
+      double aa, bb, w;
+      degrid_slopes(a, sd, L, my_t, my_c, aa, bb, w);
+      degrid_coef(aa, bb, w, c0, c1);
+      if (C > 1 && my_n > 1) {
+        double a2, b2, w2;
+        degrid_slopes(a, sd, L, my_t, my_c + 1, a2, b2, w2);
+        degrid_coef(a2 - aa, b2 - bb, w2 - w, c2, c3);
+      }
     }
     S.coef[tid >> 5][0][tid & 31] = c0;
     S.coef[tid >> 5][1][tid & 31] = c1;
+    if constexpr (C > 1) {
+      S.coef[tid >> 5][2][tid & 31] = c2;
+      S.coef[tid >> 5][3][tid & 31] = c3;
+    }
 #pragma unroll
-    for (int c = 0; c < 8; ++c) S.out[c][tid] = 0.f;
+    for (int c = 0; c < 8; ++c)
+#pragma unroll
+      for (int h = 0; h < C; ++h) S.out[c][h][tid] = 0.f;
   }
   const float2* Y = a.scratch + size_t(item.sg) * 4 * L * L;
 
   // prologue geometry: each thread builds one pixel pair (2 consecutive pixels) per chunk
-  const int pb = tid >> 2;          // block within the chunk, 0..63
+  const int pb = tid >> 2;          // block within the chunk
   const int pq = tid & 3;           // pixel pair within the block
   float2 ya[4], yb[4];              // Y of the pair, prefetched
 
@@ -180,64 +240,93 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
     const bool more = chunk + 1 < NCH;
     if (more) load_y(chunk + 1);
     // warp `warp` sums pixel blocks [warp*8, warp*8+8) of the chunk for every
-    // visibility group, over all four correlations (NP = 4) or, for a
-    // Stokes-I model seen through diagonal A-terms, XX and YY only (NP = 2:
-    // Z01 = Z10 = 0, so the predicted XY and YX are zero)
+    // lane group, over all four correlations (NP = 4) or, for a Stokes-I
+    // model seen through diagonal A-terms, XX and YY only (NP = 2: Z01 =
+    // Z10 = 0, so the predicted XY and YX are zero)
     auto sum_chunk = [&](auto np_tag) {
     constexpr int NP = decltype(np_tag)::value;
     for (int g = 0; g < n_vg; ++g) {
-      const float4 c0 = S.coef[g][0][lane], c1 = S.coef[g][1][lane];
       // Z of this lane's segment (lanes of one group may straddle the two segments)
       const float4(*zs)[kChunkBlocks][4] = S.z[buf][g * 32 + lane >= n0 ? 1 : 0];
-      const float2 ARR = make_float2(c1.y, c1.y), CRR = make_float2(c1.z, c1.z);
-      float2 RE[4], IM[4];
+      float2 RE[C][4], IM[C][4];
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        RE[p] = make_float2(0.f, 0.f);
-        IM[p] = make_float2(0.f, 0.f);
-      }
+      for (int h = 0; h < C; ++h)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          RE[h][p] = make_float2(0.f, 0.f);
+          IM[h][p] = make_float2(0.f, 0.f);
+        }
 #pragma unroll 1
       for (int b2 = warp * (kRangeBlocks / 2); b2 < (warp + 1) * (kRangeBlocks / 2); ++b2) {
         // one phase anchor per 16 pixels (pixel 8 of the block): exact reduction there, FP32 increments
-        const float4* G = S.g[buf][b2];
-        const float4 g0 = G[0];
-        const float n0 = g0.x, di0 = g0.y, dj0 = g0.z;
-        const float sh = fmaf(c0.x, di0, c0.y * dj0);
-        const float d1 = __fsub_rn(sh, round_nearest(sh));
-        const float lo = fmaf(c1.x, n0, fmaf(c0.z, di0, c0.w * dj0));
-        float rr = __fadd_rn(d1, lo);
-        rr = __fmul_rn(__fsub_rn(rr, round_nearest(rr)), kTwoPiF);
-        const float2 R0 = make_float2(rr, rr);
-#pragma unroll
+        // the lane's coefficients are re-read from shared memory per anchor (registers go to the sums)
+        const float4* Gm = S.g[buf][b2];
+        const float4 g0 = Gm[0];
+        const float4 c1 = S.coef[g][1][lane];
+        const float2 R0 = make_float2(anchor_phase(S.coef[g][0][lane], c1, g0.x, g0.y, g0.z), 0.f);
+        const float2 ARR = make_float2(c1.y, c1.y), CRR = make_float2(c1.z, c1.z);
+        float2 D0 = make_float2(0.f, 0.f);
+        [[maybe_unused]] float2 DARR = D0, DCRR = D0;
+        if constexpr (C > 1) {
+          const float4 c3 = S.coef[g][3][lane];
+          D0.x = anchor_phase(S.coef[g][2][lane], c3, g0.x, g0.y, g0.z);
+          DARR = make_float2(c3.y, c3.y);
+          DCRR = make_float2(c3.z, c3.z);
+        }
+#pragma unroll(C > 2 ? 2 : 8)
         for (int q = 0; q < 8; ++q) {
-          const float4 dn4 = G[1 + (q >> 1)];  // n' increments of pixels 4(q/2) .. 4(q/2)+3
+          const float4 dn4 = Gm[1 + (q >> 1)];  // n' increments of pixels 4(q/2) .. 4(q/2)+3
           const float2 DN = (q & 1) ? make_float2(dn4.z, dn4.w) : make_float2(dn4.x, dn4.y);
           const float2 DI = make_float2(float(2 * q - 8), float(2 * q - 7));
-          const float2 ph = ffma2(CRR, DN, ffma2(ARR, DI, R0));
+          const float2 ph = ffma2(CRR, DN, ffma2(ARR, DI, make_float2(R0.x, R0.x)));
           float2 Cs, Sn;
           __sincosf(ph.x, &Sn.x, &Cs.x);
           __sincosf(ph.y, &Sn.y, &Cs.y);
-          const float2 NS = make_float2(-Sn.x, -Sn.y);
+          float2 Rc = make_float2(1.f, 1.f), Rs = make_float2(0.f, 0.f);
+          if constexpr (C > 1) {
+            // phasor of the channel step at these pixels
+            const float2 dph = ffma2(DCRR, DN, ffma2(DARR, DI, make_float2(D0.x, D0.x)));
+            __sincosf(dph.x, &Rs.x, &Rc.x);
+            __sincosf(dph.y, &Rs.y, &Rc.y);
+          }
+          float2 ZR[NP], ZI[NP];
 #pragma unroll
           for (int pi = 0; pi < NP; ++pi) {
             const int p = NP == 4 ? pi : 3 * pi;
             const float4 z = zs[p][2 * b2 + (q >> 2)][q & 3];
-            const float2 ZR = make_float2(z.x, z.y), ZI = make_float2(z.z, z.w);
-            // V += Z conj(e): re += Zr c + Zi s, im += Zi c - Zr s
-            RE[p] = ffma2(ZR, Cs, RE[p]);
-            RE[p] = ffma2(ZI, Sn, RE[p]);
-            IM[p] = ffma2(ZI, Cs, IM[p]);
-            IM[p] = ffma2(ZR, NS, IM[p]);
+            ZR[pi] = make_float2(z.x, z.y);
+            ZI[pi] = make_float2(z.z, z.w);
+          }
+#pragma unroll
+          for (int h = 0; h < C; ++h) {
+            if (h > 0) {
+              // next channel: e^{i phi} <- e^{i phi} e^{i dphi}
+              const float2 c = ffma2(make_float2(-Sn.x, -Sn.y), Rs, fmul2(Cs, Rc));
+              Sn = ffma2(Sn, Rc, fmul2(Cs, Rs));
+              Cs = c;
+            }
+            const float2 NS = make_float2(-Sn.x, -Sn.y);
+#pragma unroll
+            for (int pi = 0; pi < NP; ++pi) {
+              const int p = NP == 4 ? pi : 3 * pi;
+              // V += Z conj(e): re += Zr c + Zi s, im += Zi c - Zr s
+              RE[h][p] = ffma2(ZR[pi], Cs, RE[h][p]);
+              RE[h][p] = ffma2(ZI[pi], Sn, RE[h][p]);
+              IM[h][p] = ffma2(ZI[pi], Cs, IM[h][p]);
+              IM[h][p] = ffma2(ZR[pi], NS, IM[h][p]);
+            }
           }
         }
       }
       const int slot = g * 32 + lane;
 #pragma unroll
-      for (int pi = 0; pi < NP; ++pi) {
-        const int p = NP == 4 ? pi : 3 * pi;
-        atomicAdd(&S.out[2 * p][slot], RE[p].x + RE[p].y);
-        atomicAdd(&S.out[2 * p + 1][slot], IM[p].x + IM[p].y);
-      }
+      for (int h = 0; h < C; ++h)
+#pragma unroll
+        for (int pi = 0; pi < NP; ++pi) {
+          const int p = NP == 4 ? pi : 3 * pi;
+          atomicAdd(&S.out[2 * p][h][slot], RE[h][p].x + RE[h][p].y);
+          atomicAdd(&S.out[2 * p + 1][h][slot], IM[h][p].x + IM[h][p].y);
+        }
     }
     };
     if (two_pol)
@@ -248,94 +337,119 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
     __syncthreads();
   }
 
-  // ---- write the visibilities of this item
-  if (tid < nv) {
-    const int nc = sd.c1 - sd.c0;
-    const int k = item.k_begin + tid;
-    const int t = sd.t0 + k / nc, ch = sd.c0 + k % nc;
-    const size_t vidx = (size_t(sd.b) * a.g.n_t + t) * a.g.n_ch + ch;
-    float4 v0 = make_float4(S.out[0][tid], S.out[1][tid], S.out[2][tid], S.out[3][tid]);
-    float4 v1 = make_float4(S.out[4][tid], S.out[5][tid], S.out[6][tid], S.out[7][tid]);
-    if (sd.flags & kSubgridMirrored) mirror_values(v0, v1);  // the visibility is the mirror's V^H
-    a.vis[2 * vidx] = v0;
-    a.vis[2 * vidx + 1] = v1;
+  // ---- write the visibilities of this item: lane tid's my_n channels
+  if (tid < nl) {
+    const size_t vrow = (size_t(sd.b) * a.g.n_t + my_t) * a.g.n_ch + my_c;
+#pragma unroll
+    for (int h = 0; h < C; ++h) {
+      if (h < my_n) {
+        float4 v0 = make_float4(S.out[0][h][tid], S.out[1][h][tid], S.out[2][h][tid], S.out[3][h][tid]);
+        float4 v1 = make_float4(S.out[4][h][tid], S.out[5][h][tid], S.out[6][h][tid], S.out[7][h][tid]);
+        if (sd.flags & kSubgridMirrored) mirror_values(v0, v1);  // the visibility is the mirror's V^H
+        a.vis[2 * (vrow + h)] = v0;
+        a.vis[2 * (vrow + h) + 1] = v1;
+      }
+    }
   }
 }
 
 // PERSIST = false: one item per block; true: blocks drain the a.queue counter.
-template <int L, bool PERSIST>
-__global__ void __launch_bounds__(kDegridThreads, 2) degridder_kernel(const DegridArgs a) {
+// C: channels per lane.
+template <int L, int C, bool PERSIST>
+__global__ void __launch_bounds__(degrid_threads(C), degrid_min_blocks(C)) degridder_kernel(const DegridArgs a) {
   extern __shared__ float4 smem_raw[];
-  DegridSmem<L>& S = *reinterpret_cast<DegridSmem<L>*>(smem_raw);
+  DegridSmem<C>& S = *reinterpret_cast<DegridSmem<C>*>(smem_raw);
   float2* s_A = reinterpret_cast<float2*>(&S + 1);  // [segment][station p, q][nodes*nodes*4]
   __shared__ int s_item;
   if constexpr (!PERSIST) {
-    degridder_item<L>(a, blockIdx.x, S, s_A);
+    degridder_item<L, C>(a, blockIdx.x, S, s_A);
   } else {
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
     __syncthreads();
     const int it = s_item;
     if (it >= a.n_items) return;
-    degridder_item<L>(a, it, S, s_A);
+    degridder_item<L, C>(a, it, S, s_A);
     __syncthreads();  // shared memory and s_item free for the next item
   }
   }
 }
 
-template <int L>
+template <int C>
 static size_t degridder_smem(int nodes) {
-  return sizeof(DegridSmem<L>) + sizeof(float2) * 2 * kDegridSegs * nodes * nodes * 4;
+  return sizeof(DegridSmem<C>) + sizeof(float2) * 2 * kDegridSegs * nodes * nodes * 4;
 }
 
 // The shared-memory limit is set for the largest node count any plan may
 // use, so plans with different node counts can share the kernels; the
 // occupancy (persistent grid size) follows this plan's own footprint.
-template <int L>
+template <int L, int C>
 static int configure_degridder_t(int nodes, int* persistent_blocks) {
-  const int smem_max = int(degridder_smem<L>(kMaxAtermNodes));
-  const int smem = int(degridder_smem<L>(nodes));
+  const int smem_max = int(degridder_smem<C>(kMaxAtermNodes));
+  const int smem = int(degridder_smem<C>(nodes));
   cudaError_t e =
-      cudaFuncSetAttribute(degridder_kernel<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+      cudaFuncSetAttribute(degridder_kernel<L, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(degridder_kernel<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    e = cudaFuncSetAttribute(degridder_kernel<L, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   int per_sm = 0, dev = 0, sms = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, degridder_kernel<L, true>, kDegridThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, degridder_kernel<L, C, true>, degrid_threads(C), smem);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   *persistent_blocks = per_sm * sms;
   return int(e);
 }
 
-template <int L>
+template <int L, int C>
 static int launch_degridder_t(const DegridArgs& a, int n_items, int persistent_blocks, void* stream) {
-  const size_t smem = degridder_smem<L>(a.g.nodes);
+  const size_t smem = degridder_smem<C>(a.g.nodes);
   if (n_items <= 0) return 0;
   if (persistent_blocks > 0)
-    degridder_kernel<L, true><<<persistent_blocks < n_items ? persistent_blocks : n_items, kDegridThreads, smem,
-                                cudaStream_t(stream)>>>(a);
+    degridder_kernel<L, C, true><<<persistent_blocks < n_items ? persistent_blocks : n_items, degrid_threads(C),
+                                   smem, cudaStream_t(stream)>>>(a);
   else
-    degridder_kernel<L, false><<<n_items, kDegridThreads, smem, cudaStream_t(stream)>>>(a);
+    degridder_kernel<L, C, false><<<n_items, degrid_threads(C), smem, cudaStream_t(stream)>>>(a);
   return int(cudaGetLastError());
 }
 
-int launch_degridder(int L, const DegridArgs& a, int n_items, int persistent_blocks, void* stream) {
-  switch (L) {
-    case 32: return launch_degridder_t<32>(a, n_items, persistent_blocks, stream);
-    case 64: return launch_degridder_t<64>(a, n_items, persistent_blocks, stream);
-    case 96: return launch_degridder_t<96>(a, n_items, persistent_blocks, stream);
-    case 128: return launch_degridder_t<128>(a, n_items, persistent_blocks, stream);
+template <int L>
+static int launch_degridder_l(const DegridArgs& a, int channels, int n_items, int persistent_blocks, void* stream) {
+  switch (channels) {
+    case 1: return launch_degridder_t<L, 1>(a, n_items, persistent_blocks, stream);
+    case 2: return launch_degridder_t<L, 2>(a, n_items, persistent_blocks, stream);
+    case 4: return launch_degridder_t<L, 4>(a, n_items, persistent_blocks, stream);
     default: return int(cudaErrorInvalidValue);
   }
 }
 
-int configure_degridder(int L, int nodes, int* persistent_blocks) {
+template <int L>
+static int configure_degridder_l(int nodes, int channels, int* persistent_blocks) {
+  switch (channels) {
+    case 1: return configure_degridder_t<L, 1>(nodes, persistent_blocks);
+    case 2: return configure_degridder_t<L, 2>(nodes, persistent_blocks);
+    case 4: return configure_degridder_t<L, 4>(nodes, persistent_blocks);
+    default: return int(cudaErrorInvalidValue);
+  }
+}
+
+bool supported_degrid_channels(int channels) { return channels == 1 || channels == 2 || channels == 4; }
+
+int launch_degridder(int L, int channels, const DegridArgs& a, int n_items, int persistent_blocks, void* stream) {
   switch (L) {
-    case 32: return configure_degridder_t<32>(nodes, persistent_blocks);
-    case 64: return configure_degridder_t<64>(nodes, persistent_blocks);
-    case 96: return configure_degridder_t<96>(nodes, persistent_blocks);
-    case 128: return configure_degridder_t<128>(nodes, persistent_blocks);
+    case 32: return launch_degridder_l<32>(a, channels, n_items, persistent_blocks, stream);
+    case 64: return launch_degridder_l<64>(a, channels, n_items, persistent_blocks, stream);
+    case 96: return launch_degridder_l<96>(a, channels, n_items, persistent_blocks, stream);
+    case 128: return launch_degridder_l<128>(a, channels, n_items, persistent_blocks, stream);
+    default: return int(cudaErrorInvalidValue);
+  }
+}
+
+int configure_degridder(int L, int nodes, int channels, int* persistent_blocks) {
+  switch (L) {
+    case 32: return configure_degridder_l<32>(nodes, channels, persistent_blocks);
+    case 64: return configure_degridder_l<64>(nodes, channels, persistent_blocks);
+    case 96: return configure_degridder_l<96>(nodes, channels, persistent_blocks);
+    case 128: return configure_degridder_l<128>(nodes, channels, persistent_blocks);
     default: return int(cudaErrorInvalidValue);
   }
 }

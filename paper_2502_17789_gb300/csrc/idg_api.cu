@@ -48,6 +48,7 @@ struct idg_plan {
   int32_t L = 0, N = 0;
   int32_t k_min = 0, n_layers = 1;  // w layers of the master grid
   int32_t npol = 4;                  // master-grid planes per layer: 4, or 1 with IDG_STOKES_I
+  int32_t degrid_channels = 1;       // channels per degridder lane
   cudaStream_t stream = nullptr;
   bool host_only = false;
   Partition part;
@@ -308,6 +309,8 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     return set_err(nullptr, IDG_ERR_INVALID_ARG, "unknown taper_kind");
   if (g->taper_kind == IDG_TAPER_USER && !g->taper_user)
     return set_err(nullptr, IDG_ERR_INVALID_ARG, "taper_user is NULL");
+  if (g->degrid_channels != 0 && !supported_degrid_channels(g->degrid_channels))
+    return set_err(nullptr, IDG_ERR_INVALID_ARG, "degrid_channels must be 0, 1, 2 or 4");
 
   idg_plan* p = new (std::nothrow) idg_plan();
   if (!p) return set_err(nullptr, IDG_ERR_OOM, "host allocation failed");
@@ -358,6 +361,17 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
   p->k_min = k_lo;
   p->n_layers = k_hi - k_lo + 1;
   p->npol = (g->flags & IDG_STOKES_I) ? 1 : 4;
+  // channel groups per degridder lane: rotation by the channel-step phasor
+  // needs one step along the whole band (equal to 1e-12 relative)
+  {
+    bool uniform = true;
+    for (int c = 2; c < n_channels && uniform; ++c) {
+      const double s1 = freqs_hz[1] - freqs_hz[0], sc = freqs_hz[c] - freqs_hz[c - 1];
+      uniform = std::fabs(sc - s1) <= 1e-12 * std::fabs(s1);
+    }
+    const int want = g->degrid_channels > 0 ? g->degrid_channels : kDefaultDegridChannels;
+    p->degrid_channels = uniform ? want : 1;
+  }
   for (SubgridDesc& d : p->exec) d.layer -= k_lo;  // device tables hold the grid plane set
   if (host_only) {
     *out = p;
@@ -395,22 +409,27 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     });
     for (int32_t o : order)
       for (int t = 0; t < tiles; ++t) gitems.push_back(GridItem{o, t});
-    // degridder items: pieces of <= kDegridMaxVis visibilities of one
-    // segment; a piece that ends its segment shares its item with the first
-    // piece of the next segment when both fit
+    // degridder items: pieces of <= `lanes` channel groups of one segment
+    // (a segment's rows times G groups per row); a piece that ends its
+    // segment shares its item with the first piece of the next segment when
+    // both fit
+    const int lanes = degrid_lanes(p->degrid_channels);
     for (int32_t o : order) {
       const SubgridDesc& d = p->exec[s0 + o];
+      const int width = d.c1 - d.c0;
+      const int G = (width + p->degrid_channels - 1) / p->degrid_channels;
       bool open = false;  // the last item can take a piece of the next segment
       for (int gidx = d.seg_begin; gidx < d.seg_begin + d.seg_count; ++gidx) {
         const SegmentDesc& sgd = p->part.segments[gidx];
-        for (int k = sgd.k_begin; k < sgd.k_end; k += kDegridMaxVis) {
-          const int ke = std::min(k + kDegridMaxVis, sgd.k_end);
-          if (open && k == sgd.k_begin && ditems.back().k_end - ditems.back().k_begin + (ke - k) <= kDegridMaxVis) {
+        const int g_begin = sgd.k_begin / width * G, g_end = sgd.k_end / width * G;
+        for (int k = g_begin; k < g_end; k += lanes) {
+          const int ke = std::min(k + lanes, g_end);
+          if (open && k == g_begin && ditems.back().k_end - ditems.back().k_begin + (ke - k) <= lanes) {
             ditems.back().k_end = ke;  // second segment of the item
             open = false;
           } else {
             ditems.push_back(DegridItem{o, gidx, k, ke, ke, 0});
-            open = ke == sgd.k_end;
+            open = ke == g_end;
           }
         }
       }
@@ -441,7 +460,7 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
   int pg = 0, pd = 0;
   int e = configure_kernels(L);
   if (!e) e = configure_gridder(L, &pg);
-  if (!e) e = configure_degridder(L, g->aterm_nodes, &pd);
+  if (!e) e = configure_degridder(L, g->aterm_nodes, p->degrid_channels, &pd);
   if (g->flags & IDG_PERSISTENT) {
     p->persistent_grid_blocks = pg;
     p->persistent_degrid_blocks = pd;
@@ -630,7 +649,8 @@ idg_status idg_degrid(idg_plan* plan, const void* grid_c128, const void* aterms_
     da.scratch = plan->d_scratch;
     da.g = kgeom(plan);
     e = timed(plan, kDegridder, [&] {
-      return launch_degridder(L, da, b.di_count, plan->persistent_degrid_blocks, plan->stream);
+      return launch_degridder(L, plan->degrid_channels, da, b.di_count, plan->persistent_degrid_blocks,
+                              plan->stream);
     });
     if (e) return cuda_err(plan, e, "degridder launch");
   }
@@ -926,6 +946,7 @@ idg_status idg_plan_stats(const idg_plan* plan, idg_plan_stats_t* out) {
   out->n_pol = plan->npol;
   out->w_layer_min = plan->k_min;
   out->w_layer_step = plan->part.w_step;
+  out->degrid_channels = plan->degrid_channels;
   return IDG_OK;
 }
 

@@ -51,9 +51,13 @@ struct GridItem {
   int32_t tile;  // row tile
 };
 
-// Degridder work item: up to kDegridMaxVis visibilities of one segment.
-// Visibilities [k_begin, k_mid) belong to segment `segment`, [k_mid, k_end)
-// (if any) to segment `segment` + 1 of the same subgrid.
+// Degridder work item: up to degrid_lanes(C) lanes of one or two segments,
+// a lane being a channel group -- up to C consecutive channels of one
+// timestep row.  A subgrid row of nc channels has G = ceil(nc / C) groups,
+// numbered row-major over the subgrid (group g = row * G + gi covers channels
+// c0 + gi nc / G .. c0 + (gi + 1) nc / G - 1).  Groups [k_begin, k_mid) belong
+// to segment `segment`, [k_mid, k_end) (if any) to segment `segment` + 1 of
+// the same subgrid.  With C = 1 a group is one visibility.
 struct DegridItem {
   int32_t sg;       // index into the batch's device subgrid table
   int32_t segment;  // global index of the first segment
@@ -61,7 +65,9 @@ struct DegridItem {
   int32_t pad;
 };
 
-constexpr int kDegridMaxVis = 256;
+// lanes (channel groups) per degridder work item for C channels per lane
+__host__ __device__ constexpr int degrid_lanes(int C) { return C == 1 ? 256 : 128; }
+constexpr int kDefaultDegridChannels = 1;  // channels per degridder lane when the geometry leaves it 0
 constexpr int kMaxAtermNodes = 25;  // A-term samples per axis (bounds the degridder's shared memory)
 constexpr int kDegridSegs = 2;  // segments per degridder work item
 
@@ -184,7 +190,9 @@ struct FftArgs {
 // persistent_blocks > 0: persistent launch of that many blocks draining a.queue
 int launch_gridder(int L, const GridArgs& a, int n_items, int persistent_blocks, void* stream);
 int configure_gridder(int L, int* persistent_blocks);   // attributes + persistent grid size
-int configure_degridder(int L, int nodes, int* persistent_blocks);
+// channels: channels per degridder lane (1, 2 or 4; > 1 needs uniform channel spacing)
+int configure_degridder(int L, int nodes, int channels, int* persistent_blocks);
+bool supported_degrid_channels(int channels);
 int launch_stage_records(int L, const StageArgs& a, int n_subgrids, void* stream);
 // element-wise pass over the 4 N x N complex128 planes of one w layer (image-domain wrapper):
 // out (+)= in * c * w[x] w[y] * (-1)^(x+y) * e^{i 2 pi w0 n'(x,y)}; w may be null
@@ -199,7 +207,7 @@ int launch_image_pass(int npol, const double2* in, double2* out, const double* w
 int launch_wait_selftest(int* status, int64_t limit_ns, void* stream);
 // flags[i][s] = 1 when every node of A-term (interval i, station s) has zero off-diagonal entries
 int launch_aterm_flags(const float2* aterms, uint8_t* flags, int n_int, int n_st, int nodes, void* stream);
-int launch_degridder(int L, const DegridArgs& a, int n_items, int persistent_blocks, void* stream);
+int launch_degridder(int L, int channels, const DegridArgs& a, int n_items, int persistent_blocks, void* stream);
 // mode 0: FFT + add into grid; mode 1: FFT in place in scratch (inspection)
 int launch_fft_adder(int L, const FftArgs& a, int n_subgrids, int mode, void* stream);
 int launch_splitter_ifft(int L, const FftArgs& a, int n_subgrids, void* stream);

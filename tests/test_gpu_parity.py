@@ -37,10 +37,10 @@ def _oracle_geom(oracle_mod, obs, L, flags):
 
 
 class Case:
-    def __init__(self, idg_mod, oracle_mod, obs, A, vis, L=None, flags=0):
+    def __init__(self, idg_mod, oracle_mod, obs, A, vis, L=None, flags=0, degrid_channels=0):
         import torch
         self.obs, self.L = obs, L or obs.subgrid_size
-        self.plan = idg_mod.Plan(obs, subgrid_size=self.L, flags=flags)
+        self.plan = idg_mod.Plan(obs, subgrid_size=self.L, flags=flags, degrid_channels=degrid_channels)
         self.geom = _oracle_geom(oracle_mod, obs, self.L, flags)
         self.ref_plan = oracle_mod.plan(self.geom, obs.uvw, obs.freqs, obs.aterm_offsets)
         np.testing.assert_array_equal(self.plan.subgrids(), self.ref_plan.subgrids)
@@ -139,6 +139,33 @@ def test_reduced_mwa_like_random_aterms(idg_mod, oracle_mod, cuda_device, L, spl
     for Gin in (G_ref, Grand):
         V_ref = c.oracle_degrid(Gin)
         assert _degrid_err(c.gpu_degrid(Gin), V_ref) < DEGRID_TOL
+
+
+@pytest.mark.parametrize("channels", [1, 2, 4])
+@pytest.mark.parametrize("L,n_ch", [(32, 17), (64, 7), (96, 24), (128, 13)])
+def test_degrid_channel_groups(idg_mod, oracle_mod, cuda_device, channels, L, n_ch):
+    """Degridder lanes of 1, 2 or 4 channels (the first by sine and cosine,
+    the rest by rotation with the channel-step phasor): ragged and balanced
+    groups (17 channels in groups of 4 are 5 groups of 3 or 4), two segments
+    per work item, one block per item and the persistent queue."""
+    import torch
+    obs = synth.config(2, n_stations=8, n_timesteps=11, n_channels=n_ch)
+    A, vis = _random_problem(900 + L + n_ch, obs, n_int=3)
+    rng = np.random.default_rng(L)
+    N = obs.grid_size
+    Grand = (rng.standard_normal((4, N, N)) + 1j * rng.standard_normal((4, N, N))) * 1e-3
+    c = Case(idg_mod, oracle_mod, obs, A, vis, L=L, degrid_channels=channels)
+    assert c.plan.stats().degrid_channels == channels
+    V_ref = c.oracle_degrid(Grand)
+    assert _degrid_err(c.gpu_degrid(Grand), V_ref) < DEGRID_TOL
+    pp = idg_mod.Plan(obs, subgrid_size=L, flags=idg_mod.IDG_PERSISTENT, degrid_channels=channels)
+    try:
+        V = torch.full(c.vis.shape, 7.0 + 7.0j, dtype=torch.complex64, device="cuda")
+        pp.degrid(torch.as_tensor(Grand).cuda(), c.A_d, V)
+        pp.synchronize()
+        assert _degrid_err(V.cpu().numpy(), V_ref) < DEGRID_TOL
+    finally:
+        pp.close()
 
 
 def test_grid_accumulates_into_existing_grid(idg_mod, oracle_mod, cuda_device):
@@ -312,6 +339,11 @@ def test_channel_spacing(idg_mod, oracle_mod, cuda_device, spacing):
     N = obs.grid_size
     Grand = (rng.standard_normal((4, N, N)) + 1j * rng.standard_normal((4, N, N))) * 1e-3
     c = Case(idg_mod, oracle_mod, obs, A, vis)
+    # the degridder's channel groups need one frequency step along the band
+    assert c.plan.stats().degrid_channels == 1
+    c4 = idg_mod.Plan(obs, degrid_channels=4)
+    assert c4.stats().degrid_channels == (1 if spacing != "single" else 4)
+    c4.close()
     assert _rel(c.gpu_grid(), c.oracle_grid()) < GRID_TOL
     assert _degrid_err(c.gpu_degrid(Grand), c.oracle_degrid(Grand)) < DEGRID_TOL
 

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
-def _setup(idg_mod, oracle_mod, seed=0, flags=0, oflags=0, obs=None, diagonal=None):
+def _setup(idg_mod, oracle_mod, seed=0, flags=0, oflags=0, obs=None, diagonal=None, degrid_channels=0):
     obs = obs or synth.config(2, seed=seed, n_stations=14, n_timesteps=12, n_channels=16)
     rng = np.random.default_rng(seed + 1)
     A = synth.aterms_random(rng, obs.n_intervals, obs.n_stations, obs.aterm_nodes)
@@ -22,7 +22,7 @@ def _setup(idg_mod, oracle_mod, seed=0, flags=0, oflags=0, obs=None, diagonal=No
         A[::2, ::2, ..., 1:3] = 0.0
         A[1::2, 1::2, ..., 1:3] = 0.0
     vis = synth.random_visibilities(rng, obs).astype(np.complex64)
-    plan = idg_mod.Plan(obs, flags=idg_mod.IDG_STOKES_I | flags)
+    plan = idg_mod.Plan(obs, flags=idg_mod.IDG_STOKES_I | flags, degrid_channels=degrid_channels)
     geom = oracle_mod.Geometry(obs.grid_size, obs.subgrid_size, obs.kernel_padding, obs.image_size,
                                aterm_nodes=obs.aterm_nodes, flags=oracle_mod.FLAG_STOKES_I | oflags)
     pl = oracle_mod.plan(geom, obs.uvw, obs.freqs, obs.aterm_offsets)
@@ -57,6 +57,27 @@ def test_stokes_i_grid_and_degrid(idg_mod, oracle_mod, cuda_device, persistent, 
     assert derr < TOL, derr
     if diagonal == "all":
         assert not V.cpu().numpy()[..., 1:3].any()
+    plan.close()
+
+
+@pytest.mark.parametrize("channels,diagonal", [(2, "all"), (4, "all"), (4, "mixed")])
+def test_stokes_i_degrid_channel_groups(idg_mod, oracle_mod, cuda_device, channels, diagonal):
+    """Stokes-I prediction with 2 or 4 channels per degridder lane (rotation
+    by the channel-step phasor), on the XX/YY-only path (diagonal A-terms)
+    and with items that mix it with full Jones matrices."""
+    import torch
+    obs, A, vis, plan, geom, pl, args = _setup(idg_mod, oracle_mod, seed=5, diagonal=diagonal,
+                                                degrid_channels=channels)
+    assert plan.stats().degrid_channels == channels
+    rng = np.random.default_rng(10)
+    N = obs.grid_size
+    Gr = (rng.standard_normal((1, N, N)) + 1j * rng.standard_normal((1, N, N))) * 1e-3
+    V = torch.empty(vis.shape, dtype=torch.complex64, device="cuda")
+    plan.degrid(torch.as_tensor(Gr).cuda(), torch.as_tensor(A).cuda(), V)
+    plan.synchronize()
+    V_ref = oracle_mod.degrid(*args, Gr, A.astype(np.complex128))
+    derr = np.sqrt(np.mean(np.abs(V.cpu().numpy() - V_ref) ** 2)) / np.abs(V_ref).max()
+    assert derr < TOL, derr
     plan.close()
 
 
