@@ -48,11 +48,22 @@ FLOP_PER_VISPX = 34.0            # 16 FMA (4-pol complex MAC) + 1 FMA (phase) = 
 SM_MAX_MHZ_FALLBACK = 2070.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "kernel_traffic.json")
 CSRC = os.path.join(ROOT, "paper_2502_17789_gb300", "csrc")
-# the capture that --record-traffic reads (one pass per launch, full-size workload)
-NCU_LAUNCH_LIST = ('ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum '
-                   '--clock-control none -k regex:"gridder|fft|splitter|stage|aterm" -c 300 --csv '
-                   '--log-file launches.csv python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e '
-                   '--serving-requests 0 --image-steps 0 --stokes-steps 0 --wlayer-steps 0 --normalize-steps 0')
+# ncu recipes behind profiles/: the launch list of the bench's own workload (device time of every
+# launch, one pass), and per kernel the DRAM bytes of its first two launches on the 90-station
+# reduction of the same workload (a few GB on the device), which --record-traffic scales to a
+# full-size launch by the algorithmic bytes of the two launches
+BENCH_SHORT = ('python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e --serving-requests 0 '
+               '--image-steps 0 --stokes-steps 0 --wlayer-steps 0 --normalize-steps 0 --uneven-steps 0 '
+               '--small-steps 0')
+NCU_LAUNCH_LIST = ('ncu --metrics gpu__time_duration.sum --clock-control none --kernel-name-base demangled '
+                   '-k regex:"idg::" -c 400 --csv --log-file launches.csv ' + BENCH_SHORT)
+TRAFFIC_STATIONS = 90
+
+
+def ncu_traffic_command(kern: str) -> str:
+    return (f'ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none '
+            f'--kernel-name-base demangled -k regex:"idg::{kern}_kernel<" -c 2 --csv '
+            f'--log-file traffic_{kern}.csv {BENCH_SHORT} --stations {TRAFFIC_STATIONS}')
 KERNEL_SOURCES = {"gridder": ["gridder.cu", "kernels_common.cuh", "idg_internal.h"],
                   "degridder": ["degridder.cu", "kernels_common.cuh", "idg_internal.h"]}
 
@@ -77,10 +88,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (small profiling runs)")
     ap.add_argument("--stations", type=int, default=None, help="reduce the workload's stations (profiling)")
     ap.add_argument("--timesteps", type=int, default=None, help="reduce the workload's timesteps (profiling)")
-    ap.add_argument("--record-traffic", metavar="NCU_CSV", default=None,
-                    help="read an ncu launch list (--csv, with dram__bytes_read.sum and dram__bytes_write.sum) "
-                         "of this command's default workload and store the per-launch DRAM bytes of the gridder "
-                         "and degridder, keyed by the digest of their sources, in profiles/kernel_traffic.json")
+    ap.add_argument("--record-traffic", metavar="DIR", default=None,
+                    help="read traffic_gridder.csv and traffic_degridder.csv (the ncu_traffic_command captures) "
+                         "from DIR and store each kernel's DRAM bytes per launch, scaled to a launch of the "
+                         "default workload and keyed by the digest of its sources, in profiles/kernel_traffic.json")
     ap.add_argument("--image-steps", type=int, default=2,
                     help="timed invert + predict calls of the image-domain wrapper; 0 = skip")
     ap.add_argument("--stokes-steps", type=int, default=5,
@@ -91,6 +102,11 @@ def parse_args():
     ap.add_argument("--normalize-steps", type=int, default=3,
                     help="timed grid and invert calls with the A-term power normalisation "
                          "(IDG_NORMALIZE_ATERM) on the same workload; 0 = skip")
+    ap.add_argument("--uneven-steps", type=int, default=2,
+                    help="timed CUDA-graph replays of grid + degrid of the 256-station uneven workload "
+                         "(352.5 M visibilities, 8192^2 grid, L = 64); 0 = skip")
+    ap.add_argument("--small-steps", type=int, default=50,
+                    help="timed CUDA-graph replays of grid + degrid of the small 32-station workload; 0 = skip")
     ap.add_argument("--serving-requests", type=int, default=24,
                     help="requests of the serving comparison (batched vs plain at 2x plain capacity); 0 = skip")
     ap.add_argument("--aterms", choices=["beam", "full"], default="beam",
@@ -233,11 +249,31 @@ def _oracle_sample(obs, aterms_np, vis_np, grid_np, budget_s: float, seed: int =
     return pl, nv, n, run
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(obs, aterms_np, vis_np, grid_np, budget_s):
     pl, nv, n, run = _oracle_sample(obs, aterms_np, vis_np, grid_np, budget_s)
     t = run(pl)
     cores = os.cpu_count()
-    return {"value": 2.0 * nv / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": 2.0 * nv / t, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
             "sample": f"{n} seeded-random subgrids ({nv} visibilities) of the workload, grid + degrid, "
                       f"FP64 C oracle with OpenMP over subgrids, {t:.1f} s",
             "seconds": t}
@@ -270,36 +306,164 @@ def recorded_traffic(kern: str, workload: str):
     return entry.get("dram_bytes_per_launch")
 
 
-def record_traffic(csv_path: str, workload: str, command: str):
+def algorithmic_bytes_per_launch(kern: str, obs, L: int) -> float:
+    """DRAM bytes a launch must move, averaged over the plan's batches:
+    gridder 128 B staged record read per visibility + 32 B subgrid image
+    written per pixel; degridder 32 B image read per pixel + 32 B per
+    visibility written (host-only plan, no device work)."""
+    from paper_2502_17789_gb300 import idg
+
+    g, keep = idg.make_geometry(obs.grid_size, L, obs.kernel_padding, obs.image_size, aterm_nodes=obs.aterm_nodes,
+                                flags=idg.IDG_HOST_ONLY)
+    h = idg.idg_plan_create(g, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets)
+    try:
+        st = idg.idg_plan_stats(h)
+    finally:
+        idg.idg_plan_destroy(h)
+    n_sg = st.n_subgrids - st.n_subgrids_dropped
+    n_vis = st.n_vis - st.n_vis_dropped
+    # the same batching rule as the library (1 GiB of subgrid images per batch)
+    per_sg = 4 * L * L * 8
+    n_batches = max(1, -(-n_sg // max(1, (1 << 30) // per_sg)))
+    pix = n_sg * L * L * 32.0
+    total = (128.0 * n_vis + pix) if kern == "gridder" else (pix + 32.0 * n_vis)
+    return total / n_batches
+
+
+def record_traffic(folder: str, full_obs, workload: str):
+    """Per-launch DRAM bytes (read + write) of the gridder and degridder from
+    their captures on the 90-station case, scaled to a full-size launch by
+    the ratio of algorithmic bytes per launch."""
     import csv
     import collections
+    from paper_2502_17789_gb300 import synth
+
     scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
-    with open(csv_path) as f:
-        rows = [r for r in csv.reader(f)]
-    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "Metric Name" in r)
-    h = rows[hi]
-    ki, mi, vi, ui, ii = (h.index(k) for k in ("Kernel Name", "Metric Name", "Metric Value", "Metric Unit", "ID"))
-    per = collections.defaultdict(lambda: [None, 0.0, 0])
-    for r in rows[hi + 1:]:
-        if len(r) <= vi or r[mi] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
-            continue
-        name = r[ki]
-        kern = "degridder" if "degridder_kernel" in name else ("gridder" if "gridder_kernel" in name else None)
-        if kern is None or "noalloc" in name:
-            continue
-        e = per[r[ii]]
-        e[0] = kern
-        e[1] += float(r[vi].replace(",", "")) * scale.get(r[ui], 1.0)
+    small = synth.config(2, seed=0, n_stations=TRAFFIC_STATIONS)
     out = {}
     for kern in KERNEL_SOURCES:
-        vals = [v[1] for v in per.values() if v[0] == kern]
-        if vals:
-            out[kern] = {"dram_bytes_per_launch": sum(vals) / len(vals), "launches": len(vals),
-                         "source_sha256": source_digest(kern), "workload": workload, "command": command}
+        with open(os.path.join(folder, f"traffic_{kern}.csv")) as f:
+            rows = [r for r in csv.reader(f)]
+        hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "Metric Name" in r)
+        h = rows[hi]
+        ki, mi, vi, ui, ii = (h.index(k) for k in ("Kernel Name", "Metric Name", "Metric Value", "Metric Unit", "ID"))
+        per = collections.defaultdict(float)
+        for r in rows[hi + 1:]:
+            if len(r) > vi and r[mi] in ("dram__bytes_read.sum", "dram__bytes_write.sum") and \
+                    f"{kern}_kernel" in r[ki] and not (kern == "gridder" and "degridder" in r[ki]):
+                per[r[ii]] += float(r[vi].replace(",", "")) * scale.get(r[ui], 1.0)
+        if not per:
+            continue
+        measured = sum(per.values()) / len(per)
+        alg_small = algorithmic_bytes_per_launch(kern, small, small.subgrid_size)
+        alg_full = algorithmic_bytes_per_launch(kern, full_obs, full_obs.subgrid_size)
+        out[kern] = {"dram_bytes_per_launch": measured * alg_full / alg_small,
+                     "captured_bytes_per_launch": measured, "captured_launches": len(per),
+                     "captured_over_algorithmic": measured / alg_small,
+                     "algorithmic_bytes_per_launch": alg_full,
+                     "source_sha256": source_digest(kern), "workload": workload,
+                     "command": ncu_traffic_command(kern) + f"; python bench.py --record-traffic <dir>",
+                     "note": f"captured on the {TRAFFIC_STATIONS}-station case, scaled to a full-size launch "
+                             "by algorithmic bytes per launch"}
     with open(TRAFFIC_FILE, "w") as f:
         json.dump(out, f, indent=1, sort_keys=True)
         f.write("\n")
     print(json.dumps(out, indent=1))
+
+
+def _graph_legs(plan, vis, A, G, out, steps, side):
+    """Mean ms of grid and degrid CUDA-graph replays, after one warm-up replay."""
+    import torch
+    plan.grid_graph(vis, A, G)
+    plan.degrid_graph(G, A, out)
+    plan.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    g_ms = d_ms = 0.0
+    for _ in range(steps):
+        e[0].record(side)
+        plan.grid_graph(vis, A, G)
+        e[1].record(side)
+        plan.degrid_graph(G, A, out)
+        e[2].record(side)
+        plan.synchronize()
+        g_ms += e[0].elapsed_time(e[1])
+        d_ms += e[1].elapsed_time(e[2])
+    return g_ms / steps, d_ms / steps
+
+
+def _kernel_fracs(plan, vis, A, G, out, n_sm, sm_max, r_vp_meas):
+    """Per-kernel device time of one profiled (non-graph) grid + degrid, and
+    the gridder's and degridder's fractions of the nominal and measured R_vp."""
+    plan.profile(True)
+    plan.profile_read()
+    plan.grid(vis, A, G)
+    plan.degrid(G, A, out)
+    prof = plan.profile_read()
+    plan.profile(False)
+    vispx = float(plan.stats().vis_pixels)
+    r_vp_nom = n_sm * FP32_LANES_PER_SM * sm_max * 1e6 / (FLOP_PER_VISPX / 2.0)
+    kern = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}
+    for k in ("gridder", "degridder"):
+        if prof[k][0] > 0:
+            r = vispx / (prof[k][0] * 1e-3)
+            kern[k].update(vispx_per_s=r, frac_nominal=round(r / r_vp_nom, 4), frac_measured=round(r / r_vp_meas, 4))
+    return kern
+
+
+def uneven_leg(idg, synth, dev, steps, n_sm, sm_max, r_vp_meas):
+    import torch
+    t0 = time.time()
+    obs = synth.config(4, seed=0)
+    model = synth.beam_screen_model(np.random.default_rng(0), rms_rad=2.0)
+    A = torch.as_tensor(synth.aterms_beam_screen(obs, model), device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    vis = torch.randn((obs.n_baselines, obs.n_timesteps, obs.n_channels, 4), dtype=torch.complex64, device=dev,
+                      generator=g)
+    side = torch.cuda.Stream(dev)
+    L = 64
+    plan = idg.Plan(obs, subgrid_size=L, stream=side.cuda_stream)
+    t_plan = time.time() - t0
+    st = plan.stats()
+    N = obs.grid_size
+    G = torch.zeros((4, N, N), dtype=torch.complex128, device=dev)
+    out = torch.empty_like(vis)
+    torch.cuda.synchronize(dev)
+    g_ms, d_ms = _graph_legs(plan, vis, A, G, out, steps, side)
+    kern = _kernel_fracs(plan, vis, A, G, out, n_sm, sm_max, r_vp_meas)
+    sg = plan.subgrids()
+    nv = (sg[:, 2] - sg[:, 1]) * (sg[:, 4] - sg[:, 3])
+    res = {"value": 2.0 * obs.n_vis / ((g_ms + d_ms) * 1e-3), "unit": UNIT, "steps": steps,
+           "workload": "256 stations, log-normal radii (median 300 m, <= 3 km), 32640 baselines, 360 x 0.5 s, "
+                       "30 ch 140-170 MHz, 8192^2 FP64 grid, L = 64, P = 18, FOV 0.5, A-terms every 4 s "
+                       "(beam x screen), random visibilities",
+           "n_vis": int(obs.n_vis), "launch": "one block per work item (autotuned on GB300), CUDA-graph replay",
+           "graph_replay_ms": {"grid": g_ms, "degrid": d_ms}, "subgrids": int(st.n_subgrids),
+           "vis_per_subgrid_min_median_max": [int(nv.min()), int(np.median(nv)), int(nv.max())],
+           "vis_pixels_per_direction": float(st.vis_pixels), "kernels": kern, "plan_seconds": t_plan}
+    plan.close()
+    del G, out, vis
+    torch.cuda.empty_cache()
+    return res
+
+
+def small_leg(idg, dev, steps, n_sm, sm_max, r_vp_meas):
+    import torch
+    obs, A, vis, _ = make_workload(1, dev)
+    side = torch.cuda.Stream(dev)
+    plan = idg.Plan(obs, stream=side.cuda_stream)
+    N = obs.grid_size
+    G = torch.zeros((4, N, N), dtype=torch.complex128, device=dev)
+    out = torch.empty_like(vis)
+    torch.cuda.synchronize(dev)
+    g_ms, d_ms = _graph_legs(plan, vis, A, G, out, steps, side)
+    kern = _kernel_fracs(plan, vis, A, G, out, n_sm, sm_max, r_vp_meas)
+    res = {"value": 2.0 * obs.n_vis / ((g_ms + d_ms) * 1e-3), "unit": UNIT, "steps": steps,
+           "workload": workload_description(1, obs), "n_vis": int(obs.n_vis),
+           "launch": "one block per work item, CUDA-graph replay", "graph_replay_ms": {"grid": g_ms, "degrid": d_ms},
+           "kernels": kern}
+    plan.close()
+    return res
 
 
 def run_native(args):
@@ -317,20 +481,27 @@ def run_native(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     libbuild.build()
-    obs, A_d, vis_d, desc = make_workload(args.workload, dev, args.stations, args.timesteps, args.aterms)
+    obs, A_d, vis_full, desc = make_workload(args.workload, dev, args.stations, args.timesteps, args.aterms)
     stream = torch.cuda.current_stream(dev)
-    plan = idg.Plan(obs, stream=stream.cuda_stream)
+    # N GPUs share one observation (Section 3.5: workers own subsets of the data): rank r grids the
+    # baselines r, r + N, ... into its own FP64 master-grid replica, one all-reduce sums the replicas,
+    # and every rank degrids its own baselines from the (replicated) model grid
+    obs_r, shard = parallel.shard_observation(obs, rank, world)
+    vis_d = vis_full if world == 1 else vis_full[torch.as_tensor(shard, device=dev)].contiguous()
+    del vis_full
+    plan = idg.Plan(obs_r, stream=stream.cuda_stream)
     st = plan.stats()
     N = obs.grid_size
     G_model = torch.zeros((4, N, N), dtype=torch.complex128, device=dev)
     plan.grid(vis_d, A_d, G_model)                     # the model grid the degrid leg predicts from
+    if world > 1:
+        parallel.reduce_grids(G_model)
     G_out = torch.empty_like(G_model)
     vis_pred = torch.empty_like(vis_d)
 
     def step():
-        G_out.zero_()
-        plan.grid(vis_d, A_d, G_out)
-        plan.degrid(G_model, A_d, vis_pred)
+        parallel.sharded_step(lambda g: plan.grid(vis_d, A_d, g), lambda: plan.degrid(G_model, A_d, vis_pred),
+                              G_out, world)
 
     for _ in range(args.warmup):
         step()
@@ -357,7 +528,7 @@ def run_native(args):
     plan.profile(False)
     if world > 1:
         ms = parallel.max_over_ranks(ms, device=dev)
-    total_vis = 2.0 * obs.n_vis * args.steps * world
+    total_vis = 2.0 * obs.n_vis * args.steps   # the whole observation, over all ranks
     value = total_vis / (ms * 1e-3)
 
     # roofline of the dominant kernel (gridder or degridder), live from the timed region
@@ -384,6 +555,22 @@ def run_native(args):
                 "launches": k_launches, "avg_launch_ms": k_ms / max(k_launches, 1)}
     if clocks.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = round(achieved / (peak_tflops * clocks["sm_mhz"] / sm_max), 4)
+    # the same fractions against the rates the library's probe kernels measure on this device (FP32
+    # FMA and __sincosf throughput): R_vp = min(F_fma / 17, F_sincos), one sincos per visibility-pixel
+    f_fma, f_sin = idg.idg_peak_rates(stream.cuda_stream)
+    clk = float(clocks.get("sm_mhz") or sm_max) * 1e6
+    r_vp_meas = min(f_fma / (FLOP_PER_VISPX / 2.0), f_sin)
+    r_vp_nom = n_sm * FP32_LANES_PER_SM * sm_max * 1e6 / (FLOP_PER_VISPX / 2.0)
+    roofline["peak_measured"] = {
+        "fma_per_s": f_fma, "sincos_per_s": f_sin, "vispx_per_s": r_vp_meas,
+        "fma_lanes_per_clk_per_sm": f_fma / (n_sm * clk), "sincos_per_clk_per_sm": f_sin / (n_sm * clk),
+        "clock_mhz": clk / 1e6,
+        "basis": "idg_peak_rates: independent f32x2 FMA chains and __sincosf chains on every SM, CUDA events; "
+                 "R_vp = min(F_fma / 17, F_sincos)"}
+    roofline["frac_measured"] = round(achieved_vispx / r_vp_meas, 4)
+    roofline["kernel_fractions"] = {
+        k: {"vispx_per_s": vispx / (prof[k][0] * 1e-3), "frac_nominal": round(vispx / (prof[k][0] * 1e-3) / r_vp_nom, 4),
+            "frac_measured": round(vispx / (prof[k][0] * 1e-3) / r_vp_meas, 4)} for k in ("gridder", "degridder")}
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps} for k, v in prof.items()}
     # the paper's kernel rates (Section 5.3: gridder 480 and degridder 400 M visibilities/s on an A100 at
     # 32 x 32 subgrids), beside this run's; a visibility costs L^2 pixel updates, so the per
@@ -399,6 +586,9 @@ def run_native(args):
     # image-domain wrapper (Eq. 11 / Eq. 12): invert = grid + master-grid transform + taper correction,
     # predict = the reverse; one timed call each after an untimed one that makes the cuFFT plan
     image_domain = None
+    if world > 1:   # the legs below are single-GPU diagnostics of the same build
+        args.image_steps = args.stokes_steps = args.wlayer_steps = args.normalize_steps = 0
+        args.uneven_steps = args.small_steps = 0
     if args.image_steps > 0:
         img = torch.empty_like(G_out)
         plan.invert(vis_d, A_d, G_out, img)
@@ -563,6 +753,8 @@ def run_native(args):
                     stream.wait_event(ev["grid_copied"][b])  # step k-2's grid has left gout_d[b]
                 gout_d[b].zero_()
                 plan.grid(vis_in[b], A_d, gout_d[b])
+                if world > 1:
+                    parallel.reduce_grids(gout_d[b])
                 ev["grid_done"][b].record(stream)
                 stream.wait_event(ev["gm_ready"][b])
                 if k >= 2:
@@ -591,7 +783,7 @@ def run_native(args):
         e2e_ms = t0.elapsed_time(t1)
         if world > 1:
             e2e_ms = parallel.max_over_ranks(e2e_ms, device=dev)
-        e2e = {"value": 2.0 * obs.n_vis * args.e2e_steps * world / (e2e_ms * 1e-3), "unit": UNIT,
+        e2e = {"value": 2.0 * obs.n_vis * args.e2e_steps / (e2e_ms * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(vis_h.numel() * 8 + gmodel_h.numel() * 16),
                "d2h_bytes_per_step": int(gout_h[0].numel() * 16 + vpred_h[0].numel() * 8),
                "ms_per_step": e2e_ms / args.e2e_steps,
@@ -599,6 +791,16 @@ def run_native(args):
                          "grid's H2D overlaps the gridding, the output grid's D2H the degridding, and the "
                          "neighbouring steps' copies the kernels"}
         del vis_in, gmodel_in, gout_d, vpred_d, gout_h, vpred_h
+
+    # the 256-station uneven workload (352.5 M visibilities, subgrids of 360 to 10800 visibilities,
+    # 8192^2 grid) at L = 64 with one block per work item, the autotuner's choice on GB300, as CUDA-graph
+    # replays; random visibilities (the work does not depend on their values)
+    uneven = None
+    if args.uneven_steps > 0 and args.stations is None and args.timesteps is None:
+        uneven = uneven_leg(idg, synth, dev, args.uneven_steps, n_sm, sm_max, r_vp_meas)
+    small = None
+    if args.small_steps > 0:
+        small = small_leg(idg, dev, args.small_steps, n_sm, sm_max, r_vp_meas)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the oracle baseline runs at N = 1 only
@@ -625,16 +827,17 @@ def run_native(args):
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded point-source sky through beam x phase-screen A-terms, noise)",
         "config": {"workload": desc, "n_vis": obs.n_vis, "form": "plain (one observation per call)",
                    "l2": "inputs larger than L2 (350 MB visibilities, 1 GiB grids); no flush",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "parallelism": (f"baseline shards x{world} (round-robin), one NCCL all-reduce of the FP64 grid "
+                                   f"per step" if world > 1 else "single GPU"),
                    "subgrids": st.n_subgrids, "segments": st.n_segments, "batches": st.n_batches,
                    "vis_pixels_per_direction": st.vis_pixels},
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches,
         "kernels": kernels, "image_domain": image_domain, "paper_context": paper_context, "stokes_i": stokes_i, "w_layers": w_layers,
-        "normalized": normalized, "serving": serving,
+        "normalized": normalized, "serving": serving, "uneven": uneven, "small": small,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -684,11 +887,10 @@ def run_reference(args):
 def main():
     args = parse_args()
     if args.record_traffic:
-        import torch  # noqa: F401  (make_workload's description only)
         from paper_2502_17789_gb300 import synth
         obs = synth.config(args.workload, seed=0, n_stations=args.stations, n_timesteps=args.timesteps)
         desc = workload_description(args.workload, obs, args.stations, args.timesteps, args.aterms)
-        record_traffic(args.record_traffic, desc, NCU_LAUNCH_LIST + "; python bench.py --record-traffic launches.csv")
+        record_traffic(args.record_traffic, obs, desc)
         return
     if args.impl == "reference":
         run_reference(args)

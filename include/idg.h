@@ -361,6 +361,22 @@ const char* idg_last_error(const idg_plan* plan);
  * stream, which is synchronised; other streams are not). NULL is a no-op. */
 idg_status idg_plan_destroy(idg_plan* plan);
 
+/*
+ * idg_peak_rates -- measured throughput of the two units the phasor sums use
+ * (Section 5.1: the kernels are bounded by the hardware's measured FP32
+ * rate).  Runs, on cuda_stream with every SM of the current device filled,
+ * one kernel of independent packed f32x2 FMA chains and one of independent
+ * __sincosf evaluations, each timed with CUDA events after a warm-up run.
+ *   fma_per_s     receives FP32 fused multiply-adds per second (an f32x2 FMA
+ *                 counts as two)
+ *   sincos_per_s  receives __sincosf evaluations per second (one sine and one
+ *                 cosine each)
+ * Allocates a few hundred KB (stream-ordered) and synchronises the stream.
+ * IDG_ERR_INVALID_ARG for NULL outputs, IDG_ERR_CUDA / IDG_ERR_OOM otherwise
+ * (message in idg_last_error(NULL)).
+ */
+idg_status idg_peak_rates(void* cuda_stream, double* fma_per_s, double* sincos_per_s);
+
 /* Library version (IDG_ABI_VERSION). */
 int32_t idg_abi_version(void);
 

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libidg.so")
-SOURCES = ["planner.cpp", "gridder.cu", "fft.cu", "degridder.cu", "idg_api.cu", "noalloc.cu", "image.cu"]
+SOURCES = ["planner.cpp", "gridder.cu", "fft.cu", "degridder.cu", "idg_api.cu", "noalloc.cu", "image.cu", "probe.cu"]
 HEADERS = ["idg_internal.h", "kernels_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")

@@ -28,7 +28,7 @@ IDG_NORMALIZE_ATERM, IDG_STOKES_I = 32, 64
 EXPORTS = ["idg_plan_create", "idg_grid", "idg_degrid", "idg_grid_graph", "idg_degrid_graph", "idg_set_stream", "idg_plan_stats", "idg_plan_subgrids",
            "idg_plan_segments", "idg_plan_layers", "idg_subgrid_images", "idg_synchronize", "idg_profile_enable", "idg_profile_read",
            "idg_grid_noalloc", "idg_invert", "idg_predict", "idg_wait_selftest", "idg_aterm_weights", "idg_last_error",
-           "idg_plan_destroy", "idg_abi_version"]
+           "idg_plan_destroy", "idg_abi_version", "idg_peak_rates"]
 KERNEL_CLASSES = ["gridder", "fft_adder", "splitter_ifft", "degridder", "stage", "aterm_flags"]
 
 
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.idg_invert.argtypes = [P, P, P, P, P]
     lib.idg_predict.argtypes = [P, P, P, P, P]
     lib.idg_profile_enable.argtypes = [P, i32]
+    lib.idg_peak_rates.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.idg_profile_read.argtypes = [P, P, P]
     lib.idg_last_error.argtypes = [P]
     lib.idg_last_error.restype = ctypes.c_char_p
@@ -231,6 +232,14 @@ def idg_last_error(plan=None) -> str:
 
 def idg_plan_destroy(plan):
     _check(load().idg_plan_destroy(plan), "idg_plan_destroy")
+
+
+def idg_peak_rates(stream=None) -> tuple[float, float]:
+    """(FP32 FMA per second, __sincosf evaluations per second) measured on the
+    current device by the library's probe kernels (see idg_peak_rates in idg.h)."""
+    f, s = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().idg_peak_rates(stream, ctypes.byref(f), ctypes.byref(s)), "idg_peak_rates")
+    return float(f.value), float(s.value)
 
 
 def idg_abi_version() -> int:

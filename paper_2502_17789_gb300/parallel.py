@@ -22,10 +22,27 @@ def shard_baselines(n_baselines: int, rank: int, world: int) -> np.ndarray:
 
 
 def reduce_grids(grid, group=None):
-    """Sum the ranks' master-grid replicas in place (all-reduce)."""
+    """Sum the ranks' master-grid replicas in place (all-reduce); complex
+    grids travel as their real and imaginary parts."""
+    import torch
     import torch.distributed as dist
 
-    dist.all_reduce(grid, op=dist.ReduceOp.SUM, group=group)
+    buf = torch.view_as_real(grid) if grid.is_complex() else grid
+    dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
+    return grid
+
+
+def sharded_step(grid_fn, degrid_fn, grid, world: int, group=None):
+    """One grid + degrid step of a rank that owns a baseline shard: zero its
+    master-grid replica, grid its visibilities into it (grid_fn(grid)), sum
+    the replicas over the ranks (the one exchange step; skipped on one rank),
+    then predict its visibilities from the model grid (degrid_fn()).  After
+    it every rank holds the grid of the whole observation."""
+    grid.zero_()
+    grid_fn(grid)
+    if world > 1:
+        reduce_grids(grid, group)
+    degrid_fn()
     return grid
 
 
@@ -37,6 +54,13 @@ def max_over_ranks(value: float, device=None, group=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
     return float(t.item())
+
+
+def shard_observation(obs, rank: int, world: int):
+    """(sub-observation, baseline indices) of `rank`'s round-robin shard;
+    the whole observation on one rank."""
+    bls = shard_baselines(obs.n_baselines, rank, world)
+    return (obs, bls) if world == 1 else (sub_observation(obs, bls), bls)
 
 
 def sub_observation(obs, baselines: np.ndarray):

@@ -1,6 +1,7 @@
 """Host logic of bench.py that needs no GPU: the DRAM-traffic record behind
-roofline.traffic (per-launch averages from an ncu launch list, keyed by the
-kernel sources' digest and the workload)."""
+roofline.traffic (per-launch averages of single-kernel ncu captures on the
+90-station case, scaled to a full-size launch by algorithmic bytes, keyed
+by the kernel sources' digest and the workload)."""
 import csv
 import json
 
@@ -29,38 +30,58 @@ def traffic_file(tmp_path, monkeypatch):
     return path
 
 
-def test_record_traffic_averages_per_launch(tmp_path, traffic_file):
-    g = "void idg::gridder_kernel<96, 8, 0, 0>(idg::GridArgs)"
-    d = "void idg::degridder_kernel<96, 0>(idg::DegridArgs)"
-    rows = [
+def _captures(tmp_path, gridder_rows, degridder_rows):
+    _write_launch_list(tmp_path / "traffic_gridder.csv", gridder_rows)
+    _write_launch_list(tmp_path / "traffic_degridder.csv", degridder_rows)
+    return str(tmp_path)
+
+
+@pytest.fixture(scope="module")
+def full_obs(idg_mod):
+    from paper_2502_17789_gb300 import synth
+    return synth.config(2, seed=0)
+
+
+def test_record_traffic_scales_per_launch_captures(tmp_path, traffic_file, full_obs):
+    """Each kernel's capture (its first launches on the 90-station case) is
+    averaged per launch and scaled to a full-size launch by the ratio of
+    algorithmic bytes per launch (host-only plans of both workloads)."""
+    from paper_2502_17789_gb300 import synth
+    g = "void idg::gridder_kernel<96, 8, false, false>(idg::GridArgs)"
+    d = "void idg::degridder_kernel<96, 1, false>(idg::DegridArgs)"
+    folder = _captures(tmp_path, [
         (0, g, "dram__bytes_read.sum", "Mbyte", "400"), (0, g, "dram__bytes_write.sum", "Gbyte", "1.0"),
-        (0, g, "gpu__time_duration.sum", "msecond", "21.2"),
-        (1, "void idg::fft_adder_kernel<96, 0>(idg::FftArgs)", "dram__bytes_read.sum", "Gbyte", "1.0"),
         (2, g, "dram__bytes_read.sum", "Mbyte", "200"), (2, g, "dram__bytes_write.sum", "Mbyte", "1,000"),
+    ], [
         (3, d, "dram__bytes_read.sum", "Gbyte", "1.05"), (3, d, "dram__bytes_write.sum", "byte", "35000000"),
-        (4, "void idg::gridder_noalloc_kernel<96>(idg::GridArgs)", "dram__bytes_read.sum", "Gbyte", "9"),
-    ]
-    csv_path = tmp_path / "launches.csv"
-    _write_launch_list(csv_path, rows)
-    bench.record_traffic(str(csv_path), "workload A", "the command")
+    ])
+    bench.record_traffic(folder, full_obs, "workload A")
     rec = json.loads(traffic_file.read_text())
     assert set(rec) == {"gridder", "degridder"}
-    assert rec["gridder"]["launches"] == 2
-    assert rec["gridder"]["dram_bytes_per_launch"] == pytest.approx((1.4e9 + 1.2e9) / 2)
-    assert rec["degridder"]["launches"] == 1
-    assert rec["degridder"]["dram_bytes_per_launch"] == pytest.approx(1.085e9)
-    for k in ("gridder", "degridder"):
-        assert rec[k]["source_sha256"] == bench.source_digest(k)
-        assert rec[k]["workload"] == "workload A" and rec[k]["command"] == "the command"
+    small = synth.config(2, seed=0, n_stations=bench.TRAFFIC_STATIONS)
+    for kern, measured, n in (("gridder", (1.4e9 + 1.2e9) / 2, 2), ("degridder", 1.085e9, 1)):
+        r = rec[kern]
+        assert r["captured_launches"] == n
+        assert r["captured_bytes_per_launch"] == pytest.approx(measured)
+        alg_small = bench.algorithmic_bytes_per_launch(kern, small, small.subgrid_size)
+        alg_full = bench.algorithmic_bytes_per_launch(kern, full_obs, full_obs.subgrid_size)
+        assert r["algorithmic_bytes_per_launch"] == pytest.approx(alg_full)
+        assert r["dram_bytes_per_launch"] == pytest.approx(measured * alg_full / alg_small)
+        assert r["source_sha256"] == bench.source_digest(kern) and r["workload"] == "workload A"
+        assert f"-k regex:\"idg::{kern}_kernel<\" -c 2" in r["command"] and "--stations 90" in r["command"]
+    # the full-size degridder launch of the MWA-like workload: 3270 subgrids of 96^2 pixels read
+    # (32 B each) and their 2.73 M visibilities written (32 B each), on average over 4 batches
+    assert rec["degridder"]["algorithmic_bytes_per_launch"] == pytest.approx(
+        (13082 * 96 * 96 * 32 + 32 * full_obs.n_vis) / 4)
 
 
-def test_recorded_traffic_needs_same_sources_and_workload(tmp_path, traffic_file, monkeypatch):
-    d = "void idg::degridder_kernel<96, 0>(idg::DegridArgs)"
-    csv_path = tmp_path / "launches.csv"
-    _write_launch_list(csv_path, [(0, d, "dram__bytes_read.sum", "Gbyte", "1.0"),
-                                  (0, d, "dram__bytes_write.sum", "Mbyte", "100")])
-    bench.record_traffic(str(csv_path), "workload A", "cmd")
-    assert bench.recorded_traffic("degridder", "workload A") == pytest.approx(1.1e9)
+def test_recorded_traffic_needs_same_sources_and_workload(tmp_path, traffic_file, monkeypatch, full_obs):
+    d = "void idg::degridder_kernel<96, 1, false>(idg::DegridArgs)"
+    folder = _captures(tmp_path, [], [(0, d, "dram__bytes_read.sum", "Gbyte", "1.0"),
+                                      (0, d, "dram__bytes_write.sum", "Mbyte", "100")])
+    bench.record_traffic(folder, full_obs, "workload A")
+    got = bench.recorded_traffic("degridder", "workload A")
+    assert got is not None and got > 1e9
     assert bench.recorded_traffic("degridder", "workload B") is None
     assert bench.recorded_traffic("gridder", "workload A") is None       # no gridder launch recorded
     monkeypatch.setattr(bench, "source_digest", lambda kern: "0" * 64)  # the sources changed since
