@@ -87,6 +87,81 @@ __device__ __forceinline__ float anchor_phase(float4 c0, float4 c1, float n0, fl
   return __fmul_rn(__fsub_rn(rr, round_nearest(rr)), kTwoPiF);
 }
 
+// A lane's phase anchor at one 16-pixel block: reduced phase and slopes of its
+// first channel, and of the channel step (C > 1)
+struct Anchor {
+  float r0, d0;
+  float2 arr, crr, darr, dcrr;
+};
+
+template <int C>
+__device__ __forceinline__ Anchor lane_anchor(const DegridSmem<C>& S, int g, int sl, const float4 g0) {
+  Anchor an;
+  const float4 c1 = S.coef[g][1][sl];
+  an.r0 = anchor_phase(S.coef[g][0][sl], c1, g0.x, g0.y, g0.z);
+  an.arr = make_float2(c1.y, c1.y);
+  an.crr = make_float2(c1.z, c1.z);
+  an.d0 = 0.f;
+  an.darr = an.dcrr = make_float2(0.f, 0.f);
+  if constexpr (C > 1) {
+    const float4 c3 = S.coef[g][3][sl];
+    an.d0 = anchor_phase(S.coef[g][2][sl], c3, g0.x, g0.y, g0.z);
+    an.darr = make_float2(c3.y, c3.y);
+    an.dcrr = make_float2(c3.z, c3.z);
+  }
+  return an;
+}
+
+// Phasor sum of pixel pair q of 16-pixel block b2 into a lane's C x NP
+// accumulators (NP = 4 correlations, or 2: XX and YY)
+template <int C, int NP, int CB>
+__device__ __forceinline__ void mac_pair(const float4* Gm, const Anchor& an, const float4* zs, int b2, int q,
+                                         float2* RE, float2* IM) {
+  const float4 dn4 = Gm[1 + (q >> 1)];  // n' increments of pixels 4(q/2) .. 4(q/2)+3
+  const float2 DN = (q & 1) ? make_float2(dn4.z, dn4.w) : make_float2(dn4.x, dn4.y);
+  const float2 DI = make_float2(float(2 * q - 8), float(2 * q - 7));
+  const float2 ph = ffma2(an.crr, DN, ffma2(an.arr, DI, make_float2(an.r0, an.r0)));
+  float2 Cs, Sn;
+  __sincosf(ph.x, &Sn.x, &Cs.x);
+  __sincosf(ph.y, &Sn.y, &Cs.y);
+  float2 Rc = make_float2(1.f, 1.f), Rs = make_float2(0.f, 0.f);
+  if constexpr (C > 1) {
+    // phasor of the channel step at these pixels
+    const float2 dph = ffma2(an.dcrr, DN, ffma2(an.darr, DI, make_float2(an.d0, an.d0)));
+    __sincosf(dph.x, &Rs.x, &Rc.x);
+    __sincosf(dph.y, &Rs.y, &Rc.y);
+  }
+  float2 ZR[NP], ZI[NP];
+#pragma unroll
+  for (int pi = 0; pi < NP; ++pi) {
+    const int p = NP == 4 ? pi : 3 * pi;
+    const float4 z = zs[(p * CB + 2 * b2 + (q >> 2)) * 4 + (q & 3)];  // Z[pol][block][pair]
+    ZR[pi] = make_float2(z.x, z.y);
+    ZI[pi] = make_float2(z.z, z.w);
+  }
+#pragma unroll
+  for (int h = 0; h < C; ++h) {
+    if (h > 0) {
+      // next channel: e^{i phi} <- e^{i phi} e^{i dphi}
+      const float2 c = ffma2(make_float2(-Sn.x, -Sn.y), Rs, fmul2(Cs, Rc));
+      Sn = ffma2(Sn, Rc, fmul2(Cs, Rs));
+      Cs = c;
+    }
+    const float2 NS = make_float2(-Sn.x, -Sn.y);
+#pragma unroll
+    for (int pi = 0; pi < NP; ++pi) {
+      const int p = NP == 4 ? pi : 3 * pi;
+      // V += Z conj(e): re += Zr c + Zi s, im += Zi c - Zr s
+      float2& re = RE[h * 4 + p];
+      float2& im = IM[h * 4 + p];
+      re = ffma2(ZR[pi], Cs, re);
+      re = ffma2(ZI[pi], Sn, re);
+      im = ffma2(ZI[pi], Cs, im);
+      im = ffma2(ZR[pi], NS, im);
+    }
+  }
+}
+
 template <int L, int C>
 __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx, DegridSmem<C>& S, float2* s_A) {
   constexpr int TPR = L / 8;
@@ -104,6 +179,10 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
   const int n0 = item.k_mid - item.k_begin;          // lanes of the first segment
   const int n_seg = item.k_mid < item.k_end ? 2 : 1;
   const int n_vg = (nl + 31) >> 5;  // groups of 32 lanes
+  // lanes per slot: items of at most 16 lanes spread each slot over R = 32 / 2^ceil(log2 nl) lanes
+  int R = 1;
+  if (nl <= 16)
+    while (R * 2 * nl <= 32 && R < 32) R *= 2;
   const int nodes = a.g.nodes;
   const int nA = nodes * nodes * 4;
   const int nc = sd.c1 - sd.c0;
@@ -245,78 +324,63 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
     // Z10 = 0, so the predicted XY and YX are zero)
     auto sum_chunk = [&](auto np_tag) {
     constexpr int NP = decltype(np_tag)::value;
-    for (int g = 0; g < n_vg; ++g) {
-      // Z of this lane's segment (lanes of one group may straddle the two segments)
-      const float4(*zs)[kChunkBlocks][4] = S.z[buf][g * 32 + lane >= n0 ? 1 : 0];
-      float2 RE[C][4], IM[C][4];
+    if (R > 1) {
+      // few lanes in the item (low occupancy, Section 3.2): the R lanes of
+      // slot lane / R take every R-th pixel pair of the warp's range and
+      // their partial sums are added with warp shuffles, instead of one
+      // lane per slot and the other lanes idle
+      const int sl = lane / R, sub = lane % R;
+      const float4* zs = &S.z[buf][sl >= n0 ? 1 : 0][0][0][0];
+      float2 RE[C * 4], IM[C * 4];
 #pragma unroll
       for (int h = 0; h < C; ++h)
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
-          RE[h][p] = make_float2(0.f, 0.f);
-          IM[h][p] = make_float2(0.f, 0.f);
+          RE[h * 4 + p] = make_float2(0.f, 0.f);
+          IM[h * 4 + p] = make_float2(0.f, 0.f);
+        }
+#pragma unroll 1
+      for (int pp = sub; pp < 4 * kRangeBlocks; pp += R) {
+        const int b2 = warp * (kRangeBlocks / 2) + (pp >> 3), q = pp & 7;
+        const float4* Gm = S.g[buf][b2];
+        mac_pair<C, NP, DegridSmem<C>::CB>(Gm, lane_anchor<C>(S, 0, sl, Gm[0]), zs, b2, q, RE, IM);
+      }
+#pragma unroll
+      for (int h = 0; h < C; ++h)
+#pragma unroll
+        for (int pi = 0; pi < NP; ++pi) {
+          const int p = NP == 4 ? pi : 3 * pi;
+          float re = RE[h * 4 + p].x + RE[h * 4 + p].y, im = IM[h * 4 + p].x + IM[h * 4 + p].y;
+          for (int off = R >> 1; off > 0; off >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, off);
+            im += __shfl_xor_sync(0xffffffffu, im, off);
+          }
+          if (sub == 0) {
+            atomicAdd(&S.out[2 * p][h][sl], re);
+            atomicAdd(&S.out[2 * p + 1][h][sl], im);
+          }
+        }
+    } else {
+    for (int g = 0; g < n_vg; ++g) {
+      // Z of this lane's segment (lanes of one group may straddle the two segments)
+      const float4* zs = &S.z[buf][g * 32 + lane >= n0 ? 1 : 0][0][0][0];
+      float2 RE[C * 4], IM[C * 4];
+#pragma unroll
+      for (int h = 0; h < C; ++h)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          RE[h * 4 + p] = make_float2(0.f, 0.f);
+          IM[h * 4 + p] = make_float2(0.f, 0.f);
         }
 #pragma unroll 1
       for (int b2 = warp * (kRangeBlocks / 2); b2 < (warp + 1) * (kRangeBlocks / 2); ++b2) {
-        // one phase anchor per 16 pixels (pixel 8 of the block): exact reduction there, FP32 increments
-        // the lane's coefficients are re-read from shared memory per anchor (registers go to the sums)
+        // one phase anchor per 16 pixels (pixel 8 of the block): exact reduction there, FP32
+        // increments; the lane's coefficients are re-read from shared memory per anchor
+        // (registers go to the sums)
         const float4* Gm = S.g[buf][b2];
-        const float4 g0 = Gm[0];
-        const float4 c1 = S.coef[g][1][lane];
-        const float2 R0 = make_float2(anchor_phase(S.coef[g][0][lane], c1, g0.x, g0.y, g0.z), 0.f);
-        const float2 ARR = make_float2(c1.y, c1.y), CRR = make_float2(c1.z, c1.z);
-        float2 D0 = make_float2(0.f, 0.f);
-        [[maybe_unused]] float2 DARR = D0, DCRR = D0;
-        if constexpr (C > 1) {
-          const float4 c3 = S.coef[g][3][lane];
-          D0.x = anchor_phase(S.coef[g][2][lane], c3, g0.x, g0.y, g0.z);
-          DARR = make_float2(c3.y, c3.y);
-          DCRR = make_float2(c3.z, c3.z);
-        }
+        const Anchor an = lane_anchor<C>(S, g, lane, Gm[0]);
 #pragma unroll(C > 2 ? 2 : 8)
-        for (int q = 0; q < 8; ++q) {
-          const float4 dn4 = Gm[1 + (q >> 1)];  // n' increments of pixels 4(q/2) .. 4(q/2)+3
-          const float2 DN = (q & 1) ? make_float2(dn4.z, dn4.w) : make_float2(dn4.x, dn4.y);
-          const float2 DI = make_float2(float(2 * q - 8), float(2 * q - 7));
-          const float2 ph = ffma2(CRR, DN, ffma2(ARR, DI, make_float2(R0.x, R0.x)));
-          float2 Cs, Sn;
-          __sincosf(ph.x, &Sn.x, &Cs.x);
-          __sincosf(ph.y, &Sn.y, &Cs.y);
-          float2 Rc = make_float2(1.f, 1.f), Rs = make_float2(0.f, 0.f);
-          if constexpr (C > 1) {
-            // phasor of the channel step at these pixels
-            const float2 dph = ffma2(DCRR, DN, ffma2(DARR, DI, make_float2(D0.x, D0.x)));
-            __sincosf(dph.x, &Rs.x, &Rc.x);
-            __sincosf(dph.y, &Rs.y, &Rc.y);
-          }
-          float2 ZR[NP], ZI[NP];
-#pragma unroll
-          for (int pi = 0; pi < NP; ++pi) {
-            const int p = NP == 4 ? pi : 3 * pi;
-            const float4 z = zs[p][2 * b2 + (q >> 2)][q & 3];
-            ZR[pi] = make_float2(z.x, z.y);
-            ZI[pi] = make_float2(z.z, z.w);
-          }
-#pragma unroll
-          for (int h = 0; h < C; ++h) {
-            if (h > 0) {
-              // next channel: e^{i phi} <- e^{i phi} e^{i dphi}
-              const float2 c = ffma2(make_float2(-Sn.x, -Sn.y), Rs, fmul2(Cs, Rc));
-              Sn = ffma2(Sn, Rc, fmul2(Cs, Rs));
-              Cs = c;
-            }
-            const float2 NS = make_float2(-Sn.x, -Sn.y);
-#pragma unroll
-            for (int pi = 0; pi < NP; ++pi) {
-              const int p = NP == 4 ? pi : 3 * pi;
-              // V += Z conj(e): re += Zr c + Zi s, im += Zi c - Zr s
-              RE[h][p] = ffma2(ZR[pi], Cs, RE[h][p]);
-              RE[h][p] = ffma2(ZI[pi], Sn, RE[h][p]);
-              IM[h][p] = ffma2(ZI[pi], Cs, IM[h][p]);
-              IM[h][p] = ffma2(ZR[pi], NS, IM[h][p]);
-            }
-          }
-        }
+        for (int q = 0; q < 8; ++q) mac_pair<C, NP, DegridSmem<C>::CB>(Gm, an, zs, b2, q, RE, IM);
       }
       const int slot = g * 32 + lane;
 #pragma unroll
@@ -324,9 +388,10 @@ __device__ __forceinline__ void degridder_item(const DegridArgs& a, int item_idx
 #pragma unroll
         for (int pi = 0; pi < NP; ++pi) {
           const int p = NP == 4 ? pi : 3 * pi;
-          atomicAdd(&S.out[2 * p][h][slot], RE[h][p].x + RE[h][p].y);
-          atomicAdd(&S.out[2 * p + 1][h][slot], IM[h][p].x + IM[h][p].y);
+          atomicAdd(&S.out[2 * p][h][slot], RE[h * 4 + p].x + RE[h * 4 + p].y);
+          atomicAdd(&S.out[2 * p + 1][h][slot], IM[h * 4 + p].x + IM[h * 4 + p].y);
         }
+    }
     }
     };
     if (two_pol)

@@ -29,9 +29,12 @@
 //   layer and the side of the run's first visibility (checked on the channel
 //   run's ends, the time growth's corners and in the final shrink).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <numeric>
+#include <thread>
 
 #include "idg_internal.h"
 
@@ -116,6 +119,20 @@ class BaselinePixels {
   std::vector<int32_t> layer_;
 };
 
+// Host threads for one partition: up to IDG_PLANNER_THREADS (default: the
+// hardware's, at most 16), fewer for small observations.
+int planner_threads(int n_bl, size_t n_vis) {
+  int hw = int(std::thread::hardware_concurrency());
+  if (const char* e = std::getenv("IDG_PLANNER_THREADS")) {
+    const int v = std::atoi(e);
+    if (v >= 1) hw = v;
+  } else {
+    hw = std::min(hw, 16);
+  }
+  const int by_work = int(std::min<size_t>(n_vis / 200000 + 1, size_t(n_bl)));
+  return std::max(1, std::min(hw, by_work));
+}
+
 }  // namespace
 
 idg_status partition(const PlanInput& in, Partition* out, std::string* err) {
@@ -154,28 +171,37 @@ idg_status partition(const PlanInput& in, Partition* out, std::string* err) {
   const double w_step = 2.0 * (w_limit / (grad * in.fov));
   if (layered && !(w_step > 0.0)) return fail(IDG_ERR_INVALID_ARG, "w layers need kernel_padding > 2");
   out->w_step = layered ? w_step : 0.0;
-  for (int b = 0; b < in.n_bl && !layered; ++b)
-    for (int t = 0; t < in.n_t; ++t) {
-      const double wm = in.uvw[(size_t(b) * in.n_t + t) * 3 + 2];
-      for (int c = 0; c < in.n_ch; ++c) {
-        const double w = (wm * in.freqs[c]) / kSpeedOfLight;
-        if (std::fabs(w) * grad * in.fov > w_limit) {
-          std::snprintf(msg, sizeof msg, "|w| = %.3f wavelengths (baseline %d, t %d, ch %d) exceeds the %.2f-pixel "
-                        "w fringe limit", std::fabs(w), b, t, c, w_limit);
-          return fail(IDG_ERR_W_TOO_LARGE, msg);
+  // Baselines are partitioned independently (the rules above never look
+  // across baselines), so they are planned on a few host threads and the
+  // results concatenated in baseline order: the same tables as one thread.
+  struct BaselinePlan {
+    std::vector<SubgridDesc> sg;   // plan_index and seg_begin relative to the baseline
+    std::vector<SegmentDesc> seg;  // subgrid relative to the baseline
+    idg_status st = IDG_OK;
+    std::string err;
+  };
+  const bool split = (in.flags & IDG_SPLIT_AT_ATERM_INTERVALS) != 0;
+  auto plan_baseline = [&](int b, BaselinePlan& bp) {
+    char m[256];
+    if (!layered) {  // w check of this baseline, in (t, c) order
+      for (int t = 0; t < in.n_t; ++t) {
+        const double wm = in.uvw[(size_t(b) * in.n_t + t) * 3 + 2];
+        for (int c = 0; c < in.n_ch; ++c) {
+          const double w = (wm * in.freqs[c]) / kSpeedOfLight;
+          if (std::fabs(w) * grad * in.fov > w_limit) {
+            std::snprintf(m, sizeof m, "|w| = %.3f wavelengths (baseline %d, t %d, ch %d) exceeds the %.2f-pixel "
+                          "w fringe limit", std::fabs(w), b, t, c, w_limit);
+            bp.st = IDG_ERR_W_TOO_LARGE;
+            bp.err = m;
+            return;
+          }
         }
       }
     }
-
-  out->subgrids.clear();
-  out->segments.clear();
-  const bool split = (in.flags & IDG_SPLIT_AT_ATERM_INTERVALS) != 0;
-  std::vector<Run> runs;
-  std::vector<Pending> todo;
-  for (int b = 0; b < in.n_bl; ++b) {
-    if (in.n_t == 0 || in.n_ch == 0) break;
+    if (in.n_t == 0 || in.n_ch == 0) return;
     const BaselinePixels px(in, b, layered ? w_step : 0.0);
-    runs.clear();
+    std::vector<Run> runs;
+    std::vector<Pending> todo;
     const int n_blocks = split ? in.n_int : 1;
     for (int blk = 0; blk < n_blocks; ++blk) {
       const int ta = split ? in.aterm_offsets[blk] : 0;
@@ -235,26 +261,71 @@ idg_status partition(const PlanInput& in, Partition* out, std::string* err) {
       d.n_vis = (r.te - r.ts) * (r.c_hi - r.c_lo);
       d.layer = r.layer >> 1;
       d.flags = mirror ? kSubgridMirrored : 0;
-      d.plan_index = int32_t(out->subgrids.size());
+      d.plan_index = int32_t(bp.sg.size());
       const bool outside = d.x0 < 0 || d.y0 < 0 || d.x0 > in.N - in.L || d.y0 > in.N - in.L;
       if (outside) {
         if (!(in.flags & IDG_DROP_OUT_OF_GRID)) {
-          std::snprintf(msg, sizeof msg, "baseline %d timesteps [%d,%d) channels [%d,%d) need a subgrid at (%d,%d), "
+          std::snprintf(m, sizeof m, "baseline %d timesteps [%d,%d) channels [%d,%d) need a subgrid at (%d,%d), "
                         "outside the %d-pixel grid", b, r.ts, r.te, r.c_lo, r.c_hi, d.x0, d.y0, in.N);
-          return fail(IDG_ERR_UV_OUT_OF_GRID, msg);
+          bp.st = IDG_ERR_UV_OUT_OF_GRID;
+          bp.err = m;
+          return;
         }
         d.flags |= kSubgridDropped;
       }
-      d.seg_begin = int32_t(out->segments.size());
+      d.seg_begin = int32_t(bp.seg.size());
       for (int a = 0; a < in.n_int; ++a) {
         const int lo = std::max(in.aterm_offsets[a], r.ts), hi = std::min(in.aterm_offsets[a + 1], r.te);
         if (lo >= hi) continue;
         const int width = r.c_hi - r.c_lo;
-        out->segments.push_back(SegmentDesc{d.plan_index, a, (lo - r.ts) * width, (hi - r.ts) * width});
+        bp.seg.push_back(SegmentDesc{d.plan_index, a, (lo - r.ts) * width, (hi - r.ts) * width});
       }
-      d.seg_count = int32_t(out->segments.size()) - d.seg_begin;
+      d.seg_count = int32_t(bp.seg.size()) - d.seg_begin;
+      bp.sg.push_back(d);
+    }
+  };
+
+  std::vector<BaselinePlan> per(size_t(std::max(0, in.n_bl)));
+  const int n_threads = planner_threads(in.n_bl, size_t(in.n_bl) * in.n_t * in.n_ch);
+  if (n_threads <= 1) {
+    for (int b = 0; b < in.n_bl; ++b) plan_baseline(b, per[b]);
+  } else {
+    std::atomic<int> next{0};
+    std::vector<std::thread> pool;
+    for (int k = 0; k < n_threads; ++k)
+      pool.emplace_back([&] {
+        for (int b = next.fetch_add(1); b < in.n_bl; b = next.fetch_add(1)) plan_baseline(b, per[b]);
+      });
+    for (std::thread& th : pool) th.join();
+  }
+  // errors as the sequential order would report them: a w error of any
+  // baseline first (the w check precedes all partitioning), then the first
+  // baseline with a subgrid outside the grid
+  for (int b = 0; b < in.n_bl; ++b)
+    if (per[b].st == IDG_ERR_W_TOO_LARGE) return fail(per[b].st, per[b].err.c_str());
+  for (int b = 0; b < in.n_bl; ++b)
+    if (per[b].st != IDG_OK) return fail(per[b].st, per[b].err.c_str());
+  out->subgrids.clear();
+  out->segments.clear();
+  size_t n_sg = 0, n_seg = 0;
+  for (const BaselinePlan& bp : per) {
+    n_sg += bp.sg.size();
+    n_seg += bp.seg.size();
+  }
+  out->subgrids.reserve(n_sg);
+  out->segments.reserve(n_seg);
+  for (BaselinePlan& bp : per) {
+    const int32_t sg0 = int32_t(out->subgrids.size()), seg0 = int32_t(out->segments.size());
+    for (SubgridDesc d : bp.sg) {
+      d.plan_index += sg0;
+      d.seg_begin += seg0;
       out->subgrids.push_back(d);
     }
+    for (SegmentDesc g : bp.seg) {
+      g.subgrid += sg0;
+      out->segments.push_back(g);
+    }
+    bp = BaselinePlan{};
   }
   return IDG_OK;
 }

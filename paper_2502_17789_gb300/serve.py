@@ -12,13 +12,23 @@ admitted.  Plan creation (host partitioning) runs on a thread pool so it
 overlaps GPU work.  The "plain" mode runs one request at a time on one
 stream: the per-request baseline.
 
+Results come back through a pool of page-locked host buffers that the
+process keeps and reuses (page-locking a buffer of a GiB or more is a slow
+host operation, so a server reserves its staging memory once, as it does
+its device memory).
+
 Failures stay on the host: a request whose footprint can never fit is
 rejected, a cancelled request is skipped, and a plan that cannot be made
 (for example IDG_ERR_W_TOO_LARGE) fails that request only.
+
+Every result carries its host planning time, its device time (CUDA events
+on its stream) and its pinned-buffer wait, so a run shows where a request's
+latency goes.
 """
 from __future__ import annotations
 
 import concurrent.futures as cf
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -54,6 +64,9 @@ class Result:
     admitted: float = 0.0
     finished: float = 0.0
     output: np.ndarray | None = None
+    plan_s: float = 0.0             # host planning (idg_plan_create, on the planning pool)
+    gpu_s: float = 0.0              # device time of the request's work on its stream
+    pinned_s: float = 0.0           # time spent obtaining the page-locked result buffer
 
     @property
     def latency(self) -> float:
@@ -79,6 +92,44 @@ def request_shape(n_st, n_ch, n_t):
     return n_st * (n_st - 1) // 2 * n_ch * n_t
 
 
+class PinnedPool:
+    """Page-locked host buffers kept for the life of the process and handed
+    out again to any request whose result fits (smallest free buffer that is
+    large enough; a new one, rounded up to a power of two, only when none
+    is)."""
+
+    def __init__(self):
+        self._free: list = []
+        self._lock = threading.Lock()
+        self.allocated_bytes = 0
+
+    def take(self, nbytes: int):
+        import torch
+        with self._lock:
+            fits = [i for i, b in enumerate(self._free) if b.numel() >= nbytes]
+            if fits:
+                i = min(fits, key=lambda k: self._free[k].numel())
+                return self._free.pop(i)
+        size = 1 << max(20, int(nbytes - 1).bit_length())
+        buf = torch.empty(size, dtype=torch.uint8, pin_memory=True)
+        with self._lock:
+            self.allocated_bytes += size
+        return buf
+
+    def give(self, buf):
+        with self._lock:
+            self._free.append(buf)
+
+
+PINNED = PinnedPool()
+
+
+def _pinned_view(buf, shape, dtype):
+    import torch
+    n = int(np.prod(shape)) * torch.empty((), dtype=dtype).element_size()
+    return buf[:n].view(dtype).view(shape)
+
+
 @dataclass
 class _Slot:
     req: Request
@@ -87,8 +138,12 @@ class _Slot:
     plan: idg.Plan | None = None
     stream: object = None
     event: object = None
+    start: object = None
     bufs: dict = field(default_factory=dict)
     host_out: object = None
+    host_buf: object = None
+    plan_s: float = 0.0
+    pinned_s: float = 0.0
 
 
 class Server:
@@ -110,13 +165,17 @@ class Server:
     # ---------------------------------------------------------------- request lifecycle
 
     def _make_plan(self, req: Request, stream_handle: int):
-        return idg.Plan(req.obs, stream=stream_handle)
+        t = time.perf_counter()
+        plan = idg.Plan(req.obs, stream=stream_handle)
+        return plan, time.perf_counter() - t
 
     def _launch(self, slot: _Slot):
         torch = self.torch
         req = slot.req
         o = req.obs
         with torch.cuda.stream(slot.stream):
+            slot.start = torch.cuda.Event(enable_timing=True)
+            slot.start.record(slot.stream)
             A = torch.as_tensor(req.aterms).to(self.device, non_blocking=True)
             N = o.grid_size
             gen = torch.Generator(device=self.device)
@@ -126,7 +185,7 @@ class Server:
                                   device=self.device, generator=gen)
                 G = torch.zeros((4, N, N), dtype=torch.complex128, device=self.device)
                 slot.plan.grid(vis, A, G)
-                out = torch.empty(G.shape, dtype=G.dtype, pin_memory=True)
+                out = self._host_buffer(slot, G.shape, G.dtype)
                 out.copy_(G, non_blocking=True)
                 slot.bufs = {"A": A, "vis": vis, "G": G}
             else:
@@ -144,12 +203,19 @@ class Server:
                 vis = torch.empty((o.n_baselines, o.n_timesteps, o.n_channels, 4), dtype=torch.complex64,
                                   device=self.device)
                 slot.plan.degrid(G, A, vis)
-                out = torch.empty(vis.shape, dtype=vis.dtype, pin_memory=True)
+                out = self._host_buffer(slot, vis.shape, vis.dtype)
                 out.copy_(vis, non_blocking=True)
                 slot.bufs = {"A": A, "vis": vis, "G": G}
             slot.host_out = out
-            slot.event = torch.cuda.Event()
+            slot.event = torch.cuda.Event(enable_timing=True)
             slot.event.record(slot.stream)
+
+    def _host_buffer(self, slot: _Slot, shape, dtype):
+        t = time.perf_counter()
+        n = int(np.prod(shape)) * self.torch.empty((), dtype=dtype).element_size()
+        slot.host_buf = PINNED.take(n)
+        slot.pinned_s = time.perf_counter() - t
+        return _pinned_view(slot.host_buf, shape, dtype)
 
     def run(self, requests: list[Request]) -> list[Result]:
         """Serve `requests` (arrival times relative to now); returns one
@@ -194,7 +260,7 @@ class Server:
                 for slot in list(running):
                     if slot.plan is None and slot.future is not None and slot.future.done():
                         try:
-                            slot.plan = slot.future.result()
+                            slot.plan, slot.plan_s = slot.future.result()
                         except idg.IdgError as e:
                             running.remove(slot)
                             used -= footprint_bytes(slot.req)
@@ -209,8 +275,11 @@ class Server:
                     elif slot.event is not None and slot.event.query():
                         slot.plan.synchronize()
                         r = Result(slot.req.rid, slot.req.kind, "ok", slot.req.obs.n_vis, slot.req.arrival,
-                                   slot.admitted, now(), slot.host_out.numpy() if self.keep_outputs else None)
+                                   slot.admitted, now(), slot.host_out.numpy().copy() if self.keep_outputs else None,
+                                   plan_s=slot.plan_s, gpu_s=1e-3 * slot.start.elapsed_time(slot.event),
+                                   pinned_s=slot.pinned_s)
                         results[r.rid] = r
+                        PINNED.give(slot.host_buf)
                         slot.plan.close()
                         slot.bufs.clear()
                         running.remove(slot)
@@ -262,7 +331,12 @@ def summarize(results: list[Result], t_wall: float | None = None) -> dict:
             "cancelled": sum(r.status == "cancelled" for r in results),
             "vis": int(sum(r.n_vis for r in ok)), "makespan_s": span,
             "throughput_vis_per_s": (sum(r.n_vis for r in ok) / span) if ok else 0.0,
-            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99))}
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            # where the time goes, summed over the served requests
+            "host_plan_s": float(sum(r.plan_s for r in ok)), "gpu_s": float(sum(r.gpu_s for r in ok)),
+            "pinned_wait_s": float(sum(r.pinned_s for r in ok)),
+            "per_request": [[r.kind, r.n_vis, round(1e3 * r.plan_s, 1), round(1e3 * r.gpu_s, 1),
+                             round(1e3 * (r.admitted - r.arrival), 1), round(1e3 * r.latency, 1)] for r in ok]}
 
 
 def compare(n_requests: int = 40, seed: int = 0, loads=(0.7, 2.0), budget_gb: float = 64.0, slots: int = 8,

@@ -168,6 +168,25 @@ def test_degrid_channel_groups(idg_mod, oracle_mod, cuda_device, channels, L, n_
         pp.close()
 
 
+@pytest.mark.parametrize("channels", [1, 2, 4])
+@pytest.mark.parametrize("n_ch,n_t,steps", [(1, 1, 1), (1, 3, 1), (2, 2, 1), (3, 3, 3), (5, 4, 2), (4, 8, 4)])
+def test_degrid_low_occupancy(idg_mod, oracle_mod, cuda_device, channels, n_ch, n_t, steps):
+    """Work items of few lanes (1 to 16: subgrids of a few visibilities,
+    Section 3.2) spread each visibility's pixels over R = 32 / 2^ceil(log2
+    lanes) lanes of a warp and add the partial sums with shuffles; one or
+    two segments per item."""
+    obs = synth.config(2, n_stations=9, n_timesteps=n_t, n_channels=n_ch)
+    obs.aterm_offsets = np.array(list(range(0, n_t, steps)) + [n_t], np.int32)
+    A, vis = _random_problem(700 + 10 * n_ch + n_t, obs)
+    rng = np.random.default_rng(n_ch * n_t)
+    N = obs.grid_size
+    Grand = (rng.standard_normal((4, N, N)) + 1j * rng.standard_normal((4, N, N))) * 1e-3
+    c = Case(idg_mod, oracle_mod, obs, A, vis, degrid_channels=channels)
+    V_ref = c.oracle_degrid(Grand)
+    assert _degrid_err(c.gpu_degrid(Grand), V_ref) < DEGRID_TOL
+    assert _rel(c.gpu_grid(), c.oracle_grid()) < GRID_TOL
+
+
 def test_grid_accumulates_into_existing_grid(idg_mod, oracle_mod, cuda_device):
     obs = synth.config(1, n_stations=8)
     A, vis = _random_problem(3, obs, n_int=2)
