@@ -97,6 +97,8 @@ typedef struct {
                               cosine, the others by rotation with the channel-step phasor (the phase is
                               linear in frequency, Eq. 7); it needs uniformly spaced channels and falls back
                               to 1 otherwise (idg_plan_stats reports the value in use) */
+  int32_t grid_chunk;      /* gridder: staged visibility records per chunk copied to shared memory, 8 .. 64,
+                              or 0 for the default (48); a tuning choice, the results do not depend on it */
 } idg_geometry;
 
 typedef struct {
@@ -119,6 +121,7 @@ typedef struct {
   double w_layer_step;        /* layer width 2 w_max in wavelengths, w_max = (P/2 - 1) / (max|grad n'| FOV) */
   int32_t n_pol;              /* planes per layer of grids and images: 4, or 1 with IDG_STOKES_I */
   int32_t degrid_channels;    /* channels per degridder lane in use */
+  int32_t grid_chunk;         /* gridder records per chunk in use */
 } idg_plan_stats_t;
 
 /*

@@ -168,7 +168,7 @@ struct GridCfg {
   static constexpr int QN = PX / 2;      // pixel pairs per thread
   static constexpr int TPR = L / PX;     // threads per row
   static constexpr int NT = ROWS * TPR;  // threads per block
-  static constexpr int VC = 48;          // records per chunk
+  static constexpr int VC_MAX = 64;      // records per chunk at most (the plan's grid_chunk, GridArgs::vc)
   static constexpr int MINB = NT <= 128 ? 3 : (NT <= 192 ? 2 : 1);
   static_assert(L % 8 == 0 && L % ROWS == 0 && (PX == 4 || PX == 8), "gridder shape");
 };
@@ -180,9 +180,9 @@ struct ChunkCursor {
   int end;    // end of the segment
 };
 
-template <int VC>
-__device__ __forceinline__ void cursor_advance(ChunkCursor& cur, const SegmentDesc* seg, int seg_begin, int seg_count) {
-  cur.k += VC;
+__device__ __forceinline__ void cursor_advance(ChunkCursor& cur, int vc, const SegmentDesc* seg, int seg_begin,
+                                               int seg_count) {
+  cur.k += vc;
   if (cur.k >= cur.end) {
     ++cur.seg;
     if (cur.seg < seg_count) {
@@ -202,6 +202,7 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
                                              float* s_acc, float* s_w, uint64_t* s_bar) {
   using C = GridCfg<L, ROWS>;
   const GridItem item = a.items[item_idx];
+  const int VC = a.vc;  // records per chunk
   const SubgridDesc sd = a.sg[item.sg];
   const int tid = threadIdx.x;
   const int j = item.tile * ROWS + tid / C::TPR;
@@ -214,7 +215,7 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
   int n_chunks = 0;
   for (int g = 0; g < sd.seg_count; ++g) {
     const SegmentDesc s = a.seg[sd.seg_begin + g];
-    n_chunks += (s.k_end - s.k_begin + C::VC - 1) / C::VC;
+    n_chunks += (s.k_end - s.k_begin + VC - 1) / VC;
   }
   const float4* rec_base = a.records + size_t(sd.rec_offset) * kRecordFloat4;
 
@@ -225,11 +226,11 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
     pc = {0, s0.k_begin, s0.k_end};
   }
   auto issue = [&](int buf) {
-    const int nv = imin(C::VC, pc.end - pc.k);
+    const int nv = imin(VC, pc.end - pc.k);
     const uint32_t bytes = uint32_t(nv) * kRecordFloat4 * 16;
     mbar_arrive_expect_tx(&s_bar[buf], bytes);
-    bulk_copy_g2s(s_rec + buf * C::VC * kRecordFloat4, rec_base + size_t(pc.k) * kRecordFloat4, bytes, &s_bar[buf]);
-    cursor_advance<C::VC>(pc, a.seg, sd.seg_begin, sd.seg_count);
+    bulk_copy_g2s(s_rec + buf * VC * kRecordFloat4, rec_base + size_t(pc.k) * kRecordFloat4, bytes, &s_bar[buf]);
+    cursor_advance(pc, VC, a.seg, sd.seg_begin, sd.seg_count);
   };
   if (tid == 0) {
     issue(int(cg & 1));
@@ -271,7 +272,7 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
     const uint32_t cc_g = cg + uint32_t(c);
     const int buf = int(cc_g & 1);
     const bool ok = mbar_wait_bounded(&s_bar[buf], (cc_g >> 1) & 1);
-    const int nv = imin(C::VC, cc.end - cc.k);
+    const int nv = imin(VC, cc.end - cc.k);
     // Stokes I with both stations' A-terms of this chunk's segment diagonal:
     // I = (conj(p0) X00 q0 + conj(p1) X11 q1) / 2 needs only the XX and YY sums
     bool two_pol = false;
@@ -282,7 +283,7 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
     // the record loop, for all four correlations (NP = 4) or XX and YY only (NP = 2)
     auto records = [&](auto np_tag) {
       constexpr int NP = decltype(np_tag)::value;
-      const float4* rb = s_rec + buf * C::VC * kRecordFloat4;
+      const float4* rb = s_rec + buf * VC * kRecordFloat4;
 #pragma unroll 1
       for (int v = 0; v < nv; ++v) {
         const float4* rec = rb + v * kRecordFloat4;
@@ -371,7 +372,7 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
       fence_proxy_async();
       issue(buf);
     }
-    const bool seg_done = cc.k + C::VC >= cc.end;
+    const bool seg_done = cc.k + VC >= cc.end;
     if (seg_done) {
       // ---- epilogue of segment cc.seg: A_p^H X A_q, taper, centring sign (Section 3.3)
       const SegmentDesc seg = a.seg[sd.seg_begin + cc.seg];
@@ -440,7 +441,7 @@ __device__ __forceinline__ bool gridder_item(const GridArgs& a, int item_idx, ui
           IM[p][q] = make_float2(0.f, 0.f);
         }
     }
-    cursor_advance<C::VC>(cc, a.seg, sd.seg_begin, sd.seg_count);
+    cursor_advance(cc, VC, a.seg, sd.seg_begin, sd.seg_count);
   }
 
   // ---- A-term weights of this thread's pixels, and the subgrid's visibility count once
@@ -487,8 +488,8 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
     gridder_kernel(const GridArgs a) {
   using C = GridCfg<L, ROWS>;
   extern __shared__ float4 smem[];
-  float4* s_rec = smem;                                                        // [2][VC][8]
-  float* s_acc = reinterpret_cast<float*>(s_rec + 2 * C::VC * kRecordFloat4);  // [8 PX][NT]
+  float4* s_rec = smem;                                                      // [2][vc][8]
+  float* s_acc = reinterpret_cast<float*>(s_rec + 2 * a.vc * kRecordFloat4);  // [8 PX][NT]
   float* s_w = s_acc + 8 * C::PX * C::NT;                                      // [PX][NT] A-term weights
   uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_w + C::PX * C::NT);          // [2]
   int* s_item = reinterpret_cast<int*>(s_bar + 2);
@@ -514,22 +515,26 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
 }
 
 template <int L, int ROWS>
-static size_t gridder_smem() {
+static size_t gridder_smem(int vc) {
   using C = GridCfg<L, ROWS>;
-  return sizeof(float4) * 2 * C::VC * kRecordFloat4 + sizeof(float) * 9 * C::PX * C::NT + 2 * sizeof(uint64_t) + 16;
+  return sizeof(float4) * 2 * vc * kRecordFloat4 + sizeof(float) * 9 * C::PX * C::NT + 2 * sizeof(uint64_t) + 16;
 }
 
+// The shared-memory limit is set for the largest chunk, so plans with
+// different chunks share the kernels; the occupancy (persistent grid size)
+// follows this plan's chunk.
 template <int L, int ROWS>
-static int configure_gridder_t(int* persistent_blocks) {
+static int configure_gridder_t(int vc, int* persistent_blocks) {
   using C = GridCfg<L, ROWS>;
-  const int smem = int(gridder_smem<L, ROWS>());
+  const int smem_max = int(gridder_smem<L, ROWS>(C::VC_MAX));
+  const int smem = int(gridder_smem<L, ROWS>(vc));
   const void* fns[4] = {reinterpret_cast<const void*>(gridder_kernel<L, ROWS, false, false>),
                         reinterpret_cast<const void*>(gridder_kernel<L, ROWS, true, false>),
                         reinterpret_cast<const void*>(gridder_kernel<L, ROWS, false, true>),
                         reinterpret_cast<const void*>(gridder_kernel<L, ROWS, true, true>)};
   cudaError_t e = cudaSuccess;
   for (const void* fn : fns)
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   int per_sm = 0, dev = 0, sms = 0;
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gridder_kernel<L, ROWS, true, false>, C::NT, smem);
@@ -542,7 +547,7 @@ static int configure_gridder_t(int* persistent_blocks) {
 template <int L, int ROWS>
 static int launch_gridder_t(const GridArgs& a, int n_items, int persistent_blocks, void* stream) {
   using C = GridCfg<L, ROWS>;
-  const size_t smem = gridder_smem<L, ROWS>();
+  const size_t smem = gridder_smem<L, ROWS>(a.vc);
   if (n_items <= 0) return 0;
   const int pb = persistent_blocks < n_items ? persistent_blocks : n_items;
   cudaStream_t st = cudaStream_t(stream);
@@ -581,12 +586,12 @@ int launch_gridder(int L, const GridArgs& a, int n_items, int persistent_blocks,
   }
 }
 
-int configure_gridder(int L, int* persistent_blocks) {
+int configure_gridder(int L, int vc, int* persistent_blocks) {
   switch (L) {
-    case 32: return configure_gridder_t<32, 32>(persistent_blocks);
-    case 64: return configure_gridder_t<64, 16>(persistent_blocks);
-    case 96: return configure_gridder_t<96, 8>(persistent_blocks);
-    case 128: return configure_gridder_t<128, 8>(persistent_blocks);
+    case 32: return configure_gridder_t<32, 32>(vc, persistent_blocks);
+    case 64: return configure_gridder_t<64, 16>(vc, persistent_blocks);
+    case 96: return configure_gridder_t<96, 8>(vc, persistent_blocks);
+    case 128: return configure_gridder_t<128, 8>(vc, persistent_blocks);
     default: return int(cudaErrorInvalidValue);
   }
 }

@@ -49,6 +49,7 @@ struct idg_plan {
   int32_t k_min = 0, n_layers = 1;  // w layers of the master grid
   int32_t npol = 4;                  // master-grid planes per layer: 4, or 1 with IDG_STOKES_I
   int32_t degrid_channels = 1;       // channels per degridder lane
+  int32_t grid_chunk = kDefaultGridChunk;  // staged records per gridder chunk
   cudaStream_t stream = nullptr;
   bool host_only = false;
   Partition part;
@@ -311,6 +312,8 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     return set_err(nullptr, IDG_ERR_INVALID_ARG, "taper_user is NULL");
   if (g->degrid_channels != 0 && !supported_degrid_channels(g->degrid_channels))
     return set_err(nullptr, IDG_ERR_INVALID_ARG, "degrid_channels must be 0, 1, 2 or 4");
+  if (g->grid_chunk != 0 && (g->grid_chunk < kMinGridChunk || g->grid_chunk > kMaxGridChunk))
+    return set_err(nullptr, IDG_ERR_INVALID_ARG, "grid_chunk must be 0 or in [8, 64]");
 
   idg_plan* p = new (std::nothrow) idg_plan();
   if (!p) return set_err(nullptr, IDG_ERR_OOM, "host allocation failed");
@@ -372,6 +375,7 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     const int want = g->degrid_channels > 0 ? g->degrid_channels : kDefaultDegridChannels;
     p->degrid_channels = uniform ? want : 1;
   }
+  p->grid_chunk = g->grid_chunk > 0 ? g->grid_chunk : kDefaultGridChunk;
   for (SubgridDesc& d : p->exec) d.layer -= k_lo;  // device tables hold the grid plane set
   if (host_only) {
     *out = p;
@@ -459,7 +463,7 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
   }
   int pg = 0, pd = 0;
   int e = configure_kernels(L);
-  if (!e) e = configure_gridder(L, &pg);
+  if (!e) e = configure_gridder(L, p->grid_chunk, &pg);
   if (!e) e = configure_degridder(L, g->aterm_nodes, p->degrid_channels, &pd);
   if (g->flags & IDG_PERSISTENT) {
     p->persistent_grid_blocks = pg;
@@ -561,6 +565,7 @@ static GridArgs grid_args(const idg_plan* p, const Batch& b, const void* vis, co
   ga.blk = p->d_blk;
   ga.scratch = p->d_scratch;
   ga.aweights = p->d_aweights;
+  ga.vc = p->grid_chunk;
   ga.g = kgeom(p);
   return ga;
 }
@@ -947,6 +952,7 @@ idg_status idg_plan_stats(const idg_plan* plan, idg_plan_stats_t* out) {
   out->w_layer_min = plan->k_min;
   out->w_layer_step = plan->part.w_step;
   out->degrid_channels = plan->degrid_channels;
+  out->grid_chunk = plan->grid_chunk;
   return IDG_OK;
 }
 

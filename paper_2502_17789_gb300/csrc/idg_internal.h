@@ -68,6 +68,10 @@ struct DegridItem {
 // lanes (channel groups) per degridder work item for C channels per lane
 __host__ __device__ constexpr int degrid_lanes(int C) { return C == 1 ? 256 : 128; }
 constexpr int kDefaultDegridChannels = 1;  // channels per degridder lane when the geometry leaves it 0
+// staged visibility records per gridder chunk (bulk copy into shared memory)
+constexpr int kDefaultGridChunk = 48;
+constexpr int kMinGridChunk = 8;
+constexpr int kMaxGridChunk = 64;
 constexpr int kMaxAtermNodes = 25;  // A-term samples per axis (bounds the degridder's shared memory)
 constexpr int kDegridSegs = 2;  // segments per degridder work item
 
@@ -157,6 +161,7 @@ struct GridArgs {
   const float4* blk;          // [L][L/8][3] block geometry (n0, anchor offsets) (dn[0..3]) (dn[4..7])
   float2* scratch;            // [batch][4][L][L]
   double* aweights;           // A-term power weights [L*L + 1] (IDG_NORMALIZE_ATERM), else NULL
+  int vc = kDefaultGridChunk;  // staged records per chunk, kMinGridChunk .. kMaxGridChunk
   KernelGeom g;
 };
 
@@ -189,7 +194,7 @@ struct FftArgs {
 // Launchers (return cudaError_t as int).  `n` is the item or subgrid count.
 // persistent_blocks > 0: persistent launch of that many blocks draining a.queue
 int launch_gridder(int L, const GridArgs& a, int n_items, int persistent_blocks, void* stream);
-int configure_gridder(int L, int* persistent_blocks);   // attributes + persistent grid size
+int configure_gridder(int L, int vc, int* persistent_blocks);   // attributes + persistent grid size
 // channels: channels per degridder lane (1, 2 or 4; > 1 needs uniform channel spacing)
 int configure_degridder(int L, int nodes, int channels, int* persistent_blocks);
 bool supported_degrid_channels(int channels);

@@ -42,7 +42,7 @@ class Geometry(ctypes.Structure):
     _fields_ = [("grid_size", ctypes.c_int32), ("subgrid_size", ctypes.c_int32), ("kernel_padding", ctypes.c_int32),
                 ("image_size", ctypes.c_double), ("taper_kind", ctypes.c_int32), ("taper_beta", ctypes.c_double),
                 ("taper_user", ctypes.POINTER(ctypes.c_double)), ("aterm_nodes", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("degrid_channels", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("degrid_channels", ctypes.c_int32), ("grid_chunk", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -52,7 +52,7 @@ class PlanStats(ctypes.Structure):
                 ("occupancy_hist", ctypes.c_int64 * 16), ("device_bytes", ctypes.c_int64),
                 ("vis_pixels", ctypes.c_int64), ("subgrid_size", ctypes.c_int32), ("batch_capacity", ctypes.c_int32),
                 ("n_w_layers", ctypes.c_int32), ("w_layer_min", ctypes.c_int32), ("w_layer_step", ctypes.c_double),
-                ("n_pol", ctypes.c_int32), ("degrid_channels", ctypes.c_int32)]
+                ("n_pol", ctypes.c_int32), ("degrid_channels", ctypes.c_int32), ("grid_chunk", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -249,7 +249,7 @@ def idg_abi_version() -> int:
 # ----------------------------------------------------------------- torch-facing wrapper
 
 def make_geometry(grid_size, subgrid_size, kernel_padding, image_size, taper_beta=0.0, aterm_nodes=9, flags=0,
-                  taper_user=None, degrid_channels=0) -> tuple[Geometry, object]:
+                  taper_user=None, degrid_channels=0, grid_chunk=0) -> tuple[Geometry, object]:
     g = Geometry()
     g.grid_size, g.subgrid_size, g.kernel_padding = int(grid_size), int(subgrid_size), int(kernel_padding)
     g.image_size = float(image_size)
@@ -264,6 +264,7 @@ def make_geometry(grid_size, subgrid_size, kernel_padding, image_size, taper_bet
     g.aterm_nodes = int(aterm_nodes)
     g.flags = int(flags)
     g.degrid_channels = int(degrid_channels)
+    g.grid_chunk = int(grid_chunk)
     return g, keep
 
 
@@ -277,7 +278,7 @@ class Plan:
 
     def __init__(self, obs=None, *, grid_size=None, subgrid_size=None, kernel_padding=None, image_size=None,
                  n_stations=None, baselines=None, uvw=None, freqs=None, aterm_offsets=None, aterm_nodes=9,
-                 flags=0, taper_beta=0.0, taper_user=None, stream=None, degrid_channels=0):
+                 flags=0, taper_beta=0.0, taper_user=None, stream=None, degrid_channels=0, grid_chunk=0):
         if obs is not None:
             grid_size = obs.grid_size if grid_size is None else grid_size
             subgrid_size = obs.subgrid_size if subgrid_size is None else subgrid_size
@@ -286,7 +287,7 @@ class Plan:
             n_stations, baselines, uvw = obs.n_stations, obs.baselines, obs.uvw
             freqs, aterm_offsets, aterm_nodes = obs.freqs, obs.aterm_offsets, obs.aterm_nodes
         self.geometry, self._keep = make_geometry(grid_size, subgrid_size, kernel_padding, image_size, taper_beta,
-                                                  aterm_nodes, flags, taper_user, degrid_channels)
+                                                  aterm_nodes, flags, taper_user, degrid_channels, grid_chunk)
         if stream is None and not (flags & IDG_HOST_ONLY):
             import torch
             stream = torch.cuda.current_stream().cuda_stream  # 0 when that is the legacy default stream

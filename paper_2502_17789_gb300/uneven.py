@@ -4,8 +4,9 @@
 30 channels 140-170 MHz, A-terms every 4 s (45 intervals) on 9 x 9 nodes,
 8192^2 FP64 grid: subgrids hold 360 to 10800 visibilities and their A-term
 segments 8 to 240.  The autotuner times a CUDA-graph replay of grid + degrid
-for every (subgrid size, launch mode) candidate and keeps the fastest; the
-chosen configuration is then timed over several replays.  Prints one JSON
+for every (subgrid size, launch mode) candidate, then for the gridder's
+records per chunk and the degridder's channels per lane, and keeps the
+fastest; the chosen configuration is then timed over several replays.  Prints one JSON
 line.  Parity of this workload against the FP64 oracle is checked by the
 test suite on a stratified baseline sample.
 
@@ -68,8 +69,8 @@ def main(argv=None):
                         "vis_pixels": float(st.vis_pixels)}
         p.close()
 
-    def measure(o, L, mode, budget):
-        return autotune.gpu_measure(o, L, mode, budget, trials=1, aterms=A, graph=True, vis=vis)
+    def measure(o, L, mode, chunk, channels):
+        return autotune.gpu_measure(o, L, mode, chunk, channels, trials=1, aterms=A, graph=True, vis=vis)
 
     t1 = time.time()
     choice = autotune.autotune(obs, candidates=args.candidates, modes=args.modes, cache_path=args.cache,
@@ -78,8 +79,7 @@ def main(argv=None):
 
     # the chosen configuration: graph replays of grid + degrid on a side stream
     side = torch.cuda.Stream(dev)
-    flags = idg.IDG_PERSISTENT if choice.mode == "persistent" else 0
-    plan = idg.Plan(obs, subgrid_size=choice.subgrid_size, flags=flags, stream=side.cuda_stream)
+    plan = idg.Plan(obs, stream=side.cuda_stream, **choice.plan_kwargs(idg))
     st = plan.stats()
     N = obs.grid_size
     G = torch.zeros((4, N, N), dtype=torch.complex128, device=dev)

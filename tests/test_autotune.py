@@ -7,27 +7,37 @@ from paper_2502_17789_gb300 import autotune, synth
 
 
 def test_selects_fastest_and_caches(tmp_path):
+    """Staged search: every (L, mode) at the default chunk and one channel
+    per lane, then the chunk, then the channels per lane of the best; the
+    winner is cached per GPU and shape."""
     obs = synth.config(1, n_stations=6)
     calls = []
 
-    def fake(o, L, mode, budget):
-        calls.append((L, mode, budget))
+    def fake(o, L, mode, chunk, ch):
+        calls.append((L, mode, chunk, ch))
         if L == 128:
             return None  # e.g. the plan could not be made
-        return {64: 5.0, 96: 3.0}[L] + (0.5 if mode == "persistent" else 0.0)
+        return ({64: 5.0, 96: 3.0}[L] + (0.5 if mode == "persistent" else 0.0)
+                + {32: 0.2, 48: 0.1, 64: 0.0}[chunk] + {1: 0.0, 2: -0.05, 4: 0.3}[ch])
 
     path = str(tmp_path / "tune.json")
     c = autotune.autotune(obs, cache_path=path, device_name="fake", measure=fake)
-    assert (c.subgrid_size, c.mode) == (96, "blocks") and c.ms == 3.0
+    assert (c.subgrid_size, c.mode, c.grid_chunk, c.degrid_channels) == (96, "blocks", 64, 2)
+    assert c.ms == pytest.approx(3.0 - 0.05)
     n = len(calls)
-    assert n == len(autotune.CANDIDATE_L) * len(autotune.MODES) * len(autotune.BUDGETS)
+    # stage 1: 3 x 2; stage 2: the two other chunks; stage 3: the two other channel counts
+    assert n == len(autotune.CANDIDATE_L) * len(autotune.MODES) + 2 + 2
+    assert calls[6:] == [(96, "blocks", 32, 1), (96, "blocks", 64, 1), (96, "blocks", 64, 2), (96, "blocks", 64, 4)]
     c2 = autotune.autotune(obs, cache_path=path, device_name="fake", measure=fake)
-    assert len(calls) == n and (c2.subgrid_size, c2.mode) == (96, "blocks")
+    assert len(calls) == n and (c2.grid_chunk, c2.degrid_channels) == (64, 2)
     autotune.autotune(obs, cache_path=path, device_name="fake", measure=fake, refresh=True)
     assert len(calls) == 2 * n
     # a different GPU or shape is a different key
     autotune.autotune(obs, cache_path=path, device_name="other", measure=fake)
     assert len(calls) == 3 * n
+    import types
+    fake_idg = types.SimpleNamespace(IDG_PERSISTENT=8)
+    assert c.plan_kwargs(fake_idg) == {"subgrid_size": 96, "flags": 0, "grid_chunk": 64, "degrid_channels": 2}
 
 
 def test_no_candidate_raises(tmp_path):
@@ -41,4 +51,5 @@ def test_gpu_autotune_small(tmp_path, idg_mod, cuda_device):
     obs = synth.config(2, n_stations=10, n_timesteps=8)
     c = autotune.autotune(obs, candidates=(64, 96), cache_path=str(tmp_path / "t.json"))
     assert c.subgrid_size in (64, 96) and c.mode in autotune.MODES and c.ms > 0
-    assert all(v is None or v > 0 for v in c.timings.values())
+    assert c.grid_chunk in autotune.GRID_CHUNKS and c.degrid_channels in autotune.DEGRID_CHANNELS
+    assert len(c.timings) == 4 + 2 + 2 and all(v is None or v > 0 for v in c.timings.values())

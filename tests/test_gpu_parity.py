@@ -187,6 +187,28 @@ def test_degrid_low_occupancy(idg_mod, oracle_mod, cuda_device, channels, n_ch, 
     assert _rel(c.gpu_grid(), c.oracle_grid()) < GRID_TOL
 
 
+@pytest.mark.parametrize("chunk", [8, 32, 64])
+def test_grid_chunk_sizes(idg_mod, oracle_mod, cuda_device, chunk):
+    """Gridder record chunks other than the default (the autotuner's choice):
+    chunks that end inside a segment, ragged chunk tails, one block per item
+    and the persistent queue."""
+    import torch
+    obs = synth.config(2, n_stations=10, n_timesteps=13, n_channels=17)
+    A, vis = _random_problem(400 + chunk, obs, n_int=4)
+    G_ref = oracle_mod.grid(*Case(idg_mod, oracle_mod, obs, A, vis).args(), vis.astype(np.complex64).astype(np.complex128),
+                            A.astype(np.complex64).astype(np.complex128))
+    for flags in (0, idg_mod.IDG_PERSISTENT):
+        plan = idg_mod.Plan(obs, flags=flags, grid_chunk=chunk)
+        try:
+            assert plan.stats().grid_chunk == chunk
+            G = torch.zeros((4, obs.grid_size, obs.grid_size), dtype=torch.complex128, device="cuda")
+            plan.grid(torch.as_tensor(vis.astype(np.complex64)).cuda(), torch.as_tensor(A.astype(np.complex64)).cuda(), G)
+            plan.synchronize()
+            assert _rel(G.cpu().numpy(), G_ref) < GRID_TOL
+        finally:
+            plan.close()
+
+
 def test_grid_accumulates_into_existing_grid(idg_mod, oracle_mod, cuda_device):
     obs = synth.config(1, n_stations=8)
     A, vis = _random_problem(3, obs, n_int=2)

@@ -217,3 +217,29 @@ def test_planner_shrink_golden(idg_mod):
         np.testing.assert_array_equal(idg_mod.idg_plan_subgrids(h), np.array(sc["expected"], np.int32))
     finally:
         idg_mod.idg_plan_destroy(h)
+
+
+def test_tuning_choices_are_validated_and_reported(idg_mod):
+    """grid_chunk (8 .. 64, 0 = default 48) and degrid_channels (0, 1, 2, 4)
+    are checked at plan creation and reported by idg_plan_stats; channel
+    groups need uniformly spaced channels and fall back to 1."""
+    obs = _brute.tiny_observation(seed=1)
+    for chunk, ch, ok in ((0, 0, True), (8, 2, True), (64, 4, True), (7, 1, False), (65, 1, False), (48, 3, False)):
+        g, _ = idg_mod.make_geometry(obs.grid_size, obs.subgrid_size, obs.kernel_padding, obs.image_size,
+                                     flags=idg_mod.IDG_HOST_ONLY, grid_chunk=chunk, degrid_channels=ch)
+        if ok:
+            h = idg_mod.idg_plan_create(g, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets)
+            st = idg_mod.idg_plan_stats(h)
+            assert st.grid_chunk == (chunk or 48) and st.degrid_channels == (ch or 1)
+            idg_mod.idg_plan_destroy(h)
+        else:
+            with pytest.raises(idg_mod.IdgError) as e:
+                idg_mod.idg_plan_create(g, obs.n_stations, obs.baselines, obs.uvw, obs.freqs, obs.aterm_offsets)
+            assert e.value.status == 1
+    freqs = obs.freqs.copy()
+    freqs[-1] += 0.3e6   # one uneven step
+    g, _ = idg_mod.make_geometry(obs.grid_size, obs.subgrid_size, obs.kernel_padding, obs.image_size,
+                                 flags=idg_mod.IDG_HOST_ONLY, degrid_channels=4)
+    h = idg_mod.idg_plan_create(g, obs.n_stations, obs.baselines, obs.uvw, freqs, obs.aterm_offsets)
+    assert idg_mod.idg_plan_stats(h).degrid_channels == 1
+    idg_mod.idg_plan_destroy(h)
