@@ -814,15 +814,20 @@ def run_native(args):
         plan.close()
         del G_out, vis_pred
         torch.cuda.empty_cache()
-        cmp = serve.compare(args.serving_requests, seed=0, loads=(2.0,))
-        sat = cmp["load_2"]
+        cmp = serve.compare(args.serving_requests, seed=0, loads=(2.0, "burst"),
+                            modes=("plain", "streams", "batched"))
 
         def brief(r):
             return {"vis_per_s": r["throughput_vis_per_s"], "p50_ms": 1e3 * r["p50_latency_s"],
-                    "p99_ms": 1e3 * r["p99_latency_s"], "requests_ok": r["ok"]}
-        serving = {"requests": args.serving_requests, "arrival": "Poisson at 2x the plain capacity",
+                    "p99_ms": 1e3 * r["p99_latency_s"], "requests_ok": r["ok"], "makespan_s": r["makespan_s"],
+                    "host_plan_s": r["host_plan_s"], "gpu_s": r["gpu_s"]}
+        serving = {"requests": args.serving_requests,
                    "plain_capacity_requests_per_s": cmp["calibration_plain_requests_per_s"],
-                   "batched": brief(sat["batched"]), "plain": brief(sat["plain"])}
+                   "modes": {"plain": "one request at a time", "streams": "each request on its own stream",
+                             "batched": "continuous batching: waves of admitted requests share one launch per "
+                                        "kind of work (idg_grid_many / idg_degrid_many)"}}
+        for key, name in (("load_2", "poisson_2x_plain_capacity"), ("burst", "burst_all_at_once")):
+            serving[name] = {m: brief(cmp[key][m]) for m in ("plain", "streams", "batched")}
         plan = None
 
     line = {

@@ -365,6 +365,34 @@ const char* idg_last_error(const idg_plan* plan);
 idg_status idg_plan_destroy(idg_plan* plan);
 
 /*
+ * idg_grid_many / idg_degrid_many -- idg_grid / idg_degrid of n plans whose
+ * work items share one launch per wave: wave w runs batch w of every plan
+ * that has one (Section 3.4 works through the visibilities in batches that
+ * fit memory; here the batches of several observations fill one launch),
+ * with the items of all those batches in one gridder (degridder) launch,
+ * longest first across plans.  This is the shared work queue a serving loop
+ * drains for the requests it has admitted (continuous batching).  Each plan's
+ * result is the one idg_grid / idg_degrid gives it.
+ *   n            number of plans, >= 1
+ *   plans        [n] device plans, distinct, sharing the subgrid size, the
+ *                Stokes-I flag, the A-term normalisation flag and
+ *                degrid_channels (IDG_ERR_INVALID_ARG otherwise)
+ *   vis_c64, aterms_c64, grid_c128
+ *                [n] device buffers, per plan as for idg_grid / idg_degrid
+ *   cuda_stream  the stream every launch of the call goes to (the plans' own
+ *                streams are not used: work queued on them must be complete
+ *                or ordered before the call by the caller)
+ * Uses each plan's scratch and staging buffers, so a plan may not run
+ * anything else until the call's work on cuda_stream has finished.
+ * Allocates two small tables per wave (stream-ordered).  Persistent launch
+ * mode is not used here.
+ */
+idg_status idg_grid_many(int32_t n, idg_plan* const* plans, const void* const* vis_c64,
+                         const void* const* aterms_c64, void* const* grid_c128, void* cuda_stream);
+idg_status idg_degrid_many(int32_t n, idg_plan* const* plans, const void* const* grid_c128,
+                           const void* const* aterms_c64, void* const* vis_c64, void* cuda_stream);
+
+/*
  * idg_peak_rates -- measured throughput of the two units the phasor sums use
  * (Section 5.1: the kernels are bounded by the hardware's measured FP32
  * rate).  Runs, on cuda_stream with every SM of the current device filled,

@@ -440,6 +440,22 @@ __global__ void __launch_bounds__(degrid_threads(C), degrid_min_blocks(C)) degri
   }
 }
 
+// One launch over the work items of several plans (the serving loop's
+// shared work queue): block b runs item items[b] = (plan slot, item index
+// in that slot's batch) with the slot's arguments copied to shared memory.
+template <int L, int C>
+__global__ void __launch_bounds__(degrid_threads(C), degrid_min_blocks(C))
+    degridder_multi_kernel(const DegridArgs* args, const int2* items) {
+  extern __shared__ float4 smem_raw[];
+  DegridSmem<C>& S = *reinterpret_cast<DegridSmem<C>*>(smem_raw);
+  float2* s_A = reinterpret_cast<float2*>(&S + 1);
+  __shared__ DegridArgs s_args;
+  const int2 it = items[blockIdx.x];
+  if (threadIdx.x == 0) s_args = args[it.x];
+  __syncthreads();
+  degridder_item<L, C>(s_args, it.y, S, s_A);
+}
+
 template <int C>
 static size_t degridder_smem(int nodes) {
   return sizeof(DegridSmem<C>) + sizeof(float2) * 2 * kDegridSegs * nodes * nodes * 4;
@@ -498,6 +514,40 @@ static int configure_degridder_l(int nodes, int channels, int* persistent_blocks
 }
 
 bool supported_degrid_channels(int channels) { return channels == 1 || channels == 2 || channels == 4; }
+
+template <int L, int C>
+static int launch_degridder_multi_t(const DegridArgs* args, const int2* items, int n_items, int max_nodes,
+                                    void* stream) {
+  if (n_items <= 0) return 0;
+  cudaError_t e = cudaFuncSetAttribute(degridder_multi_kernel<L, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(degridder_smem<C>(kMaxAtermNodes)));
+  if (e != cudaSuccess) return int(e);
+  degridder_multi_kernel<L, C><<<n_items, degrid_threads(C), degridder_smem<C>(max_nodes), cudaStream_t(stream)>>>(
+      args, items);
+  return int(cudaGetLastError());
+}
+
+template <int L>
+static int launch_degridder_multi_l(int channels, const DegridArgs* args, const int2* items, int n_items,
+                                    int max_nodes, void* stream) {
+  switch (channels) {
+    case 1: return launch_degridder_multi_t<L, 1>(args, items, n_items, max_nodes, stream);
+    case 2: return launch_degridder_multi_t<L, 2>(args, items, n_items, max_nodes, stream);
+    case 4: return launch_degridder_multi_t<L, 4>(args, items, n_items, max_nodes, stream);
+    default: return int(cudaErrorInvalidValue);
+  }
+}
+
+int launch_degridder_multi(int L, int channels, const DegridArgs* args, const int2* items, int n_items, int max_nodes,
+                           void* stream) {
+  switch (L) {
+    case 32: return launch_degridder_multi_l<32>(channels, args, items, n_items, max_nodes, stream);
+    case 64: return launch_degridder_multi_l<64>(channels, args, items, n_items, max_nodes, stream);
+    case 96: return launch_degridder_multi_l<96>(channels, args, items, n_items, max_nodes, stream);
+    case 128: return launch_degridder_multi_l<128>(channels, args, items, n_items, max_nodes, stream);
+    default: return int(cudaErrorInvalidValue);
+  }
+}
 
 int launch_degridder(int L, int channels, const DegridArgs& a, int n_items, int persistent_blocks, void* stream) {
   switch (L) {

@@ -514,6 +514,34 @@ __global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
   }
 }
 
+// One launch over the work items of several plans (the serving loop's
+// shared work queue): block b runs item items[b] = (plan slot, item index
+// in that slot's batch), with the slot's arguments copied to shared memory
+// first.  One item per block, in the order given (longest first).
+template <int L, int ROWS, bool NORM>
+__global__ void __launch_bounds__(GridCfg<L, ROWS>::NT, GridCfg<L, ROWS>::MINB)
+    gridder_multi_kernel(const GridArgs* args, const int2* items) {
+  using C = GridCfg<L, ROWS>;
+  __shared__ GridArgs s_args;
+  extern __shared__ float4 smem[];
+  const int2 it = items[blockIdx.x];
+  if (threadIdx.x == 0) s_args = args[it.x];
+  __syncthreads();
+  const GridArgs& a = s_args;
+  float4* s_rec = smem;                                                      // [2][vc][8]
+  float* s_acc = reinterpret_cast<float*>(s_rec + 2 * a.vc * kRecordFloat4);  // [8 PX][NT]
+  float* s_w = s_acc + 8 * C::PX * C::NT;                                    // [PX][NT]
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_w + C::PX * C::NT);        // [2]
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t cg = 0;
+  gridder_item<L, ROWS, NORM>(a, it.y, cg, s_rec, s_acc, s_w, s_bar);
+}
+
 template <int L, int ROWS>
 static size_t gridder_smem(int vc) {
   using C = GridCfg<L, ROWS>;
@@ -563,6 +591,31 @@ static int launch_gridder_t(const GridArgs& a, int n_items, int persistent_block
       gridder_kernel<L, ROWS, false, false><<<n_items, C::NT, smem, st>>>(a);
   }
   return int(cudaGetLastError());
+}
+
+template <int L, int ROWS>
+static int launch_gridder_multi_t(const GridArgs* args, const int2* items, int n_items, bool norm, int max_vc,
+                                  void* stream) {
+  using C = GridCfg<L, ROWS>;
+  if (n_items <= 0) return 0;
+  const size_t smem = gridder_smem<L, ROWS>(max_vc);
+  const auto fn = norm ? gridder_multi_kernel<L, ROWS, true> : gridder_multi_kernel<L, ROWS, false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(gridder_smem<L, ROWS>(C::VC_MAX)));
+  if (e != cudaSuccess) return int(e);
+  fn<<<n_items, C::NT, smem, cudaStream_t(stream)>>>(args, items);
+  return int(cudaGetLastError());
+}
+
+int launch_gridder_multi(int L, const GridArgs* args, const int2* items, int n_items, bool norm, int max_vc,
+                         void* stream) {
+  switch (L) {
+    case 32: return launch_gridder_multi_t<32, 32>(args, items, n_items, norm, max_vc, stream);
+    case 64: return launch_gridder_multi_t<64, 16>(args, items, n_items, norm, max_vc, stream);
+    case 96: return launch_gridder_multi_t<96, 8>(args, items, n_items, norm, max_vc, stream);
+    case 128: return launch_gridder_multi_t<128, 8>(args, items, n_items, norm, max_vc, stream);
+    default: return int(cudaErrorInvalidValue);
+  }
 }
 
 // rows per gridder tile for each supported subgrid size

@@ -57,6 +57,8 @@ struct idg_plan {
   std::vector<Batch> batches;
   int32_t batch_cap = 0;
   int64_t n_grid_items = 0, n_degrid_items = 0;
+  // work estimate per item, host copies (the order of the items of several plans in one launch)
+  std::vector<int32_t> gcost, dcost;
   int64_t n_vis_dropped = 0, n_sg_dropped = 0;
   int64_t vis_pixels = 0;
   int64_t device_bytes = 0;
@@ -444,6 +446,14 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
   }
   p->n_grid_items = int64_t(gitems.size());
   p->n_degrid_items = int64_t(ditems.size());
+  p->gcost.resize(gitems.size());
+  for (size_t i = 0; i < gitems.size(); ++i) {
+    const Batch& bb = *std::upper_bound(p->batches.begin(), p->batches.end(), int32_t(i),
+                                        [](int32_t v, const Batch& x) { return v < x.gi_offset + x.gi_count; });
+    p->gcost[i] = p->exec[bb.sg_offset + gitems[i].sg].n_vis;
+  }
+  p->dcost.resize(ditems.size());
+  for (size_t i = 0; i < ditems.size(); ++i) p->dcost[i] = ditems[i].k_end - ditems[i].k_begin;
 
   // device tables
   std::vector<double> fscale(n_channels);
@@ -745,6 +755,189 @@ idg_status idg_grid_graph(idg_plan* plan, const void* vis_c64, const void* aterm
 
 idg_status idg_degrid_graph(idg_plan* plan, const void* grid_c128, const void* aterms_c64, void* vis_c64) {
   return run_graph(plan, true, grid_c128, aterms_c64, vis_c64);
+}
+
+// ------------------------------------------------------------------ several plans, one launch per wave
+
+}  // extern "C"
+
+namespace {
+
+// The plans of one grid_many / degrid_many call must share the kernel
+// instantiation: subgrid size, planes per layer, normalisation, degridder
+// channels per lane.
+idg_status check_many(int32_t n, idg_plan* const* plans, const void* const* a, const void* const* b,
+                      void* const* c, const char* an, const char* bn, const char* cn) {
+  if (n < 1 || !plans || !a || !b || !c) return set_err(nullptr, IDG_ERR_INVALID_ARG, "NULL array or n < 1");
+  for (int32_t k = 0; k < n; ++k) {
+    idg_plan* p = plans[k];
+    if (!p) return set_err(nullptr, IDG_ERR_INVALID_ARG, "a plan is NULL");
+    if (p->host_only) return set_err(p, IDG_ERR_INVALID_ARG, "plan was created with IDG_HOST_ONLY");
+    idg_status st;
+    if ((st = check_buffer(p, a[k], an)) || (st = check_buffer(p, b[k], bn)) || (st = check_buffer(p, c[k], cn)))
+      return st;
+    const idg_plan* p0 = plans[0];
+    if (p->L != p0->L || p->npol != p0->npol || (p->d_aweights != nullptr) != (p0->d_aweights != nullptr) ||
+        p->degrid_channels != p0->degrid_channels)
+      return set_err(p, IDG_ERR_INVALID_ARG,
+                     "plans of one call must share subgrid size, Stokes-I mode, normalisation and degrid_channels");
+    for (int32_t j = 0; j < k; ++j)
+      if (plans[j] == p) return set_err(p, IDG_ERR_INVALID_ARG, "a plan appears twice");
+  }
+  return IDG_OK;
+}
+
+// Items of several plans' batches merged longest first (each plan's batch is
+// already in that order): (slot, item index within the slot's batch).
+std::vector<int2> merge_items(const std::vector<const int32_t*>& cost, const std::vector<int32_t>& count) {
+  std::vector<int2> out;
+  size_t total = 0;
+  for (int32_t c : count) total += size_t(c);
+  out.reserve(total);
+  std::vector<int32_t> pos(count.size(), 0);
+  while (out.size() < total) {
+    int best = -1;
+    for (size_t s = 0; s < count.size(); ++s)
+      if (pos[s] < count[s] && (best < 0 || cost[s][pos[s]] > cost[best][pos[best]])) best = int(s);
+    out.push_back(make_int2(best, pos[best]++));
+  }
+  return out;
+}
+
+// device copies of the wave's argument table and item list (stream-ordered, freed after the launch)
+template <typename A>
+int upload_wave(cudaStream_t st, const std::vector<A>& args, const std::vector<int2>& items, A** d_args,
+                int2** d_items) {
+  int e = int(cudaMallocAsync(reinterpret_cast<void**>(d_args), sizeof(A) * args.size(), st));
+  if (!e) e = int(cudaMallocAsync(reinterpret_cast<void**>(d_items), sizeof(int2) * std::max<size_t>(1, items.size()), st));
+  if (!e) e = int(cudaMemcpyAsync(*d_args, args.data(), sizeof(A) * args.size(), cudaMemcpyHostToDevice, st));
+  if (!e && !items.empty())
+    e = int(cudaMemcpyAsync(*d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, st));
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+idg_status idg_grid_many(int32_t n, idg_plan* const* plans, const void* const* vis_c64,
+                         const void* const* aterms_c64, void* const* grid_c128, void* cuda_stream) {
+  idg_status st = check_many(n, plans, vis_c64, aterms_c64, grid_c128, "vis", "aterms", "grid");
+  if (st) return st;
+  cudaStream_t strm = cudaStream_t(cuda_stream);
+  const int L = plans[0]->L;
+  size_t n_waves = 0;
+  for (int32_t k = 0; k < n; ++k) {
+    idg_plan* p = plans[k];
+    n_waves = std::max(n_waves, p->batches.size());
+    const int e = launch_aterm_flags(static_cast<const float2*>(aterms_c64[k]), p->d_adiag, p->n_int, p->n_st,
+                                     p->geom.aterm_nodes, strm);
+    if (e) return cuda_err(p, e, "A-term flag launch");
+  }
+  for (size_t w = 0; w < n_waves; ++w) {
+    std::vector<GridArgs> args;
+    std::vector<const int32_t*> cost;
+    std::vector<int32_t> count;
+    std::vector<int32_t> slot_plan;
+    int max_vc = kMinGridChunk;
+    for (int32_t k = 0; k < n; ++k) {
+      idg_plan* p = plans[k];
+      if (w >= p->batches.size()) continue;
+      const Batch& b = p->batches[w];
+      const int e = launch_stage_records(L, stage_args(p, b, vis_c64[k]), b.sg_count, strm);
+      if (e) return cuda_err(p, e, "staging launch");
+      GridArgs ga = grid_args(p, b, vis_c64[k], aterms_c64[k]);
+      ga.n_items = b.gi_count;
+      args.push_back(ga);
+      cost.push_back(p->gcost.data() + b.gi_offset);
+      count.push_back(b.gi_count);
+      slot_plan.push_back(k);
+      max_vc = std::max(max_vc, p->grid_chunk);
+    }
+    const std::vector<int2> items = merge_items(cost, count);
+    GridArgs* d_args = nullptr;
+    int2* d_items = nullptr;
+    int e = upload_wave(strm, args, items, &d_args, &d_items);
+    if (!e)
+      e = launch_gridder_multi(L, d_args, d_items, int(items.size()), plans[0]->d_aweights != nullptr, max_vc, strm);
+    if (d_args) cudaFreeAsync(d_args, strm);
+    if (d_items) cudaFreeAsync(d_items, strm);
+    if (e) return cuda_err(plans[0], e, "gridder launch (several plans)");
+    for (size_t s = 0; s < slot_plan.size(); ++s) {
+      idg_plan* p = plans[slot_plan[s]];
+      const Batch& b = p->batches[w];
+      FftArgs fa{p->d_sg + b.sg_offset, p->d_scratch, static_cast<double2*>(grid_c128[slot_plan[s]]), p->d_twiddle,
+                 p->N, p->npol};
+      e = launch_fft_adder(L, fa, b.sg_count, 0, strm);
+      if (e) return cuda_err(p, e, "fft/adder launch");
+    }
+  }
+  return IDG_OK;
+}
+
+idg_status idg_degrid_many(int32_t n, idg_plan* const* plans, const void* const* grid_c128,
+                           const void* const* aterms_c64, void* const* vis_c64, void* cuda_stream) {
+  idg_status st = check_many(n, plans, grid_c128, aterms_c64, vis_c64, "grid", "aterms", "vis");
+  if (st) return st;
+  if (!vis_c64) return set_err(nullptr, IDG_ERR_INVALID_ARG, "NULL array");
+  cudaStream_t strm = cudaStream_t(cuda_stream);
+  const int L = plans[0]->L;
+  size_t n_waves = 0;
+  int max_nodes = 2;
+  for (int32_t k = 0; k < n; ++k) {
+    idg_plan* p = plans[k];
+    n_waves = std::max(n_waves, p->batches.size());
+    max_nodes = std::max(max_nodes, int(p->geom.aterm_nodes));
+    if (p->n_vis_dropped > 0) {
+      const size_t bytes = size_t(p->n_bl) * p->n_t * p->n_ch * 4 * sizeof(float2);
+      const int e = int(cudaMemsetAsync(vis_c64[k], 0, bytes, strm));
+      if (e) return cuda_err(p, e, "zeroing dropped visibilities");
+    }
+    const int e = launch_aterm_flags(static_cast<const float2*>(aterms_c64[k]), p->d_adiag, p->n_int, p->n_st,
+                                     p->geom.aterm_nodes, strm);
+    if (e) return cuda_err(p, e, "A-term flag launch");
+  }
+  for (size_t w = 0; w < n_waves; ++w) {
+    std::vector<DegridArgs> args;
+    std::vector<const int32_t*> cost;
+    std::vector<int32_t> count;
+    for (int32_t k = 0; k < n; ++k) {
+      idg_plan* p = plans[k];
+      if (w >= p->batches.size()) continue;
+      const Batch& b = p->batches[w];
+      FftArgs fa{p->d_sg + b.sg_offset, p->d_scratch,
+                 const_cast<double2*>(static_cast<const double2*>(grid_c128[k])), p->d_twiddle, p->N, p->npol};
+      const int e = launch_splitter_ifft(L, fa, b.sg_count, strm);
+      if (e) return cuda_err(p, e, "splitter/ifft launch");
+      DegridArgs da{};
+      da.adiag = p->d_adiag;
+      da.n_items = b.di_count;
+      da.vis = static_cast<float4*>(vis_c64[k]);
+      da.uvw = p->d_uvw;
+      da.fscale = p->d_fscale;
+      da.aterms = static_cast<const float2*>(aterms_c64[k]);
+      da.sg = p->d_sg + b.sg_offset;
+      da.seg = p->d_seg;
+      da.items = p->d_ditems + b.di_offset;
+      da.taper = p->d_taper;
+      da.blk16 = p->d_blk16;
+      da.scratch = p->d_scratch;
+      da.g = kgeom(p);
+      args.push_back(da);
+      cost.push_back(p->dcost.data() + b.di_offset);
+      count.push_back(b.di_count);
+    }
+    const std::vector<int2> items = merge_items(cost, count);
+    DegridArgs* d_args = nullptr;
+    int2* d_items = nullptr;
+    int e = upload_wave(strm, args, items, &d_args, &d_items);
+    if (!e)
+      e = launch_degridder_multi(L, plans[0]->degrid_channels, d_args, d_items, int(items.size()), max_nodes, strm);
+    if (d_args) cudaFreeAsync(d_args, strm);
+    if (d_items) cudaFreeAsync(d_items, strm);
+    if (e) return cuda_err(plans[0], e, "degridder launch (several plans)");
+  }
+  return IDG_OK;
 }
 
 // ------------------------------------------------------------------ image-domain wrapper

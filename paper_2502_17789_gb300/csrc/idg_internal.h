@@ -194,6 +194,10 @@ struct FftArgs {
 // Launchers (return cudaError_t as int).  `n` is the item or subgrid count.
 // persistent_blocks > 0: persistent launch of that many blocks draining a.queue
 int launch_gridder(int L, const GridArgs& a, int n_items, int persistent_blocks, void* stream);
+// one launch over the items of several plans: args[slot] in device memory, items (slot, item index) in
+// launch order; max_vc the largest records-per-chunk among the slots
+int launch_gridder_multi(int L, const GridArgs* args, const int2* items, int n_items, bool norm, int max_vc,
+                         void* stream);
 int configure_gridder(int L, int vc, int* persistent_blocks);   // attributes + persistent grid size
 // channels: channels per degridder lane (1, 2 or 4; > 1 needs uniform channel spacing)
 int configure_degridder(int L, int nodes, int channels, int* persistent_blocks);
@@ -213,6 +217,8 @@ int launch_wait_selftest(int* status, int64_t limit_ns, void* stream);
 // flags[i][s] = 1 when every node of A-term (interval i, station s) has zero off-diagonal entries
 int launch_aterm_flags(const float2* aterms, uint8_t* flags, int n_int, int n_st, int nodes, void* stream);
 int launch_degridder(int L, int channels, const DegridArgs& a, int n_items, int persistent_blocks, void* stream);
+int launch_degridder_multi(int L, int channels, const DegridArgs* args, const int2* items, int n_items, int max_nodes,
+                           void* stream);
 // mode 0: FFT + add into grid; mode 1: FFT in place in scratch (inspection)
 int launch_fft_adder(int L, const FftArgs& a, int n_subgrids, int mode, void* stream);
 int launch_splitter_ifft(int L, const FftArgs& a, int n_subgrids, void* stream);

@@ -28,7 +28,7 @@ IDG_NORMALIZE_ATERM, IDG_STOKES_I = 32, 64
 EXPORTS = ["idg_plan_create", "idg_grid", "idg_degrid", "idg_grid_graph", "idg_degrid_graph", "idg_set_stream", "idg_plan_stats", "idg_plan_subgrids",
            "idg_plan_segments", "idg_plan_layers", "idg_subgrid_images", "idg_synchronize", "idg_profile_enable", "idg_profile_read",
            "idg_grid_noalloc", "idg_invert", "idg_predict", "idg_wait_selftest", "idg_aterm_weights", "idg_last_error",
-           "idg_plan_destroy", "idg_abi_version", "idg_peak_rates"]
+           "idg_plan_destroy", "idg_abi_version", "idg_peak_rates", "idg_grid_many", "idg_degrid_many"]
 KERNEL_CLASSES = ["gridder", "fft_adder", "splitter_ifft", "degridder", "stage", "aterm_flags"]
 
 
@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.idg_predict.argtypes = [P, P, P, P, P]
     lib.idg_profile_enable.argtypes = [P, i32]
     lib.idg_peak_rates.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.idg_grid_many.argtypes = [i32, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), P]
+    lib.idg_degrid_many.argtypes = [i32, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), P]
     lib.idg_profile_read.argtypes = [P, P, P]
     lib.idg_last_error.argtypes = [P]
     lib.idg_last_error.restype = ctypes.c_char_p
@@ -240,6 +242,39 @@ def idg_peak_rates(stream=None) -> tuple[float, float]:
     f, s = ctypes.c_double(0.0), ctypes.c_double(0.0)
     _check(load().idg_peak_rates(stream, ctypes.byref(f), ctypes.byref(s)), "idg_peak_rates")
     return float(f.value), float(s.value)
+
+
+def _ptr_array(values):
+    arr = (ctypes.c_void_p * len(values))()
+    for k, v in enumerate(values):
+        arr[k] = v
+    return arr
+
+
+def grid_many(plans, vis, aterms, grids, stream=None):
+    """idg_grid_many: grid several plans' visibilities (CUDA torch tensors,
+    one per plan) with their work items sharing one launch per wave on
+    `stream` (default: torch's current stream)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    n = len(plans)
+    _check(load().idg_grid_many(n, _ptr_array([p.handle for p in plans]), _ptr_array([_dev_ptr(v) for v in vis]),
+                                _ptr_array([_dev_ptr(a) for a in aterms]), _ptr_array([_dev_ptr(g) for g in grids]),
+                                stream), "idg_grid_many", plans[0].handle)
+    return grids
+
+
+def degrid_many(plans, grids, aterms, vis, stream=None):
+    """idg_degrid_many: the degridding counterpart of grid_many."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    n = len(plans)
+    _check(load().idg_degrid_many(n, _ptr_array([p.handle for p in plans]), _ptr_array([_dev_ptr(g) for g in grids]),
+                                  _ptr_array([_dev_ptr(a) for a in aterms]), _ptr_array([_dev_ptr(v) for v in vis]),
+                                  stream), "idg_degrid_many", plans[0].handle)
+    return vis
 
 
 def idg_abi_version() -> int:

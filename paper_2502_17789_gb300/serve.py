@@ -3,14 +3,23 @@
 A request grids the visibilities of one snapshot observation (or degrids a
 model grid into them).  Requests arrive as a Poisson stream.  The server
 admits a request when its device footprint fits the HBM budget and a slot is
-free; every admitted request runs on its own CUDA stream, so work of requests
-that arrive while others are on the GPU overlaps on the device (continuous
-batching at the granularity of the library's kernels).  Its plan,
-visibilities and grid stay resident until its result has been copied back;
-then the memory and the slot are released and the next waiting request is
-admitted.  Plan creation (host partitioning) runs on a thread pool so it
-overlaps GPU work.  The "plain" mode runs one request at a time on one
-stream: the per-request baseline.
+free; its plan, visibilities and grid stay resident on the device until its
+result has been copied back, then the memory and the slot are released and
+the next waiting request is admitted.  Plan creation (host partitioning)
+runs on a thread pool so it overlaps GPU work.
+
+Modes:
+  "batched"  continuous batching through the library's shared work queue:
+             the admitted requests whose plans are ready go to the GPU
+             together as a wave -- per kind of work one idg_grid_many or
+             idg_degrid_many call, whose launches hold the work items of all
+             the wave's requests, longest first -- while the next wave
+             collects the requests that arrive meanwhile; two waves are in
+             flight at a time, on two streams.
+  "streams"  every admitted request runs its own idg_grid / idg_degrid on
+             its own stream (requests overlap at the granularity of the
+             kernels).
+  "plain"    one request at a time on one stream: the per-request baseline.
 
 Results come back through a pool of page-locked host buffers that the
 process keeps and reuses (page-locking a buffer of a GiB or more is a slow
@@ -130,7 +139,7 @@ def _pinned_view(buf, shape, dtype):
     return buf[:n].view(dtype).view(shape)
 
 
-@dataclass
+@dataclass(eq=False)   # slots compare by identity
 class _Slot:
     req: Request
     admitted: float
@@ -151,8 +160,8 @@ class Server:
                  device: int = 0, keep_outputs: bool = True, plan_workers: int = 4):
         import torch
 
-        if mode not in ("batched", "plain"):
-            raise ValueError("mode must be 'batched' or 'plain'")
+        if mode not in ("batched", "streams", "plain"):
+            raise ValueError("mode must be 'batched', 'streams' or 'plain'")
         self.torch = torch
         self.budget = int(hbm_budget_bytes)
         self.max_slots = 1 if mode == "plain" else int(max_slots)
@@ -171,41 +180,18 @@ class Server:
 
     def _launch(self, slot: _Slot):
         torch = self.torch
-        req = slot.req
-        o = req.obs
         with torch.cuda.stream(slot.stream):
             slot.start = torch.cuda.Event(enable_timing=True)
             slot.start.record(slot.stream)
-            A = torch.as_tensor(req.aterms).to(self.device, non_blocking=True)
-            N = o.grid_size
-            gen = torch.Generator(device=self.device)
-            gen.manual_seed(req.seed)
-            if req.kind == "grid":
-                vis = torch.randn((o.n_baselines, o.n_timesteps, o.n_channels, 4), dtype=torch.complex64,
-                                  device=self.device, generator=gen)
-                G = torch.zeros((4, N, N), dtype=torch.complex128, device=self.device)
-                slot.plan.grid(vis, A, G)
-                out = self._host_buffer(slot, G.shape, G.dtype)
-                out.copy_(G, non_blocking=True)
-                slot.bufs = {"A": A, "vis": vis, "G": G}
+            self._synthesize(slot)
+            if slot.req.kind == "grid":
+                slot.plan.grid(slot.bufs["vis"], slot.bufs["A"], slot.bufs["G"])
+                res = slot.bufs["G"]
             else:
-                # model: a few point sources in the central third of the field,
-                # sum_s a_s exp(-2 pi i (u l_s + v m_s)) on every grid cell
-                u = (torch.arange(N, device=self.device, dtype=torch.float64) - N // 2) / o.image_size
-                lm = (torch.rand((4, 2), device=self.device, dtype=torch.float64, generator=gen) - 0.5) \
-                    * (o.image_size / 1.5)
-                amp = torch.randn((4,), dtype=torch.complex128, device=self.device, generator=gen)
-                ex = torch.polar(torch.ones_like(u)[None, :].expand(4, N), -2 * np.pi * lm[:, :1] * u[None, :])
-                ey = torch.polar(torch.ones_like(u)[None, :].expand(4, N), -2 * np.pi * lm[:, 1:] * u[None, :])
-                G = torch.zeros((4, N, N), dtype=torch.complex128, device=self.device)
-                G[0] = torch.einsum("s,sy,sx->yx", amp, ey, ex)
-                G[3] = G[0]
-                vis = torch.empty((o.n_baselines, o.n_timesteps, o.n_channels, 4), dtype=torch.complex64,
-                                  device=self.device)
-                slot.plan.degrid(G, A, vis)
-                out = self._host_buffer(slot, vis.shape, vis.dtype)
-                out.copy_(vis, non_blocking=True)
-                slot.bufs = {"A": A, "vis": vis, "G": G}
+                slot.plan.degrid(slot.bufs["G"], slot.bufs["A"], slot.bufs["vis"])
+                res = slot.bufs["vis"]
+            out = self._host_buffer(slot, res.shape, res.dtype)
+            out.copy_(res, non_blocking=True)
             slot.host_out = out
             slot.event = torch.cuda.Event(enable_timing=True)
             slot.event.record(slot.stream)
@@ -217,9 +203,85 @@ class Server:
         slot.pinned_s = time.perf_counter() - t
         return _pinned_view(slot.host_buf, shape, dtype)
 
+    def _synthesize(self, slot: _Slot):
+        """Inputs of a request on the current stream: its A-terms, and its
+        visibilities (grid) or model grid (degrid), from its seed."""
+        torch = self.torch
+        req = slot.req
+        o = req.obs
+        A = torch.as_tensor(req.aterms).to(self.device, non_blocking=True)
+        N = o.grid_size
+        gen = torch.Generator(device=self.device)
+        gen.manual_seed(req.seed)
+        if req.kind == "grid":
+            vis = torch.randn((o.n_baselines, o.n_timesteps, o.n_channels, 4), dtype=torch.complex64,
+                              device=self.device, generator=gen)
+            G = torch.zeros((4, N, N), dtype=torch.complex128, device=self.device)
+        else:
+            u = (torch.arange(N, device=self.device, dtype=torch.float64) - N // 2) / o.image_size
+            lm = (torch.rand((4, 2), device=self.device, dtype=torch.float64, generator=gen) - 0.5) \
+                * (o.image_size / 1.5)
+            amp = torch.randn((4,), dtype=torch.complex128, device=self.device, generator=gen)
+            ex = torch.polar(torch.ones_like(u)[None, :].expand(4, N), -2 * np.pi * lm[:, :1] * u[None, :])
+            ey = torch.polar(torch.ones_like(u)[None, :].expand(4, N), -2 * np.pi * lm[:, 1:] * u[None, :])
+            G = torch.zeros((4, N, N), dtype=torch.complex128, device=self.device)
+            G[0] = torch.einsum("s,sy,sx->yx", amp, ey, ex)
+            G[3] = G[0]
+            vis = torch.empty((o.n_baselines, o.n_timesteps, o.n_channels, 4), dtype=torch.complex64,
+                              device=self.device)
+        slot.bufs = {"A": A, "vis": vis, "G": G}
+
+    def _launch_wave(self, slots: list[_Slot], stream):
+        """One wave.  Each request makes its inputs on its own stream; the
+        wave's stream waits for all of them and runs, per kind of work, one
+        call whose launches share the work items of the wave's requests;
+        each request's stream then copies its result back and records its
+        completion event.  Inputs and copies of one wave thus overlap the
+        shared launches of others."""
+        torch = self.torch
+        inputs_ready = []
+        for slot in slots:
+            with torch.cuda.stream(slot.stream):
+                slot.start = torch.cuda.Event(enable_timing=True)
+                slot.start.record(slot.stream)
+                self._synthesize(slot)
+                ev = torch.cuda.Event()
+                ev.record(slot.stream)
+                inputs_ready.append(ev)
+        with torch.cuda.stream(stream):
+            for ev in inputs_ready:
+                stream.wait_event(ev)
+            groups: dict = {}
+            for slot in slots:
+                st = slot.plan.stats()
+                groups.setdefault((slot.req.kind, int(st.subgrid_size), int(st.degrid_channels)), []).append(slot)
+            for (kind, _, _), grp in groups.items():
+                plans = [sl.plan for sl in grp]
+                A = [sl.bufs["A"] for sl in grp]
+                if kind == "grid":
+                    idg.grid_many(plans, [sl.bufs["vis"] for sl in grp], A, [sl.bufs["G"] for sl in grp],
+                                  stream=stream.cuda_stream)
+                else:
+                    idg.degrid_many(plans, [sl.bufs["G"] for sl in grp], A, [sl.bufs["vis"] for sl in grp],
+                                    stream=stream.cuda_stream)
+            done = torch.cuda.Event()
+            done.record(stream)
+        for slot in slots:
+            with torch.cuda.stream(slot.stream):
+                slot.stream.wait_event(done)
+                res = slot.bufs["G"] if slot.req.kind == "grid" else slot.bufs["vis"]
+                out = self._host_buffer(slot, res.shape, res.dtype)
+                out.copy_(res, non_blocking=True)
+                slot.host_out = out
+                slot.event = torch.cuda.Event(enable_timing=True)
+                slot.event.record(slot.stream)
+        return done
+
     def run(self, requests: list[Request]) -> list[Result]:
         """Serve `requests` (arrival times relative to now); returns one
         Result per request in request order."""
+        if self.mode == "batched":
+            return self._run_waves(requests)
         torch = self.torch
         pending = sorted(requests, key=lambda r: r.arrival)
         queue: list[Request] = []
@@ -294,6 +356,112 @@ class Server:
         return [results[r.rid] for r in requests]
 
 
+class _Wave:
+    """A wave in flight: its stream (free again once `done`, the event after
+    its shared launches, has passed) and its requests not yet finished."""
+
+    def __init__(self, stream, done, slots):
+        self.stream, self.done, self.slots = stream, done, slots
+
+
+def _finish(server, slot, now):
+    r = Result(slot.req.rid, slot.req.kind, "ok", slot.req.obs.n_vis, slot.req.arrival, slot.admitted, now,
+               slot.host_out.numpy().copy() if server.keep_outputs else None, plan_s=slot.plan_s,
+               gpu_s=1e-3 * slot.start.elapsed_time(slot.event), pinned_s=slot.pinned_s)
+    PINNED.give(slot.host_buf)
+    slot.plan.close()
+    slot.bufs.clear()
+    return r
+
+
+def _run_waves(self, requests):
+    """The batched mode: see the module docstring."""
+    torch = self.torch
+    pending = sorted(requests, key=lambda r: r.arrival)
+    queue: list[Request] = []
+    planning: list[_Slot] = []
+    ready: list[_Slot] = []
+    waves: list[_Wave] = []                  # in flight
+    free_streams = [torch.cuda.Stream(self.device) for _ in range(4)]
+    request_streams = list(self.streams)     # one per admitted request
+    admitted = 0
+    used = 0
+    results: dict[int, Result] = {}
+    pool = cf.ThreadPoolExecutor(max_workers=self.plan_workers)
+    t0 = time.perf_counter()
+    now = lambda: time.perf_counter() - t0
+    plan_stream = torch.cuda.Stream(self.device)   # plan uploads; every plan synchronises it when made
+    try:
+        while pending or queue or planning or ready or waves:
+            t = now()
+            while pending and pending[0].arrival <= t:
+                queue.append(pending.pop(0))
+            while queue and admitted < self.max_slots:
+                req = queue[0]
+                if req.cancelled:
+                    queue.pop(0)
+                    results[req.rid] = Result(req.rid, req.kind, "cancelled", req.obs.n_vis, req.arrival)
+                    continue
+                need = footprint_bytes(req)
+                if need > self.budget:
+                    queue.pop(0)
+                    results[req.rid] = Result(req.rid, req.kind, "rejected: footprint exceeds the HBM budget",
+                                              req.obs.n_vis, req.arrival)
+                    continue
+                if used + need > self.budget:
+                    break
+                queue.pop(0)
+                slot = _Slot(req, now(), stream=request_streams.pop())
+                slot.future = pool.submit(self._make_plan, req, plan_stream.cuda_stream)
+                planning.append(slot)
+                admitted += 1
+                used += need
+            progressed = False
+            for slot in list(planning):
+                if slot.future.done():
+                    planning.remove(slot)
+                    progressed = True
+                    try:
+                        slot.plan, slot.plan_s = slot.future.result()
+                        ready.append(slot)
+                    except idg.IdgError as e:
+                        admitted -= 1
+                        used -= footprint_bytes(slot.req)
+                        request_streams.append(slot.stream)
+                        results[slot.req.rid] = Result(slot.req.rid, slot.req.kind, f"failed: {e}",
+                                                       slot.req.obs.n_vis, slot.req.arrival, slot.admitted, now())
+            for w in list(waves):
+                if w.done is not None and w.done.query():   # the shared launches are done: the stream is free
+                    free_streams.append(w.stream)
+                    w.done = None
+                for sl in list(w.slots):
+                    if sl.event.query():
+                        sl.plan.synchronize()
+                        results[sl.req.rid] = _finish(self, sl, now())
+                        w.slots = [x for x in w.slots if x is not sl]
+                        request_streams.append(sl.stream)
+                        admitted -= 1
+                        used -= footprint_bytes(sl.req)
+                        progressed = True
+                if not w.slots and w.done is None:
+                    waves = [x for x in waves if x is not w]
+            if ready and free_streams:
+                stream = free_streams.pop()
+                done = self._launch_wave(ready, stream)
+                waves.append(_Wave(stream, done, list(ready)))
+                ready = []
+                progressed = True
+            if not progressed:
+                time.sleep(0.0002)
+    finally:
+        pool.shutdown(wait=True)
+        torch.cuda.synchronize(self.device)
+    return [results[r.rid] for r in requests]
+
+
+Server._run_waves = _run_waves
+
+
 # -------------------------------------------------------------------- workload
 
 def make_stream(n_requests: int = 200, seed: int = 0, rate_hz: float = 2.0, stations=(64, 256),
@@ -340,26 +508,29 @@ def summarize(results: list[Result], t_wall: float | None = None) -> dict:
 
 
 def compare(n_requests: int = 40, seed: int = 0, loads=(0.7, 2.0), budget_gb: float = 64.0, slots: int = 8,
-            stations=(64, 256), channels=(8, 48), timesteps=(8, 120)) -> dict:
-    """Batched vs plain on the same Poisson streams: a calibration pass
-    measures the plain capacity (requests/s, 8 requests arriving at once),
-    then each load (a fraction of that capacity) is run in both modes."""
+            stations=(64, 256), channels=(8, 48), timesteps=(8, 120), modes=("plain", "batched")) -> dict:
+    """Modes side by side on the same Poisson streams.  A calibration pass
+    measures the plain capacity on the stream's own mix of requests (its
+    first 8, arriving at once); each load is an arrival rate in units of that
+    capacity, and load "burst" puts every request at t = 0 (service capacity
+    under saturation)."""
     import torch
 
     torch.cuda.init()
     shape = dict(stations=tuple(stations), channels=tuple(channels), timesteps=tuple(timesteps))
-    calib = make_stream(min(8, n_requests), seed=seed + 1000, rate_hz=1e9, **shape)
-    plain = Server(int(budget_gb * 2**30), mode="plain", keep_outputs=False)
+    calib = make_stream(min(8, n_requests), seed=seed, rate_hz=1e9, **shape)
     Server(int(budget_gb * 2**30), mode="plain", keep_outputs=False).run(calib[:1])  # warm-up
     t = time.perf_counter()
-    plain.run(calib)
+    Server(int(budget_gb * 2**30), mode="plain", keep_outputs=False).run(calib)
     cap = len(calib) / (time.perf_counter() - t)
     out = {"calibration_plain_requests_per_s": cap, "shape": shape, "budget_gb": budget_gb, "slots": slots}
     for load in loads:
-        key = f"load_{load:g}"
-        out[key] = {"arrival_rate_hz": load * cap}
-        for mode in ("plain", "batched"):
-            stream = make_stream(n_requests, seed=seed, rate_hz=load * cap, **shape)
+        burst = load == "burst"
+        key = "burst" if burst else f"load_{load:g}"
+        rate = 1e9 if burst else load * cap
+        out[key] = {"arrival_rate_hz": None if burst else rate}
+        for mode in modes:
+            stream = make_stream(n_requests, seed=seed, rate_hz=rate, **shape)
             srv = Server(int(budget_gb * 2**30), max_slots=slots, mode=mode, keep_outputs=False)
             out[key][mode] = summarize(srv.run(stream))
             del stream

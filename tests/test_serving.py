@@ -26,10 +26,14 @@ def test_stream_is_poisson_and_seeded():
 
 
 @pytest.mark.gpu
-def test_same_result_alone_and_in_the_mix(idg_mod, cuda_device):
+@pytest.mark.parametrize("mode", ["batched", "streams"])
+def test_same_result_alone_and_in_the_mix(idg_mod, cuda_device, mode):
+    """Each result of a mixed stream (grid and degrid, both geometries,
+    requests overlapping on the GPU) equals the same request served alone,
+    in the wave mode (shared launches) and the stream-per-request mode."""
     reqs = [_req(i, kind=("grid" if i % 2 == 0 else "degrid"), n_st=8 + 2 * i, arrival=0.01 * i,
                  idx=1 if i % 3 else 2, n_timesteps=6) for i in range(8)]
-    mixed = serve.Server(hbm_budget_bytes=48 << 30, max_slots=6, mode="batched").run(reqs)
+    mixed = serve.Server(hbm_budget_bytes=48 << 30, max_slots=6, mode=mode).run(reqs)
     assert all(r.status == "ok" for r in mixed)
     for r in reqs:
         r.arrival = 0.0
@@ -45,7 +49,8 @@ def test_same_result_alone_and_in_the_mix(idg_mod, cuda_device):
 
 
 @pytest.mark.gpu
-def test_rejection_cancellation_and_failed_plans(idg_mod, cuda_device):
+@pytest.mark.parametrize("mode", ["batched", "streams"])
+def test_rejection_cancellation_and_failed_plans(idg_mod, cuda_device, mode):
     ok = _req(0, n_st=6)
     too_big = _req(1, n_st=6)
     cancelled = _req(2, n_st=6)
@@ -54,7 +59,7 @@ def test_rejection_cancellation_and_failed_plans(idg_mod, cuda_device):
     bad.obs.uvw = bad.obs.uvw.copy()
     bad.obs.uvw[..., 2] = 5000.0  # w fringe too wide: the plan fails
     budget = serve.footprint_bytes(ok) + 1
-    srv = serve.Server(hbm_budget_bytes=budget, max_slots=2, mode="batched")
+    srv = serve.Server(hbm_budget_bytes=budget, max_slots=2, mode=mode)
     too_big.obs = synth.config(2, seed=1, n_stations=6)  # 4096^2 grid: needs more than the budget
     res = srv.run([ok, too_big, cancelled, bad])
     assert res[0].status == "ok"
