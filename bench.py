@@ -64,8 +64,8 @@ def ncu_traffic_command(kern: str) -> str:
     return (f'ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none '
             f'--kernel-name-base demangled -k regex:"idg::{kern}_kernel<" -c 2 --csv '
             f'--log-file traffic_{kern}.csv {BENCH_SHORT} --stations {TRAFFIC_STATIONS}')
-KERNEL_SOURCES = {"gridder": ["gridder.cu", "kernels_common.cuh", "idg_internal.h"],
-                  "degridder": ["degridder.cu", "kernels_common.cuh", "idg_internal.h"]}
+KERNEL_SOURCES = {"gridder": ["gridder.cu", "gridder_kernels.cuh", "kernels_common.cuh", "idg_internal.h"],
+                  "degridder": ["degridder.cu", "degridder_kernels.cuh", "kernels_common.cuh", "idg_internal.h"]}
 
 
 def _env_int(name, default):
@@ -422,7 +422,7 @@ def uneven_leg(idg, synth, dev, steps, n_sm, sm_max, r_vp_meas):
                       generator=g)
     side = torch.cuda.Stream(dev)
     L = 64
-    plan = idg.Plan(obs, subgrid_size=L, stream=side.cuda_stream)
+    plan = idg.Plan(obs, subgrid_size=L, stream=side.cuda_stream, grid_chunk=64)
     t_plan = time.time() - t0
     st = plan.stats()
     N = obs.grid_size
@@ -437,7 +437,9 @@ def uneven_leg(idg, synth, dev, steps, n_sm, sm_max, r_vp_meas):
            "workload": "256 stations, log-normal radii (median 300 m, <= 3 km), 32640 baselines, 360 x 0.5 s, "
                        "30 ch 140-170 MHz, 8192^2 FP64 grid, L = 64, P = 18, FOV 0.5, A-terms every 4 s "
                        "(beam x screen), random visibilities",
-           "n_vis": int(obs.n_vis), "launch": "one block per work item (autotuned on GB300), CUDA-graph replay",
+           "n_vis": int(obs.n_vis),
+           "launch": "one block per work item, gridder chunks of 64 records (the autotuner's choice on GB300), "
+                     "CUDA-graph replay",
            "graph_replay_ms": {"grid": g_ms, "degrid": d_ms}, "subgrids": int(st.n_subgrids),
            "vis_per_subgrid_min_median_max": [int(nv.min()), int(np.median(nv)), int(nv.max())],
            "vis_pixels_per_direction": float(st.vis_pixels), "kernels": kern, "plan_seconds": t_plan}
@@ -793,8 +795,9 @@ def run_native(args):
         del vis_in, gmodel_in, gout_d, vpred_d, gout_h, vpred_h
 
     # the 256-station uneven workload (352.5 M visibilities, subgrids of 360 to 10800 visibilities,
-    # 8192^2 grid) at L = 64 with one block per work item, the autotuner's choice on GB300, as CUDA-graph
-    # replays; random visibilities (the work does not depend on their values)
+    # 8192^2 grid) at L = 64 with one block per work item and gridder chunks of 64 records, the
+    # autotuner's choice on GB300, as CUDA-graph replays; random visibilities (the work does not depend
+    # on their values)
     uneven = None
     if args.uneven_steps > 0 and args.stations is None and args.timesteps is None:
         uneven = uneven_leg(idg, synth, dev, args.uneven_steps, n_sm, sm_max, r_vp_meas)

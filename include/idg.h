@@ -97,8 +97,8 @@ typedef struct {
                               cosine, the others by rotation with the channel-step phasor (the phase is
                               linear in frequency, Eq. 7); it needs uniformly spaced channels and falls back
                               to 1 otherwise (idg_plan_stats reports the value in use) */
-  int32_t grid_chunk;      /* gridder: staged visibility records per chunk copied to shared memory, 8 .. 64,
-                              or 0 for the default (48); a tuning choice, the results do not depend on it */
+  int32_t grid_chunk;      /* gridder: staged visibility records per chunk copied to shared memory, 32, 48 or
+                              64, or 0 for the default (48); a tuning choice, the results do not depend on it */
 } idg_geometry;
 
 typedef struct {
@@ -375,8 +375,8 @@ idg_status idg_plan_destroy(idg_plan* plan);
  * result is the one idg_grid / idg_degrid gives it.
  *   n            number of plans, >= 1
  *   plans        [n] device plans, distinct, sharing the subgrid size, the
- *                Stokes-I flag, the A-term normalisation flag and
- *                degrid_channels (IDG_ERR_INVALID_ARG otherwise)
+ *                Stokes-I flag, the A-term normalisation flag, grid_chunk
+ *                and degrid_channels (IDG_ERR_INVALID_ARG otherwise)
  *   vis_c64, aterms_c64, grid_c128
  *                [n] device buffers, per plan as for idg_grid / idg_degrid
  *   cuda_stream  the stream every launch of the call goes to (the plans' own

@@ -1,0 +1,10 @@
+// Degridder kernels for 32 x 32 subgrids (see degridder_kernels.cuh).
+#include "degridder_kernels.cuh"
+
+namespace idg {
+
+template int launch_degridder_l<32>(const DegridArgs&, int, int, int, void*, bool);
+template int configure_degridder_l<32>(int, int, int*);
+template int launch_degridder_multi_l<32>(int, bool, const DegridArgs*, const int2*, int, int, void*);
+
+}  // namespace idg

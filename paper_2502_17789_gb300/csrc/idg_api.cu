@@ -31,7 +31,8 @@ constexpr double kPi = 3.14159265358979323846;
 struct Batch {
   int32_t sg_offset, sg_count;
   int32_t gi_offset, gi_count;
-  int32_t di_offset, di_count;
+  int32_t di_offset, di_count;  // degridder items; then ds_count items of at most kSplitLanes lanes
+  int32_t ds_count;
 };
 
 template <typename T>
@@ -314,8 +315,8 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     return set_err(nullptr, IDG_ERR_INVALID_ARG, "taper_user is NULL");
   if (g->degrid_channels != 0 && !supported_degrid_channels(g->degrid_channels))
     return set_err(nullptr, IDG_ERR_INVALID_ARG, "degrid_channels must be 0, 1, 2 or 4");
-  if (g->grid_chunk != 0 && (g->grid_chunk < kMinGridChunk || g->grid_chunk > kMaxGridChunk))
-    return set_err(nullptr, IDG_ERR_INVALID_ARG, "grid_chunk must be 0 or in [8, 64]");
+  if (g->grid_chunk != 0 && !supported_grid_chunk(g->grid_chunk))
+    return set_err(nullptr, IDG_ERR_INVALID_ARG, "grid_chunk must be 0, 32, 48 or 64");
 
   idg_plan* p = new (std::nothrow) idg_plan();
   if (!p) return set_err(nullptr, IDG_ERR_OOM, "host allocation failed");
@@ -398,7 +399,7 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
   std::vector<DegridItem> ditems;
   for (size_t s0 = 0; s0 < p->exec.size(); s0 += p->batch_cap) {
     const int32_t cnt = int32_t(std::min<size_t>(p->batch_cap, p->exec.size() - s0));
-    Batch b{int32_t(s0), cnt, int32_t(gitems.size()), 0, int32_t(ditems.size()), 0};
+    Batch b{int32_t(s0), cnt, int32_t(gitems.size()), 0, int32_t(ditems.size()), 0, 0};
     // staged records of the batch, in batch order
     int64_t recs = 0;
     for (int32_t o = 0; o < cnt; ++o) {
@@ -420,6 +421,7 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     // segment shares its item with the first piece of the next segment when
     // both fit
     const int lanes = degrid_lanes(p->degrid_channels);
+    const size_t d_first = ditems.size();
     for (int32_t o : order) {
       const SubgridDesc& d = p->exec[s0 + o];
       const int width = d.c1 - d.c0;
@@ -440,8 +442,15 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
         }
       }
     }
+    // items of at most kSplitLanes lanes go last, for the kernel that spreads a visibility over
+    // several lanes; both parts keep the longest-first order
+    std::stable_partition(ditems.begin() + d_first, ditems.end(),
+                          [](const DegridItem& it) { return it.k_end - it.k_begin > kSplitLanes; });
+    size_t n_small = 0;
+    for (size_t i = d_first; i < ditems.size(); ++i) n_small += ditems[i].k_end - ditems[i].k_begin <= kSplitLanes;
     b.gi_count = int32_t(gitems.size()) - b.gi_offset;
-    b.di_count = int32_t(ditems.size()) - b.di_offset;
+    b.ds_count = int32_t(n_small);
+    b.di_count = int32_t(ditems.size()) - b.di_offset - b.ds_count;
     p->batches.push_back(b);
   }
   p->n_grid_items = int64_t(gitems.size());
@@ -665,9 +674,18 @@ idg_status idg_degrid(idg_plan* plan, const void* grid_c128, const void* aterms_
     da.g = kgeom(plan);
     e = timed(plan, kDegridder, [&] {
       return launch_degridder(L, plan->degrid_channels, da, b.di_count, plan->persistent_degrid_blocks,
-                              plan->stream);
+                              plan->stream, false);
     });
     if (e) return cuda_err(plan, e, "degridder launch");
+    if (b.ds_count > 0) {  // items of few lanes (low occupancy)
+      DegridArgs ds = da;
+      ds.items = plan->d_ditems + b.di_offset + b.di_count;
+      ds.n_items = b.ds_count;
+      e = timed(plan, kDegridder, [&] {
+        return launch_degridder(L, plan->degrid_channels, ds, b.ds_count, 0, plan->stream, true);
+      });
+      if (e) return cuda_err(plan, e, "degridder launch (items of few lanes)");
+    }
   }
   return IDG_OK;
 }
@@ -778,9 +796,10 @@ idg_status check_many(int32_t n, idg_plan* const* plans, const void* const* a, c
       return st;
     const idg_plan* p0 = plans[0];
     if (p->L != p0->L || p->npol != p0->npol || (p->d_aweights != nullptr) != (p0->d_aweights != nullptr) ||
-        p->degrid_channels != p0->degrid_channels)
+        p->degrid_channels != p0->degrid_channels || p->grid_chunk != p0->grid_chunk)
       return set_err(p, IDG_ERR_INVALID_ARG,
-                     "plans of one call must share subgrid size, Stokes-I mode, normalisation and degrid_channels");
+                     "plans of one call must share subgrid size, Stokes-I mode, normalisation, grid_chunk and "
+                     "degrid_channels");
     for (int32_t j = 0; j < k; ++j)
       if (plans[j] == p) return set_err(p, IDG_ERR_INVALID_ARG, "a plan appears twice");
   }
@@ -839,7 +858,6 @@ idg_status idg_grid_many(int32_t n, idg_plan* const* plans, const void* const* v
     std::vector<const int32_t*> cost;
     std::vector<int32_t> count;
     std::vector<int32_t> slot_plan;
-    int max_vc = kMinGridChunk;
     for (int32_t k = 0; k < n; ++k) {
       idg_plan* p = plans[k];
       if (w >= p->batches.size()) continue;
@@ -852,14 +870,14 @@ idg_status idg_grid_many(int32_t n, idg_plan* const* plans, const void* const* v
       cost.push_back(p->gcost.data() + b.gi_offset);
       count.push_back(b.gi_count);
       slot_plan.push_back(k);
-      max_vc = std::max(max_vc, p->grid_chunk);
     }
     const std::vector<int2> items = merge_items(cost, count);
     GridArgs* d_args = nullptr;
     int2* d_items = nullptr;
     int e = upload_wave(strm, args, items, &d_args, &d_items);
     if (!e)
-      e = launch_gridder_multi(L, d_args, d_items, int(items.size()), plans[0]->d_aweights != nullptr, max_vc, strm);
+      e = launch_gridder_multi(L, d_args, d_items, int(items.size()), plans[0]->d_aweights != nullptr,
+                               plans[0]->grid_chunk, strm);
     if (d_args) cudaFreeAsync(d_args, strm);
     if (d_items) cudaFreeAsync(d_items, strm);
     if (e) return cuda_err(plans[0], e, "gridder launch (several plans)");
@@ -899,8 +917,8 @@ idg_status idg_degrid_many(int32_t n, idg_plan* const* plans, const void* const*
   }
   for (size_t w = 0; w < n_waves; ++w) {
     std::vector<DegridArgs> args;
-    std::vector<const int32_t*> cost;
-    std::vector<int32_t> count;
+    std::vector<const int32_t*> cost, cost_s;
+    std::vector<int32_t> count, count_s;
     for (int32_t k = 0; k < n; ++k) {
       idg_plan* p = plans[k];
       if (w >= p->batches.size()) continue;
@@ -926,13 +944,23 @@ idg_status idg_degrid_many(int32_t n, idg_plan* const* plans, const void* const*
       args.push_back(da);
       cost.push_back(p->dcost.data() + b.di_offset);
       count.push_back(b.di_count);
+      cost_s.push_back(p->dcost.data() + b.di_offset + b.di_count);
+      count_s.push_back(b.ds_count);
     }
-    const std::vector<int2> items = merge_items(cost, count);
+    // regular items, then the items of few lanes; the latter index their plan's item table past
+    // the regular ones
+    std::vector<int2> items = merge_items(cost, count);
+    const size_t n_regular = items.size();
+    for (int2 it : merge_items(cost_s, count_s)) items.push_back(make_int2(it.x, count[it.x] + it.y));
     DegridArgs* d_args = nullptr;
     int2* d_items = nullptr;
     int e = upload_wave(strm, args, items, &d_args, &d_items);
     if (!e)
-      e = launch_degridder_multi(L, plans[0]->degrid_channels, d_args, d_items, int(items.size()), max_nodes, strm);
+      e = launch_degridder_multi(L, plans[0]->degrid_channels, false, d_args, d_items, int(n_regular), max_nodes,
+                                 strm);
+    if (!e && items.size() > n_regular)
+      e = launch_degridder_multi(L, plans[0]->degrid_channels, true, d_args, d_items + n_regular,
+                                 int(items.size() - n_regular), max_nodes, strm);
     if (d_args) cudaFreeAsync(d_args, strm);
     if (d_items) cudaFreeAsync(d_items, strm);
     if (e) return cuda_err(plans[0], e, "degridder launch (several plans)");

@@ -68,12 +68,14 @@ struct DegridItem {
 // lanes (channel groups) per degridder work item for C channels per lane
 __host__ __device__ constexpr int degrid_lanes(int C) { return C == 1 ? 256 : 128; }
 constexpr int kDefaultDegridChannels = 1;  // channels per degridder lane when the geometry leaves it 0
-// staged visibility records per gridder chunk (bulk copy into shared memory)
+// staged visibility records per gridder chunk (bulk copy into shared memory):
+// 32, 48 or 64 (supported_grid_chunk), one kernel instantiation each
 constexpr int kDefaultGridChunk = 48;
-constexpr int kMinGridChunk = 8;
-constexpr int kMaxGridChunk = 64;
 constexpr int kMaxAtermNodes = 25;  // A-term samples per axis (bounds the degridder's shared memory)
 constexpr int kDegridSegs = 2;  // segments per degridder work item
+// degridder items of at most this many lanes run in the kernel that spreads a
+// visibility over several lanes (low occupancy)
+constexpr int kSplitLanes = 8;
 
 // ---------------------------------------------------------------- planner
 
@@ -161,7 +163,7 @@ struct GridArgs {
   const float4* blk;          // [L][L/8][3] block geometry (n0, anchor offsets) (dn[0..3]) (dn[4..7])
   float2* scratch;            // [batch][4][L][L]
   double* aweights;           // A-term power weights [L*L + 1] (IDG_NORMALIZE_ATERM), else NULL
-  int vc = kDefaultGridChunk;  // staged records per chunk, kMinGridChunk .. kMaxGridChunk
+  int vc = kDefaultGridChunk;  // staged records per chunk: 32, 48 or 64
   KernelGeom g;
 };
 
@@ -195,9 +197,10 @@ struct FftArgs {
 // persistent_blocks > 0: persistent launch of that many blocks draining a.queue
 int launch_gridder(int L, const GridArgs& a, int n_items, int persistent_blocks, void* stream);
 // one launch over the items of several plans: args[slot] in device memory, items (slot, item index) in
-// launch order; max_vc the largest records-per-chunk among the slots
-int launch_gridder_multi(int L, const GridArgs* args, const int2* items, int n_items, bool norm, int max_vc,
+// launch order; vc the slots' common records per chunk
+int launch_gridder_multi(int L, const GridArgs* args, const int2* items, int n_items, bool norm, int vc,
                          void* stream);
+bool supported_grid_chunk(int vc);
 int configure_gridder(int L, int vc, int* persistent_blocks);   // attributes + persistent grid size
 // channels: channels per degridder lane (1, 2 or 4; > 1 needs uniform channel spacing)
 int configure_degridder(int L, int nodes, int channels, int* persistent_blocks);
@@ -216,9 +219,12 @@ int launch_image_pass(int npol, const double2* in, double2* out, const double* w
 int launch_wait_selftest(int* status, int64_t limit_ns, void* stream);
 // flags[i][s] = 1 when every node of A-term (interval i, station s) has zero off-diagonal entries
 int launch_aterm_flags(const float2* aterms, uint8_t* flags, int n_int, int n_st, int nodes, void* stream);
-int launch_degridder(int L, int channels, const DegridArgs& a, int n_items, int persistent_blocks, void* stream);
-int launch_degridder_multi(int L, int channels, const DegridArgs* args, const int2* items, int n_items, int max_nodes,
-                           void* stream);
+// split: the items are of at most kSplitLanes lanes and run in the kernel that spreads each
+// visibility's pixels over several lanes (one block per item; persistent_blocks is ignored)
+int launch_degridder(int L, int channels, const DegridArgs& a, int n_items, int persistent_blocks, void* stream,
+                     bool split);
+int launch_degridder_multi(int L, int channels, bool split, const DegridArgs* args, const int2* items, int n_items,
+                           int max_nodes, void* stream);
 // mode 0: FFT + add into grid; mode 1: FFT in place in scratch (inspection)
 int launch_fft_adder(int L, const FftArgs& a, int n_subgrids, int mode, void* stream);
 int launch_splitter_ifft(int L, const FftArgs& a, int n_subgrids, void* stream);

@@ -187,7 +187,7 @@ def test_degrid_low_occupancy(idg_mod, oracle_mod, cuda_device, channels, n_ch, 
     assert _rel(c.gpu_grid(), c.oracle_grid()) < GRID_TOL
 
 
-@pytest.mark.parametrize("chunk", [8, 32, 64])
+@pytest.mark.parametrize("chunk", [32, 64])
 def test_grid_chunk_sizes(idg_mod, oracle_mod, cuda_device, chunk):
     """Gridder record chunks other than the default (the autotuner's choice):
     chunks that end inside a segment, ragged chunk tails, one block per item

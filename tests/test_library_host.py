@@ -220,11 +220,11 @@ def test_planner_shrink_golden(idg_mod):
 
 
 def test_tuning_choices_are_validated_and_reported(idg_mod):
-    """grid_chunk (8 .. 64, 0 = default 48) and degrid_channels (0, 1, 2, 4)
+    """grid_chunk (32, 48, 64; 0 = default 48) and degrid_channels (0, 1, 2, 4)
     are checked at plan creation and reported by idg_plan_stats; channel
     groups need uniformly spaced channels and fall back to 1."""
     obs = _brute.tiny_observation(seed=1)
-    for chunk, ch, ok in ((0, 0, True), (8, 2, True), (64, 4, True), (7, 1, False), (65, 1, False), (48, 3, False)):
+    for chunk, ch, ok in ((0, 0, True), (32, 2, True), (64, 4, True), (8, 1, False), (65, 1, False), (48, 3, False)):
         g, _ = idg_mod.make_geometry(obs.grid_size, obs.subgrid_size, obs.kernel_padding, obs.image_size,
                                      flags=idg_mod.IDG_HOST_ONLY, grid_chunk=chunk, degrid_channels=ch)
         if ok:
