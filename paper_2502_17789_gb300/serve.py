@@ -543,11 +543,13 @@ def main(argv=None):
 
     from . import build
 
-    ap = argparse.ArgumentParser(description="IDG serving benchmark: batched vs plain on one GPU")
+    ap = argparse.ArgumentParser(description="IDG serving benchmark: shared-queue, per-stream and plain forms "
+                                             "on one GPU")
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--load", type=float, default=0.7, help="arrival rate as a fraction of plain capacity")
     ap.add_argument("--saturated-load", type=float, default=2.0, help="second, saturating arrival rate")
+    ap.add_argument("--modes", nargs="+", default=["plain", "streams", "batched"])
     ap.add_argument("--budget-gb", type=float, default=64.0)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--stations", type=int, nargs=2, default=(64, 256))
@@ -555,8 +557,8 @@ def main(argv=None):
     ap.add_argument("--timesteps", type=int, nargs=2, default=(8, 120))
     args = ap.parse_args(argv)
     build.build()
-    out = compare(args.requests, args.seed, (args.load, args.saturated_load), args.budget_gb, args.slots,
-                  args.stations, args.channels, args.timesteps)
+    out = compare(args.requests, args.seed, (args.load, args.saturated_load, "burst"), args.budget_gb, args.slots,
+                  args.stations, args.channels, args.timesteps, modes=tuple(args.modes))
     print(json.dumps(out))
 
 
