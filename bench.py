@@ -679,8 +679,14 @@ def run_native(args):
         plan_w.profile_read()
         w_ms = timed(step_w, args.wlayer_steps)
         prof_w = plan_w.profile_read()
+        # the layer count of the signed set {k * 2 w_max, k integer} without the conjugate mirror, for
+        # the same visibilities: the set the paper's {w_max, 3 w_max, ...} with w >= 0 roughly halves
+        w_lam = obs_w.uvw[:, :, 2][:, :, None] * (obs_w.freqs / synth.SPEED_OF_LIGHT)[None, None, :]
+        signed_layers = int(np.unique(np.floor(w_lam / float(st_w.w_layer_step) + 0.5)).size)
+        del w_lam
         w_layers = {"value": 2.0 * obs_w.n_vis / (w_ms * 1e-3), "unit": UNIT, "ms_per_step": w_ms,
                     "steps": args.wlayer_steps, "n_w_layers": int(st_w.n_w_layers),
+                    "n_w_layers_signed_unmirrored": signed_layers,
                     "w_layer_step_wavelengths": float(st_w.w_layer_step), "subgrids": int(st_w.n_subgrids),
                     "grid": f"complex128 [{int(st_w.n_w_layers)}][4][{N}][{N}]",
                     "array": "the 128-station 3 km disk with station heights of 50 m rms",
