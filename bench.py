@@ -65,7 +65,9 @@ def ncu_traffic_command(kern: str) -> str:
             f'--kernel-name-base demangled -k regex:"idg::{kern}_kernel<" -c 2 --csv '
             f'--log-file traffic_{kern}.csv {BENCH_SHORT} --stations {TRAFFIC_STATIONS}')
 KERNEL_SOURCES = {"gridder": ["gridder.cu", "gridder_kernels.cuh", "kernels_common.cuh", "idg_internal.h"],
-                  "degridder": ["degridder.cu", "degridder_kernels.cuh", "kernels_common.cuh", "idg_internal.h"]}
+                  "degridder": ["degridder.cu", "degridder_kernels.cuh", "kernels_common.cuh", "idg_internal.h"],
+                  "degridder_tc": ["degridder.cu", "degridder_tc_kernels.cuh", "degridder_kernels.cuh",
+                                   "kernels_common.cuh", "idg_internal.h"]}
 
 
 def _env_int(name, default):
@@ -342,6 +344,8 @@ def record_traffic(folder: str, full_obs, workload: str):
     small = synth.config(2, seed=0, n_stations=TRAFFIC_STATIONS)
     out = {}
     for kern in KERNEL_SOURCES:
+        if not os.path.exists(os.path.join(folder, f"traffic_{kern}.csv")):
+            continue
         with open(os.path.join(folder, f"traffic_{kern}.csv")) as f:
             rows = [r for r in csv.reader(f)]
         hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r and "Metric Name" in r)

@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define IDG_ABI_VERSION 2
+#define IDG_ABI_VERSION 3
 
 typedef struct idg_plan idg_plan; /* opaque, owned by the library */
 
@@ -61,6 +61,15 @@ typedef enum {
 } idg_status;
 
 enum { IDG_TAPER_KB = 0, IDG_TAPER_USER = 1 };
+
+/* Unit that takes the phasor sums' multiply-accumulate (idg_geometry.mac_unit). */
+enum {
+  IDG_MAC_DEFAULT = 0, /* the build's default (IDG_MAC_FP32) */
+  IDG_MAC_FP32 = 1,    /* FP32 FMA pipe of the CUDA cores */
+  IDG_MAC_TENSOR = 2   /* degridder: tensor cores, split-TF32 operands (A_hi B_hi + A_lo B_hi + A_hi B_lo,
+                          about FP32 accuracy) with FP32 accumulation; one visibility per row, so it uses one
+                          channel per lane whatever degrid_channels asks.  The gridder stays on FP32 */
+};
 
 enum {
   IDG_DROP_OUT_OF_GRID = 1,         /* drop subgrids that leave the grid instead of failing */
@@ -99,6 +108,8 @@ typedef struct {
                               to 1 otherwise (idg_plan_stats reports the value in use) */
   int32_t grid_chunk;      /* gridder: staged visibility records per chunk copied to shared memory, 32, 48 or
                               64, or 0 for the default (48); a tuning choice, the results do not depend on it */
+  int32_t mac_unit;        /* IDG_MAC_DEFAULT, IDG_MAC_FP32 or IDG_MAC_TENSOR: a tuning choice; the results
+                              agree to FP32 rounding */
 } idg_geometry;
 
 typedef struct {
@@ -122,6 +133,7 @@ typedef struct {
   int32_t n_pol;              /* planes per layer of grids and images: 4, or 1 with IDG_STOKES_I */
   int32_t degrid_channels;    /* channels per degridder lane in use */
   int32_t grid_chunk;         /* gridder records per chunk in use */
+  int32_t mac_unit;           /* IDG_MAC_FP32 or IDG_MAC_TENSOR in use */
 } idg_plan_stats_t;
 
 /*
@@ -375,8 +387,8 @@ idg_status idg_plan_destroy(idg_plan* plan);
  * result is the one idg_grid / idg_degrid gives it.
  *   n            number of plans, >= 1
  *   plans        [n] device plans, distinct, sharing the subgrid size, the
- *                Stokes-I flag, the A-term normalisation flag, grid_chunk
- *                and degrid_channels (IDG_ERR_INVALID_ARG otherwise)
+ *                Stokes-I flag, the A-term normalisation flag, grid_chunk,
+ *                degrid_channels and mac_unit (IDG_ERR_INVALID_ARG otherwise)
  *   vis_c64, aterms_c64, grid_c128
  *                [n] device buffers, per plan as for idg_grid / idg_degrid
  *   cuda_stream  the stream every launch of the call goes to (the plans' own

@@ -51,6 +51,53 @@ IDG_DEGRID_EXTERN(96)
 IDG_DEGRID_EXTERN(128)
 #undef IDG_DEGRID_EXTERN
 
+template <int L>
+int launch_degridder_tc_l(const DegridArgs& a, int n_items, int persistent_blocks, void* stream);
+template <int L>
+int configure_degridder_tc_l(int nodes, int* persistent_blocks);
+template <int L>
+int launch_degridder_tc_multi_l(const DegridArgs* args, const int2* items, int n_items, int max_nodes, void* stream);
+#define IDG_DEGRID_TC_EXTERN(L)                                                                                  \
+  extern template int launch_degridder_tc_l<L>(const DegridArgs&, int, int, void*);                             \
+  extern template int configure_degridder_tc_l<L>(int, int*);                                                   \
+  extern template int launch_degridder_tc_multi_l<L>(const DegridArgs*, const int2*, int, int, void*);
+IDG_DEGRID_TC_EXTERN(32)
+IDG_DEGRID_TC_EXTERN(64)
+IDG_DEGRID_TC_EXTERN(96)
+IDG_DEGRID_TC_EXTERN(128)
+#undef IDG_DEGRID_TC_EXTERN
+
+int launch_degridder_tc(int L, const DegridArgs& a, int n_items, int persistent_blocks, void* stream) {
+  switch (L) {
+    case 32: return launch_degridder_tc_l<32>(a, n_items, persistent_blocks, stream);
+    case 64: return launch_degridder_tc_l<64>(a, n_items, persistent_blocks, stream);
+    case 96: return launch_degridder_tc_l<96>(a, n_items, persistent_blocks, stream);
+    case 128: return launch_degridder_tc_l<128>(a, n_items, persistent_blocks, stream);
+    default: return int(cudaErrorInvalidValue);
+  }
+}
+
+int configure_degridder_tc(int L, int nodes, int* persistent_blocks) {
+  switch (L) {
+    case 32: return configure_degridder_tc_l<32>(nodes, persistent_blocks);
+    case 64: return configure_degridder_tc_l<64>(nodes, persistent_blocks);
+    case 96: return configure_degridder_tc_l<96>(nodes, persistent_blocks);
+    case 128: return configure_degridder_tc_l<128>(nodes, persistent_blocks);
+    default: return int(cudaErrorInvalidValue);
+  }
+}
+
+int launch_degridder_tc_multi(int L, const DegridArgs* args, const int2* items, int n_items, int max_nodes,
+                              void* stream) {
+  switch (L) {
+    case 32: return launch_degridder_tc_multi_l<32>(args, items, n_items, max_nodes, stream);
+    case 64: return launch_degridder_tc_multi_l<64>(args, items, n_items, max_nodes, stream);
+    case 96: return launch_degridder_tc_multi_l<96>(args, items, n_items, max_nodes, stream);
+    case 128: return launch_degridder_tc_multi_l<128>(args, items, n_items, max_nodes, stream);
+    default: return int(cudaErrorInvalidValue);
+  }
+}
+
 bool supported_degrid_channels(int channels) { return channels == 1 || channels == 2 || channels == 4; }
 
 int launch_degridder_multi(int L, int channels, bool split, const DegridArgs* args, const int2* items, int n_items,

@@ -51,6 +51,7 @@ struct idg_plan {
   int32_t npol = 4;                  // master-grid planes per layer: 4, or 1 with IDG_STOKES_I
   int32_t degrid_channels = 1;       // channels per degridder lane
   int32_t grid_chunk = kDefaultGridChunk;  // staged records per gridder chunk
+  int32_t mac = IDG_MAC_FP32;        // multiply-accumulate unit of the degridder
   cudaStream_t stream = nullptr;
   bool host_only = false;
   Partition part;
@@ -317,6 +318,8 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     return set_err(nullptr, IDG_ERR_INVALID_ARG, "degrid_channels must be 0, 1, 2 or 4");
   if (g->grid_chunk != 0 && !supported_grid_chunk(g->grid_chunk))
     return set_err(nullptr, IDG_ERR_INVALID_ARG, "grid_chunk must be 0, 32, 48 or 64");
+  if (g->mac_unit != IDG_MAC_DEFAULT && g->mac_unit != IDG_MAC_FP32 && g->mac_unit != IDG_MAC_TENSOR)
+    return set_err(nullptr, IDG_ERR_INVALID_ARG, "mac_unit must be IDG_MAC_DEFAULT, IDG_MAC_FP32 or IDG_MAC_TENSOR");
 
   idg_plan* p = new (std::nothrow) idg_plan();
   if (!p) return set_err(nullptr, IDG_ERR_OOM, "host allocation failed");
@@ -378,6 +381,8 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     const int want = g->degrid_channels > 0 ? g->degrid_channels : kDefaultDegridChannels;
     p->degrid_channels = uniform ? want : 1;
   }
+  p->mac = g->mac_unit == IDG_MAC_TENSOR ? IDG_MAC_TENSOR : IDG_MAC_FP32;
+  if (p->mac == IDG_MAC_TENSOR) p->degrid_channels = 1;  // one visibility per row of the tensor-core product
   p->grid_chunk = g->grid_chunk > 0 ? g->grid_chunk : kDefaultGridChunk;
   for (SubgridDesc& d : p->exec) d.layer -= k_lo;  // device tables hold the grid plane set
   if (host_only) {
@@ -432,7 +437,10 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
         const int g_begin = sgd.k_begin / width * G, g_end = sgd.k_end / width * G;
         for (int k = g_begin; k < g_end; k += lanes) {
           const int ke = std::min(k + lanes, g_end);
-          if (open && k == g_begin && ditems.back().k_end - ditems.back().k_begin + (ke - k) <= lanes) {
+          // the tensor-core degridder starts the second segment at the next 16-row tile
+          const int first = ditems.empty() ? 0 : ditems.back().k_end - ditems.back().k_begin;
+          const int held = p->mac == IDG_MAC_TENSOR ? (first + 15) / 16 * 16 : first;
+          if (open && k == g_begin && held + (ke - k) <= lanes) {
             ditems.back().k_end = ke;  // second segment of the item
             open = false;
           } else {
@@ -483,7 +491,9 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
   int pg = 0, pd = 0;
   int e = configure_kernels(L);
   if (!e) e = configure_gridder(L, p->grid_chunk, &pg);
+  // the FP32 kernels serve the items of few visibilities in either mode
   if (!e) e = configure_degridder(L, g->aterm_nodes, p->degrid_channels, &pd);
+  if (!e && p->mac == IDG_MAC_TENSOR) e = configure_degridder_tc(L, g->aterm_nodes, &pd);
   if (g->flags & IDG_PERSISTENT) {
     p->persistent_grid_blocks = pg;
     p->persistent_degrid_blocks = pd;
@@ -673,6 +683,8 @@ idg_status idg_degrid(idg_plan* plan, const void* grid_c128, const void* aterms_
     da.scratch = plan->d_scratch;
     da.g = kgeom(plan);
     e = timed(plan, kDegridder, [&] {
+      if (plan->mac == IDG_MAC_TENSOR)
+        return launch_degridder_tc(L, da, b.di_count, plan->persistent_degrid_blocks, plan->stream);
       return launch_degridder(L, plan->degrid_channels, da, b.di_count, plan->persistent_degrid_blocks,
                               plan->stream, false);
     });
@@ -796,10 +808,10 @@ idg_status check_many(int32_t n, idg_plan* const* plans, const void* const* a, c
       return st;
     const idg_plan* p0 = plans[0];
     if (p->L != p0->L || p->npol != p0->npol || (p->d_aweights != nullptr) != (p0->d_aweights != nullptr) ||
-        p->degrid_channels != p0->degrid_channels || p->grid_chunk != p0->grid_chunk)
+        p->degrid_channels != p0->degrid_channels || p->grid_chunk != p0->grid_chunk || p->mac != p0->mac)
       return set_err(p, IDG_ERR_INVALID_ARG,
-                     "plans of one call must share subgrid size, Stokes-I mode, normalisation, grid_chunk and "
-                     "degrid_channels");
+                     "plans of one call must share subgrid size, Stokes-I mode, normalisation, grid_chunk, "
+                     "degrid_channels and mac_unit");
     for (int32_t j = 0; j < k; ++j)
       if (plans[j] == p) return set_err(p, IDG_ERR_INVALID_ARG, "a plan appears twice");
   }
@@ -956,8 +968,10 @@ idg_status idg_degrid_many(int32_t n, idg_plan* const* plans, const void* const*
     int2* d_items = nullptr;
     int e = upload_wave(strm, args, items, &d_args, &d_items);
     if (!e)
-      e = launch_degridder_multi(L, plans[0]->degrid_channels, false, d_args, d_items, int(n_regular), max_nodes,
-                                 strm);
+      e = plans[0]->mac == IDG_MAC_TENSOR
+              ? launch_degridder_tc_multi(L, d_args, d_items, int(n_regular), max_nodes, strm)
+              : launch_degridder_multi(L, plans[0]->degrid_channels, false, d_args, d_items, int(n_regular),
+                                       max_nodes, strm);
     if (!e && items.size() > n_regular)
       e = launch_degridder_multi(L, plans[0]->degrid_channels, true, d_args, d_items + n_regular,
                                  int(items.size() - n_regular), max_nodes, strm);
@@ -1174,6 +1188,7 @@ idg_status idg_plan_stats(const idg_plan* plan, idg_plan_stats_t* out) {
   out->w_layer_step = plan->part.w_step;
   out->degrid_channels = plan->degrid_channels;
   out->grid_chunk = plan->grid_chunk;
+  out->mac_unit = plan->mac;
   return IDG_OK;
 }
 

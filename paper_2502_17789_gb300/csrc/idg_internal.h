@@ -76,6 +76,7 @@ constexpr int kDegridSegs = 2;  // segments per degridder work item
 // degridder items of at most this many lanes run in the kernel that spreads a
 // visibility over several lanes (low occupancy)
 constexpr int kSplitLanes = 8;
+constexpr int kTcItemRows = 256;  // rows (16-row tiles) per item of the tensor-core degridder
 
 // ---------------------------------------------------------------- planner
 
@@ -225,6 +226,12 @@ int launch_degridder(int L, int channels, const DegridArgs& a, int n_items, int 
                      bool split);
 int launch_degridder_multi(int L, int channels, bool split, const DegridArgs* args, const int2* items, int n_items,
                            int max_nodes, void* stream);
+// the degridder on the tensor cores (split-TF32 mma.sync, one visibility per row); its items may hold
+// two segments only when the first, rounded up to 16 rows, and the second fit in kTcItemRows rows
+int launch_degridder_tc(int L, const DegridArgs& a, int n_items, int persistent_blocks, void* stream);
+int configure_degridder_tc(int L, int nodes, int* persistent_blocks);
+int launch_degridder_tc_multi(int L, const DegridArgs* args, const int2* items, int n_items, int max_nodes,
+                              void* stream);
 // mode 0: FFT + add into grid; mode 1: FFT in place in scratch (inspection)
 int launch_fft_adder(int L, const FftArgs& a, int n_subgrids, int mode, void* stream);
 int launch_splitter_ifft(int L, const FftArgs& a, int n_subgrids, void* stream);

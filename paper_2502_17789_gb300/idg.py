@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "IDG_OK", 1: "IDG_ERR_INVALID_ARG", 2: "IDG_ERR_UNSORTED_FREQ
 IDG_TAPER_KB, IDG_TAPER_USER = 0, 1
 IDG_DROP_OUT_OF_GRID, IDG_SPLIT_AT_ATERM_INTERVALS, IDG_HOST_ONLY, IDG_PERSISTENT, IDG_W_LAYERS = 1, 2, 4, 8, 16
 IDG_NORMALIZE_ATERM, IDG_STOKES_I = 32, 64
+IDG_MAC_DEFAULT, IDG_MAC_FP32, IDG_MAC_TENSOR = 0, 1, 2
 
 # every function declared in include/idg.h
 EXPORTS = ["idg_plan_create", "idg_grid", "idg_degrid", "idg_grid_graph", "idg_degrid_graph", "idg_set_stream", "idg_plan_stats", "idg_plan_subgrids",
@@ -42,7 +43,8 @@ class Geometry(ctypes.Structure):
     _fields_ = [("grid_size", ctypes.c_int32), ("subgrid_size", ctypes.c_int32), ("kernel_padding", ctypes.c_int32),
                 ("image_size", ctypes.c_double), ("taper_kind", ctypes.c_int32), ("taper_beta", ctypes.c_double),
                 ("taper_user", ctypes.POINTER(ctypes.c_double)), ("aterm_nodes", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("degrid_channels", ctypes.c_int32), ("grid_chunk", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("degrid_channels", ctypes.c_int32), ("grid_chunk", ctypes.c_int32),
+                ("mac_unit", ctypes.c_int32)]
 
 
 class PlanStats(ctypes.Structure):
@@ -52,7 +54,8 @@ class PlanStats(ctypes.Structure):
                 ("occupancy_hist", ctypes.c_int64 * 16), ("device_bytes", ctypes.c_int64),
                 ("vis_pixels", ctypes.c_int64), ("subgrid_size", ctypes.c_int32), ("batch_capacity", ctypes.c_int32),
                 ("n_w_layers", ctypes.c_int32), ("w_layer_min", ctypes.c_int32), ("w_layer_step", ctypes.c_double),
-                ("n_pol", ctypes.c_int32), ("degrid_channels", ctypes.c_int32), ("grid_chunk", ctypes.c_int32)]
+                ("n_pol", ctypes.c_int32), ("degrid_channels", ctypes.c_int32), ("grid_chunk", ctypes.c_int32),
+                ("mac_unit", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -284,7 +287,7 @@ def idg_abi_version() -> int:
 # ----------------------------------------------------------------- torch-facing wrapper
 
 def make_geometry(grid_size, subgrid_size, kernel_padding, image_size, taper_beta=0.0, aterm_nodes=9, flags=0,
-                  taper_user=None, degrid_channels=0, grid_chunk=0) -> tuple[Geometry, object]:
+                  taper_user=None, degrid_channels=0, grid_chunk=0, mac_unit=0) -> tuple[Geometry, object]:
     g = Geometry()
     g.grid_size, g.subgrid_size, g.kernel_padding = int(grid_size), int(subgrid_size), int(kernel_padding)
     g.image_size = float(image_size)
@@ -300,6 +303,7 @@ def make_geometry(grid_size, subgrid_size, kernel_padding, image_size, taper_bet
     g.flags = int(flags)
     g.degrid_channels = int(degrid_channels)
     g.grid_chunk = int(grid_chunk)
+    g.mac_unit = int(mac_unit)
     return g, keep
 
 
@@ -313,7 +317,8 @@ class Plan:
 
     def __init__(self, obs=None, *, grid_size=None, subgrid_size=None, kernel_padding=None, image_size=None,
                  n_stations=None, baselines=None, uvw=None, freqs=None, aterm_offsets=None, aterm_nodes=9,
-                 flags=0, taper_beta=0.0, taper_user=None, stream=None, degrid_channels=0, grid_chunk=0):
+                 flags=0, taper_beta=0.0, taper_user=None, stream=None, degrid_channels=0, grid_chunk=0,
+                 mac_unit=0):
         if obs is not None:
             grid_size = obs.grid_size if grid_size is None else grid_size
             subgrid_size = obs.subgrid_size if subgrid_size is None else subgrid_size
@@ -322,7 +327,8 @@ class Plan:
             n_stations, baselines, uvw = obs.n_stations, obs.baselines, obs.uvw
             freqs, aterm_offsets, aterm_nodes = obs.freqs, obs.aterm_offsets, obs.aterm_nodes
         self.geometry, self._keep = make_geometry(grid_size, subgrid_size, kernel_padding, image_size, taper_beta,
-                                                  aterm_nodes, flags, taper_user, degrid_channels, grid_chunk)
+                                                  aterm_nodes, flags, taper_user, degrid_channels, grid_chunk,
+                                                  mac_unit)
         if stream is None and not (flags & IDG_HOST_ONLY):
             import torch
             stream = torch.cuda.current_stream().cuda_stream  # 0 when that is the legacy default stream

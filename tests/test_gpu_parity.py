@@ -37,10 +37,11 @@ def _oracle_geom(oracle_mod, obs, L, flags):
 
 
 class Case:
-    def __init__(self, idg_mod, oracle_mod, obs, A, vis, L=None, flags=0, degrid_channels=0):
+    def __init__(self, idg_mod, oracle_mod, obs, A, vis, L=None, flags=0, degrid_channels=0, mac_unit=0):
         import torch
         self.obs, self.L = obs, L or obs.subgrid_size
-        self.plan = idg_mod.Plan(obs, subgrid_size=self.L, flags=flags, degrid_channels=degrid_channels)
+        self.plan = idg_mod.Plan(obs, subgrid_size=self.L, flags=flags, degrid_channels=degrid_channels,
+                                 mac_unit=mac_unit)
         self.geom = _oracle_geom(oracle_mod, obs, self.L, flags)
         self.ref_plan = oracle_mod.plan(self.geom, obs.uvw, obs.freqs, obs.aterm_offsets)
         np.testing.assert_array_equal(self.plan.subgrids(), self.ref_plan.subgrids)

@@ -30,7 +30,7 @@ def test_library_exports_every_declared_symbol(idg_mod):
     assert sorted(idg_mod.EXPORTS) == names
     for n in names:
         assert hasattr(lib, n), n
-    assert idg_mod.idg_abi_version() == 2
+    assert idg_mod.idg_abi_version() == 3
 
 
 def _host_plan(idg_mod, obs, flags=0, L=None):
