@@ -66,6 +66,64 @@ __device__ __forceinline__ int tc_row(int l, int n0, int r1, int n_seg) {
   return (n_seg == 2 && l >= n0) ? r1 + (l - n0) : l;
 }
 
+// The sums of CNT tiles (tiles gb .. gb + CNT - 1) over this lane's 16-pixel
+// run of the chunk, added into S.out.  CNT is a compile-time count so that
+// the tiles' independent sine/cosine, split and MMA chains interleave.
+template <int CNT>
+__device__ __forceinline__ void tc_group_sum(DegridTcSmem& S, const float2* zs, const float* dn, const float4 g0,
+                                             int gb, int g, int t) {
+  const bool odd = g & 1;
+  float2 R0[CNT], AR[CNT], CR[CNT];
+#pragma unroll
+  for (int m = 0; m < CNT; ++m) {
+    const int ra = 16 * (gb + m) + g;
+    const float4 c1a = S.coef[1][ra], c1b = S.coef[1][ra + 8];
+    R0[m] = make_float2(anchor_phase(S.coef[0][ra], c1a, g0.x, g0.y, g0.z),
+                        anchor_phase(S.coef[0][ra + 8], c1b, g0.x, g0.y, g0.z));
+    AR[m] = make_float2(c1a.y, c1b.y);
+    CR[m] = make_float2(c1a.z, c1b.z);
+  }
+  float acc[CNT][4];
+#pragma unroll
+  for (int m = 0; m < CNT; ++m) acc[m][0] = acc[m][1] = acc[m][2] = acc[m][3] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    // B fragment of step k: this lane's column is pol g/2, re (g even) or im (g odd)
+    const float2 z = zs[k * kTcZRow];
+    uint32_t Bh[2], Bl[2];
+    tf32_split(odd ? z.y : z.x, Bh[0], Bl[0]);
+    tf32_split(odd ? -z.x : z.y, Bh[1], Bl[1]);
+    const float dnk = dn[k];
+    const float2 DN = make_float2(dnk, dnk);
+    const float2 DI = make_float2(float(k - 8), float(k - 8));
+#pragma unroll
+    for (int m = 0; m < CNT; ++m) {
+      const float2 ph = ffma2(CR[m], DN, ffma2(AR[m], DI, R0[m]));
+      float ca, sa, cb, sb;
+      __sincosf(ph.x, &sa, &ca);
+      __sincosf(ph.y, &sb, &cb);
+      // A fragment: (row g, col t) cos, (row g+8, col t) cos, (row g, col t+4) sin, (row g+8, col t+4) sin
+      uint32_t Ah[4], Al[4];
+      tf32_split(ca, Ah[0], Al[0]);
+      tf32_split(cb, Ah[1], Al[1]);
+      tf32_split(sa, Ah[2], Al[2]);
+      tf32_split(sb, Ah[3], Al[3]);
+      mma_tf32_16x8x8(acc[m], Ah, Bh);
+      mma_tf32_16x8x8(acc[m], Al, Bh);
+      mma_tf32_16x8x8(acc[m], Ah, Bl);
+    }
+  }
+  // D fragment: (row g, cols 2t, 2t+1) and (row g+8, cols 2t, 2t+1) = pol t (re, im)
+#pragma unroll
+  for (int m = 0; m < CNT; ++m) {
+    const int ra = 16 * (gb + m) + g;
+    atomicAdd(&S.out[2 * t][ra], acc[m][0]);
+    atomicAdd(&S.out[2 * t + 1][ra], acc[m][1]);
+    atomicAdd(&S.out[2 * t][ra + 8], acc[m][2]);
+    atomicAdd(&S.out[2 * t + 1][ra + 8], acc[m][3]);
+  }
+}
+
 template <int L>
 __device__ __forceinline__ void degridder_tc_item(const DegridArgs& a, int item_idx, DegridTcSmem& S, float2* s_A) {
   constexpr int TPR = L / 8;
@@ -188,11 +246,9 @@ __device__ __forceinline__ void degridder_tc_item(const DegridArgs& a, int item_
   build_z(0, 0);
   __syncthreads();
 
-  const bool odd = g & 1;
   for (int chunk = 0; chunk < NCH; ++chunk) {
     const int buf = chunk & 1;
     const bool more = chunk + 1 < NCH;
-    if (more) load_y(chunk + 1);
     const float4* Gm = S.g[buf][4 * warp + t];  // this lane's 16-pixel anchor block
     const float4 g0 = Gm[0];
     const float* dn = reinterpret_cast<const float*>(Gm + 1);  // n' increments of its 16 pixels
@@ -202,66 +258,18 @@ __device__ __forceinline__ void degridder_tc_item(const DegridArgs& a, int item_
       const int tb = s == 0 ? 0 : T0, te = s == 0 ? T0 : T0 + T1;
 #pragma unroll 1
       for (int gb = tb; gb < te; gb += kTcGroup) {
-        const int cnt = imin(kTcGroup, te - gb);
-        float2 R0[kTcGroup], AR[kTcGroup], CR[kTcGroup];
-#pragma unroll
-        for (int m = 0; m < kTcGroup; ++m) {
-          R0[m] = AR[m] = CR[m] = make_float2(0.f, 0.f);
-          if (m < cnt) {
-            const int ra = 16 * (gb + m) + g;
-            const float4 c1a = S.coef[1][ra], c1b = S.coef[1][ra + 8];
-            R0[m] = make_float2(anchor_phase(S.coef[0][ra], c1a, g0.x, g0.y, g0.z),
-                                anchor_phase(S.coef[0][ra + 8], c1b, g0.x, g0.y, g0.z));
-            AR[m] = make_float2(c1a.y, c1b.y);
-            CR[m] = make_float2(c1a.z, c1b.z);
-          }
-        }
-        float acc[kTcGroup][4];
-#pragma unroll
-        for (int m = 0; m < kTcGroup; ++m) acc[m][0] = acc[m][1] = acc[m][2] = acc[m][3] = 0.f;
-#pragma unroll 4
-        for (int k = 0; k < 16; ++k) {
-          // B fragment of step k: this lane's column is pol g/2, re (g even) or im (g odd)
-          const float2 z = zs[k * kTcZRow];
-          uint32_t Bh[2], Bl[2];
-          tf32_split(odd ? z.y : z.x, Bh[0], Bl[0]);
-          tf32_split(odd ? -z.x : z.y, Bh[1], Bl[1]);
-          const float dnk = dn[k];
-          const float2 DN = make_float2(dnk, dnk);
-          const float2 DI = make_float2(float(k - 8), float(k - 8));
-#pragma unroll
-          for (int m = 0; m < kTcGroup; ++m) {
-            if (m < cnt) {
-              const float2 ph = ffma2(CR[m], DN, ffma2(AR[m], DI, R0[m]));
-              float ca, sa, cb, sb;
-              __sincosf(ph.x, &sa, &ca);
-              __sincosf(ph.y, &sb, &cb);
-              // A fragment: (row g, col t) cos, (row g+8, col t) cos, (row g, col t+4) sin, (row g+8, col t+4) sin
-              uint32_t Ah[4], Al[4];
-              tf32_split(ca, Ah[0], Al[0]);
-              tf32_split(cb, Ah[1], Al[1]);
-              tf32_split(sa, Ah[2], Al[2]);
-              tf32_split(sb, Ah[3], Al[3]);
-              mma_tf32_16x8x8(acc[m], Ah, Bh);
-              mma_tf32_16x8x8(acc[m], Al, Bh);
-              mma_tf32_16x8x8(acc[m], Ah, Bl);
-            }
-          }
-        }
-        // D fragment: (row g, cols 2t, 2t+1) and (row g+8, cols 2t, 2t+1) = pol t (re, im)
-#pragma unroll
-        for (int m = 0; m < kTcGroup; ++m) {
-          if (m < cnt) {
-            const int ra = 16 * (gb + m) + g;
-            atomicAdd(&S.out[2 * t][ra], acc[m][0]);
-            atomicAdd(&S.out[2 * t + 1][ra], acc[m][1]);
-            atomicAdd(&S.out[2 * t][ra + 8], acc[m][2]);
-            atomicAdd(&S.out[2 * t + 1][ra + 8], acc[m][3]);
-          }
+        switch (imin(kTcGroup, te - gb)) {
+          case 4: tc_group_sum<4>(S, zs, dn, g0, gb, g, t); break;
+          case 3: tc_group_sum<3>(S, zs, dn, g0, gb, g, t); break;
+          case 2: tc_group_sum<2>(S, zs, dn, g0, gb, g, t); break;
+          default: tc_group_sum<1>(S, zs, dn, g0, gb, g, t); break;
         }
       }
     }
-    if (more) build_z(chunk + 1, buf ^ 1);
+    if (more) {
+      load_y(chunk + 1);
+      build_z(chunk + 1, buf ^ 1);
+    }
     __syncthreads();
   }
 
