@@ -67,7 +67,16 @@ def ncu_traffic_command(kern: str) -> str:
 KERNEL_SOURCES = {"gridder": ["gridder.cu", "gridder_kernels.cuh", "kernels_common.cuh", "idg_internal.h"],
                   "degridder": ["degridder.cu", "degridder_kernels.cuh", "kernels_common.cuh", "idg_internal.h"],
                   "degridder_tc": ["degridder.cu", "degridder_tc_kernels.cuh", "degridder_kernels.cuh",
-                                   "kernels_common.cuh", "idg_internal.h"]}
+                                   "kernels_common.cuh", "idg_internal.h"],
+                  "gridder_tc": ["gridder.cu", "gridder_tc_kernels.cuh", "kernels_common.cuh", "idg_internal.h"]}
+
+
+def kernel_of(kind: str, mac_unit: int) -> str:
+    """The kernel (ncu name prefix, traffic key) a plan with `mac_unit` in use
+    runs for the timing class `kind` (gridder or degridder)."""
+    if kind == "gridder":
+        return "gridder_tc" if mac_unit == 2 else "gridder"
+    return "degridder" if mac_unit == 1 else "degridder_tc"
 
 
 def _env_int(name, default):
@@ -328,7 +337,7 @@ def algorithmic_bytes_per_launch(kern: str, obs, L: int) -> float:
     per_sg = 4 * L * L * 8
     n_batches = max(1, -(-n_sg // max(1, (1 << 30) // per_sg)))
     pix = n_sg * L * L * 32.0
-    total = (128.0 * n_vis + pix) if kern == "gridder" else (pix + 32.0 * n_vis)
+    total = (128.0 * n_vis + pix) if kern.startswith("gridder") else (pix + 32.0 * n_vis)
     return total / n_batches
 
 
@@ -354,7 +363,7 @@ def record_traffic(folder: str, full_obs, workload: str):
         per = collections.defaultdict(float)
         for r in rows[hi + 1:]:
             if len(r) > vi and r[mi] in ("dram__bytes_read.sum", "dram__bytes_write.sum") and \
-                    f"{kern}_kernel" in r[ki] and not (kern == "gridder" and "degridder" in r[ki]):
+                    f"{kern}_kernel" in r[ki] and not (kern.startswith("gridder") and "degridder" in r[ki]):
                 per[r[ii]] += float(r[vi].replace(",", "")) * scale.get(r[ui], 1.0)
         if not per:
             continue
@@ -553,8 +562,9 @@ def run_native(args):
     peak_tflops = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved_vispx = vispx / (k_ms * 1e-3)
     achieved = achieved_vispx * FLOP_PER_VISPX / 1e12
-    traffic = recorded_traffic(kern, desc)
-    roofline = {"bound": "alu", "kernel": kern, "achieved": round(achieved, 3), "peak": round(peak_tflops, 3),
+    kern_name = kernel_of(kern, int(st.mac_unit))
+    traffic = recorded_traffic(kern_name, desc)
+    roofline = {"bound": "alu", "kernel": kern_name, "achieved": round(achieved, 3), "peak": round(peak_tflops, 3),
                 "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": traffic,
                 "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)",
                 "achieved_vispx_per_s": achieved_vispx, "flop_per_vispx": FLOP_PER_VISPX,

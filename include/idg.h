@@ -62,13 +62,16 @@ typedef enum {
 
 enum { IDG_TAPER_KB = 0, IDG_TAPER_USER = 1 };
 
-/* Unit that takes the phasor sums' multiply-accumulate (idg_geometry.mac_unit). */
+/* Units that take the phasor sums' multiply-accumulate (idg_geometry.mac_unit).  On the tensor cores the
+   operands are split into TF32 hi and lo parts (A_hi B_hi + A_lo B_hi + A_hi B_lo, about FP32 accuracy) and
+   accumulated in FP32; the tensor-core degridder takes one visibility per row (one channel per lane whatever
+   degrid_channels asks), the tensor-core gridder needs uniformly spaced channels and no A-term normalisation
+   (the plan keeps the FP32 gridder otherwise). */
 enum {
-  IDG_MAC_DEFAULT = 0, /* the build's default (IDG_MAC_FP32) */
-  IDG_MAC_FP32 = 1,    /* FP32 FMA pipe of the CUDA cores */
-  IDG_MAC_TENSOR = 2   /* degridder: tensor cores, split-TF32 operands (A_hi B_hi + A_lo B_hi + A_hi B_lo,
-                          about FP32 accuracy) with FP32 accumulation; one visibility per row, so it uses one
-                          channel per lane whatever degrid_channels asks.  The gridder stays on FP32 */
+  IDG_MAC_DEFAULT = 0,       /* IDG_MAC_TENSOR_DEGRID, or IDG_MAC_FP32 when degrid_channels asks for 2 or 4 */
+  IDG_MAC_FP32 = 1,          /* gridder and degridder on the FP32 FMA pipe of the CUDA cores */
+  IDG_MAC_TENSOR = 2,        /* gridder and degridder on the tensor cores */
+  IDG_MAC_TENSOR_DEGRID = 3  /* degridder on the tensor cores, gridder on the FP32 pipe */
 };
 
 enum {
@@ -108,8 +111,8 @@ typedef struct {
                               to 1 otherwise (idg_plan_stats reports the value in use) */
   int32_t grid_chunk;      /* gridder: staged visibility records per chunk copied to shared memory, 32, 48 or
                               64, or 0 for the default (48); a tuning choice, the results do not depend on it */
-  int32_t mac_unit;        /* IDG_MAC_DEFAULT, IDG_MAC_FP32 or IDG_MAC_TENSOR: a tuning choice; the results
-                              agree to FP32 rounding */
+  int32_t mac_unit;        /* IDG_MAC_DEFAULT, IDG_MAC_FP32, IDG_MAC_TENSOR or IDG_MAC_TENSOR_DEGRID: a tuning
+                              choice; the results agree to FP32 rounding */
 } idg_geometry;
 
 typedef struct {
@@ -133,7 +136,8 @@ typedef struct {
   int32_t n_pol;              /* planes per layer of grids and images: 4, or 1 with IDG_STOKES_I */
   int32_t degrid_channels;    /* channels per degridder lane in use */
   int32_t grid_chunk;         /* gridder records per chunk in use */
-  int32_t mac_unit;           /* IDG_MAC_FP32 or IDG_MAC_TENSOR in use */
+  int32_t mac_unit;           /* in use: IDG_MAC_FP32, IDG_MAC_TENSOR (both kernels on the tensor cores) or
+                                 IDG_MAC_TENSOR_DEGRID */
 } idg_plan_stats_t;
 
 /*

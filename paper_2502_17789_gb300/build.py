@@ -17,9 +17,10 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libidg.so")
 SOURCES = (["planner.cpp", "gridder.cu", "fft.cu", "degridder.cu", "idg_api.cu", "noalloc.cu", "image.cu", "probe.cu"]
            + [f"gridder_l{L}.cu" for L in (32, 64, 96, 128)] + [f"degridder_l{L}.cu" for L in (32, 64, 96, 128)]
-           + [f"degridder_tc_l{L}.cu" for L in (32, 64, 96, 128)])
+           + [f"degridder_tc_l{L}.cu" for L in (32, 64, 96, 128)]
+           + [f"gridder_tc_l{L}.cu" for L in (32, 64, 96, 128)])
 HEADERS = ["idg_internal.h", "kernels_common.cuh", "gridder_kernels.cuh", "degridder_kernels.cuh",
-           "degridder_tc_kernels.cuh"]
+           "degridder_tc_kernels.cuh", "gridder_tc_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math",

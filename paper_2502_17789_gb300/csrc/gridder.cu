@@ -162,6 +162,57 @@ int launch_stage_records(int L, const StageArgs& a, int n_subgrids, void* stream
 
 // ------------------------------------------------------------------ gridder dispatch
 
+// the tensor-core gridder lives in gridder_tc_kernels.cuh, instantiated in gridder_tc_lNN.cu
+template <int L>
+int configure_gridder_tc_l(int* persistent_blocks);
+template <int L>
+int launch_gridder_tc_l(const GridArgs& a, int n_items, int persistent_blocks, void* stream);
+template <int L>
+int launch_gridder_tc_multi_l(const GridArgs* args, const int2* items, int n_items, void* stream);
+template <int L>
+int launch_stage_tc_l(const StageArgs& a, const SegmentDesc* seg, int n_subgrids, void* stream);
+#define IDG_GRID_TC_EXTERN(L)                                                                                    \
+  extern template int configure_gridder_tc_l<L>(int*);                                                          \
+  extern template int launch_gridder_tc_l<L>(const GridArgs&, int, int, void*);                                 \
+  extern template int launch_gridder_tc_multi_l<L>(const GridArgs*, const int2*, int, void*);                   \
+  extern template int launch_stage_tc_l<L>(const StageArgs&, const SegmentDesc*, int, void*);
+IDG_GRID_TC_EXTERN(32)
+IDG_GRID_TC_EXTERN(64)
+IDG_GRID_TC_EXTERN(96)
+IDG_GRID_TC_EXTERN(128)
+#undef IDG_GRID_TC_EXTERN
+
+#define IDG_SWITCH_L(CALL)                 \
+  switch (L) {                             \
+    case 32: return CALL(32);              \
+    case 64: return CALL(64);              \
+    case 96: return CALL(96);              \
+    case 128: return CALL(128);            \
+    default: return int(cudaErrorInvalidValue); \
+  }
+
+int configure_gridder_tc(int L, int* persistent_blocks) {
+#define C_(X) configure_gridder_tc_l<X>(persistent_blocks)
+  IDG_SWITCH_L(C_)
+#undef C_
+}
+int launch_gridder_tc(int L, const GridArgs& a, int n_items, int persistent_blocks, void* stream) {
+#define C_(X) launch_gridder_tc_l<X>(a, n_items, persistent_blocks, stream)
+  IDG_SWITCH_L(C_)
+#undef C_
+}
+int launch_gridder_tc_multi(int L, const GridArgs* args, const int2* items, int n_items, void* stream) {
+#define C_(X) launch_gridder_tc_multi_l<X>(args, items, n_items, stream)
+  IDG_SWITCH_L(C_)
+#undef C_
+}
+int launch_stage_tc(int L, const StageArgs& a, const SegmentDesc* seg, int n_subgrids, void* stream) {
+#define C_(X) launch_stage_tc_l<X>(a, seg, n_subgrids, stream)
+  IDG_SWITCH_L(C_)
+#undef C_
+}
+#undef IDG_SWITCH_L
+
 // the kernels live in gridder_kernels.cuh, instantiated per subgrid size in gridder_lNN.cu
 template <int L>
 int gridder_launch(const GridArgs& a, int n_items, int persistent_blocks, void* stream);

@@ -52,6 +52,7 @@ struct idg_plan {
   int32_t degrid_channels = 1;       // channels per degridder lane
   int32_t grid_chunk = kDefaultGridChunk;  // staged records per gridder chunk
   int32_t mac = IDG_MAC_FP32;        // multiply-accumulate unit of the degridder
+  bool grid_tc = false;              // gridder on the tensor cores (mac, uniform channels, no A-term normalisation)
   cudaStream_t stream = nullptr;
   bool host_only = false;
   Partition part;
@@ -318,8 +319,9 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     return set_err(nullptr, IDG_ERR_INVALID_ARG, "degrid_channels must be 0, 1, 2 or 4");
   if (g->grid_chunk != 0 && !supported_grid_chunk(g->grid_chunk))
     return set_err(nullptr, IDG_ERR_INVALID_ARG, "grid_chunk must be 0, 32, 48 or 64");
-  if (g->mac_unit != IDG_MAC_DEFAULT && g->mac_unit != IDG_MAC_FP32 && g->mac_unit != IDG_MAC_TENSOR)
-    return set_err(nullptr, IDG_ERR_INVALID_ARG, "mac_unit must be IDG_MAC_DEFAULT, IDG_MAC_FP32 or IDG_MAC_TENSOR");
+  if (g->mac_unit < IDG_MAC_DEFAULT || g->mac_unit > IDG_MAC_TENSOR_DEGRID)
+    return set_err(nullptr, IDG_ERR_INVALID_ARG,
+                   "mac_unit must be IDG_MAC_DEFAULT, IDG_MAC_FP32, IDG_MAC_TENSOR or IDG_MAC_TENSOR_DEGRID");
 
   idg_plan* p = new (std::nothrow) idg_plan();
   if (!p) return set_err(nullptr, IDG_ERR_OOM, "host allocation failed");
@@ -381,8 +383,20 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     const int want = g->degrid_channels > 0 ? g->degrid_channels : kDefaultDegridChannels;
     p->degrid_channels = uniform ? want : 1;
   }
-  p->mac = g->mac_unit == IDG_MAC_TENSOR ? IDG_MAC_TENSOR : IDG_MAC_FP32;
-  if (p->mac == IDG_MAC_TENSOR) p->degrid_channels = 1;  // one visibility per row of the tensor-core product
+  // the default: the degridder on the tensor cores unless channel groups were asked for, the gridder on FP32
+  p->mac = g->mac_unit != IDG_MAC_DEFAULT ? g->mac_unit
+                                          : (g->degrid_channels > 1 ? IDG_MAC_FP32 : IDG_MAC_TENSOR_DEGRID);
+  if (p->mac != IDG_MAC_FP32) p->degrid_channels = 1;  // one visibility per row of the tensor-core product
+  {
+    // the tensor-core gridder rotates phasors by one channel step along each row
+    bool uniform = true;
+    for (int c = 2; c < n_channels && uniform; ++c) {
+      const double s1 = freqs_hz[1] - freqs_hz[0], sc = freqs_hz[c] - freqs_hz[c - 1];
+      uniform = std::fabs(sc - s1) <= 1e-12 * std::fabs(s1);
+    }
+    p->grid_tc = p->mac == IDG_MAC_TENSOR && uniform && !(g->flags & IDG_NORMALIZE_ATERM);
+    if (p->mac == IDG_MAC_TENSOR && !p->grid_tc) p->mac = IDG_MAC_TENSOR_DEGRID;  // the units in use
+  }
   p->grid_chunk = g->grid_chunk > 0 ? g->grid_chunk : kDefaultGridChunk;
   for (SubgridDesc& d : p->exec) d.layer -= k_lo;  // device tables hold the grid plane set
   if (host_only) {
@@ -408,8 +422,11 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     // staged records of the batch, in batch order
     int64_t recs = 0;
     for (int32_t o = 0; o < cnt; ++o) {
-      p->exec[s0 + o].rec_offset = int32_t(recs);
-      recs += p->exec[s0 + o].n_vis;
+      SubgridDesc& d = p->exec[s0 + o];
+      d.rec_offset = int32_t(recs);
+      const int nc = d.c1 - d.c0;
+      recs += p->grid_tc ? tc_records(tc_row_groups(p->part.segments.data(), d.seg_begin, d.seg_count, nc), nc)
+                         : d.n_vis;
     }
     p->max_batch_vis = std::max(p->max_batch_vis, recs);
     // longest first: order batch subgrids by visibility count; the items of
@@ -420,7 +437,7 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
       return p->exec[s0 + x].n_vis > p->exec[s0 + y].n_vis;
     });
     for (int32_t o : order)
-      for (int t = 0; t < tiles; ++t) gitems.push_back(GridItem{o, t});
+      for (int t = 0; t < (p->grid_tc ? L * L / kGtcPixels : tiles); ++t) gitems.push_back(GridItem{o, t});
     // degridder items: pieces of <= `lanes` channel groups of one segment
     // (a segment's rows times G groups per row); a piece that ends its
     // segment shares its item with the first piece of the next segment when
@@ -439,7 +456,7 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
           const int ke = std::min(k + lanes, g_end);
           // the tensor-core degridder starts the second segment at the next 16-row tile
           const int first = ditems.empty() ? 0 : ditems.back().k_end - ditems.back().k_begin;
-          const int held = p->mac == IDG_MAC_TENSOR ? (first + 15) / 16 * 16 : first;
+          const int held = p->mac != IDG_MAC_FP32 ? (first + 15) / 16 * 16 : first;
           if (open && k == g_begin && held + (ke - k) <= lanes) {
             ditems.back().k_end = ke;  // second segment of the item
             open = false;
@@ -491,9 +508,10 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
   int pg = 0, pd = 0;
   int e = configure_kernels(L);
   if (!e) e = configure_gridder(L, p->grid_chunk, &pg);
+  if (!e && p->grid_tc) e = configure_gridder_tc(L, &pg);
   // the FP32 kernels serve the items of few visibilities in either mode
   if (!e) e = configure_degridder(L, g->aterm_nodes, p->degrid_channels, &pd);
-  if (!e && p->mac == IDG_MAC_TENSOR) e = configure_degridder_tc(L, g->aterm_nodes, &pd);
+  if (!e && p->mac != IDG_MAC_FP32) e = configure_degridder_tc(L, g->aterm_nodes, &pd);
   if (g->flags & IDG_PERSISTENT) {
     p->persistent_grid_blocks = pg;
     p->persistent_degrid_blocks = pd;
@@ -599,6 +617,17 @@ static GridArgs grid_args(const idg_plan* p, const Batch& b, const void* vis, co
   return ga;
 }
 
+// record staging and the gridder of the plan's kind (FP32 pipe or tensor cores)
+static int stage_any(const idg_plan* p, const Batch& b, const void* vis, cudaStream_t strm) {
+  return p->grid_tc ? launch_stage_tc(p->L, stage_args(p, b, vis), p->d_seg, b.sg_count, strm)
+                    : launch_stage_records(p->L, stage_args(p, b, vis), b.sg_count, strm);
+}
+
+static int gridder_any(const idg_plan* p, const GridArgs& ga, int n_items, int persistent_blocks, cudaStream_t strm) {
+  return p->grid_tc ? launch_gridder_tc(p->L, ga, n_items, persistent_blocks, strm)
+                    : launch_gridder(p->L, ga, n_items, persistent_blocks, strm);
+}
+
 idg_status idg_grid(idg_plan* plan, const void* vis_c64, const void* aterms_c64, void* grid_c128) {
   if (!plan) return set_err(nullptr, IDG_ERR_INVALID_ARG, "plan is NULL");
   if (plan->host_only) return set_err(plan, IDG_ERR_INVALID_ARG, "plan was created with IDG_HOST_ONLY");
@@ -623,10 +652,10 @@ idg_status idg_grid(idg_plan* plan, const void* vis_c64, const void* aterms_c64,
     GridArgs ga = grid_args(plan, b, vis_c64, aterms_c64);
     ga.queue = plan->d_queue + 2 * bi;
     ga.n_items = b.gi_count;
-    int es = timed(plan, kStage, [&] { return launch_stage_records(L, stage_args(plan, b, vis_c64), b.sg_count, plan->stream); });
+    int es = timed(plan, kStage, [&] { return stage_any(plan, b, vis_c64, plan->stream); });
     if (es) return cuda_err(plan, es, "staging launch");
     int e = timed(plan, kGridder, [&] {
-      return launch_gridder(L, ga, b.gi_count, plan->persistent_grid_blocks, plan->stream);
+      return gridder_any(plan, ga, b.gi_count, plan->persistent_grid_blocks, plan->stream);
     });
     if (e) return cuda_err(plan, e, "gridder launch");
     FftArgs fa{plan->d_sg + b.sg_offset, plan->d_scratch, static_cast<double2*>(grid_c128), plan->d_twiddle, plan->N,
@@ -683,7 +712,7 @@ idg_status idg_degrid(idg_plan* plan, const void* grid_c128, const void* aterms_
     da.scratch = plan->d_scratch;
     da.g = kgeom(plan);
     e = timed(plan, kDegridder, [&] {
-      if (plan->mac == IDG_MAC_TENSOR)
+      if (plan->mac != IDG_MAC_FP32)
         return launch_degridder_tc(L, da, b.di_count, plan->persistent_degrid_blocks, plan->stream);
       return launch_degridder(L, plan->degrid_channels, da, b.di_count, plan->persistent_degrid_blocks,
                               plan->stream, false);
@@ -722,9 +751,9 @@ idg_status idg_subgrid_images(idg_plan* plan, const void* vis_c64, const void* a
   if (e) return cuda_err(plan, e, "A-term flag launch");
   for (const Batch& b : plan->batches) {
     GridArgs ga = grid_args(plan, b, vis_c64, aterms_c64);
-    int es = timed(plan, kStage, [&] { return launch_stage_records(L, stage_args(plan, b, vis_c64), b.sg_count, plan->stream); });
+    int es = timed(plan, kStage, [&] { return stage_any(plan, b, vis_c64, plan->stream); });
     if (es) return cuda_err(plan, es, "staging launch");
-    e = launch_gridder(L, ga, b.gi_count, 0, plan->stream);
+    e = gridder_any(plan, ga, b.gi_count, 0, plan->stream);
     if (e) return cuda_err(plan, e, "gridder launch");
     if (stage == 1) {
       FftArgs fa{plan->d_sg + b.sg_offset, plan->d_scratch, nullptr, plan->d_twiddle, plan->N, plan->npol};
@@ -808,10 +837,11 @@ idg_status check_many(int32_t n, idg_plan* const* plans, const void* const* a, c
       return st;
     const idg_plan* p0 = plans[0];
     if (p->L != p0->L || p->npol != p0->npol || (p->d_aweights != nullptr) != (p0->d_aweights != nullptr) ||
-        p->degrid_channels != p0->degrid_channels || p->grid_chunk != p0->grid_chunk || p->mac != p0->mac)
+        p->degrid_channels != p0->degrid_channels || p->grid_chunk != p0->grid_chunk || p->mac != p0->mac ||
+        p->grid_tc != p0->grid_tc)
       return set_err(p, IDG_ERR_INVALID_ARG,
                      "plans of one call must share subgrid size, Stokes-I mode, normalisation, grid_chunk, "
-                     "degrid_channels and mac_unit");
+                     "degrid_channels, mac_unit and the gridder kind");
     for (int32_t j = 0; j < k; ++j)
       if (plans[j] == p) return set_err(p, IDG_ERR_INVALID_ARG, "a plan appears twice");
   }
@@ -874,7 +904,7 @@ idg_status idg_grid_many(int32_t n, idg_plan* const* plans, const void* const* v
       idg_plan* p = plans[k];
       if (w >= p->batches.size()) continue;
       const Batch& b = p->batches[w];
-      const int e = launch_stage_records(L, stage_args(p, b, vis_c64[k]), b.sg_count, strm);
+      const int e = stage_any(p, b, vis_c64[k], strm);
       if (e) return cuda_err(p, e, "staging launch");
       GridArgs ga = grid_args(p, b, vis_c64[k], aterms_c64[k]);
       ga.n_items = b.gi_count;
@@ -888,8 +918,9 @@ idg_status idg_grid_many(int32_t n, idg_plan* const* plans, const void* const* v
     int2* d_items = nullptr;
     int e = upload_wave(strm, args, items, &d_args, &d_items);
     if (!e)
-      e = launch_gridder_multi(L, d_args, d_items, int(items.size()), plans[0]->d_aweights != nullptr,
-                               plans[0]->grid_chunk, strm);
+      e = plans[0]->grid_tc ? launch_gridder_tc_multi(L, d_args, d_items, int(items.size()), strm)
+                            : launch_gridder_multi(L, d_args, d_items, int(items.size()),
+                                                   plans[0]->d_aweights != nullptr, plans[0]->grid_chunk, strm);
     if (d_args) cudaFreeAsync(d_args, strm);
     if (d_items) cudaFreeAsync(d_items, strm);
     if (e) return cuda_err(plans[0], e, "gridder launch (several plans)");
@@ -968,7 +999,7 @@ idg_status idg_degrid_many(int32_t n, idg_plan* const* plans, const void* const*
     int2* d_items = nullptr;
     int e = upload_wave(strm, args, items, &d_args, &d_items);
     if (!e)
-      e = plans[0]->mac == IDG_MAC_TENSOR
+      e = plans[0]->mac != IDG_MAC_FP32
               ? launch_degridder_tc_multi(L, d_args, d_items, int(n_regular), max_nodes, strm)
               : launch_degridder_multi(L, plans[0]->degrid_channels, false, d_args, d_items, int(n_regular),
                                        max_nodes, strm);

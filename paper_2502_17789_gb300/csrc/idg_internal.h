@@ -78,6 +78,35 @@ constexpr int kDegridSegs = 2;  // segments per degridder work item
 constexpr int kSplitLanes = 8;
 constexpr int kTcItemRows = 256;  // rows (16-row tiles) per item of the tensor-core degridder
 
+// channels per run of rotated phasors (one fresh evaluation per run bounds
+// the growth of the rotation's rounding error)
+constexpr int kRotateRun = 8;
+
+// Tensor-core gridder: work items of kGtcPixels pixels; staged records of a
+// subgrid are its row groups (4 rows of one segment) times (channels + the
+// phase-coefficient records of a row slot)
+constexpr int kGtcPixels = 512;  // pixels per work item
+
+__host__ __device__ constexpr int tc_runs(int nc) { return (nc + kRotateRun - 1) / kRotateRun; }
+// records per row slot for the phase coefficients: the step and one anchor per run, 2 float4 each
+__host__ __device__ constexpr int tc_anchor_records(int nc) { return (2 + 2 * tc_runs(nc) + 7) / 8; }
+
+// Row groups of a subgrid: segments contribute ceil(rows / 4) each
+__host__ __device__ inline int tc_row_groups(const SegmentDesc* seg, int seg_begin, int seg_count, int nc) {
+  int n = 0;
+  for (int s = 0; s < seg_count; ++s) {
+    const int rows = (seg[seg_begin + s].k_end - seg[seg_begin + s].k_begin) / nc;
+    n += (rows + 3) / 4;
+  }
+  return n;
+}
+
+// Staged records of a subgrid in the tensor-core layout
+__host__ __device__ inline int64_t tc_records(int n_groups, int nc) {
+  return int64_t(n_groups) * 4 * (nc + tc_anchor_records(nc));
+}
+
+
 // ---------------------------------------------------------------- planner
 
 struct PlanInput {
@@ -134,9 +163,6 @@ constexpr int kRecordFloat4 = 8;
 constexpr float kKindRotate = 0.f;
 constexpr float kKindBase = 1.f;
 constexpr float kKindStep = 2.f;
-// channels per run of rotated phasors (one fresh evaluation per run bounds
-// the growth of the rotation's rounding error)
-constexpr int kRotateRun = 8;
 
 struct StageArgs {
   const float4* vis;
@@ -229,6 +255,11 @@ int launch_degridder_multi(int L, int channels, bool split, const DegridArgs* ar
 // the degridder on the tensor cores (split-TF32 mma.sync, one visibility per row); its items may hold
 // two segments only when the first, rounded up to 16 rows, and the second fit in kTcItemRows rows
 int launch_degridder_tc(int L, const DegridArgs& a, int n_items, int persistent_blocks, void* stream);
+// the gridder on the tensor cores (records staged by launch_stage_tc; uniform channel spacing)
+int launch_stage_tc(int L, const StageArgs& a, const SegmentDesc* seg, int n_subgrids, void* stream);
+int launch_gridder_tc(int L, const GridArgs& a, int n_items, int persistent_blocks, void* stream);
+int configure_gridder_tc(int L, int* persistent_blocks);
+int launch_gridder_tc_multi(int L, const GridArgs* args, const int2* items, int n_items, void* stream);
 int configure_degridder_tc(int L, int nodes, int* persistent_blocks);
 int launch_degridder_tc_multi(int L, const DegridArgs* args, const int2* items, int n_items, int max_nodes,
                               void* stream);

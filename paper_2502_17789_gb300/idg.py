@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "IDG_OK", 1: "IDG_ERR_INVALID_ARG", 2: "IDG_ERR_UNSORTED_FREQ
 IDG_TAPER_KB, IDG_TAPER_USER = 0, 1
 IDG_DROP_OUT_OF_GRID, IDG_SPLIT_AT_ATERM_INTERVALS, IDG_HOST_ONLY, IDG_PERSISTENT, IDG_W_LAYERS = 1, 2, 4, 8, 16
 IDG_NORMALIZE_ATERM, IDG_STOKES_I = 32, 64
-IDG_MAC_DEFAULT, IDG_MAC_FP32, IDG_MAC_TENSOR = 0, 1, 2
+IDG_MAC_DEFAULT, IDG_MAC_FP32, IDG_MAC_TENSOR, IDG_MAC_TENSOR_DEGRID = 0, 1, 2, 3
 
 # every function declared in include/idg.h
 EXPORTS = ["idg_plan_create", "idg_grid", "idg_degrid", "idg_grid_graph", "idg_degrid_graph", "idg_set_stream", "idg_plan_stats", "idg_plan_subgrids",

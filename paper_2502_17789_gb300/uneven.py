@@ -69,8 +69,8 @@ def main(argv=None):
                         "vis_pixels": float(st.vis_pixels)}
         p.close()
 
-    def measure(o, L, mode, chunk, channels):
-        return autotune.gpu_measure(o, L, mode, chunk, channels, trials=1, aterms=A, graph=True, vis=vis)
+    def measure(o, L, mode, chunk, channels, mac):
+        return autotune.gpu_measure(o, L, mode, chunk, channels, mac, trials=1, aterms=A, graph=True, vis=vis)
 
     t1 = time.time()
     choice = autotune.autotune(obs, candidates=args.candidates, modes=args.modes, cache_path=args.cache,

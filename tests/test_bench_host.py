@@ -91,3 +91,26 @@ def test_recorded_traffic_needs_same_sources_and_workload(tmp_path, traffic_file
 def test_recorded_traffic_without_a_record(traffic_file):
     assert not traffic_file.exists()
     assert bench.recorded_traffic("degridder", "workload A") is None
+
+
+def test_tensor_core_kernels_recorded_under_their_own_names(tmp_path, traffic_file, full_obs):
+    """The tensor-core kernels have their own traffic entries; the gridder's
+    capture ignores degridder rows whose name contains its own."""
+    assert bench.kernel_of("gridder", 1) == "gridder" and bench.kernel_of("gridder", 3) == "gridder"
+    assert bench.kernel_of("gridder", 2) == "gridder_tc"
+    assert bench.kernel_of("degridder", 1) == "degridder"
+    assert bench.kernel_of("degridder", 2) == bench.kernel_of("degridder", 3) == "degridder_tc"
+    gt = "void idg::gridder_tc_kernel<96, false>(idg::GridArgs)"
+    dt = "void idg::degridder_tc_kernel<96, false>(idg::DegridArgs)"
+    _write_launch_list(tmp_path / "traffic_gridder_tc.csv", [
+        (0, gt, "dram__bytes_read.sum", "Mbyte", "300"), (0, gt, "dram__bytes_write.sum", "Gbyte", "1.0"),
+        (1, dt, "dram__bytes_read.sum", "Gbyte", "9.0"), (1, dt, "dram__bytes_write.sum", "Gbyte", "9.0")])
+    _write_launch_list(tmp_path / "traffic_degridder_tc.csv", [
+        (0, dt, "dram__bytes_read.sum", "Gbyte", "1.0"), (0, dt, "dram__bytes_write.sum", "Mbyte", "90")])
+    bench.record_traffic(str(tmp_path), full_obs, "workload A")
+    rec = json.loads(traffic_file.read_text())
+    assert set(rec) == {"gridder_tc", "degridder_tc"}
+    assert rec["gridder_tc"]["captured_launches"] == 1
+    assert rec["gridder_tc"]["captured_bytes_per_launch"] == pytest.approx(1.3e9)
+    assert rec["degridder_tc"]["captured_bytes_per_launch"] == pytest.approx(1.09e9)
+    assert bench.recorded_traffic("degridder_tc", "workload A") is not None

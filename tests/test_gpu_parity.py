@@ -155,11 +155,12 @@ def test_degrid_channel_groups(idg_mod, oracle_mod, cuda_device, channels, L, n_
     rng = np.random.default_rng(L)
     N = obs.grid_size
     Grand = (rng.standard_normal((4, N, N)) + 1j * rng.standard_normal((4, N, N))) * 1e-3
-    c = Case(idg_mod, oracle_mod, obs, A, vis, L=L, degrid_channels=channels)
+    c = Case(idg_mod, oracle_mod, obs, A, vis, L=L, degrid_channels=channels, mac_unit=idg_mod.IDG_MAC_FP32)
     assert c.plan.stats().degrid_channels == channels
     V_ref = c.oracle_degrid(Grand)
     assert _degrid_err(c.gpu_degrid(Grand), V_ref) < DEGRID_TOL
-    pp = idg_mod.Plan(obs, subgrid_size=L, flags=idg_mod.IDG_PERSISTENT, degrid_channels=channels)
+    pp = idg_mod.Plan(obs, subgrid_size=L, flags=idg_mod.IDG_PERSISTENT, degrid_channels=channels,
+                      mac_unit=idg_mod.IDG_MAC_FP32)
     try:
         V = torch.full(c.vis.shape, 7.0 + 7.0j, dtype=torch.complex64, device="cuda")
         pp.degrid(torch.as_tensor(Grand).cuda(), c.A_d, V)
@@ -182,7 +183,7 @@ def test_degrid_low_occupancy(idg_mod, oracle_mod, cuda_device, channels, n_ch, 
     rng = np.random.default_rng(n_ch * n_t)
     N = obs.grid_size
     Grand = (rng.standard_normal((4, N, N)) + 1j * rng.standard_normal((4, N, N))) * 1e-3
-    c = Case(idg_mod, oracle_mod, obs, A, vis, degrid_channels=channels)
+    c = Case(idg_mod, oracle_mod, obs, A, vis, degrid_channels=channels, mac_unit=idg_mod.IDG_MAC_FP32)
     V_ref = c.oracle_degrid(Grand)
     assert _degrid_err(c.gpu_degrid(Grand), V_ref) < DEGRID_TOL
     assert _rel(c.gpu_grid(), c.oracle_grid()) < GRID_TOL
