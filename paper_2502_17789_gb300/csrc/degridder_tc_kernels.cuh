@@ -61,6 +61,15 @@ __device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) 
   lo = __float_as_uint(x - __uint_as_float(hi));
 }
 
+// the same for a pair: two masks and one packed FMA, lo = x - hi
+__device__ __forceinline__ void tf32_split2(float2 x, uint32_t& hi0, uint32_t& hi1, uint32_t& lo0, uint32_t& lo1) {
+  hi0 = __float_as_uint(x.x) & kTf32Mask;
+  hi1 = __float_as_uint(x.y) & kTf32Mask;
+  const float2 lo = ffma2(make_float2(__uint_as_float(hi0), __uint_as_float(hi1)), make_float2(-1.f, -1.f), x);
+  lo0 = __float_as_uint(lo.x);
+  lo1 = __float_as_uint(lo.y);
+}
+
 // Row of the item (tile layout) for lane l: segment 1 starts at row r1
 __device__ __forceinline__ int tc_row(int l, int n0, int r1, int n_seg) {
   return (n_seg == 2 && l >= n0) ? r1 + (l - n0) : l;
@@ -91,8 +100,7 @@ __device__ __forceinline__ void tc_group_sum(DegridTcSmem& S, const float2* zs, 
     // B fragment of step k: this lane's column is pol g/2, re (g even) or im (g odd)
     const float2 z = zs[k * kTcZRow];
     uint32_t Bh[2], Bl[2];
-    tf32_split(odd ? z.y : z.x, Bh[0], Bl[0]);
-    tf32_split(odd ? -z.x : z.y, Bh[1], Bl[1]);
+    tf32_split2(make_float2(odd ? z.y : z.x, odd ? -z.x : z.y), Bh[0], Bh[1], Bl[0], Bl[1]);
     const float dnk = dn[k];
     const float2 DN = make_float2(dnk, dnk);
     const float2 DI = make_float2(float(k - 8), float(k - 8));
@@ -104,10 +112,8 @@ __device__ __forceinline__ void tc_group_sum(DegridTcSmem& S, const float2* zs, 
       __sincosf(ph.y, &sb, &cb);
       // A fragment: (row g, col t) cos, (row g+8, col t) cos, (row g, col t+4) sin, (row g+8, col t+4) sin
       uint32_t Ah[4], Al[4];
-      tf32_split(ca, Ah[0], Al[0]);
-      tf32_split(cb, Ah[1], Al[1]);
-      tf32_split(sa, Ah[2], Al[2]);
-      tf32_split(sb, Ah[3], Al[3]);
+      tf32_split2(make_float2(ca, cb), Ah[0], Ah[1], Al[0], Al[1]);
+      tf32_split2(make_float2(sa, sb), Ah[2], Ah[3], Al[2], Al[3]);
       mma_tf32_16x8x8(acc[m], Ah, Bh);
       mma_tf32_16x8x8(acc[m], Al, Bh);
       mma_tf32_16x8x8(acc[m], Ah, Bl);

@@ -14,7 +14,7 @@
 //
 // The 4 visibilities of a step are 4 rows (timesteps) of the segment at one
 // channel, so lane (g, t) follows row t along its channels: the phasors of
-// its two pixels start from an exact anchor every kRotateRun channels
+// its two pixels start from an exact anchor every kGtcRun channels
 // (__sincosf) and advance by the phasor of the channel step in between (the
 // phase is linear in frequency; the plan uses this kernel only for uniform
 // channel spacing).  Rows are taken in groups of 4 per segment, the last
@@ -25,7 +25,7 @@
 // holding the B fragments of the 8 columns, (b0_hi, b1_hi, b0_lo, b1_lo) per
 // column; then per row slot (group * 4 + t) tc_anchor_records(nc) records
 // holding the phase coefficients of the channel step and of the anchor
-// channels c0, c0 + kRotateRun, ... (the (head, tail) slope format of the
+// channels c0, c0 + kGtcRun, ... (the (head, tail) slope format of the
 // exact reduction).
 //
 // Item = (subgrid, block of 512 pixels): warp w owns pixels 64 w .. 64 w + 63
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) stage_tc_kernel(const StageArgs a, const 
       tc_put_coef(dst, c1.a - c0.a, c1.b - c0.b, c1.w - c0.w);
     }
     for (int u = 0; u < R; ++u) {
-      const TcSlopes cu = tc_slopes(a, sd, sd.t0 + row, sd.c0 + u * kRotateRun, L);
+      const TcSlopes cu = tc_slopes(a, sd, sd.t0 + row, sd.c0 + u * kGtcRun, L);
       tc_put_coef(dst + 2 + 2 * u, cu.a, cu.b, cu.w);
     }
   }
@@ -292,10 +292,10 @@ __device__ __forceinline__ bool gridder_tc_item(const GridArgs& a, int item_idx,
           const SegmentDesc d = a.seg[sd.seg_begin + seg_i];
           seg_gend += ((d.k_end - d.k_begin) / nc + 3) / 4;
         }
-        if (s % kRotateRun == 0) {
-          if (s % kGtcFlushSteps == 0) flush();  // bounds the MMA accumulation chains
+        if (s % kGtcFlushSteps == 0) flush();  // bounds the MMA accumulation chains
+        if (s % kGtcRun == 0) {
           const float4* anc = anc_base + size_t(4 * G + t) * AR * kRecordFloat4;
-          const float4 a0 = __ldg(anc + 2 + 2 * (s / kRotateRun)), a1 = __ldg(anc + 3 + 2 * (s / kRotateRun));
+          const float4 a0 = __ldg(anc + 2 + 2 * (s / kGtcRun)), a1 = __ldg(anc + 3 + 2 * (s / kGtcRun));
           float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
           if (s == 0) {
             s0 = __ldg(anc);
@@ -330,12 +330,16 @@ __device__ __forceinline__ bool gridder_tc_item(const GridArgs& a, int item_idx,
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
           // A fragment: (row g, col t) cos, (row g+8, col t) cos, (row g, col t+4) sin, (row g+8, col t+4) sin
-          const float av[4] = {Cs[m].x, Cs[m].y, Sn[m].x, Sn[m].y};
           uint32_t Ah[4], Al[4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            Ah[e] = __float_as_uint(av[e]) & kGtcMask;
-            Al[e] = __float_as_uint(av[e] - __uint_as_float(Ah[e]));
+          for (int e = 0; e < 2; ++e) {
+            const float2 x = e ? Sn[m] : Cs[m];
+            Ah[2 * e] = __float_as_uint(x.x) & kGtcMask;
+            Ah[2 * e + 1] = __float_as_uint(x.y) & kGtcMask;
+            const float2 lo = ffma2(make_float2(__uint_as_float(Ah[2 * e]), __uint_as_float(Ah[2 * e + 1])),
+                                    make_float2(-1.f, -1.f), x);  // x - hi
+            Al[2 * e] = __float_as_uint(lo.x);
+            Al[2 * e + 1] = __float_as_uint(lo.y);
           }
           mma_tf32_m16n8k8(acc[m], Ah, Bh);
           mma_tf32_m16n8k8(acc[m], Al, Bh);

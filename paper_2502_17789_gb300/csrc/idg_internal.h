@@ -87,7 +87,8 @@ constexpr int kRotateRun = 8;
 // phase-coefficient records of a row slot)
 constexpr int kGtcPixels = 512;  // pixels per work item
 
-__host__ __device__ constexpr int tc_runs(int nc) { return (nc + kRotateRun - 1) / kRotateRun; }
+constexpr int kGtcRun = kRotateRun;  // channels per run of rotated phasors in the tensor-core gridder
+__host__ __device__ constexpr int tc_runs(int nc) { return (nc + kGtcRun - 1) / kGtcRun; }
 // records per row slot for the phase coefficients: the step and one anchor per run, 2 float4 each
 __host__ __device__ constexpr int tc_anchor_records(int nc) { return (2 + 2 * tc_runs(nc) + 7) / 8; }
 
