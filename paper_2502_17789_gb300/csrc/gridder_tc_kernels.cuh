@@ -13,40 +13,40 @@
 // pixels x 4 visibilities.
 //
 // The 4 visibilities of a step are 4 rows (timesteps) of the segment at one
-// channel, so lane (g, t) follows row t along its channels: the phasors of
-// its two pixels start from an exact anchor every kGtcRun channels
-// (__sincosf) and advance by the phasor of the channel step in between (the
-// phase is linear in frequency; the plan uses this kernel only for uniform
-// channel spacing).  Rows are taken in groups of 4 per segment, the last
-// group padded with zero visibilities.
+// channel, so lane (g, t) follows row t along its channels.  The channels of
+// a row group are taken in runs of kGtcRun (the last run padded with zero
+// visibilities): the phasors of the lane's two pixels start from an exact
+// anchor at the run's first channel (__sincosf) and advance by the phasor of
+// the channel step for the others (the phase is linear in frequency; the plan
+// uses this kernel only for uniform channel spacing).  Rows are taken in
+// groups of 4 per segment, the last group padded with zero visibilities.
 //
-// Staged records (stage_tc_kernel), per subgrid from rec_offset, 128 bytes
-// each: for every row group and channel, 4 visibility records (rows t = 0..3)
-// holding the B fragments of the 8 columns, (b0_hi, b1_hi, b0_lo, b1_lo) per
-// column; then per row slot (group * 4 + t) tc_anchor_records(nc) records
-// holding the phase coefficients of the channel step and of the anchor
-// channels c0, c0 + kGtcRun, ... (the (head, tail) slope format of the
-// exact reduction).
+// Staged records (stage_tc_kernel), per subgrid from rec_offset: for every
+// row group and run, a header of 16 float4 -- for rows t = 0..3 the phase
+// coefficients of the run's first channel at [2t, 2t+1] and of the channel
+// step at [8 + 2t, 9 + 2t], in the (head, tail) slope format of the exact
+// reduction -- then kGtcRun steps of 32 float4: column n of row t at
+// [4n + t], holding (b0_hi, b1_hi, b0_lo, b1_lo), so that lane 4g + t reads
+// its B fragment from float4 number lane of the step (conflict-free).
 //
 // Item = (subgrid, block of 512 pixels): warp w owns pixels 64 w .. 64 w + 63
 // of the block as 4 tiles of 16 (pixels g and g+8 of a tile are rows g and
-// g+8 of A).  Records stream through a double buffer in shared memory by
-// bulk copies, 16 steps per chunk.  Every 16 channels the accumulators
-// are added into an FP32 sum in shared memory (this bounds the tensor
-// core's accumulation rounding); after each segment a warp applies A_p^H X
-// A_q, the taper and the centring sign to its 64 pixels and adds them to
-// the image sum.
+// g+8 of A).  Runs stream through a double buffer in shared memory by bulk
+// copies, two runs per chunk; after every chunk the accumulators are added
+// into an FP32 sum in shared memory (this bounds the tensor core's
+// accumulation rounding); after each segment a warp applies A_p^H X A_q, the
+// taper and the centring sign to its 64 pixels and adds them to the image
+// sum.
 #pragma once
 
 #include "kernels_common.cuh"
 
 namespace idg {
 
-constexpr int kGtcChunk = 16;    // steps (4 records each) per staged chunk
+constexpr int kGtcChunkRuns = 2;  // runs per staged chunk
 // pol planes of the per-pixel sums, padded so that the flush (lanes g, t ->
 // pixel g, pol t) and the epilogue (lane -> pixel) both access distinct banks
 constexpr int kGtcPolStride = kGtcPixels + 8;
-constexpr int kGtcFlushSteps = 16;  // channels between additions of the MMA accumulators into the FP32 sums
 constexpr uint32_t kGtcMask = 0xffffe000u;
 
 __device__ __forceinline__ void tc_split_store(float x, float& hi, float& lo) {
@@ -90,17 +90,20 @@ __device__ __forceinline__ void tc_put_coef(float4* dst, double aa, double bb, d
   dst[1] = make_float4(float(w), float(kTwoPi * aa), float(kTwoPi * w), 0.f);
 }
 
-// One block per subgrid of the batch: visibility records and phase coefficients
+// One block per subgrid of the batch: run headers and visibility records
 template <int L>
 __global__ void __launch_bounds__(256) stage_tc_kernel(const StageArgs a, const SegmentDesc* seg) {
   const SubgridDesc sd = a.sg[blockIdx.x];
   const int nc = sd.c1 - sd.c0;
-  const int NG = tc_row_groups(seg, sd.seg_begin, sd.seg_count, nc);
+  const int R = tc_runs(nc);
+  const int NR = tc_row_groups(seg, sd.seg_begin, sd.seg_count, nc) * R;
   float4* base = a.records + size_t(sd.rec_offset) * kRecordFloat4;
-  const int n_frag = NG * nc * 4;
-  for (int idx = threadIdx.x; idx < n_frag; idx += blockDim.x) {
-    const int G = idx / (nc * 4), rem = idx - G * nc * 4, s = rem >> 2, t = rem & 3;
-    const int row = tc_slot_row(seg, sd.seg_begin, sd.seg_count, nc, G, t);
+  // one thread per (run, step, row slot): the 8 columns of one visibility
+  const int n_vrec = NR * kGtcRun * 4;
+  for (int idx = threadIdx.x; idx < n_vrec; idx += blockDim.x) {
+    const int r = idx / (kGtcRun * 4), rem = idx - r * (kGtcRun * 4), st = rem >> 2, t = rem & 3;
+    const int G = r / R, s = (r - G * R) * kGtcRun + st;
+    const int row = s < nc ? tc_slot_row(seg, sd.seg_begin, sd.seg_count, nc, G, t) : -1;
     float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
     if (row >= 0) {
       const size_t vidx = (size_t(sd.b) * a.g.n_t + sd.t0 + row) * a.g.n_ch + sd.c0 + s;
@@ -109,7 +112,7 @@ __global__ void __launch_bounds__(256) stage_tc_kernel(const StageArgs a, const 
       if (sd.flags & kSubgridMirrored) mirror_values(v0, v1);
     }
     const float vr[4] = {v0.x, v0.z, v1.x, v1.z}, vi[4] = {v0.y, v0.w, v1.y, v1.w};
-    float4* rec = base + size_t(idx) * kRecordFloat4;
+    float4* step = base + size_t(r) * kGtcRunFloat4 + kGtcHeaderFloat4 + st * kGtcStepFloat4;
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
       const int p = n >> 1;
@@ -118,30 +121,29 @@ __global__ void __launch_bounds__(256) stage_tc_kernel(const StageArgs a, const 
       float4 f;
       tc_split_store(b0, f.x, f.z);
       tc_split_store(b1, f.y, f.w);
-      rec[n] = f;
+      step[4 * n + t] = f;
     }
   }
-  const int AR = tc_anchor_records(nc), R = tc_runs(nc);
-  float4* anc = base + size_t(n_frag) * kRecordFloat4;
-  for (int slot = threadIdx.x; slot < NG * 4; slot += blockDim.x) {
-    const int row = tc_slot_row(seg, sd.seg_begin, sd.seg_count, nc, slot >> 2, slot & 3);
-    float4* dst = anc + size_t(slot) * AR * kRecordFloat4;
-    for (int e = 0; e < AR * kRecordFloat4; ++e) dst[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  // one thread per (run, row slot): the phase coefficients of the run's first channel and of the channel step
+  for (int idx = threadIdx.x; idx < NR * 4; idx += blockDim.x) {
+    const int r = idx >> 2, t = idx & 3, G = r / R, u = r - G * R;
+    const int row = tc_slot_row(seg, sd.seg_begin, sd.seg_count, nc, G, t);
+    float4* hdr = base + size_t(r) * kGtcRunFloat4;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    hdr[2 * t] = hdr[2 * t + 1] = hdr[8 + 2 * t] = hdr[9 + 2 * t] = z;
     if (row < 0) continue;
-    const TcSlopes c0 = tc_slopes(a, sd, sd.t0 + row, sd.c0, L);
+    const TcSlopes cu = tc_slopes(a, sd, sd.t0 + row, sd.c0 + u * kGtcRun, L);
+    tc_put_coef(hdr + 2 * t, cu.a, cu.b, cu.w);
     if (nc > 1) {
+      const TcSlopes c0 = tc_slopes(a, sd, sd.t0 + row, sd.c0, L);
       const TcSlopes c1 = tc_slopes(a, sd, sd.t0 + row, sd.c0 + 1, L);
-      tc_put_coef(dst, c1.a - c0.a, c1.b - c0.b, c1.w - c0.w);
-    }
-    for (int u = 0; u < R; ++u) {
-      const TcSlopes cu = tc_slopes(a, sd, sd.t0 + row, sd.c0 + u * kGtcRun, L);
-      tc_put_coef(dst + 2 + 2 * u, cu.a, cu.b, cu.w);
+      tc_put_coef(hdr + 8 + 2 * t, c1.a - c0.a, c1.b - c0.b, c1.w - c0.w);
     }
   }
 }
 
 struct GtcSmem {
-  float4 rec[2][kGtcChunk * 4 * kRecordFloat4];  // staged steps, double buffered
+  float4 rec[2][kGtcChunkRuns * kGtcRunFloat4];  // staged runs, double buffered
   float2 x[4 * kGtcPolStride];                    // [pol][pixel] FP32 sums of the current segment
   float2 img[4 * kGtcPolStride];                  // [pol][pixel] corrected image sum over segments
   float4 geo[8][4][8];                            // [warp][tile][g]: (n0, di0, dj0, dn) of pixel g's 8-block
@@ -150,8 +152,7 @@ struct GtcSmem {
 };
 
 __device__ __forceinline__ void mma_tf32_m16n8k8(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
@@ -177,21 +178,19 @@ __device__ __forceinline__ bool gridder_tc_item(const GridArgs& a, int item_idx,
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, t = lane & 3;
   const int nc = sd.c1 - sd.c0;
-  const int NG = tc_row_groups(a.seg, sd.seg_begin, sd.seg_count, nc);
-  const int NQ = NG * nc;  // steps
-  const int n_chunks = (NQ + kGtcChunk - 1) / kGtcChunk;
+  const int R = tc_runs(nc);
+  const int NR = tc_row_groups(a.seg, sd.seg_begin, sd.seg_count, nc) * R;  // runs
+  const int n_chunks = (NR + kGtcChunkRuns - 1) / kGtcChunkRuns;
   const float4* rec_base = a.records + size_t(sd.rec_offset) * kRecordFloat4;
-  const float4* anc_base = rec_base + size_t(NQ) * 4 * kRecordFloat4;
-  const int AR = tc_anchor_records(nc);
   const int P0 = item.tile * kGtcPixels;
   const int nodes = a.g.nodes;
   const int nA = nodes * nodes * 4;
 
   auto issue = [&](int chunk, int buf) {
-    const int nq = imin(kGtcChunk, NQ - chunk * kGtcChunk);
-    const uint32_t bytes = uint32_t(nq) * 4 * kRecordFloat4 * 16;
+    const int nr = imin(kGtcChunkRuns, NR - chunk * kGtcChunkRuns);
+    const uint32_t bytes = uint32_t(nr) * kGtcRunFloat4 * 16;
     mbar_arrive_expect_tx(&S.bar[buf], bytes);
-    bulk_copy_g2s(S.rec[buf], rec_base + size_t(chunk) * kGtcChunk * 4 * kRecordFloat4, bytes, &S.bar[buf]);
+    bulk_copy_g2s(S.rec[buf], rec_base + size_t(chunk) * kGtcChunkRuns * kGtcRunFloat4, bytes, &S.bar[buf]);
   };
   if (tid == 0) {
     issue(0, int(cg & 1));
@@ -275,32 +274,28 @@ __device__ __forceinline__ bool gridder_tc_item(const GridArgs& a, int item_idx,
     const SegmentDesc d0 = a.seg[sd.seg_begin];
     seg_gend = ((d0.k_end - d0.k_begin) / nc + 3) / 4;
   }
-  int G = 0, s = 0;  // row group and channel of the next step
+  int G = 0, u = 0;  // row group and run (within the row group) of the next run
   for (int c = 0; c < n_chunks; ++c) {
     const uint32_t cc_g = cg + uint32_t(c);
     const int buf = int(cc_g & 1);
     const bool ok = mbar_wait_bounded(&S.bar[buf], (cc_g >> 1) & 1);
     if (ok) {
-      const int nq = imin(kGtcChunk, NQ - c * kGtcChunk);
-      const float4* rb = S.rec[buf];
-#pragma unroll 4
-      for (int qq = 0; qq < nq; ++qq) {
-        if (s == 0 && G == seg_gend) {  // the previous segment is complete
+      const int nr = imin(kGtcChunkRuns, NR - c * kGtcChunkRuns);
+#pragma unroll 1
+      for (int h = 0; h < nr; ++h) {
+        const float4* run = S.rec[buf] + h * kGtcRunFloat4;
+        if (u == 0 && G == seg_gend) {  // the previous segment is complete
           flush();
           epilogue(seg_i);
           ++seg_i;
           const SegmentDesc d = a.seg[sd.seg_begin + seg_i];
           seg_gend += ((d.k_end - d.k_begin) / nc + 3) / 4;
         }
-        if (s % kGtcFlushSteps == 0) flush();  // bounds the MMA accumulation chains
-        if (s % kGtcRun == 0) {
-          const float4* anc = anc_base + size_t(4 * G + t) * AR * kRecordFloat4;
-          const float4 a0 = __ldg(anc + 2 + 2 * (s / kGtcRun)), a1 = __ldg(anc + 3 + 2 * (s / kGtcRun));
-          float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0;
-          if (s == 0) {
-            s0 = __ldg(anc);
-            s1 = __ldg(anc + 1);
-          }
+        {
+          // exact anchors at the run's first channel; the channel step's phasor once per row group
+          const float4 a0 = run[2 * t], a1 = run[2 * t + 1];
+          const bool first = u == 0;
+          const float4 s0 = run[8 + 2 * t], s1 = run[9 + 2 * t];
 #pragma unroll
           for (int m = 0; m < 4; ++m) {
             const float4 ga = S.geo[warp][m][g];
@@ -308,48 +303,54 @@ __device__ __forceinline__ bool gridder_tc_item(const GridArgs& a, int item_idx,
             const float2 ph = gtc_phase(a0, a1, ga, dd, g);
             __sincosf(ph.x, &Sn[m].x, &Cs[m].x);
             __sincosf(ph.y, &Sn[m].y, &Cs[m].y);
-            if (s == 0) {
+            if (first) {
               const float2 dph = gtc_phase(s0, s1, ga, dd, g);
               __sincosf(dph.x, &Rs[m].x, &Rc[m].x);
               __sincosf(dph.y, &Rs[m].y, &Rc[m].y);
             }
           }
-        } else {
-          // next channel: e^{i phi} <- e^{i phi} e^{i dphi}
+        }
+        const float4* steps = run + kGtcHeaderFloat4;
+#pragma unroll
+        for (int st = 0; st < kGtcRun; ++st) {
+          if (st > 0) {
+            // next channel: e^{i phi} <- e^{i phi} e^{i dphi}
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+              const float2 cn = ffma2(make_float2(-Sn[m].x, -Sn[m].y), Rs[m], fmul2(Cs[m], Rc[m]));
+              Sn[m] = ffma2(Sn[m], Rc[m], fmul2(Cs[m], Rs[m]));
+              Cs[m] = cn;
+            }
+          }
+          // B fragment: visibility t of the step, column g
+          const float4 bf = steps[st * kGtcStepFloat4 + lane];
+          const uint32_t Bh[2] = {__float_as_uint(bf.x), __float_as_uint(bf.y)};
+          const uint32_t Bl[2] = {__float_as_uint(bf.z), __float_as_uint(bf.w)};
 #pragma unroll
           for (int m = 0; m < 4; ++m) {
-            const float2 cn = ffma2(make_float2(-Sn[m].x, -Sn[m].y), Rs[m], fmul2(Cs[m], Rc[m]));
-            Sn[m] = ffma2(Sn[m], Rc[m], fmul2(Cs[m], Rs[m]));
-            Cs[m] = cn;
+            // A fragment: (row g, col t) cos, (row g+8, col t) cos, (row g, col t+4) sin, (row g+8, col t+4) sin
+            uint32_t Ah[4], Al[4];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const float2 x = e ? Sn[m] : Cs[m];
+              Ah[2 * e] = __float_as_uint(x.x) & kGtcMask;
+              Ah[2 * e + 1] = __float_as_uint(x.y) & kGtcMask;
+              const float2 lo = ffma2(make_float2(__uint_as_float(Ah[2 * e]), __uint_as_float(Ah[2 * e + 1])),
+                                      make_float2(-1.f, -1.f), x);  // x - hi
+              Al[2 * e] = __float_as_uint(lo.x);
+              Al[2 * e + 1] = __float_as_uint(lo.y);
+            }
+            mma_tf32_m16n8k8(acc[m], Ah, Bh);
+            mma_tf32_m16n8k8(acc[m], Al, Bh);
+            mma_tf32_m16n8k8(acc[m], Ah, Bl);
           }
         }
-        // B fragment: visibility t of the step, column g
-        const float4 bf = rb[(qq * 4 + t) * kRecordFloat4 + g];
-        const uint32_t Bh[2] = {__float_as_uint(bf.x), __float_as_uint(bf.y)};
-        const uint32_t Bl[2] = {__float_as_uint(bf.z), __float_as_uint(bf.w)};
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          // A fragment: (row g, col t) cos, (row g+8, col t) cos, (row g, col t+4) sin, (row g+8, col t+4) sin
-          uint32_t Ah[4], Al[4];
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const float2 x = e ? Sn[m] : Cs[m];
-            Ah[2 * e] = __float_as_uint(x.x) & kGtcMask;
-            Ah[2 * e + 1] = __float_as_uint(x.y) & kGtcMask;
-            const float2 lo = ffma2(make_float2(__uint_as_float(Ah[2 * e]), __uint_as_float(Ah[2 * e + 1])),
-                                    make_float2(-1.f, -1.f), x);  // x - hi
-            Al[2 * e] = __float_as_uint(lo.x);
-            Al[2 * e + 1] = __float_as_uint(lo.y);
-          }
-          mma_tf32_m16n8k8(acc[m], Ah, Bh);
-          mma_tf32_m16n8k8(acc[m], Al, Bh);
-          mma_tf32_m16n8k8(acc[m], Ah, Bl);
-        }
-        if (++s == nc) {
-          s = 0;
+        if (++u == R) {
+          u = 0;
           ++G;
         }
       }
+      flush();  // every chunk: bounds the MMA accumulation chains
     }
     // every thread is done with this buffer: refill it with chunk c + 2
     if (__syncthreads_or(!ok)) {
@@ -365,7 +366,6 @@ __device__ __forceinline__ bool gridder_tc_item(const GridArgs& a, int item_idx,
       issue(c + 2, buf);
     }
   }
-  flush();
   epilogue(seg_i);
 
   // ---- write this block's pixels of the subgrid image: [sg][pol][j][i]; Stokes I: plane 0, (XX + YY) / 2

@@ -82,15 +82,20 @@ constexpr int kTcItemRows = 256;  // rows (16-row tiles) per item of the tensor-
 // the growth of the rotation's rounding error)
 constexpr int kRotateRun = 8;
 
-// Tensor-core gridder: work items of kGtcPixels pixels; staged records of a
-// subgrid are its row groups (4 rows of one segment) times (channels + the
-// phase-coefficient records of a row slot)
+// Tensor-core gridder: work items of kGtcPixels pixels; the staged records of
+// a subgrid are its row groups (4 rows of one segment) times the runs of
+// kGtcRun channels of a row group (the last run padded with zero
+// visibilities); a run is a header (the phase coefficients of the run's first
+// channel and of the channel step for the 4 rows, 2 float4 each) followed by
+// kGtcRun steps of 4 visibilities x 8 columns (one float4 per column)
 constexpr int kGtcPixels = 512;  // pixels per work item
 
 constexpr int kGtcRun = kRotateRun;  // channels per run of rotated phasors in the tensor-core gridder
 __host__ __device__ constexpr int tc_runs(int nc) { return (nc + kGtcRun - 1) / kGtcRun; }
-// records per row slot for the phase coefficients: the step and one anchor per run, 2 float4 each
-__host__ __device__ constexpr int tc_anchor_records(int nc) { return (2 + 2 * tc_runs(nc) + 7) / 8; }
+constexpr int kGtcHeaderFloat4 = 16;                                 // run header
+constexpr int kGtcStepFloat4 = 32;                                   // one step: 8 columns x 4 rows
+constexpr int kGtcRunFloat4 = kGtcHeaderFloat4 + kGtcRun * kGtcStepFloat4;
+static_assert(kGtcRunFloat4 % 8 == 0, "a run is a whole number of 128-byte records");
 
 // Row groups of a subgrid: segments contribute ceil(rows / 4) each
 __host__ __device__ inline int tc_row_groups(const SegmentDesc* seg, int seg_begin, int seg_count, int nc) {
@@ -102,9 +107,9 @@ __host__ __device__ inline int tc_row_groups(const SegmentDesc* seg, int seg_beg
   return n;
 }
 
-// Staged records of a subgrid in the tensor-core layout
+// Staged 128-byte records of a subgrid in the tensor-core layout
 __host__ __device__ inline int64_t tc_records(int n_groups, int nc) {
-  return int64_t(n_groups) * 4 * (nc + tc_anchor_records(nc));
+  return int64_t(n_groups) * tc_runs(nc) * (kGtcRunFloat4 / 8);
 }
 
 
