@@ -91,6 +91,9 @@ __global__ void __launch_bounds__(ROWS * L / 8, (ROWS * L / 8) <= 128 ? 3 : 2)
   const double off_x = double(sd.x0 + L / 2 - a.g.N / 2);
   const double off_y = double(sd.y0 + L / 2 - a.g.N / 2);
 
+  // this thread's column of the image sums starts at zero, so a subgrid without segments writes zeros
+#pragma unroll
+  for (int e = 0; e < 64; ++e) s_acc[e * NT + tid] = 0.f;
   for (int gi = 0; gi < sd.seg_count; ++gi) {
     const SegmentDesc seg = a.seg[sd.seg_begin + gi];
     float2 RE[4][4], IM[4][4];
@@ -184,8 +187,8 @@ __global__ void __launch_bounds__(ROWS * L / 8, (ROWS * L / 8) <= 128 ? 3 : 2)
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
         float* acc = s_acc + (px * 8 + 2 * p) * NT + tid;
-        acc[0] = (gi == 0 ? 0.f : acc[0]) + wgt * E.m[p].re;
-        acc[NT] = (gi == 0 ? 0.f : acc[NT]) + wgt * E.m[p].im;
+        acc[0] += wgt * E.m[p].re;
+        acc[NT] += wgt * E.m[p].im;
       }
     }
   }
