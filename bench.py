@@ -61,9 +61,10 @@ TRAFFIC_STATIONS = 90
 
 
 def ncu_traffic_command(kern: str) -> str:
+    mac = {"gridder_tc": " --mac-unit 2", "degridder": " --mac-unit 1"}.get(kern, "")
     return (f'ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none '
             f'--kernel-name-base demangled -k regex:"idg::{kern}_kernel<" -c 2 --csv '
-            f'--log-file traffic_{kern}.csv {BENCH_SHORT} --stations {TRAFFIC_STATIONS}')
+            f'--log-file traffic_{kern}.csv {BENCH_SHORT} --stations {TRAFFIC_STATIONS}{mac}')
 KERNEL_SOURCES = {"gridder": ["gridder.cu", "gridder_kernels.cuh", "kernels_common.cuh", "idg_internal.h"],
                   "degridder": ["degridder.cu", "degridder_kernels.cuh", "kernels_common.cuh", "idg_internal.h"],
                   "degridder_tc": ["degridder.cu", "degridder_tc_kernels.cuh", "degridder_kernels.cuh",
@@ -120,6 +121,9 @@ def parse_args():
                     help="timed CUDA-graph replays of grid + degrid of the small 32-station workload; 0 = skip")
     ap.add_argument("--serving-requests", type=int, default=24,
                     help="requests of the serving comparison (batched vs plain at 2x plain capacity); 0 = skip")
+    ap.add_argument("--mac-unit", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="the main leg's multiply-accumulate unit (idg_geometry.mac_unit: 0 the library's default, "
+                         "1 FP32 pipe, 2 tensor cores for both kernels, 3 tensor-core degridder only)")
     ap.add_argument("--aterms", choices=["beam", "full"], default="beam",
                     help="beam: the scalar beam x screen gain (diagonal Jones); full: the same plus 5%% "
                          "polarisation leakage, so every Jones matrix is full")
@@ -504,7 +508,7 @@ def run_native(args):
     obs_r, shard = parallel.shard_observation(obs, rank, world)
     vis_d = vis_full if world == 1 else vis_full[torch.as_tensor(shard, device=dev)].contiguous()
     del vis_full
-    plan = idg.Plan(obs_r, stream=stream.cuda_stream)
+    plan = idg.Plan(obs_r, stream=stream.cuda_stream, mac_unit=args.mac_unit)
     st = plan.stats()
     N = obs.grid_size
     G_model = torch.zeros((4, N, N), dtype=torch.complex128, device=dev)
@@ -862,7 +866,9 @@ def run_native(args):
                    "parallelism": (f"baseline shards x{world} (round-robin), one NCCL all-reduce of the FP64 grid "
                                    f"per step" if world > 1 else "single GPU"),
                    "subgrids": st.n_subgrids, "segments": st.n_segments, "batches": st.n_batches,
-                   "vis_pixels_per_direction": st.vis_pixels},
+                   "vis_pixels_per_direction": st.vis_pixels,
+                   "mac_unit": {1: "FP32 pipe (gridder and degridder)", 2: "tensor cores (gridder and degridder)",
+                                3: "FP32-pipe gridder, tensor-core degridder"}.get(int(st.mac_unit), str(st.mac_unit))},
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches,
         "kernels": kernels, "image_domain": image_domain, "paper_context": paper_context, "stokes_i": stokes_i, "w_layers": w_layers,
         "normalized": normalized, "serving": serving, "uneven": uneven, "small": small,
