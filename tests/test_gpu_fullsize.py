@@ -130,6 +130,27 @@ def test_full_size_grid_of_sampled_baselines_elementwise(mwa_full, oracle_mod):
     assert np.count_nonzero(G_ref) == np.count_nonzero(G)
 
 
+def test_full_size_grid_tensor_cores_sampled_baselines(mwa_full, idg_mod, oracle_mod):
+    """The same element-wise check with the tensor-core gridder (mac_unit =
+    IDG_MAC_TENSOR) gridding the whole plan."""
+    obs = mwa_full["obs"]
+    N = obs.grid_size
+    plan = idg_mod.Plan(obs, mac_unit=idg_mod.IDG_MAC_TENSOR)
+    try:
+        assert plan.stats().mac_unit == idg_mod.IDG_MAC_TENSOR
+        bls = _baseline_sample(mwa_full["ref_plan"], seed=23)
+        G = _grid_of_baselines(plan, mwa_full["vis_d"], mwa_full["A_d"], bls, N).cpu().numpy()
+    finally:
+        plan.close()
+    sub = parallel.sub_observation(obs, bls)
+    ref_plan = oracle_mod.plan(mwa_full["geom"], sub.uvw, obs.freqs, obs.aterm_offsets)
+    G_ref = oracle_mod.grid(mwa_full["geom"], obs.n_stations, sub.baselines, sub.uvw, obs.freqs, obs.aterm_offsets,
+                            ref_plan, mwa_full["vis"][bls].astype(np.complex128), mwa_full["A"].astype(np.complex128))
+    err = float(np.linalg.norm((G - G_ref).ravel()) / np.linalg.norm(G_ref.ravel()))
+    print(f"full-size tensor-core grid of {len(bls)} sampled baselines: relative L2 {err:.2e}")
+    assert err < GRID_TOL, err
+
+
 def test_full_size_grid_identities(mwa_full):
     """DC invariant and adjoint identity on the full MWA-like workload."""
     import torch

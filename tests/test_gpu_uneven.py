@@ -95,15 +95,21 @@ def test_uneven_degrid_sampled_subgrids(uneven, oracle_mod):
     assert err < DEGRID_TOL, err
 
 
-def test_uneven_grid_sampled_baselines(uneven, idg_mod, oracle_mod):
+@pytest.mark.parametrize("tensor_gridder", [False, True])
+def test_uneven_grid_sampled_baselines(uneven, idg_mod, oracle_mod, tensor_gridder):
     """Grid of the sampled subgrids' baselines, same plan rows, same launch
-    mode, against the oracle."""
+    mode, against the oracle; with the library's default gridder (FP32 pipe)
+    and with the tensor-core gridder, which the autotuner picks for this
+    workload on GB300."""
     import torch
     obs = uneven["obs"]
     _, bls = _sample(uneven)
     sub = parallel.sub_observation(obs, bls)
     side = uneven["side"]
-    plan = idg_mod.Plan(sub, subgrid_size=L, flags=idg_mod.IDG_PERSISTENT, stream=side.cuda_stream)
+    mac = idg_mod.IDG_MAC_TENSOR if tensor_gridder else 0
+    plan = idg_mod.Plan(sub, subgrid_size=L, flags=idg_mod.IDG_PERSISTENT, stream=side.cuda_stream, mac_unit=mac)
+    if tensor_gridder:
+        assert plan.stats().mac_unit == idg_mod.IDG_MAC_TENSOR
     try:
         full = uneven["ref_plan"]
         rows = full.subgrids[np.isin(full.subgrids[:, 0], bls)].copy()
