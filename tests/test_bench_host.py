@@ -114,3 +114,16 @@ def test_tensor_core_kernels_recorded_under_their_own_names(tmp_path, traffic_fi
     assert rec["gridder_tc"]["captured_bytes_per_launch"] == pytest.approx(1.3e9)
     assert rec["degridder_tc"]["captured_bytes_per_launch"] == pytest.approx(1.09e9)
     assert bench.recorded_traffic("degridder_tc", "workload A") is not None
+
+
+def test_traffic_recipe_runs_the_kernel_it_captures():
+    """Each kernel's capture command runs the bench with the MAC unit whose
+    plan launches that kernel, and names the kernel exactly."""
+    for mac in (1, 2, 3):
+        for kind in ("gridder", "degridder"):
+            kern = bench.kernel_of(kind, mac)
+            cmd = bench.ncu_traffic_command(kern)
+            assert f'regex:"idg::{kern}_kernel<"' in cmd
+            chosen = int(cmd.split("--mac-unit ")[1].split()[0]) if "--mac-unit" in cmd else 3  # the default plan
+            assert bench.kernel_of(kind, chosen) == kern
+            assert "--clock-control none" in cmd and "-c 2" in cmd
