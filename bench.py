@@ -58,10 +58,12 @@ BENCH_SHORT = ('python bench.py --steps 2 --warmup 1 --no-cpu-baseline --no-e2e 
 NCU_LAUNCH_LIST = ('ncu --metrics gpu__time_duration.sum --clock-control none --kernel-name-base demangled '
                    '-k regex:"idg::" -c 400 --csv --log-file launches.csv ' + BENCH_SHORT)
 TRAFFIC_STATIONS = 90
+MAC_NAMES = {1: "FP32 pipe (gridder and degridder)", 2: "tensor cores (gridder and degridder)",
+             3: "FP32-pipe gridder, tensor-core degridder"}
 
 
 def ncu_traffic_command(kern: str) -> str:
-    mac = {"gridder_tc": " --mac-unit 2", "degridder": " --mac-unit 1"}.get(kern, "")
+    mac = {"gridder": " --mac-unit 3", "gridder_tc": " --mac-unit 2", "degridder": " --mac-unit 1"}.get(kern, "")
     return (f'ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none '
             f'--kernel-name-base demangled -k regex:"idg::{kern}_kernel<" -c 2 --csv '
             f'--log-file traffic_{kern}.csv {BENCH_SHORT} --stations {TRAFFIC_STATIONS}{mac}')
@@ -122,7 +124,7 @@ def parse_args():
     ap.add_argument("--serving-requests", type=int, default=24,
                     help="requests of the serving comparison (batched vs plain at 2x plain capacity); 0 = skip")
     ap.add_argument("--mac-unit", type=int, default=0, choices=[0, 1, 2, 3],
-                    help="the main leg's multiply-accumulate unit (idg_geometry.mac_unit: 0 the library's default, "
+                    help="the multiply-accumulate unit of the main, uneven and small legs (idg_geometry.mac_unit: 0 the library's default, "
                          "1 FP32 pipe, 2 tensor cores for both kernels, 3 tensor-core degridder only)")
     ap.add_argument("--aterms", choices=["beam", "full"], default="beam",
                     help="beam: the scalar beam x screen gain (diagonal Jones); full: the same plus 5%% "
@@ -427,7 +429,7 @@ def _kernel_fracs(plan, vis, A, G, out, n_sm, sm_max, r_vp_meas):
     return kern
 
 
-def uneven_leg(idg, synth, dev, steps, n_sm, sm_max, r_vp_meas):
+def uneven_leg(idg, synth, dev, steps, n_sm, sm_max, r_vp_meas, mac_unit=0):
     import torch
     t0 = time.time()
     obs = synth.config(4, seed=0)
@@ -439,7 +441,7 @@ def uneven_leg(idg, synth, dev, steps, n_sm, sm_max, r_vp_meas):
                       generator=g)
     side = torch.cuda.Stream(dev)
     L = 64
-    plan = idg.Plan(obs, subgrid_size=L, stream=side.cuda_stream, grid_chunk=64)
+    plan = idg.Plan(obs, subgrid_size=L, stream=side.cuda_stream, grid_chunk=64, mac_unit=mac_unit)
     t_plan = time.time() - t0
     st = plan.stats()
     N = obs.grid_size
@@ -455,8 +457,9 @@ def uneven_leg(idg, synth, dev, steps, n_sm, sm_max, r_vp_meas):
                        "30 ch 140-170 MHz, 8192^2 FP64 grid, L = 64, P = 18, FOV 0.5, A-terms every 4 s "
                        "(beam x screen), random visibilities",
            "n_vis": int(obs.n_vis),
-           "launch": "one block per work item, gridder chunks of 64 records (the autotuner's choice on GB300), "
-                     "CUDA-graph replay",
+           "launch": "one block per work item, CUDA-graph replay, " + MAC_NAMES.get(int(st.mac_unit), "?") +
+                     (" (the autotuner's choice on GB300)" if int(st.mac_unit) == 2 else "") +
+                     ("; FP32 gridder chunks of 64 records" if int(st.mac_unit) != 2 else ""),
            "graph_replay_ms": {"grid": g_ms, "degrid": d_ms}, "subgrids": int(st.n_subgrids),
            "vis_per_subgrid_min_median_max": [int(nv.min()), int(np.median(nv)), int(nv.max())],
            "vis_pixels_per_direction": float(st.vis_pixels), "kernels": kern, "plan_seconds": t_plan}
@@ -466,11 +469,11 @@ def uneven_leg(idg, synth, dev, steps, n_sm, sm_max, r_vp_meas):
     return res
 
 
-def small_leg(idg, dev, steps, n_sm, sm_max, r_vp_meas):
+def small_leg(idg, dev, steps, n_sm, sm_max, r_vp_meas, mac_unit=0):
     import torch
     obs, A, vis, _ = make_workload(1, dev)
     side = torch.cuda.Stream(dev)
-    plan = idg.Plan(obs, stream=side.cuda_stream)
+    plan = idg.Plan(obs, stream=side.cuda_stream, mac_unit=mac_unit)
     N = obs.grid_size
     G = torch.zeros((4, N, N), dtype=torch.complex128, device=dev)
     out = torch.empty_like(vis)
@@ -824,10 +827,10 @@ def run_native(args):
     # on their values)
     uneven = None
     if args.uneven_steps > 0 and args.stations is None and args.timesteps is None:
-        uneven = uneven_leg(idg, synth, dev, args.uneven_steps, n_sm, sm_max, r_vp_meas)
+        uneven = uneven_leg(idg, synth, dev, args.uneven_steps, n_sm, sm_max, r_vp_meas, args.mac_unit)
     small = None
     if args.small_steps > 0:
-        small = small_leg(idg, dev, args.small_steps, n_sm, sm_max, r_vp_meas)
+        small = small_leg(idg, dev, args.small_steps, n_sm, sm_max, r_vp_meas, args.mac_unit)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the oracle baseline runs at N = 1 only
@@ -867,8 +870,7 @@ def run_native(args):
                                    f"per step" if world > 1 else "single GPU"),
                    "subgrids": st.n_subgrids, "segments": st.n_segments, "batches": st.n_batches,
                    "vis_pixels_per_direction": st.vis_pixels,
-                   "mac_unit": {1: "FP32 pipe (gridder and degridder)", 2: "tensor cores (gridder and degridder)",
-                                3: "FP32-pipe gridder, tensor-core degridder"}.get(int(st.mac_unit), str(st.mac_unit))},
+                   "mac_unit": MAC_NAMES.get(int(st.mac_unit), str(st.mac_unit))},
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches,
         "kernels": kernels, "image_domain": image_domain, "paper_context": paper_context, "stokes_i": stokes_i, "w_layers": w_layers,
         "normalized": normalized, "serving": serving, "uneven": uneven, "small": small,

@@ -68,8 +68,9 @@ enum { IDG_TAPER_KB = 0, IDG_TAPER_USER = 1 };
    degrid_channels asks), the tensor-core gridder needs uniformly spaced channels and no A-term normalisation
    (the plan keeps the FP32 gridder otherwise). */
 enum {
-  IDG_MAC_DEFAULT = 0,       /* IDG_MAC_TENSOR_DEGRID; IDG_MAC_FP32 when degrid_channels asks for 2 or 4 and
-                                with IDG_STOKES_I (the FP32 degridder then sums XX and YY alone) */
+  IDG_MAC_DEFAULT = 0,       /* IDG_MAC_TENSOR (IDG_MAC_TENSOR_DEGRID where the tensor-core gridder cannot
+                                run); IDG_MAC_FP32 when degrid_channels asks for 2 or 4 and with IDG_STOKES_I
+                                (the FP32 kernels then sum XX and YY alone) */
   IDG_MAC_FP32 = 1,          /* gridder and degridder on the FP32 FMA pipe of the CUDA cores */
   IDG_MAC_TENSOR = 2,        /* gridder and degridder on the tensor cores */
   IDG_MAC_TENSOR_DEGRID = 3  /* degridder on the tensor cores, gridder on the FP32 pipe */

@@ -14,8 +14,8 @@
 //
 // The 4 visibilities of a step are 4 rows (timesteps) of the segment at one
 // channel, so lane (g, t) follows row t along its channels.  The channels of
-// a row group are taken in runs of kGtcRun (the last run padded with zero
-// visibilities): the phasors of the lane's two pixels start from an exact
+// a row group are taken in runs of kGtcRun (the last run holds the rest):
+// the phasors of the lane's two pixels start from an exact
 // anchor at the run's first channel (__sincosf) and advance by the phasor of
 // the channel step for the others (the phase is linear in frequency; the plan
 // uses this kernel only for uniform channel spacing).  Rows are taken in
@@ -25,14 +25,16 @@
 // row group and run, a header of 16 float4 -- for rows t = 0..3 the phase
 // coefficients of the run's first channel at [2t, 2t+1] and of the channel
 // step at [8 + 2t, 9 + 2t], in the (head, tail) slope format of the exact
-// reduction -- then kGtcRun steps of 32 float4: column n of row t at
-// [4n + t], holding (b0_hi, b1_hi, b0_lo, b1_lo), so that lane 4g + t reads
-// its B fragment from float4 number lane of the step (conflict-free).
+// reduction -- then one step of 32 float4 per channel of the run: column n
+// of row t at [4n + t], holding (b0_hi, b1_hi, b0_lo, b1_lo), so that lane
+// 4g + t reads its B fragment from float4 number lane of the step
+// (conflict-free).  Runs are packed without padding (tc_run_offset).
 //
 // Item = (subgrid, block of 512 pixels): warp w owns pixels 64 w .. 64 w + 63
 // of the block as 4 tiles of 16 (pixels g and g+8 of a tile are rows g and
 // g+8 of A).  Runs stream through a double buffer in shared memory by bulk
-// copies, two runs per chunk; after every chunk the accumulators are added
+// copies, two runs per chunk (a whole run of kGtcRun channels fully
+// unrolled, a shorter last run in a loop); after every chunk the accumulators are added
 // into an FP32 sum in shared memory (this bounds the tensor core's
 // accumulation rounding); after each segment a warp applies A_p^H X A_q, the
 // taper and the centring sign to its 64 pixels and adds them to the image
@@ -96,14 +98,15 @@ __global__ void __launch_bounds__(256) stage_tc_kernel(const StageArgs a, const 
   const SubgridDesc sd = a.sg[blockIdx.x];
   const int nc = sd.c1 - sd.c0;
   const int R = tc_runs(nc);
-  const int NR = tc_row_groups(seg, sd.seg_begin, sd.seg_count, nc) * R;
+  const int NG = tc_row_groups(seg, sd.seg_begin, sd.seg_count, nc);
+  const int NR = NG * R;
   float4* base = a.records + size_t(sd.rec_offset) * kRecordFloat4;
-  // one thread per (run, step, row slot): the 8 columns of one visibility
-  const int n_vrec = NR * kGtcRun * 4;
+  // one thread per (row group, channel, row slot): the 8 columns of one visibility
+  const int n_vrec = NG * nc * 4;
   for (int idx = threadIdx.x; idx < n_vrec; idx += blockDim.x) {
-    const int r = idx / (kGtcRun * 4), rem = idx - r * (kGtcRun * 4), st = rem >> 2, t = rem & 3;
-    const int G = r / R, s = (r - G * R) * kGtcRun + st;
-    const int row = s < nc ? tc_slot_row(seg, sd.seg_begin, sd.seg_count, nc, G, t) : -1;
+    const int G = idx / (nc * 4), rem = idx - G * (nc * 4), s = rem >> 2, t = rem & 3;
+    const int u = s / kGtcRun, st = s - u * kGtcRun;
+    const int row = tc_slot_row(seg, sd.seg_begin, sd.seg_count, nc, G, t);
     float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
     if (row >= 0) {
       const size_t vidx = (size_t(sd.b) * a.g.n_t + sd.t0 + row) * a.g.n_ch + sd.c0 + s;
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__(256) stage_tc_kernel(const StageArgs a, const 
       if (sd.flags & kSubgridMirrored) mirror_values(v0, v1);
     }
     const float vr[4] = {v0.x, v0.z, v1.x, v1.z}, vi[4] = {v0.y, v0.w, v1.y, v1.w};
-    float4* step = base + size_t(r) * kGtcRunFloat4 + kGtcHeaderFloat4 + st * kGtcStepFloat4;
+    float4* step = base + tc_run_offset(nc, G * R + u) + kGtcHeaderFloat4 + st * kGtcStepFloat4;
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
       const int p = n >> 1;
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(256) stage_tc_kernel(const StageArgs a, const 
   for (int idx = threadIdx.x; idx < NR * 4; idx += blockDim.x) {
     const int r = idx >> 2, t = idx & 3, G = r / R, u = r - G * R;
     const int row = tc_slot_row(seg, sd.seg_begin, sd.seg_count, nc, G, t);
-    float4* hdr = base + size_t(r) * kGtcRunFloat4;
+    float4* hdr = base + tc_run_offset(nc, r);
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     hdr[2 * t] = hdr[2 * t + 1] = hdr[8 + 2 * t] = hdr[9 + 2 * t] = z;
     if (row < 0) continue;
@@ -187,10 +190,11 @@ __device__ __forceinline__ bool gridder_tc_item(const GridArgs& a, int item_idx,
   const int nA = nodes * nodes * 4;
 
   auto issue = [&](int chunk, int buf) {
-    const int nr = imin(kGtcChunkRuns, NR - chunk * kGtcChunkRuns);
-    const uint32_t bytes = uint32_t(nr) * kGtcRunFloat4 * 16;
+    const int r0 = chunk * kGtcChunkRuns, r1 = imin(r0 + kGtcChunkRuns, NR);
+    const int64_t o0 = tc_run_offset(nc, r0);
+    const uint32_t bytes = uint32_t(tc_run_offset(nc, r1) - o0) * 16;
     mbar_arrive_expect_tx(&S.bar[buf], bytes);
-    bulk_copy_g2s(S.rec[buf], rec_base + size_t(chunk) * kGtcChunkRuns * kGtcRunFloat4, bytes, &S.bar[buf]);
+    bulk_copy_g2s(S.rec[buf], rec_base + o0, bytes, &S.bar[buf]);
   };
   if (tid == 0) {
     issue(0, int(cg & 1));
@@ -281,9 +285,10 @@ __device__ __forceinline__ bool gridder_tc_item(const GridArgs& a, int item_idx,
     const bool ok = mbar_wait_bounded(&S.bar[buf], (cc_g >> 1) & 1);
     if (ok) {
       const int nr = imin(kGtcChunkRuns, NR - c * kGtcChunkRuns);
+      const float4* run = S.rec[buf];
 #pragma unroll 1
       for (int h = 0; h < nr; ++h) {
-        const float4* run = S.rec[buf] + h * kGtcRunFloat4;
+        const int len = tc_run_len(nc, u);
         if (u == 0 && G == seg_gend) {  // the previous segment is complete
           flush();
           epilogue(seg_i);
@@ -311,8 +316,7 @@ __device__ __forceinline__ bool gridder_tc_item(const GridArgs& a, int item_idx,
           }
         }
         const float4* steps = run + kGtcHeaderFloat4;
-#pragma unroll
-        for (int st = 0; st < kGtcRun; ++st) {
+        auto step = [&](int st) {
           if (st > 0) {
             // next channel: e^{i phi} <- e^{i phi} e^{i dphi}
 #pragma unroll
@@ -344,7 +348,15 @@ __device__ __forceinline__ bool gridder_tc_item(const GridArgs& a, int item_idx,
             mma_tf32_m16n8k8(acc[m], Al, Bh);
             mma_tf32_m16n8k8(acc[m], Ah, Bl);
           }
+        };
+        if (len == kGtcRun) {  // a whole run, fully unrolled
+#pragma unroll
+          for (int st = 0; st < kGtcRun; ++st) step(st);
+        } else {  // the last run of a row group: the remaining channels
+#pragma unroll 1
+          for (int st = 0; st < len; ++st) step(st);
         }
+        run += kGtcHeaderFloat4 + len * kGtcStepFloat4;
         if (++u == R) {
           u = 0;
           ++G;

@@ -383,11 +383,11 @@ idg_status idg_plan_create(idg_plan** out, const idg_geometry* g, int32_t n_stat
     const int want = g->degrid_channels > 0 ? g->degrid_channels : kDefaultDegridChannels;
     p->degrid_channels = uniform ? want : 1;
   }
-  // the default: the degridder on the tensor cores, the gridder on FP32; the FP32 degridder when channel
-  // groups were asked for, and for Stokes I (its sums over XX and YY alone, with diagonal A-terms, do half
-  // the multiply-adds of the tensor-core kernel's four correlations)
+  // the default: gridder and degridder on the tensor cores (the gridder falls back to FP32 below where it
+  // cannot run); both on FP32 when channel groups were asked for, and for Stokes I (the FP32 kernels' sums
+  // over XX and YY alone, with diagonal A-terms, do half the multiply-adds of the four correlations)
   p->mac = g->mac_unit != IDG_MAC_DEFAULT ? g->mac_unit
-           : (g->degrid_channels > 1 || (g->flags & IDG_STOKES_I)) ? IDG_MAC_FP32 : IDG_MAC_TENSOR_DEGRID;
+           : (g->degrid_channels > 1 || (g->flags & IDG_STOKES_I)) ? IDG_MAC_FP32 : IDG_MAC_TENSOR;
   if (p->mac != IDG_MAC_FP32) p->degrid_channels = 1;  // one visibility per row of the tensor-core product
   {
     // the tensor-core gridder rotates phasors by one channel step along each row

@@ -83,19 +83,32 @@ constexpr int kTcItemRows = 256;  // rows (16-row tiles) per item of the tensor-
 constexpr int kRotateRun = 8;
 
 // Tensor-core gridder: work items of kGtcPixels pixels; the staged records of
-// a subgrid are its row groups (4 rows of one segment) times the runs of
-// kGtcRun channels of a row group (the last run padded with zero
-// visibilities); a run is a header (the phase coefficients of the run's first
+// a subgrid are its row groups (4 rows of one segment) times the runs of up
+// to kGtcRun channels of a row group (the last run holds the remaining
+// channels); a run is a header (the phase coefficients of the run's first
 // channel and of the channel step for the 4 rows, 2 float4 each) followed by
-// kGtcRun steps of 4 visibilities x 8 columns (one float4 per column)
+// one step of 4 visibilities x 8 columns (one float4 per column) per channel
 constexpr int kGtcPixels = 512;  // pixels per work item
 
 constexpr int kGtcRun = kRotateRun;  // channels per run of rotated phasors in the tensor-core gridder
 __host__ __device__ constexpr int tc_runs(int nc) { return (nc + kGtcRun - 1) / kGtcRun; }
 constexpr int kGtcHeaderFloat4 = 16;                                 // run header
 constexpr int kGtcStepFloat4 = 32;                                   // one step: 8 columns x 4 rows
-constexpr int kGtcRunFloat4 = kGtcHeaderFloat4 + kGtcRun * kGtcStepFloat4;
-static_assert(kGtcRunFloat4 % 8 == 0, "a run is a whole number of 128-byte records");
+constexpr int kGtcRunFloat4 = kGtcHeaderFloat4 + kGtcRun * kGtcStepFloat4;  // the longest run
+// float4s of one row group: a header per run and a step per channel (a multiple of 16)
+__host__ __device__ constexpr int tc_group_float4(int nc) {
+  return kGtcHeaderFloat4 * tc_runs(nc) + kGtcStepFloat4 * nc;
+}
+// channels of run u of a row group
+__host__ __device__ constexpr int tc_run_len(int nc, int u) {
+  return nc - u * kGtcRun < kGtcRun ? nc - u * kGtcRun : kGtcRun;
+}
+// float4 offset of run r (row group r / runs, run r % runs) in a subgrid's records;
+// r = row groups x runs gives the end of the records
+__host__ __device__ inline int64_t tc_run_offset(int nc, int r) {
+  const int R = tc_runs(nc), G = r / R, u = r - G * R;
+  return int64_t(G) * tc_group_float4(nc) + int64_t(u) * kGtcRunFloat4;
+}
 
 // Row groups of a subgrid: segments contribute ceil(rows / 4) each
 __host__ __device__ inline int tc_row_groups(const SegmentDesc* seg, int seg_begin, int seg_count, int nc) {
@@ -109,7 +122,7 @@ __host__ __device__ inline int tc_row_groups(const SegmentDesc* seg, int seg_beg
 
 // Staged 128-byte records of a subgrid in the tensor-core layout
 __host__ __device__ inline int64_t tc_records(int n_groups, int nc) {
-  return int64_t(n_groups) * tc_runs(nc) * (kGtcRunFloat4 / 8);
+  return int64_t(n_groups) * tc_group_float4(nc) / 8;
 }
 
 

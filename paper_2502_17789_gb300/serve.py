@@ -254,8 +254,9 @@ class Server:
             groups: dict = {}
             for slot in slots:
                 st = slot.plan.stats()
-                groups.setdefault((slot.req.kind, int(st.subgrid_size), int(st.degrid_channels)), []).append(slot)
-            for (kind, _, _), grp in groups.items():
+                key = (slot.req.kind, int(st.subgrid_size), int(st.degrid_channels), int(st.mac_unit))
+                groups.setdefault(key, []).append(slot)
+            for (kind, _, _, _), grp in groups.items():
                 plans = [sl.plan for sl in grp]
                 A = [sl.bufs["A"] for sl in grp]
                 if kind == "grid":

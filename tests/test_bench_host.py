@@ -124,6 +124,6 @@ def test_traffic_recipe_runs_the_kernel_it_captures():
             kern = bench.kernel_of(kind, mac)
             cmd = bench.ncu_traffic_command(kern)
             assert f'regex:"idg::{kern}_kernel<"' in cmd
-            chosen = int(cmd.split("--mac-unit ")[1].split()[0]) if "--mac-unit" in cmd else 3  # the default plan
+            chosen = int(cmd.split("--mac-unit ")[1].split()[0]) if "--mac-unit" in cmd else 2  # the default plan
             assert bench.kernel_of(kind, chosen) == kern
             assert "--clock-control none" in cmd and "-c 2" in cmd

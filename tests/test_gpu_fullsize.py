@@ -130,14 +130,16 @@ def test_full_size_grid_of_sampled_baselines_elementwise(mwa_full, oracle_mod):
     assert np.count_nonzero(G_ref) == np.count_nonzero(G)
 
 
-def test_full_size_grid_tensor_cores_sampled_baselines(mwa_full, idg_mod, oracle_mod):
-    """The same element-wise check with the tensor-core gridder (mac_unit =
-    IDG_MAC_TENSOR) gridding the whole plan."""
+def test_full_size_grid_fp32_gridder_sampled_baselines(mwa_full, idg_mod, oracle_mod):
+    """The same element-wise check with the FP32-pipe gridder (mac_unit =
+    IDG_MAC_TENSOR_DEGRID) gridding the whole plan; the library's default
+    plan above grids on the tensor cores."""
     obs = mwa_full["obs"]
     N = obs.grid_size
-    plan = idg_mod.Plan(obs, mac_unit=idg_mod.IDG_MAC_TENSOR)
+    assert mwa_full["plan"].stats().mac_unit == idg_mod.IDG_MAC_TENSOR
+    plan = idg_mod.Plan(obs, mac_unit=idg_mod.IDG_MAC_TENSOR_DEGRID)
     try:
-        assert plan.stats().mac_unit == idg_mod.IDG_MAC_TENSOR
+        assert plan.stats().mac_unit == idg_mod.IDG_MAC_TENSOR_DEGRID
         bls = _baseline_sample(mwa_full["ref_plan"], seed=23)
         G = _grid_of_baselines(plan, mwa_full["vis_d"], mwa_full["A_d"], bls, N).cpu().numpy()
     finally:
@@ -147,7 +149,7 @@ def test_full_size_grid_tensor_cores_sampled_baselines(mwa_full, idg_mod, oracle
     G_ref = oracle_mod.grid(mwa_full["geom"], obs.n_stations, sub.baselines, sub.uvw, obs.freqs, obs.aterm_offsets,
                             ref_plan, mwa_full["vis"][bls].astype(np.complex128), mwa_full["A"].astype(np.complex128))
     err = float(np.linalg.norm((G - G_ref).ravel()) / np.linalg.norm(G_ref.ravel()))
-    print(f"full-size tensor-core grid of {len(bls)} sampled baselines: relative L2 {err:.2e}")
+    print(f"full-size FP32-gridder grid of {len(bls)} sampled baselines: relative L2 {err:.2e}")
     assert err < GRID_TOL, err
 
 

@@ -92,12 +92,15 @@ def _random_problem(seed, obs, n_int=None, identity=False):
 
 # ------------------------------------------------------------------ stage parity
 
+@pytest.mark.parametrize("mac", ["default", "fp32_gridder"])
 @pytest.mark.parametrize("L", [32, 64, 96, 128])
-def test_subgrid_images_match_oracle(idg_mod, oracle_mod, cuda_device, L):
-    """Gridder output per subgrid, before (stage 0) and after (stage 1) the FFT."""
+def test_subgrid_images_match_oracle(idg_mod, oracle_mod, cuda_device, L, mac):
+    """Gridder output per subgrid, before (stage 0) and after (stage 1) the
+    FFT, with the default (tensor-core) gridder and the FP32-pipe one."""
     obs = synth.config(2, n_stations=6, n_timesteps=9, n_channels=11)
     A, vis = _random_problem(L, obs, n_int=3)
-    c = Case(idg_mod, oracle_mod, obs, A, vis, L=L)
+    c = Case(idg_mod, oracle_mod, obs, A, vis, L=L,
+             mac_unit=idg_mod.IDG_MAC_TENSOR_DEGRID if mac == "fp32_gridder" else 0)
     _, img, uv = c.oracle_grid(want_subgrids=True)
     import torch
     for stage, ref in ((0, img), (1, uv)):
@@ -126,12 +129,15 @@ def test_small_workload_full_grid_and_degrid(idg_mod, oracle_mod, cuda_device):
     assert _degrid_err(V, V_ref) < DEGRID_TOL
 
 
+@pytest.mark.parametrize("mac", ["default", "fp32_gridder"])
 @pytest.mark.parametrize("L,split", [(32, False), (64, True), (96, False), (96, True), (128, False)])
-def test_reduced_mwa_like_random_aterms(idg_mod, oracle_mod, cuda_device, L, split):
-    """Random full-Jones A-terms, several intervals, ragged chunk tails."""
+def test_reduced_mwa_like_random_aterms(idg_mod, oracle_mod, cuda_device, L, split, mac):
+    """Random full-Jones A-terms, several intervals, ragged chunk tails; the
+    default (tensor-core) kernels and the FP32-pipe gridder."""
     obs = synth.config(2, n_stations=10, n_timesteps=13, n_channels=17)
     A, vis = _random_problem(100 + L, obs, n_int=4)
-    c = Case(idg_mod, oracle_mod, obs, A, vis, L=L, flags=2 if split else 0)
+    c = Case(idg_mod, oracle_mod, obs, A, vis, L=L, flags=2 if split else 0,
+             mac_unit=idg_mod.IDG_MAC_TENSOR_DEGRID if mac == "fp32_gridder" else 0)
     G_ref = c.oracle_grid()
     assert _rel(c.gpu_grid(), G_ref) < GRID_TOL
     rng = np.random.default_rng(L)
@@ -200,7 +206,7 @@ def test_grid_chunk_sizes(idg_mod, oracle_mod, cuda_device, chunk):
     G_ref = oracle_mod.grid(*Case(idg_mod, oracle_mod, obs, A, vis).args(), vis.astype(np.complex64).astype(np.complex128),
                             A.astype(np.complex64).astype(np.complex128))
     for flags in (0, idg_mod.IDG_PERSISTENT):
-        plan = idg_mod.Plan(obs, flags=flags, grid_chunk=chunk)
+        plan = idg_mod.Plan(obs, flags=flags, grid_chunk=chunk, mac_unit=idg_mod.IDG_MAC_TENSOR_DEGRID)
         try:
             assert plan.stats().grid_chunk == chunk
             G = torch.zeros((4, obs.grid_size, obs.grid_size), dtype=torch.complex128, device="cuda")

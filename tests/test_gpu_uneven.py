@@ -98,18 +98,17 @@ def test_uneven_degrid_sampled_subgrids(uneven, oracle_mod):
 @pytest.mark.parametrize("tensor_gridder", [False, True])
 def test_uneven_grid_sampled_baselines(uneven, idg_mod, oracle_mod, tensor_gridder):
     """Grid of the sampled subgrids' baselines, same plan rows, same launch
-    mode, against the oracle; with the library's default gridder (FP32 pipe)
-    and with the tensor-core gridder, which the autotuner picks for this
-    workload on GB300."""
+    mode, against the oracle; with the tensor-core gridder (the library's
+    default, and the autotuner's choice for this workload on GB300) and with
+    the FP32-pipe gridder."""
     import torch
     obs = uneven["obs"]
     _, bls = _sample(uneven)
     sub = parallel.sub_observation(obs, bls)
     side = uneven["side"]
-    mac = idg_mod.IDG_MAC_TENSOR if tensor_gridder else 0
+    mac = idg_mod.IDG_MAC_TENSOR if tensor_gridder else idg_mod.IDG_MAC_TENSOR_DEGRID
     plan = idg_mod.Plan(sub, subgrid_size=L, flags=idg_mod.IDG_PERSISTENT, stream=side.cuda_stream, mac_unit=mac)
-    if tensor_gridder:
-        assert plan.stats().mac_unit == idg_mod.IDG_MAC_TENSOR
+    assert plan.stats().mac_unit == mac
     try:
         full = uneven["ref_plan"]
         rows = full.subgrids[np.isin(full.subgrids[:, 0], bls)].copy()
