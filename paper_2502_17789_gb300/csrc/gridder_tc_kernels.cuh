@@ -34,8 +34,8 @@
 // of the block as 4 tiles of 16 (pixels g and g+8 of a tile are rows g and
 // g+8 of A).  Runs stream through a double buffer in shared memory by bulk
 // copies, two runs per chunk (a whole run of kGtcRun channels fully
-// unrolled, a shorter last run in a loop); after every chunk the accumulators are added
-// into an FP32 sum in shared memory (this bounds the tensor core's
+// unrolled, a shorter last run in a loop); after every run the accumulators
+// are added into an FP32 sum in shared memory (this bounds the tensor core's
 // accumulation rounding); after each segment a warp applies A_p^H X A_q, the
 // taper and the centring sign to its 64 pixels and adds them to the image
 // sum.
@@ -357,12 +357,12 @@ __device__ __forceinline__ bool gridder_tc_item(const GridArgs& a, int item_idx,
           for (int st = 0; st < len; ++st) step(st);
         }
         run += kGtcHeaderFloat4 + len * kGtcStepFloat4;
+        flush();  // every run: bounds the MMA accumulation chains
         if (++u == R) {
           u = 0;
           ++G;
         }
       }
-      flush();  // every chunk: bounds the MMA accumulation chains
     }
     // every thread is done with this buffer: refill it with chunk c + 2
     if (__syncthreads_or(!ok)) {

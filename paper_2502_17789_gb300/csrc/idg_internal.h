@@ -90,7 +90,10 @@ constexpr int kRotateRun = 8;
 // one step of 4 visibilities x 8 columns (one float4 per column) per channel
 constexpr int kGtcPixels = 512;  // pixels per work item
 
-constexpr int kGtcRun = kRotateRun;  // channels per run of rotated phasors in the tensor-core gridder
+// channels per run of rotated phasors in the tensor-core gridder: longer
+// runs than the FP32 gridder's (fewer anchor evaluations per step), for a
+// larger but bounded rotation error
+constexpr int kGtcRun = 16;
 __host__ __device__ constexpr int tc_runs(int nc) { return (nc + kGtcRun - 1) / kGtcRun; }
 constexpr int kGtcHeaderFloat4 = 16;                                 // run header
 constexpr int kGtcStepFloat4 = 32;                                   // one step: 8 columns x 4 rows
